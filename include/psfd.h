@@ -1,0 +1,180 @@
+/*
+ * psfd.h -- C ABI of the B300 Lippmann-Schwinger PSFD solver for EUV mask scattering.
+ *
+ * The library solves the scattering of plane waves by an absorber layer on top of a
+ * planar multilayer stack, following arXiv 2606.25541 (Lee, Gillijns, Kim):
+ *   - Sec. 2, Eqs. (1)-(3): the stack is removed from the computational domain and
+ *     acts through its reflection operator R (background-field decomposition);
+ *   - Sec. 3, Eq. (9): R acts per transverse Fourier mode through the stack's
+ *     reflection matrix T_R, obtained by the transfer-matrix / generalized reflection
+ *     coefficient recursion;
+ *   - Sec. 3, Eqs. (11)-(18): the remaining free-space problem is solved in
+ *     Lippmann-Schwinger form x - G*(V x) = b with V = k0^2 (eps - eps_bg), the
+ *     convolution done by FFTs with a windowed dyadic Green's function.
+ * For periodic clips the Green's function is taken exactly per transverse Bloch mode
+ * and windowed in z only (|z| < L = nf*dz/2), and R is folded into the operator:
+ *   A u = u - (I + R) G*(V u),   b = E_inc + R[E_inc],
+ * u being the total field on the absorber planes.
+ *
+ * Conventions: lengths in nm; time dependence exp(-i w t); complex numbers are stored
+ * as interleaved (re, im) pairs of double (or float where stated); field vectors are
+ * laid out [rhs][component 3][plane nslab][y ny][x nx] with x fastest; absorber plane
+ * p (0-based) sits at height (p + 1/2) dz above the stack interface z_top.
+ *
+ * Ownership: the context owns every device buffer it allocates in psfd_create and
+ * frees them in psfd_destroy. Input arrays are read during the call only. Output
+ * arrays are provided by the caller. A context is bound to one CUDA stream and is not
+ * thread safe; calls on one context must not overlap.
+ *
+ * Errors: every function returns PSFD_OK (0) or a negative PSFD_E_* code; the
+ * context keeps a human-readable description, see psfd_last_error().
+ */
+#ifndef PSFD_H
+#define PSFD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PSFD_OK 0
+#define PSFD_E_ARG (-1)           /* invalid argument (null pointer, bad size, unsupported length) */
+#define PSFD_E_NOMEM (-2)         /* device allocation failed */
+#define PSFD_E_BUDGET (-3)        /* request exceeds the context's HBM budget */
+#define PSFD_E_CUDA (-4)          /* a CUDA runtime call failed */
+#define PSFD_E_NOT_CONVERGED (-5) /* iteration cap reached before the tolerance */
+#define PSFD_E_BREAKDOWN (-6)     /* Krylov breakdown (zero or non-finite scalar) */
+#define PSFD_E_ANOMALY (-7)       /* a diffraction order grazes the interface (beta ~ 0) */
+#define PSFD_E_TIMEOUT (-8)       /* a bounded device wait gave up */
+#define PSFD_E_STATE (-9)         /* call out of order (e.g. solve before set_illumination) */
+
+#define PSFD_FP64 0         /* every step in complex FP64 */
+#define PSFD_FP32_REFINED 1 /* complex FP32 Krylov inside FP64 defect correction */
+
+#define PSFD_HOST 0   /* pointer argument is host memory */
+#define PSFD_DEVICE 1 /* pointer argument is device memory of the context's GPU */
+
+typedef struct psfd_ctx psfd_ctx;
+
+/* Discretisation of one mask clip (Sec. 3, Eq. (4): Fourier basis on a uniform grid). */
+typedef struct {
+  int nx, ny;        /* transverse grid; x and y are periodic with pitch nx*dx, ny*dy */
+  int nslab;         /* absorber planes (the support of V) */
+  int nf;            /* z FFT length, nf >= 2*nslab + 2 and psfd_supported_length(nf) */
+  double dx, dy, dz; /* grid spacing, nm */
+  double wavelength; /* vacuum wavelength, nm */
+  double eps_bg;     /* real permittivity of the background medium (1 = vacuum) */
+} psfd_grid;
+
+/* Options of psfd_solve. Zero-initialised fields take the defaults in brackets. */
+typedef struct {
+  double tol;       /* target relative residual ||b - A x|| / ||b|| in FP64 [1e-10] */
+  int max_iter;     /* Krylov iteration cap per solve or per refinement sweep [500] */
+  int max_outer;    /* refinement sweep cap for PSFD_FP32_REFINED [12] */
+  double inner_tol; /* relative tolerance of each FP32 inner solve [1e-4] */
+  int check_every;  /* iterations between host reads of the device convergence flags [4] */
+  int reserved[4];
+} psfd_solve_opts;
+
+typedef struct {
+  int iterations;   /* Krylov iterations (operator applications / 2), max over RHS */
+  int outer;        /* refinement sweeps performed */
+  double relres;    /* true FP64 relative residual after the solve, max over RHS */
+  double seconds;   /* wall time of psfd_solve */
+  int status;       /* PSFD_OK or the first failure */
+  int reserved[3];
+} psfd_report;
+
+/* Text of a status code (static storage). */
+const char* psfd_strerror(int status);
+
+/* Description of the last failure on this context ("" if none). */
+const char* psfd_last_error(const psfd_ctx* ctx);
+
+/* 1 if n is an FFT length the kernels are built for, else 0. */
+int psfd_supported_length(int n);
+
+/* Device bytes psfd_create would allocate for this grid, precision and RHS capacity. */
+int psfd_workspace_bytes(const psfd_grid* grid, int precision, int max_rhs, size_t* bytes);
+
+/* Create a solver context on the current CUDA device.
+ *   grid       discretisation; validated (supported lengths, nf >= 2*nslab+2)
+ *   precision  PSFD_FP64 or PSFD_FP32_REFINED
+ *   max_rhs    capacity in illuminations solved together
+ *   hbm_budget bytes the context may allocate (0 = no limit); PSFD_E_BUDGET if exceeded
+ *   stream     cudaStream_t to run on (NULL = legacy default stream)
+ * On success *out receives the context. */
+int psfd_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs,
+                size_t hbm_budget, void* stream);
+
+/* Free every resource of the context (NULL is accepted). */
+int psfd_destroy(psfd_ctx* ctx);
+
+/* Rebind the context to another stream. */
+int psfd_set_stream(psfd_ctx* ctx, void* stream);
+
+/* Planar stack below z_top (Sec. 2, Fig. 1): n_layers layers listed top to bottom with
+ * complex refractive index n_complex[2*j], n_complex[2*j+1] and thickness thickness_nm[j],
+ * on a substrate of index n_sub[0] + i n_sub[1]. eps = n^2. n_layers may be 0. */
+int psfd_set_stack(psfd_ctx* ctx, int n_layers, const double* n_complex,
+                   const double* thickness_nm, const double* n_sub);
+
+/* Absorber permittivity eps on the nslab x ny x nx cells, complex interleaved, laid out
+ * [plane][y][x] (where = PSFD_HOST or PSFD_DEVICE). V = k0^2 (eps - eps_bg) is formed on
+ * the device in FP64 and FP32 (Sec. 2, Eq. (1)). */
+int psfd_set_potential(psfd_ctx* ctx, const double* eps_complex, int where);
+
+/* Plane-wave illuminations (host arrays of length n_rhs <= max_rhs): polar angle theta
+ * and azimuth phi in degrees (k_inc = k_bg (sin t cos f, sin t sin f, -cos t)) and
+ * polarisation pol (0 = s, i.e. E along z x q; 1 = p). Builds, on the device and in FP64,
+ * the per-mode stack reflection r_s, r_p by the Parratt recursion and the right-hand side
+ * b = E_inc + R[E_inc]. Returns PSFD_E_ANOMALY if some order has |beta| < 1e-9 k0. */
+int psfd_set_illumination(psfd_ctx* ctx, int n_rhs, const double* theta_deg,
+                          const double* phi_deg, const int* pol);
+
+/* Solve A u = b for every illumination (Krylov: BiCGStab; PSFD_FP32_REFINED runs it in
+ * complex FP32 inside FP64 defect correction r = b - A u, u += A^-1 r). opts may be NULL.
+ * The Krylov loop stays on the device; the host reads the convergence flags every
+ * check_every iterations. report may be NULL. Returns PSFD_E_NOT_CONVERGED if some
+ * right-hand side missed the tolerance (the solution is still stored). */
+int psfd_solve(psfd_ctx* ctx, const psfd_solve_opts* opts, psfd_report* report);
+
+/* Number of propagating reflected orders (|q_mn| < k_bg) of illumination rhs. */
+int psfd_num_orders(psfd_ctx* ctx, int rhs, int* n_orders);
+
+/* Reflected diffraction orders of illumination rhs after psfd_solve (Sec. 2, Eq. (3);
+ * Sec. 3, Eq. (9)): for each propagating order (m, n), written to host arrays of
+ * capacity `capacity` orders,
+ *   mn[2k], mn[2k+1]  signed order indices,
+ *   amp[6k..6k+5]     complex field vector A_mn (x, y, z) referenced at z_top,
+ *   sp[4k..4k+3]      complex s and p amplitudes (bilinear projections on s, p+),
+ *   eff[k]            diffraction efficiency |A|^2 Re(beta_mn) / beta_00.
+ * Any of amp, sp, eff may be NULL. *n_orders receives the count. */
+int psfd_diffraction_orders(psfd_ctx* ctx, int rhs, int capacity, int* n_orders, int* mn,
+                            double* amp, double* sp, double* eff);
+
+/* One operator application out = A u for right-hand sides rhs0 .. rhs0+n_rhs-1 with the
+ * current potential and illumination tables (the Krylov hot path, Eq. (18) with Eq. (9)).
+ * precision selects complex FP64 (double pairs) or complex FP32 (float pairs) data.
+ * u and out are device arrays [n_rhs][3][nslab][ny][nx]; they must not alias. */
+int psfd_apply(psfd_ctx* ctx, int precision, int rhs0, int n_rhs, const void* u, void* out);
+
+/* Copy the FP64 solution u (or the right-hand side b) of illumination rhs,
+ * [3][nslab][ny][nx] complex double, to dst (where = PSFD_HOST or PSFD_DEVICE). */
+int psfd_get_solution(psfd_ctx* ctx, int rhs, double* dst, int where);
+int psfd_get_rhs(psfd_ctx* ctx, int rhs, double* dst, int where);
+
+/* Per-mode tables of illumination rhs, each [ny][nx] complex double on the host:
+ * beta (z wavenumber, Im >= 0) and the stack reflection coefficients r_s, r_p. */
+int psfd_get_mode_tables(psfd_ctx* ctx, int rhs, double* beta, double* r_s, double* r_p);
+
+/* Test hook for the device FFT: `count` contiguous transforms of length n, in place, on
+ * device data (complex double if fp64 else complex float). inverse = 1 applies the
+ * unnormalised inverse. Runs on the legacy default stream and synchronises. */
+int psfd_test_fft(int n, int count, int inverse, int fp64, void* data);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSFD_H */

@@ -1,0 +1,214 @@
+// fft.cuh -- mixed-radix Stockham FFT on shared memory, executed by groups of lanes
+// inside one warp.
+//
+// Sec. 3 of the paper evaluates every derivative / convolution with FFTs (Eqs. (6),
+// (18)); this is the project's own transform. A length-N transform is carried out by a
+// group of G lanes of one warp (G divides 32) on data that already sits in shared
+// memory with element stride `es`. Each stage of radix R loads R elements per
+// butterfly into registers, applies the twiddles, does the radix-R DFT in registers,
+// and writes the results in self-sorting (Stockham) order, so that the output is in
+// natural order without a bit-reversal pass. Stages are separated by __syncwarp only:
+// warps progress independently. Radices: 8 first, then 4, 2, 3, 5.
+//
+// Twiddles come from a table tw[t] = exp(-2 pi i t / N), t < N, prepared in FP64 on
+// the host and placed in shared memory by the caller. Forward transforms use
+// exp(-i ...); inverse transforms are unnormalised.
+#pragma once
+
+#include "common.cuh"
+
+namespace psfd {
+
+__host__ __device__ constexpr int fft_plan_radix(int n, int stage) {
+  int s = 0;
+  while (n % 8 == 0 && n >= 8) { if (s == stage) return 8; n /= 8; ++s; }
+  while (n % 4 == 0) { if (s == stage) return 4; n /= 4; ++s; }
+  while (n % 2 == 0) { if (s == stage) return 2; n /= 2; ++s; }
+  while (n % 3 == 0) { if (s == stage) return 3; n /= 3; ++s; }
+  while (n % 5 == 0) { if (s == stage) return 5; n /= 5; ++s; }
+  return 0;
+}
+
+__host__ __device__ constexpr int fft_plan_stages(int n) {
+  int s = 0;
+  while (fft_plan_radix(n, s) != 0) ++s;
+  return s;
+}
+
+// Lanes per transform: N/8 rounded down to a power of two, clamped to [1, 32].
+__host__ __device__ constexpr int fft_group_lanes(int n) {
+  int g = 1;
+  while (g * 2 <= n / 8 && g * 2 <= 32) g *= 2;
+  return g;
+}
+
+// ---------------------------------------------------------------------------
+// radix-R DFTs in registers (forward: exp(-2 pi i r k / R); INV: conjugate kernel)
+// ---------------------------------------------------------------------------
+template <typename C, bool INV>
+__device__ __forceinline__ void dft2(C& a, C& b) {
+  C t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <typename C, bool INV>
+__device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
+  C t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3), t3 = csub(v1, v3);
+  t3 = INV ? cmul_i(t3) : cmul_mi(t3);
+  v0 = cadd(t0, t2);
+  v2 = csub(t0, t2);
+  v1 = cadd(t1, t3);
+  v3 = csub(t1, t3);
+}
+
+template <typename C, int R, bool INV> struct Dft;
+
+template <typename C, bool INV> struct Dft<C, 2, INV> {
+  __device__ __forceinline__ static void run(C* v) { dft2<C, INV>(v[0], v[1]); }
+};
+
+template <typename C, bool INV> struct Dft<C, 4, INV> {
+  __device__ __forceinline__ static void run(C* v) { dft4<C, INV>(v[0], v[1], v[2], v[3]); }
+};
+
+template <typename C, bool INV> struct Dft<C, 8, INV> {
+  __device__ __forceinline__ static void run(C* v) {
+    using R = typename RealOf<C>::T;
+    const R h = (R)0.70710678118654752440;  // 1/sqrt(2)
+    C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<C, INV>(e0, e1, e2, e3);
+    dft4<C, INV>(o0, o1, o2, o3);
+    // o_k *= exp(-+ i pi k / 4)
+    if (INV) {
+      o1 = mk((o1.x - o1.y) * h, (o1.x + o1.y) * h);
+      o2 = cmul_i(o2);
+      o3 = mk(-(o3.x + o3.y) * h, (o3.x - o3.y) * h);
+    } else {
+      o1 = mk((o1.x + o1.y) * h, (o1.y - o1.x) * h);
+      o2 = cmul_mi(o2);
+      o3 = mk((o3.y - o3.x) * h, -(o3.x + o3.y) * h);
+    }
+    v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+  }
+};
+
+template <typename C, bool INV> struct Dft<C, 3, INV> {
+  __device__ __forceinline__ static void run(C* v) {
+    using R = typename RealOf<C>::T;
+    const R c = (R)-0.5;
+    const R s = (R)0.86602540378443864676;  // sin(2 pi / 3)
+    C t = cadd(v[1], v[2]);
+    C u = csub(v[1], v[2]);
+    C m = mk(v[0].x + c * t.x, v[0].y + c * t.y);
+    C su = cscale(u, s);
+    C isu = INV ? cmul_i(su) : cmul_mi(su);  // -+ i s u
+    v[0] = cadd(v[0], t);
+    v[1] = cadd(m, isu);
+    v[2] = csub(m, isu);
+  }
+};
+
+template <typename C, bool INV> struct Dft<C, 5, INV> {
+  __device__ __forceinline__ static void run(C* v) {
+    using R = typename RealOf<C>::T;
+    const R c1 = (R)0.30901699437494742410;   // cos(2 pi / 5)
+    const R c2 = (R)-0.80901699437494742410;  // cos(4 pi / 5)
+    const R s1 = (R)0.95105651629515357212;   // sin(2 pi / 5)
+    const R s2 = (R)0.58778525229247312917;   // sin(4 pi / 5)
+    C t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+    C u1 = csub(v[1], v[4]), u2 = csub(v[2], v[3]);
+    C a1 = mk(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+    C a2 = mk(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+    C b1 = mk(s1 * u1.x + s2 * u2.x, s1 * u1.y + s2 * u2.y);
+    C b2 = mk(s2 * u1.x - s1 * u2.x, s2 * u1.y - s1 * u2.y);
+    C ib1 = INV ? cmul_i(b1) : cmul_mi(b1);  // -+ i b1
+    C ib2 = INV ? cmul_i(b2) : cmul_mi(b2);
+    v[0] = cadd(v[0], cadd(t1, t2));
+    v[1] = cadd(a1, ib1);
+    v[4] = csub(a1, ib1);
+    v[2] = cadd(a2, ib2);
+    v[3] = csub(a2, ib2);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Stockham stages. Butterfly b of a radix-R stage (after stages whose radices multiply
+// to NS) reads elements b + r N/R, twiddles them by exp(-2 pi i r (b mod NS)/(NS R)),
+// and writes element r of its DFT to (b / NS) NS R + (b mod NS) + r NS.
+// ---------------------------------------------------------------------------
+template <typename C, int N, int G, bool INV, int S, int NS>
+__device__ __forceinline__ void fft_stages(C* a, int es, int g, const C* tw, bool valid) {
+  if constexpr (S < fft_plan_stages(N)) {
+    constexpr int R = fft_plan_radix(N, S);
+    constexpr int NB = N / R;
+    constexpr int K = (NB + G - 1) / G;
+    constexpr int TWS = N / (NS * R);
+    C v[K][R];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int b = g + k * G;
+      if (valid && (NB % G == 0 || b < NB)) {
+        const int jj = b % NS;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[k][r] = a[(b + r * NB) * es];
+        if constexpr (NS > 1) {
+#pragma unroll
+          for (int r = 1; r < R; ++r) {
+            C w = tw[r * jj * TWS];
+            if (INV) w = cconj(w);
+            v[k][r] = cmul(v[k][r], w);
+          }
+        }
+        Dft<C, R, INV>::run(v[k]);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int b = g + k * G;
+      if (valid && (NB % G == 0 || b < NB)) {
+        const int jj = b % NS;
+        const int base = (b / NS) * NS * R + jj;
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[(base + r * NS) * es] = v[k][r];
+      }
+    }
+    __syncwarp();
+    fft_stages<C, N, G, INV, S + 1, NS * R>(a, es, g, tw, valid);
+  }
+}
+
+// One length-N transform per group of G lanes. Every lane of the warp must call this
+// (lanes of groups without work pass valid = false) because stages end in __syncwarp.
+template <typename C, int N, bool INV>
+__device__ __forceinline__ void group_fft(C* a, int es, int g, const C* tw, bool valid) {
+  constexpr int G = fft_group_lanes(N);
+  fft_stages<C, N, G, INV, 0, 1>(a, es, g, tw, valid);
+}
+
+// Batched transforms by a whole CTA: `count` transforms, transform f starting at
+// a + f * fs with element stride es. Each warp handles 32/G transforms at a time.
+template <typename C, int N, bool INV>
+__device__ __forceinline__ void cta_fft(C* a, int count, int fs, int es, const C* tw) {
+  constexpr int G = fft_group_lanes(N);
+  constexpr int GPW = 32 / G;  // groups per warp
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int gid = warp * GPW + lane / G;
+  const int g = lane % G;
+  const int ngroups = nwarps * GPW;
+  const int rounds = (count + ngroups - 1) / ngroups;
+  for (int it = 0; it < rounds; ++it) {
+    const int f = gid + it * ngroups;
+    const bool valid = f < count;
+    group_fft<C, N, INV>(a + (valid ? f : 0) * fs, es, g, tw, valid);
+  }
+}
+
+}  // namespace psfd

@@ -1,0 +1,109 @@
+// internal.h -- structures shared by the CUDA translation units of libpsfd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace psfd {
+
+// Per-illumination parameters on the device.
+struct RhsParam {
+  double qix, qiy;    // transverse wavevector of the incident wave
+  double cphi, sphi;  // azimuth; orients s at q = 0
+  double2 e_inc[3];   // incident polarisation vector (bilinear unit)
+  double2 r_inc[3];   // T_R(q_00) e_inc: reflected incident amplitude at z_top
+  double2 beta00;     // z wavenumber of the specular order
+  int slot;           // row of the mode tables (illuminations at one angle share it)
+  int pol;
+};
+
+// Per transverse mode (m, n) and angle slot, computed in FP64 by the stack kernel.
+struct ModeEntry {
+  double2 beta;  // sqrt(k_bg^2 - |q|^2), Im >= 0
+  double2 ebL;   // exp(i beta L), L = nf dz / 2
+  double2 rs;    // stack reflection coefficient, s (E-field)
+  double2 rp;    // stack reflection coefficient, p (H-field)
+};
+
+// Krylov scalars per right-hand side (BiCGStab), all FP64.
+struct KScal {
+  double2 rho, alpha, omega, beta;
+  double bnorm2;  // ||b||^2 of the system being solved
+  double rnorm2;  // ||r||^2 of the recursively updated residual
+  double scale;   // defect-correction scale ||r64|| of this sweep
+  int iters;
+  int active;  // 1 while iterating
+  int status;  // PSFD_OK / PSFD_E_BREAKDOWN / PSFD_E_NOT_CONVERGED
+  int pad;
+};
+
+enum InMode { IN_PLAIN = 0, IN_PUPDATE = 1, IN_SUPDATE = 2 };
+enum EpiMode { EPI_AU = 0, EPI_RESID = 1, EPI_NONE = 2 };
+enum DotBits { DOT_R0_OUT = 1, DOT_OUT_U = 2, DOT_OUT_OUT = 4 };
+constexpr int NDOT = 3;
+
+// Everything one operator application needs. Vector pointers address the first RHS of
+// the batch (local index 0); tables are indexed with rhs0 + local index.
+template <typename C>
+struct OpCall {
+  int nx, ny, nslab, nf;
+  int rhs0, nrhs;
+  double dx, dy, dz, kb;
+  const C* V;                                   // [nslab][ny][nx]
+  const double2 *twx, *twy, *twz;               // exp(-2 pi i t / n) tables (FP64)
+  const RhsParam* rhsp;
+  const ModeEntry* modes;
+  const int* active;  // per global rhs, or null = all active
+  // input stage: J = V * in, in = u | r + beta (u - omega v) | r - alpha v
+  int in_mode;
+  const C* u;
+  C* ustore;  // updated p or s (IN_PUPDATE / IN_SUPDATE)
+  const C* r;
+  const C* v;
+  const KScal* sc;
+  C* work;  // [nrhs][3][nslab][ny][nx] spectral intermediate
+  // epilogue: out = in - w (EPI_AU) or b - (in - w) (EPI_RESID), with dot products
+  int epi;
+  C* out;
+  const C* b;
+  const C* r0;
+  double2* partials;  // [global rhs][NDOT][maxblk]
+  int maxblk;
+  int dot_mask;
+  C* side;  // [global rhs][2][3][ny][nx] normalised spectra of G*(V u), planes 0, nslab+1
+  cudaStream_t stream;
+};
+
+// Runs K1 (V multiply + forward xy FFT), K2 (z column) and K3 (inverse xy + epilogue).
+// Returns the number of partial-sum blocks per RHS written (>= 0) or a negative status.
+template <typename C> int op_apply(const OpCall<C>& call);
+
+// Partial-sum blocks per RHS that op_apply's epilogue writes for this grid.
+int op_blocks_per_rhs(int nx, int ny, int nslab, bool fp64);
+
+// Whether the kernels are built for an FFT length.
+bool fft_length_supported(int n);
+
+}  // namespace psfd
+
+namespace psfd {
+
+// One batched BiCGStab solve A x = b over right-hand sides op.rhs0 .. op.rhs0+op.nrhs-1.
+template <typename C>
+struct KrylovCall {
+  OpCall<C> op;  // grid, tables, potential, stream, partial-sum buffer
+  int n;         // complex elements per right-hand side
+  const C* b;
+  C *x, *r, *r0, *p, *v, *s, *t, *work;
+  KScal* sc;           // per global rhs
+  int* act;            // per global rhs, device
+  const int* act_in;   // initial activity (device) or null
+  int* h_act;          // pinned host mirror of act (>= rhs0 + nrhs entries)
+  double tol;
+  int max_iter;
+  int check_every;
+};
+template <typename C> int bicgstab(const KrylovCall<C>& k);
+
+}  // namespace psfd

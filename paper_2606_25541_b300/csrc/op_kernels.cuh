@@ -1,0 +1,469 @@
+// op_kernels.cuh -- the Lippmann-Schwinger operator application, templated on the
+// complex type (float2 for the FP32 bulk path, double2 for the FP64 path).
+//
+// One application A u = u - (I + R) G*(V u) (Sec. 3, Eq. (18) with the reflection
+// operator of Eq. (9) folded in) runs as three passes over HBM:
+//   K1  per (rhs, component, absorber plane): J = V * u, forward 2-D FFT over (y, x);
+//   K2  per (rhs, transverse mode): the nslab planes of all three components are zero
+//       padded to nf, transformed along z, multiplied by the windowed dyadic Green's
+//       function (a symmetric 3x3 per wavevector, evaluated on the fly), transformed
+//       back, and the stack reflection T_R E(plane 0) exp(i beta (p-1) dz) is added;
+//   K3  per (rhs, component, plane): inverse 2-D FFT and the epilogue out = u - w
+//       (or the FP64 residual b - (u - w)), fused with the Krylov dot products.
+// Planes that fit in shared memory are transformed in one CTA (K1/K3 "plane"
+// kernels); larger planes use a row pass and a column pass.
+#pragma once
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "internal.h"
+
+namespace psfd {
+
+template <typename T, typename P>
+__device__ __forceinline__ T* align16(P* p) {
+  return reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
+}
+
+template <typename C> struct Prec;
+template <> struct Prec<float2> { static constexpr int PHI_TERMS = 10; };
+template <> struct Prec<double2> { static constexpr int PHI_TERMS = 17; };
+
+__device__ __forceinline__ void split_hi_lo(double2 v, float2& hi, float2& lo) {
+  hi = to_c32(v);
+  lo = make_float2((float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y));
+}
+__device__ __forceinline__ void split_hi_lo(double2 v, double2& hi, double2& lo) {
+  hi = v;
+  lo = make_double2(0.0, 0.0);
+}
+__device__ __forceinline__ void split_hi_lo_r(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+__device__ __forceinline__ void split_hi_lo_r(double v, double& hi, double& lo) {
+  hi = v;
+  lo = 0.0;
+}
+
+__device__ __forceinline__ float2 cexp_r(float2 z) {
+  float s, c;
+  sincosf(z.y, &s, &c);
+  float e = expf(z.x);
+  return make_float2(e * c, e * s);
+}
+__device__ __forceinline__ double2 cexp_r(double2 z) { return cexp_d(z); }
+
+// ---------------------------------------------------------------------------
+// input stage (K1) and epilogue (K3) element operations
+// ---------------------------------------------------------------------------
+template <typename C> struct InScal { C a, b; };
+
+template <typename C, int IN>
+__device__ __forceinline__ InScal<C> load_in_scalars(const OpCall<C>& a, int g) {
+  InScal<C> s;
+  s.a = mk((typename RealOf<C>::T)0, (typename RealOf<C>::T)0);
+  s.b = s.a;
+  if constexpr (IN == IN_PUPDATE) {
+    s.a = from_c64<C>(a.sc[g].beta);
+    s.b = from_c64<C>(a.sc[g].omega);
+  } else if constexpr (IN == IN_SUPDATE) {
+    s.a = from_c64<C>(a.sc[g].alpha);
+  }
+  return s;
+}
+
+// The vector the operator is applied to, element idx; updates p or s on the way.
+template <typename C, int IN>
+__device__ __forceinline__ C input_elem(const OpCall<C>& a, size_t idx, const InScal<C>& s) {
+  if constexpr (IN == IN_PLAIN) {
+    return a.u[idx];
+  } else if constexpr (IN == IN_PUPDATE) {
+    // p = r + beta (p - omega v)
+    C p = a.u[idx], r = a.r[idx], v = a.v[idx];
+    C val = cadd(r, cmul(s.a, csub(p, cmul(s.b, v))));
+    a.ustore[idx] = val;
+    return val;
+  } else {
+    // s = r - alpha v
+    C val = csub(a.r[idx], cmul(s.a, a.v[idx]));
+    a.ustore[idx] = val;
+    return val;
+  }
+}
+
+template <typename C> struct Acc;
+template <> struct Acc<float2> { using T = float2; };
+template <> struct Acc<double2> { using T = double2; };
+
+template <typename C>
+struct Dots {
+  typename Acc<C>::T d[NDOT];
+};
+
+template <typename C, int EPI>
+__device__ __forceinline__ C epilogue_elem(const OpCall<C>& a, const C* uin, size_t idx, C w, Dots<C>& dt) {
+  C u = uin[idx];
+  C out = csub(u, w);
+  if constexpr (EPI == EPI_RESID) out = csub(a.b[idx], out);
+  a.out[idx] = out;
+  if (a.dot_mask & DOT_R0_OUT) dt.d[0] = cadd(dt.d[0], cmulc(a.r0[idx], out));
+  if (a.dot_mask & DOT_OUT_U) dt.d[1] = cadd(dt.d[1], cmulc(out, u));
+  if (a.dot_mask & DOT_OUT_OUT) dt.d[2].x += out.x * out.x + out.y * out.y;
+  return out;
+}
+
+__device__ __forceinline__ double2 shfl_down_d2(double2 v, int o) {
+  return make_double2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
+}
+
+// Deterministic block reduction of the (up to three) dot products; thread 0 writes
+// dst[k * stride] for every requested k. Needs 3 * 32 double2 of shared scratch.
+template <typename C>
+__device__ __forceinline__ void block_write_dots(const Dots<C>& dt, int mask, double2* dst, int stride,
+                                                 double2* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NDOT; ++k) {
+    if (!(mask & (1 << k))) continue;
+    double2 v = as_c64(dt.d[k]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = cadd(v, shfl_down_d2(v, o));
+    if (lane == 0) scratch[k * 32 + warp] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NDOT; ++k) {
+      if (!(mask & (1 << k))) continue;
+      double2 v = lane < nw ? scratch[k * 32 + lane] : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = cadd(v, shfl_down_d2(v, o));
+      if (lane == 0) dst[k * stride] = v;
+    }
+  }
+}
+
+template <typename C>
+__device__ __forceinline__ void zero_dots(Dots<C>& dt) {
+#pragma unroll
+  for (int k = 0; k < NDOT; ++k) dt.d[k] = mk((typename RealOf<C>::T)0, (typename RealOf<C>::T)0);
+}
+
+// ---------------------------------------------------------------------------
+// K1 / K3 for planes that fit in shared memory
+// ---------------------------------------------------------------------------
+template <typename C, int NX, int NY, int IN, int NT>
+__global__ void __launch_bounds__(NT) k_plane_fwd(OpCall<C> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int PITCH = NX + 1;
+  C* tile = reinterpret_cast<C*>(smem);
+  C* twx = tile + NY * PITCH;
+  C* twy = twx + NX;
+  const int p = blockIdx.x, c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
+  if (a.active && !a.active[g]) return;
+  for (int i = threadIdx.x; i < NX; i += NT) twx[i] = from_c64<C>(a.twx[i]);
+  for (int i = threadIdx.x; i < NY; i += NT) twy[i] = from_c64<C>(a.twy[i]);
+  const InScal<C> s = load_in_scalars<C, IN>(a, g);
+  const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
+  const C* Vp = a.V + (size_t)p * (NX * NY);
+  for (int i = threadIdx.x; i < NX * NY; i += NT) {
+    C val = input_elem<C, IN>(a, plane + i, s);
+    tile[(i / NX) * PITCH + (i % NX)] = cmul(Vp[i], val);
+  }
+  __syncthreads();
+  cta_fft<C, NX, false>(tile, NY, PITCH, 1, twx);
+  __syncthreads();
+  cta_fft<C, NY, false>(tile, NX, 1, PITCH, twy);
+  __syncthreads();
+  for (int i = threadIdx.x; i < NX * NY; i += NT) a.work[plane + i] = tile[(i / NX) * PITCH + (i % NX)];
+}
+
+template <typename C, int NX, int NY, int EPI, int NT>
+__global__ void __launch_bounds__(NT) k_plane_inv(OpCall<C> a, const C* uin) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int PITCH = NX + 1;
+  C* tile = reinterpret_cast<C*>(smem);
+  C* twx = tile + NY * PITCH;
+  C* twy = twx + NX;
+  double2* scratch = align16<double2>(twy + NY);
+  const int p = blockIdx.x, c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
+  if (a.active && !a.active[g]) return;
+  for (int i = threadIdx.x; i < NX; i += NT) twx[i] = from_c64<C>(a.twx[i]);
+  for (int i = threadIdx.x; i < NY; i += NT) twy[i] = from_c64<C>(a.twy[i]);
+  const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
+  for (int i = threadIdx.x; i < NX * NY; i += NT) tile[(i / NX) * PITCH + (i % NX)] = a.work[plane + i];
+  __syncthreads();
+  cta_fft<C, NY, true>(tile, NX, 1, PITCH, twy);
+  __syncthreads();
+  cta_fft<C, NX, true>(tile, NY, PITCH, 1, twx);
+  __syncthreads();
+  Dots<C> dt;
+  zero_dots(dt);
+  for (int i = threadIdx.x; i < NX * NY; i += NT)
+    epilogue_elem<C, EPI>(a, uin, plane + i, tile[(i / NX) * PITCH + (i % NX)], dt);
+  if (a.dot_mask) {
+    const int blk = c * a.nslab + p;
+    block_write_dots(dt, a.dot_mask, a.partials + ((size_t)g * NDOT) * a.maxblk + blk, a.maxblk, scratch);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// split path: row pass and column pass (planes larger than shared memory)
+// ---------------------------------------------------------------------------
+// blockIdx.x = plane * (ny / rb) + row block; each CTA transforms rb rows of length NX.
+template <typename C, int NX, int IN, int NT>
+__global__ void __launch_bounds__(NT) k_rows_fwd(OpCall<C> a, int rb) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  C* tile = reinterpret_cast<C*>(smem);
+  C* tw = tile + rb * NX;
+  const int nrb = a.ny / rb;
+  const int p = blockIdx.x / nrb, y0 = (blockIdx.x % nrb) * rb;
+  const int c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
+  if (a.active && !a.active[g]) return;
+  for (int i = threadIdx.x; i < NX; i += NT) tw[i] = from_c64<C>(a.twx[i]);
+  const InScal<C> s = load_in_scalars<C, IN>(a, g);
+  const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
+  const C* Vp = a.V + ((size_t)p * a.ny + y0) * NX;
+  for (int i = threadIdx.x; i < rb * NX; i += NT) tile[i] = cmul(Vp[i], input_elem<C, IN>(a, base + i, s));
+  __syncthreads();
+  cta_fft<C, NX, false>(tile, rb, NX, 1, tw);
+  __syncthreads();
+  for (int i = threadIdx.x; i < rb * NX; i += NT) a.work[base + i] = tile[i];
+}
+
+template <typename C, int NX, int EPI, int NT>
+__global__ void __launch_bounds__(NT) k_rows_inv(OpCall<C> a, const C* uin, int rb) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  C* tile = reinterpret_cast<C*>(smem);
+  C* tw = tile + rb * NX;
+  double2* scratch = align16<double2>(tw + NX);
+  const int nrb = a.ny / rb;
+  const int p = blockIdx.x / nrb, y0 = (blockIdx.x % nrb) * rb;
+  const int c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
+  if (a.active && !a.active[g]) return;
+  for (int i = threadIdx.x; i < NX; i += NT) tw[i] = from_c64<C>(a.twx[i]);
+  const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
+  for (int i = threadIdx.x; i < rb * NX; i += NT) tile[i] = a.work[base + i];
+  __syncthreads();
+  cta_fft<C, NX, true>(tile, rb, NX, 1, tw);
+  __syncthreads();
+  Dots<C> dt;
+  zero_dots(dt);
+  for (int i = threadIdx.x; i < rb * NX; i += NT) epilogue_elem<C, EPI>(a, uin, base + i, tile[i], dt);
+  if (a.dot_mask) {
+    const int blk = (c * a.nslab + p) * nrb + (y0 / rb);
+    block_write_dots(dt, a.dot_mask, a.partials + ((size_t)g * NDOT) * a.maxblk + blk, a.maxblk, scratch);
+  }
+}
+
+// In-place transforms along y of tx consecutive columns of one plane.
+// blockIdx.x = plane * (nx / tx) + column block.
+template <typename C, int NY, bool INV, int NT>
+__global__ void __launch_bounds__(NT) k_cols(OpCall<C> a, int tx) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int PITCH = NY + 1;
+  C* tile = reinterpret_cast<C*>(smem);
+  C* tw = tile + tx * PITCH;
+  const int ncb = a.nx / tx;
+  const int p = blockIdx.x / ncb, x0 = (blockIdx.x % ncb) * tx;
+  const int c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
+  if (a.active && !a.active[g]) return;
+  for (int i = threadIdx.x; i < NY; i += NT) tw[i] = from_c64<C>(a.twy[i]);
+  const size_t base = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)NY * a.nx + x0;
+  for (int i = threadIdx.x; i < NY * tx; i += NT) {
+    const int y = i / tx, xx = i % tx;
+    tile[xx * PITCH + y] = a.work[base + (size_t)y * a.nx + xx];
+  }
+  __syncthreads();
+  cta_fft<C, NY, INV>(tile, tx, PITCH, 1, tw);
+  __syncthreads();
+  for (int i = threadIdx.x; i < NY * tx; i += NT) {
+    const int y = i / tx, xx = i % tx;
+    a.work[base + (size_t)y * a.nx + xx] = tile[xx * PITCH + y];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: z columns -- zero padding, FFT_z, dyadic Green's function, IFFT_z, reflection
+// ---------------------------------------------------------------------------
+// Windowed periodic-transverse Green's function of one mode (q, beta) at kz_l:
+//   F[G_L] = S (I - k k^T / kb^2) - (E / kb^2) z z^T,  k = (qx, qy, kz_l),
+//   E = (-1)^l exp(i beta L),  S = (1 - E) / (kz^2 - beta^2),
+// with L = nf dz / 2 so that kz_l L = pi l. Writing kappa = |kz_l| and
+// delta = beta - kappa, E = exp(i delta L) and S = i L phi1(i delta L) / (kappa + beta),
+// phi1(w) = (e^w - 1)/w. Near the removable singularity (|delta L| < 1/2) phi1 is summed
+// as its Taylor series; elsewhere S = (E - 1)/(delta (kappa + beta)) with E from the FP64
+// table exp(i beta L). delta is formed from hi/lo splits of beta and kappa so that it
+// stays accurate in FP32 when beta ~ kappa.
+template <typename C>
+__device__ __forceinline__ void green_apply(C& J0, C& J1, C& J2, typename RealOf<C>::T qx,
+                                            typename RealOf<C>::T qy, typename RealOf<C>::T kz,
+                                            typename RealOf<C>::T kh, typename RealOf<C>::T kl, C bh, C bl,
+                                            C E, typename RealOf<C>::T L, typename RealOf<C>::T cinv,
+                                            typename RealOf<C>::T scale) {
+  using R = typename RealOf<C>::T;
+  const C d = mk((bh.x - kh) + (bl.x - kl), bh.y + bl.y);
+  const C kpb = mk((kh + bh.x) + (kl + bl.x), bh.y + bl.y);
+  const C w = mk(-d.y * L, d.x * L);
+  C S;
+  if (w.x * w.x + w.y * w.y < (R)0.25) {
+    C phi = mk((R)1, (R)0);
+#pragma unroll
+    for (int k = Prec<C>::PHI_TERMS; k >= 2; --k) {
+      C t = cmul(w, phi);
+      phi = mk((R)1 + t.x / (R)k, t.y / (R)k);
+    }
+    S = cdiv(mk(-phi.y * L, phi.x * L), kpb);  // i L phi1 / (kappa + beta)
+  } else {
+    S = cdiv(mk(E.x - (R)1, E.y), cmul(d, kpb));
+  }
+  S = cscale(S, scale);
+  const C Es = cscale(E, cinv * scale);
+  const C kJ = cadd(cadd(cscale(J0, qx), cscale(J1, qy)), cscale(J2, kz));
+  const C ckJ = cscale(kJ, cinv);
+  const C W0 = cmul(S, csub(J0, cscale(ckJ, qx)));
+  const C W1 = cmul(S, csub(J1, cscale(ckJ, qy)));
+  const C W2 = csub(cmul(S, csub(J2, cscale(ckJ, kz))), cmul(Es, J2));
+  J0 = W0;
+  J1 = W1;
+  J2 = W2;
+}
+
+// grid (nx / tx, ny, nrhs); dynamic shared memory: 3 tx (NF + 1) columns + tables.
+template <typename C, int NF, int NT>
+__global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
+  using R = typename RealOf<C>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int P = NF + 1;
+  C* col = reinterpret_cast<C*>(smem);
+  C* tw = col + 3 * tx * P;
+  R* kh = reinterpret_cast<R*>(tw + NF);
+  R* kl = kh + NF;
+  R* kzs = kl + NF;
+  C* cb_h = reinterpret_cast<C*>(kzs + NF);  // per column: beta hi
+  C* cb_l = cb_h + tx;                        // beta lo
+  C* cebl = cb_l + tx;                        // exp(i beta L)
+  C* cbdz = cebl + tx;                        // beta dz
+  C* R0 = cbdz + tx;                          // 3 tx: T_R E(plane 0)
+  R* cqx = reinterpret_cast<R*>(R0 + 3 * tx);
+  R* cqy = cqx + tx;
+
+  const int x0 = blockIdx.x * tx, y = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
+  if (a.active && !a.active[g]) return;
+  const int nx = a.nx, ny = a.ny, ns = a.nslab;
+  const RhsParam rp = a.rhsp[g];
+  const double two_pi = 6.283185307179586476925286766559;
+
+  for (int i = threadIdx.x; i < NF; i += NT) {
+    tw[i] = from_c64<C>(a.twz[i]);
+    const int lf = fft_freq(i, NF);
+    const double kz64 = two_pi * (double)lf / ((double)NF * a.dz);
+    split_hi_lo_r(fabs(kz64), kh[i], kl[i]);
+    kzs[i] = (R)kz64;
+  }
+  const int ni = fft_freq(y, ny);
+  const double qy64 = rp.qiy + two_pi * (double)ni / ((double)ny * a.dy);
+  for (int t = threadIdx.x; t < tx; t += NT) {
+    const int x = x0 + t;
+    const int mi = fft_freq(x, nx);
+    const double qx64 = rp.qix + two_pi * (double)mi / ((double)nx * a.dx);
+    const ModeEntry me = a.modes[((size_t)rp.slot * ny + y) * nx + x];
+    split_hi_lo(me.beta, cb_h[t], cb_l[t]);
+    cebl[t] = from_c64<C>(me.ebL);
+    cbdz[t] = from_c64<C>(make_double2(me.beta.x * a.dz, me.beta.y * a.dz));
+    cqx[t] = (R)qx64;
+    cqy[t] = (R)qy64;
+  }
+  // zero padding: plane 0 and planes ns+1 .. NF-1
+  for (int i = threadIdx.x; i < 3 * tx * (NF - ns); i += NT) {
+    const int cc = i / (NF - ns), zz = i % (NF - ns);
+    col[cc * P + (zz == 0 ? 0 : ns + zz)] = mk((R)0, (R)0);
+  }
+  const size_t rhs_base = (size_t)lr * 3 * ns * ny * nx;
+  for (int i = threadIdx.x; i < 3 * ns * tx; i += NT) {
+    const int t = i % tx, rest = i / tx, pl = rest % ns, cc = rest / ns;
+    col[(cc * tx + t) * P + pl + 1] = a.work[rhs_base + (((size_t)cc * ns + pl) * ny + y) * nx + x0 + t];
+  }
+  __syncthreads();
+  cta_fft<C, NF, false>(col, 3 * tx, P, 1, tw);
+  __syncthreads();
+
+  const R L = (R)(0.5 * NF * a.dz);
+  const R cinv = (R)(1.0 / (a.kb * a.kb));
+  const R scale = (R)(1.0 / ((double)NF * nx * ny));
+  for (int i = threadIdx.x; i < tx * NF; i += NT) {
+    const int t = i / NF, l = i % NF;
+    C E = cebl[t];
+    if (fft_freq(l, NF) & 1) E = cneg(E);
+    C* c0 = col + (0 * tx + t) * P + l;
+    C* c1 = col + (1 * tx + t) * P + l;
+    C* c2 = col + (2 * tx + t) * P + l;
+    C J0 = *c0, J1 = *c1, J2 = *c2;
+    green_apply(J0, J1, J2, cqx[t], cqy[t], kzs[l], kh[l], kl[l], cb_h[t], cb_l[t], E, L, cinv, scale);
+    *c0 = J0;
+    *c1 = J1;
+    *c2 = J2;
+  }
+  __syncthreads();
+  cta_fft<C, NF, true>(col, 3 * tx, P, 1, tw);
+  __syncthreads();
+
+  // normalised spectra of G*(V u) on plane 0 and plane ns+1
+  if (a.side) {
+    for (int i = threadIdx.x; i < 3 * tx; i += NT) {
+      const int cc = i / tx, t = i % tx;
+      const size_t o = (((size_t)g * 2) * 3 + cc) * ny * nx + (size_t)y * nx + x0 + t;
+      a.side[o] = col[(cc * tx + t) * P];
+      a.side[o + (size_t)3 * ny * nx] = col[(cc * tx + t) * P + ns + 1];
+    }
+  }
+  // stack reflection of the downgoing field on plane 0: R0 = T_R E0 (Eq. (9)),
+  // T_R = r_s s s^T + r_p p+ p-^T with s = z x q/|q|, p+- = (-+beta qhat, |q|)/kb.
+  for (int t = threadIdx.x; t < tx; t += NT) {
+    const int x = x0 + t;
+    const ModeEntry me = a.modes[((size_t)rp.slot * ny + y) * nx + x];
+    const int mi = fft_freq(x, nx);
+    const double qx64 = rp.qix + two_pi * (double)mi / ((double)nx * a.dx);
+    const double qn = sqrt(qx64 * qx64 + qy64 * qy64);
+    const double hx = qn > 0.0 ? qx64 / qn : rp.cphi;
+    const double hy = qn > 0.0 ? qy64 / qn : rp.sphi;
+    const double2 e0 = as_c64(col[(0 * tx + t) * P]);
+    const double2 e1 = as_c64(col[(1 * tx + t) * P]);
+    const double2 e2 = as_c64(col[(2 * tx + t) * P]);
+    const double ikb = 1.0 / a.kb;
+    // s . E0 and p- . E0 (bilinear)
+    const double2 sE = make_double2(-hy * e0.x + hx * e1.x, -hy * e0.y + hx * e1.y);
+    const double2 bq = cscale(me.beta, ikb);  // beta / kb
+    const double2 tq = cadd(cscale(e0, hx), cscale(e1, hy));
+    const double2 pmE = cadd(cmul(bq, tq), cscale(e2, qn * ikb));  // (+beta qhat . E + |q| Ez)/kb
+    const double2 as = cmul(me.rs, sE);
+    const double2 ap = cmul(me.rp, pmE);
+    // r_s s (s.E) + r_p p+ (p-.E), p+ = (-beta hx, -beta hy, |q|)/kb
+    const double2 mbq = cneg(bq);
+    const double2 Rx = cadd(cscale(as, -hy), cmul(ap, cscale(mbq, hx)));
+    const double2 Ry = cadd(cscale(as, hx), cmul(ap, cscale(mbq, hy)));
+    const double2 Rz = cscale(ap, qn * ikb);
+    R0[0 * tx + t] = from_c64<C>(Rx);
+    R0[1 * tx + t] = from_c64<C>(Ry);
+    R0[2 * tx + t] = from_c64<C>(Rz);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < tx * ns; i += NT) {
+    const int t = i % tx, pl = i / tx;
+    const C bdz = cbdz[t];
+    const C ph = cexp_r(mk(-bdz.y * (R)pl, bdz.x * (R)pl));  // exp(i beta pl dz)
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      C* e = col + (cc * tx + t) * P + pl + 1;
+      *e = cadd(*e, cmul(R0[cc * tx + t], ph));
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 3 * ns * tx; i += NT) {
+    const int t = i % tx, rest = i / tx, pl = rest % ns, cc = rest / ns;
+    a.work[rhs_base + (((size_t)cc * ns + pl) * ny + y) * nx + x0 + t] = col[(cc * tx + t) * P + pl + 1];
+  }
+}
+
+}  // namespace psfd

@@ -1,0 +1,239 @@
+// op_launch.cuh -- host dispatch of the operator kernels (included once per precision).
+#pragma once
+
+#include "op_kernels.cuh"
+#include "../../include/psfd.h"
+
+namespace psfd {
+
+// FFT lengths the kernels are instantiated for.
+#define PSFD_FOR_EACH_LENGTH(X) \
+  X(4) X(8) X(16) X(32) X(64) X(96) X(128) X(160) X(192) X(256) X(320) X(384) X(512)
+
+template <typename C> struct Tune;
+template <> struct Tune<float2> {
+  static constexpr int FUSED_MAX = 128;   // largest square plane transformed in one CTA
+  static constexpr int COL_TILE = 16;     // columns per CTA (128-byte segments)
+  static constexpr int ROW_ELEMS = 4096;  // row-pass tile size in elements
+};
+template <> struct Tune<double2> {
+  static constexpr int FUSED_MAX = 64;
+  static constexpr int COL_TILE = 8;
+  static constexpr int ROW_ELEMS = 2048;
+};
+
+template <typename C>
+inline bool use_fused(int nx, int ny) {
+  return nx == ny && nx <= Tune<C>::FUSED_MAX && (nx & (nx - 1)) == 0 && nx >= 4;
+}
+
+inline int row_block(int nx, int ny, int max_elems) {
+  int rb = 1;
+  while (rb * 2 * nx <= max_elems && ny % (rb * 2) == 0) rb *= 2;
+  return rb;
+}
+
+template <typename C>
+inline int blocks_per_rhs_t(int nx, int ny, int nslab) {
+  if (use_fused<C>(nx, ny)) return 3 * nslab;
+  return 3 * nslab * (ny / row_block(nx, ny, Tune<C>::ROW_ELEMS));
+}
+
+#define PSFD_CHECK_LAUNCH()                                \
+  do {                                                     \
+    if (cudaGetLastError() != cudaSuccess) return PSFD_E_CUDA; \
+  } while (0)
+
+template <typename K>
+inline int set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+      return PSFD_E_CUDA;
+  }
+  return PSFD_OK;
+}
+
+// ---------------------------------------------------------------------------
+template <typename C, int N, int IN>
+int launch_plane_fwd(const OpCall<C>& a) {
+  constexpr int NT = N >= 128 ? 512 : 256;
+  const size_t smem = (size_t)(N * (N + 1) + 2 * N) * sizeof(C);
+  auto k = k_plane_fwd<C, N, N, IN, NT>;
+  if (set_smem(k, smem)) return PSFD_E_CUDA;
+  k<<<dim3(a.nslab, 3, a.nrhs), NT, smem, a.stream>>>(a);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+template <typename C, int N, int EPI>
+int launch_plane_inv(const OpCall<C>& a, const C* uin) {
+  constexpr int NT = N >= 128 ? 512 : 256;
+  const size_t smem = (size_t)(N * (N + 1) + 2 * N) * sizeof(C) + 16 + NDOT * 32 * sizeof(double2);
+  auto k = k_plane_inv<C, N, N, EPI, NT>;
+  if (set_smem(k, smem)) return PSFD_E_CUDA;
+  k<<<dim3(a.nslab, 3, a.nrhs), NT, smem, a.stream>>>(a, uin);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+template <typename C, int NX, int IN>
+int launch_rows_fwd(const OpCall<C>& a) {
+  constexpr int NT = 256;
+  const int rb = row_block(NX, a.ny, Tune<C>::ROW_ELEMS);
+  const size_t smem = (size_t)(rb * NX + NX) * sizeof(C);
+  auto k = k_rows_fwd<C, NX, IN, NT>;
+  if (set_smem(k, smem)) return PSFD_E_CUDA;
+  k<<<dim3(a.nslab * (a.ny / rb), 3, a.nrhs), NT, smem, a.stream>>>(a, rb);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+template <typename C, int NX, int EPI>
+int launch_rows_inv(const OpCall<C>& a, const C* uin) {
+  constexpr int NT = 256;
+  const int rb = row_block(NX, a.ny, Tune<C>::ROW_ELEMS);
+  const size_t smem = (size_t)(rb * NX + NX) * sizeof(C) + 16 + NDOT * 32 * sizeof(double2);
+  auto k = k_rows_inv<C, NX, EPI, NT>;
+  if (set_smem(k, smem)) return PSFD_E_CUDA;
+  k<<<dim3(a.nslab * (a.ny / rb), 3, a.nrhs), NT, smem, a.stream>>>(a, uin, rb);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+template <typename C, int NY, bool INV>
+int launch_cols(const OpCall<C>& a) {
+  constexpr int NT = 256;
+  const int tx = a.nx < Tune<C>::COL_TILE ? a.nx : Tune<C>::COL_TILE;
+  const size_t smem = (size_t)(tx * (NY + 1) + NY) * sizeof(C);
+  auto k = k_cols<C, NY, INV, NT>;
+  if (set_smem(k, smem)) return PSFD_E_CUDA;
+  k<<<dim3(a.nslab * (a.nx / tx), 3, a.nrhs), NT, smem, a.stream>>>(a, tx);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+template <typename C, int NF>
+size_t zcol_smem(int tx) {
+  using R = typename RealOf<C>::T;
+  return (size_t)(3 * tx * (NF + 1) + NF) * sizeof(C) + 3 * NF * sizeof(R) + 7 * tx * sizeof(C) +
+         2 * tx * sizeof(R) + 16;
+}
+
+template <typename C, int NF>
+int launch_zcol(const OpCall<C>& a) {
+  constexpr int NT = 256;
+  const int tx = a.nx < Tune<C>::COL_TILE ? a.nx : Tune<C>::COL_TILE;
+  const size_t smem = zcol_smem<C, NF>(tx);
+  auto k = k_zcol<C, NF, NT>;
+  if (set_smem(k, smem)) return PSFD_E_CUDA;
+  k<<<dim3(a.nx / tx, a.ny, a.nrhs), NT, smem, a.stream>>>(a, tx);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+// ---------------------------------------------------------------------------
+template <typename C, int IN>
+int dispatch_fwd(const OpCall<C>& a) {
+  if (use_fused<C>(a.nx, a.ny)) {
+    switch (a.nx) {
+#define X(n) \
+  case n:    \
+    if constexpr (n <= Tune<C>::FUSED_MAX && (n & (n - 1)) == 0) return launch_plane_fwd<C, n, IN>(a); \
+    break;
+      PSFD_FOR_EACH_LENGTH(X)
+#undef X
+    }
+    return PSFD_E_ARG;
+  }
+  int rc = PSFD_E_ARG;
+  switch (a.nx) {
+#define X(n) \
+  case n:    \
+    rc = launch_rows_fwd<C, n, IN>(a); \
+    break;
+    PSFD_FOR_EACH_LENGTH(X)
+#undef X
+  }
+  if (rc) return rc;
+  rc = PSFD_E_ARG;
+  switch (a.ny) {
+#define X(n) \
+  case n:    \
+    rc = launch_cols<C, n, false>(a); \
+    break;
+    PSFD_FOR_EACH_LENGTH(X)
+#undef X
+  }
+  return rc;
+}
+
+template <typename C, int EPI>
+int dispatch_inv(const OpCall<C>& a, const C* uin) {
+  if (use_fused<C>(a.nx, a.ny)) {
+    switch (a.nx) {
+#define X(n) \
+  case n:    \
+    if constexpr (n <= Tune<C>::FUSED_MAX && (n & (n - 1)) == 0) return launch_plane_inv<C, n, EPI>(a, uin); \
+    break;
+      PSFD_FOR_EACH_LENGTH(X)
+#undef X
+    }
+    return PSFD_E_ARG;
+  }
+  int rc = PSFD_E_ARG;
+  switch (a.ny) {
+#define X(n) \
+  case n:    \
+    rc = launch_cols<C, n, true>(a); \
+    break;
+    PSFD_FOR_EACH_LENGTH(X)
+#undef X
+  }
+  if (rc) return rc;
+  rc = PSFD_E_ARG;
+  switch (a.nx) {
+#define X(n) \
+  case n:    \
+    rc = launch_rows_inv<C, n, EPI>(a, uin); \
+    break;
+    PSFD_FOR_EACH_LENGTH(X)
+#undef X
+  }
+  return rc;
+}
+
+template <typename C>
+int dispatch_z(const OpCall<C>& a) {
+  switch (a.nf) {
+#define X(n) \
+  case n:    \
+    return launch_zcol<C, n>(a);
+    PSFD_FOR_EACH_LENGTH(X)
+#undef X
+  }
+  return PSFD_E_ARG;
+}
+
+template <typename C>
+int op_apply_impl(const OpCall<C>& a) {
+  int rc;
+  switch (a.in_mode) {
+    case IN_PLAIN: rc = dispatch_fwd<C, IN_PLAIN>(a); break;
+    case IN_PUPDATE: rc = dispatch_fwd<C, IN_PUPDATE>(a); break;
+    case IN_SUPDATE: rc = dispatch_fwd<C, IN_SUPDATE>(a); break;
+    default: return PSFD_E_ARG;
+  }
+  if (rc) return rc;
+  if ((rc = dispatch_z<C>(a))) return rc;
+  if (a.epi == EPI_NONE) return blocks_per_rhs_t<C>(a.nx, a.ny, a.nslab);
+  const C* uin = a.in_mode == IN_PLAIN ? a.u : a.ustore;
+  switch (a.epi) {
+    case EPI_AU: rc = dispatch_inv<C, EPI_AU>(a, uin); break;
+    case EPI_RESID: rc = dispatch_inv<C, EPI_RESID>(a, uin); break;
+    default: return PSFD_E_ARG;
+  }
+  if (rc) return rc;
+  return blocks_per_rhs_t<C>(a.nx, a.ny, a.nslab);
+}
+
+}  // namespace psfd

@@ -1,0 +1,350 @@
+// tables.cu -- FP64 set-up and post-processing kernels: scattering potential, per-mode
+// stack reflection (Parratt recursion), right-hand side, diffraction orders, the
+// defect-correction helpers, and the FFT test hook.
+#include <vector>
+
+#include "fft.cuh"
+#include "krylov.cuh"
+#include "tables.h"
+
+namespace psfd {
+
+// ---------------------------------------------------------------------------
+// V = k0^2 (eps - eps_bg) in FP64 and FP32 (Sec. 2, Eq. (1); Sec. 3, Eq. (10))
+// ---------------------------------------------------------------------------
+__global__ void k_potential(size_t n, const double2* eps, double k02, double eps_bg, double2* V64, float2* V32) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 e = eps[i];
+    const double2 v = make_double2(k02 * (e.x - eps_bg), k02 * e.y);
+    V64[i] = v;
+    V32[i] = to_c32(v);
+  }
+}
+
+int launch_potential(size_t n, const double2* eps, double k02, double eps_bg, double2* V64, float2* V32,
+                     cudaStream_t st) {
+  k_potential<<<592, 256, 0, st>>>(n, eps, k02, eps_bg, V64, V32);
+  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Stack response per transverse mode (Sec. 2: generalized reflection coefficients /
+// transfer-matrix method; Sec. 3, Eq. (9): T_R). Media: 0 = background, 1..M layers
+// top to bottom, M+1 substrate; k_zj = sqrt(k0^2 eps_j - q^2) with Im >= 0.
+//   s: r_ij = (k_zi - k_zj) / (k_zi + k_zj)                       (E field)
+//   p: r_ij = (eps_j k_zi - eps_i k_zj) / (eps_j k_zi + eps_i k_zj) (H field)
+//   Gamma_M = r_{M,M+1},  Gamma_{j-1} = (r + Gamma_j e) / (1 + r Gamma_j e),
+//   r = r_{j-1,j}, e = exp(2 i k_zj d_j); the reflection at z_top is Gamma_0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 fresnel_d(double2 kzi, double2 kzj, double2 ei, double2 ej, int pol) {
+  if (pol == 0) return cdiv(csub(kzi, kzj), cadd(kzi, kzj));
+  const double2 a = cmul(ej, kzi), b = cmul(ei, kzj);
+  return cdiv(csub(a, b), cadd(a, b));
+}
+
+__device__ __forceinline__ double2 kz_of(double k02, double2 eps, double q2) {
+  return csqrt_upper_d(make_double2(k02 * eps.x - q2, k02 * eps.y));
+}
+
+__device__ double2 parratt_d(double k02, double q2, double2 eps_amb, const StackDev& st, int pol) {
+  const int M = st.n_layers;
+  double2 e_j = M > 0 ? st.eps[M - 1] : eps_amb;
+  double2 kz_j = kz_of(k02, e_j, q2);
+  double2 gam = fresnel_d(kz_j, kz_of(k02, st.eps_sub, q2), e_j, st.eps_sub, pol);
+  for (int j = M; j >= 1; --j) {
+    const double2 e_a = (j >= 2) ? st.eps[j - 2] : eps_amb;
+    const double2 kz_a = kz_of(k02, e_a, q2);
+    const double2 ph = cexp_d(make_double2(-2.0 * kz_j.y * st.d[j - 1], 2.0 * kz_j.x * st.d[j - 1]));
+    const double2 r = fresnel_d(kz_a, kz_j, e_a, e_j, pol);
+    const double2 ge = cmul(gam, ph);
+    gam = cdiv(cadd(r, ge), cadd(make_double2(1.0, 0.0), cmul(r, ge)));
+    kz_j = kz_a;
+    e_j = e_a;
+  }
+  return gam;
+}
+
+// grid (ceil(nx / 128), ny, n_slots)
+__global__ void k_modes(ModesArgs a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, slot = blockIdx.z;
+  if (x >= a.nx) return;
+  const double two_pi = 6.283185307179586476925286766559;
+  const double qx = a.slot_qix[slot] + two_pi * fft_freq(x, a.nx) / (a.nx * a.dx);
+  const double qy = a.slot_qiy[slot] + two_pi * fft_freq(y, a.ny) / (a.ny * a.dy);
+  const double q2 = qx * qx + qy * qy;
+  const double kb2 = a.k0 * a.k0 * a.eps_bg;
+  const double2 beta = csqrt_upper_d(make_double2(kb2 - q2, 0.0));
+  if (sqrt(cabs2(beta)) < 1e-9 * a.k0) atomicOr(a.anomaly, 1);
+  ModeEntry m;
+  m.beta = beta;
+  m.ebL = cexp_d(make_double2(-beta.y * a.L, beta.x * a.L));
+  const double k02 = a.k0 * a.k0;
+  const double2 eb = make_double2(a.eps_bg, 0.0);
+  if (a.stack.reflect) {
+    m.rs = parratt_d(k02, q2, eb, a.stack, 0);
+    m.rp = parratt_d(k02, q2, eb, a.stack, 1);
+  } else {
+    m.rs = make_double2(0.0, 0.0);
+    m.rp = make_double2(0.0, 0.0);
+  }
+  a.modes[((size_t)slot * a.ny + y) * a.nx + x] = m;
+}
+
+int launch_modes(const ModesArgs& a, int n_slots, cudaStream_t st) {
+  dim3 grid((a.nx + 127) / 128, a.ny, n_slots);
+  k_modes<<<grid, 128, 0, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+}
+
+// Bilinear triad of a mode: s = z x qhat, p+- = (-+beta qhat, |q|)/kb.
+struct Triad {
+  double sx, sy;
+  double2 pp[3], pm[3];
+};
+__device__ __forceinline__ Triad triad_d(double qx, double qy, double2 beta, double kb, double cphi, double sphi) {
+  const double qn = sqrt(qx * qx + qy * qy);
+  const double hx = qn > 0.0 ? qx / qn : cphi;
+  const double hy = qn > 0.0 ? qy / qn : sphi;
+  Triad t;
+  t.sx = -hy;
+  t.sy = hx;
+  const double2 bq = cscale(beta, 1.0 / kb);
+  t.pp[0] = cscale(bq, -hx);
+  t.pp[1] = cscale(bq, -hy);
+  t.pp[2] = make_double2(qn / kb, 0.0);
+  t.pm[0] = cscale(bq, hx);
+  t.pm[1] = cscale(bq, hy);
+  t.pm[2] = t.pp[2];
+  return t;
+}
+
+// T_R v = r_s s (s.v) + r_p p+ (p-.v)
+__device__ __forceinline__ void apply_TR(const Triad& t, double2 rs, double2 rp, const double2 v[3], double2 out[3]) {
+  const double2 sv = cadd(cscale(v[0], t.sx), cscale(v[1], t.sy));
+  const double2 pv = cadd(cadd(cmul(t.pm[0], v[0]), cmul(t.pm[1], v[1])), cmul(t.pm[2], v[2]));
+  const double2 as = cmul(rs, sv), ap = cmul(rp, pv);
+  out[0] = cadd(cscale(as, t.sx), cmul(ap, t.pp[0]));
+  out[1] = cadd(cscale(as, t.sy), cmul(ap, t.pp[1]));
+  out[2] = cmul(ap, t.pp[2]);
+}
+
+// One thread per illumination: incident vector e (s or p-) and its reflection T_R e.
+__global__ void k_rhs_params(int rhs0, int nrhs, RhsParam* rp, const ModeEntry* modes, int nx, int ny, double kb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrhs) return;
+  RhsParam p = rp[rhs0 + i];
+  const ModeEntry m = modes[(size_t)p.slot * ny * nx];  // mode (0, 0)
+  const Triad t = triad_d(p.qix, p.qiy, m.beta, kb, p.cphi, p.sphi);
+  if (p.pol == 0) {
+    p.e_inc[0] = make_double2(t.sx, 0.0);
+    p.e_inc[1] = make_double2(t.sy, 0.0);
+    p.e_inc[2] = make_double2(0.0, 0.0);
+  } else {
+    for (int c = 0; c < 3; ++c) p.e_inc[c] = t.pm[c];
+  }
+  apply_TR(t, m.rs, m.rp, p.e_inc, p.r_inc);
+  p.beta00 = m.beta;
+  rp[rhs0 + i] = p;
+}
+
+// b = E_inc + R[E_inc] on the absorber planes (Eqs. (3), (9)): uniform in (x, y),
+// e exp(-i beta00 z_p) + T_R e exp(+i beta00 z_p), z_p = (p + 1/2) dz.
+__global__ void k_build_rhs(int rhs0, int nrhs, const RhsParam* rp, int nslab, int plane, double dz, double2* b) {
+  const size_t per = (size_t)3 * nslab * plane;
+  const size_t total = per * nrhs;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int lr = (int)(i / per);
+    const size_t k = i % per;
+    const int cp = (int)(k / plane);
+    const int c = cp / nslab, p = cp % nslab;
+    const RhsParam& q = rp[rhs0 + lr];
+    const double z = (p + 0.5) * dz;
+    const double2 bz = cscale(q.beta00, z);
+    const double2 down = cexp_d(make_double2(bz.y, -bz.x));  // exp(-i beta00 z)
+    const double2 up = cexp_d(make_double2(-bz.y, bz.x));    // exp(+i beta00 z)
+    b[i] = cadd(cmul(q.e_inc[c], down), cmul(q.r_inc[c], up));
+  }
+}
+
+int launch_rhs(int rhs0, int nrhs, RhsParam* rp, const ModeEntry* modes, int nx, int ny, int nslab, double dz,
+               double kb, double2* b, cudaStream_t st) {
+  k_rhs_params<<<(nrhs + 63) / 64, 64, 0, st>>>(rhs0, nrhs, rp, modes, nx, ny, kb);
+  if (cudaGetLastError() != cudaSuccess) return PSFD_E_CUDA;
+  k_build_rhs<<<1184, 256, 0, st>>>(rhs0, nrhs, rp, nslab, nx * ny, dz, b);
+  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Diffraction orders (Eqs. (3), (9)): amplitude at z_top of every propagating order,
+//   A = T_R (delta_{mn,00} e + E0 exp(-i beta dz/2)) + Etop exp(-i beta (nslab + 1/2) dz),
+// E0 / Etop being the normalised spectra of G*(V u) on plane 0 (z = -dz/2) and plane
+// nslab+1. Output per order: A (3 complex), a_s, a_p (s . A, p+ . A), efficiency.
+// ---------------------------------------------------------------------------
+__global__ void k_orders(OrdersArgs a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, g = blockIdx.y;
+  if (k >= a.n_orders[g]) return;
+  const int mi = a.mn[((size_t)g * a.max_orders + k) * 2], ni = a.mn[((size_t)g * a.max_orders + k) * 2 + 1];
+  const int x = (mi + a.nx) % a.nx, y = (ni + a.ny) % a.ny;
+  const RhsParam p = a.rhsp[g];
+  const ModeEntry m = a.modes[((size_t)p.slot * a.ny + y) * a.nx + x];
+  const double two_pi = 6.283185307179586476925286766559;
+  const double qx = p.qix + two_pi * mi / (a.nx * a.dx);
+  const double qy = p.qiy + two_pi * ni / (a.ny * a.dy);
+  const Triad t = triad_d(qx, qy, m.beta, a.kb, p.cphi, p.sphi);
+  const size_t plane = (size_t)a.ny * a.nx;
+  const size_t o0 = ((size_t)g * 2 * 3) * plane + (size_t)y * a.nx + x;
+  const double2 bh = cscale(m.beta, 0.5 * a.dz);
+  const double2 ph0 = cexp_d(make_double2(bh.y, -bh.x));  // exp(-i beta dz/2)
+  const double2 bt = cscale(m.beta, (a.nslab + 0.5) * a.dz);
+  const double2 pht = cexp_d(make_double2(bt.y, -bt.x));
+  double2 down[3], A[3];
+  for (int c = 0; c < 3; ++c) {
+    down[c] = cmul(a.side[o0 + c * plane], ph0);
+    if (mi == 0 && ni == 0) down[c] = cadd(down[c], p.e_inc[c]);
+  }
+  apply_TR(t, m.rs, m.rp, down, A);
+  for (int c = 0; c < 3; ++c) A[c] = cadd(A[c], cmul(a.side[o0 + (3 + c) * plane], pht));
+  double* out = a.out + ((size_t)g * a.max_orders + k) * 12;
+  for (int c = 0; c < 3; ++c) {
+    out[2 * c] = A[c].x;
+    out[2 * c + 1] = A[c].y;
+  }
+  const double2 as = cadd(cscale(A[0], t.sx), cscale(A[1], t.sy));
+  const double2 ap = cadd(cadd(cmul(t.pp[0], A[0]), cmul(t.pp[1], A[1])), cmul(t.pp[2], A[2]));
+  out[6] = as.x;
+  out[7] = as.y;
+  out[8] = ap.x;
+  out[9] = ap.y;
+  out[10] = (cabs2(A[0]) + cabs2(A[1]) + cabs2(A[2])) * m.beta.x / p.beta00.x;
+  out[11] = 0.0;
+}
+
+int launch_orders(const OrdersArgs& a, int nrhs, cudaStream_t st) {
+  dim3 grid((a.max_orders + 127) / 128, nrhs);
+  k_orders<<<grid, 128, 0, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// defect correction helpers (FP64 outer loop around the FP32 Krylov solve)
+// ---------------------------------------------------------------------------
+// partial ||v||^2 per block into slot 2
+__global__ void __launch_bounds__(VEC_NT) k_norm2_partials(int n, int nblk, int rhs0, const double2* v,
+                                                            double2* partials, int maxblk) {
+  const int blk = blockIdx.x, lr = blockIdx.y, g = rhs0 + lr;
+  const size_t off = (size_t)lr * n;
+  const int chunk = (n + nblk - 1) / nblk;
+  const int lo = blk * chunk, hi = min(n, lo + chunk);
+  double2 d2 = make_double2(0.0, 0.0);
+  for (int i = lo + threadIdx.x; i < hi; i += VEC_NT) d2.x += cabs2(v[off + i]);
+  vec_block_dots<double2>(make_double2(0.0, 0.0), d2, DOT_OUT_OUT, partials + ((size_t)g * NDOT) * maxblk + blk,
+                          maxblk);
+}
+
+// mode 0: bnorm2 = rnorm2 = sum (initial residual = b); mode 1: rnorm2 = sum.
+// act = rnorm2 > tol2 * bnorm2.
+__global__ void __launch_bounds__(VEC_NT) k_norm_finish(int rhs0, int nblk, const double2* partials, int maxblk,
+                                                         int mode, double tol2, KScal* sc, int* act) {
+  __shared__ double2 sh[33];
+  const int g = rhs0 + blockIdx.x;
+  const double2 s = block_sum_fixed(slot_ptr(partials, g, 2, maxblk), nblk, sh);
+  if (threadIdx.x == 0) {
+    if (mode == 0) sc[g].bnorm2 = s.x;
+    sc[g].rnorm2 = s.x;
+    act[g] = (s.x > tol2 * sc[g].bnorm2) && isfinite(s.x);
+  }
+}
+
+int launch_norm(int n, int nblk, int rhs0, int nrhs, const double2* v, double2* partials, int maxblk, int mode,
+                double tol2, KScal* sc, int* act, cudaStream_t st) {
+  if (v) {
+    k_norm2_partials<<<dim3(nblk, nrhs), VEC_NT, 0, st>>>(n, nblk, rhs0, v, partials, maxblk);
+    if (cudaGetLastError() != cudaSuccess) return PSFD_E_CUDA;
+  }
+  k_norm_finish<<<nrhs, VEC_NT, 0, st>>>(rhs0, nblk, partials, maxblk, mode, tol2, sc, act);
+  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+}
+
+// r32 = r64 / ||r64||  (only right-hand sides still active)
+__global__ void k_ref_scale(int n, int rhs0, const int* act, const KScal* sc, const double2* r64, float2* r32) {
+  const int lr = blockIdx.y, g = rhs0 + lr;
+  if (!act[g]) return;
+  const double inv = 1.0 / sqrt(sc[g].rnorm2);
+  const size_t off = (size_t)lr * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    r32[off + i] = to_c32(cscale(r64[off + i], inv));
+}
+
+// x64 += ||r64|| x32
+__global__ void k_ref_update(int n, int rhs0, const int* act, const KScal* sc, double2* x64, const float2* x32) {
+  const int lr = blockIdx.y, g = rhs0 + lr;
+  if (!act[g]) return;
+  const double s = sqrt(sc[g].rnorm2);
+  const size_t off = (size_t)lr * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x64[off + i] = cadd(x64[off + i], cscale(to_c64(x32[off + i]), s));
+}
+
+int launch_ref_scale(int n, int rhs0, int nrhs, const int* act, const KScal* sc, const double2* r64, float2* r32,
+                     cudaStream_t st) {
+  const int bx = (n + 256 * 8 - 1) / (256 * 8);
+  k_ref_scale<<<dim3(bx, nrhs), 256, 0, st>>>(n, rhs0, act, sc, r64, r32);
+  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+}
+
+int launch_ref_update(int n, int rhs0, int nrhs, const int* act, const KScal* sc, double2* x64, const float2* x32,
+                      cudaStream_t st) {
+  const int bx = (n + 256 * 8 - 1) / (256 * 8);
+  k_ref_update<<<dim3(bx, nrhs), 256, 0, st>>>(n, rhs0, act, sc, x64, x32);
+  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// FFT test hook: `count` contiguous length-N transforms, B per CTA.
+// ---------------------------------------------------------------------------
+template <typename C, int N, bool INV>
+__global__ void __launch_bounds__(256) k_test_fft(C* data, int count, const double2* tw64) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int B = N >= 2048 ? 1 : 2048 / N;
+  C* tile = reinterpret_cast<C*>(smem);
+  C* tw = tile + B * N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = from_c64<C>(tw64[i]);
+  const int f0 = blockIdx.x * B;
+  const int nb = min(B, count - f0);
+  for (int i = threadIdx.x; i < nb * N; i += blockDim.x) tile[i] = data[(size_t)f0 * N + i];
+  __syncthreads();
+  cta_fft<C, N, INV>(tile, nb, N, 1, tw);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nb * N; i += blockDim.x) data[(size_t)f0 * N + i] = tile[i];
+}
+
+template <typename C, int N>
+int run_test_fft(C* data, int count, bool inv, const double2* tw) {
+  constexpr int B = N >= 2048 ? 1 : 2048 / N;
+  const size_t smem = (size_t)(B * N + N) * sizeof(C);
+  const int grid = (count + B - 1) / B;
+  if (inv) {
+    auto k = k_test_fft<C, N, true>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, 256, smem>>>(data, count, tw);
+  } else {
+    auto k = k_test_fft<C, N, false>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, 256, smem>>>(data, count, tw);
+  }
+  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+}
+
+int launch_test_fft(int n, int count, bool inv, bool fp64, void* data, const double2* tw) {
+  switch (n) {
+#define X(v)                                                                              \
+  case v:                                                                                 \
+    return fp64 ? run_test_fft<double2, v>((double2*)data, count, inv, tw)                \
+                : run_test_fft<float2, v>((float2*)data, count, inv, tw);
+    X(4) X(8) X(16) X(32) X(64) X(96) X(128) X(160) X(192) X(256) X(320) X(384) X(512)
+#undef X
+  }
+  return PSFD_E_ARG;
+}
+
+}  // namespace psfd

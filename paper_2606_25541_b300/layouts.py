@@ -76,9 +76,8 @@ class Problem:
 # ---------------------------------------------------------------------------
 # z padding
 # ---------------------------------------------------------------------------
-SUPPORTED_LENGTHS = tuple(
-    sorted({b * (1 << a) for b in (1, 3, 5) for a in range(0, 11) if 2 <= b * (1 << a) <= 1024})
-)
+# FFT lengths the CUDA kernels are instantiated for (psfd_supported_length).
+SUPPORTED_LENGTHS = (4, 8, 16, 32, 64, 96, 128, 160, 192, 256, 320, 384, 512)
 
 
 def padded_nf(nslab: int, nz_min: int = 0) -> int:

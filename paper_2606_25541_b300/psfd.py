@@ -1,0 +1,274 @@
+"""ctypes binding of ``libpsfd.so`` (C ABI in ``include/psfd.h``).
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels. Host arrays are numpy complex128/float64/int32; device arrays are torch
+CUDA tensors, passed by pointer. Loading fails loudly if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpsfd.so")
+
+OK = 0
+E_ARG, E_NOMEM, E_BUDGET, E_CUDA, E_NOT_CONVERGED, E_BREAKDOWN, E_ANOMALY, E_TIMEOUT, E_STATE = \
+    -1, -2, -3, -4, -5, -6, -7, -8, -9
+FP64, FP32_REFINED = 0, 1
+HOST, DEVICE = 0, 1
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nslab", ctypes.c_int), ("nf", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("wavelength", ctypes.c_double), ("eps_bg", ctypes.c_double)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_outer", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer", ctypes.c_int), ("relres", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("status", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+
+
+class PsfdError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"psfd status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+
+_SIGS = {
+    "psfd_strerror": (ctypes.c_char_p, [_I]),
+    "psfd_last_error": (ctypes.c_char_p, [_P]),
+    "psfd_supported_length": (_I, [_I]),
+    "psfd_workspace_bytes": (_I, [ctypes.POINTER(Grid), _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
+    "psfd_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(Grid), _I, _I, ctypes.c_size_t, _P]),
+    "psfd_destroy": (_I, [_P]),
+    "psfd_set_stream": (_I, [_P, _P]),
+    "psfd_set_stack": (_I, [_P, _I, _D, _D, _D]),
+    "psfd_set_potential": (_I, [_P, _P, _I]),
+    "psfd_set_illumination": (_I, [_P, _I, _D, _D, _IP]),
+    "psfd_solve": (_I, [_P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Report)]),
+    "psfd_num_orders": (_I, [_P, _I, _IP]),
+    "psfd_diffraction_orders": (_I, [_P, _I, _I, _IP, _IP, _D, _D, _D]),
+    "psfd_apply": (_I, [_P, _I, _I, _I, _P, _P]),
+    "psfd_get_solution": (_I, [_P, _I, _P, _I]),
+    "psfd_get_rhs": (_I, [_P, _I, _P, _I]),
+    "psfd_get_mode_tables": (_I, [_P, _I, _D, _D, _D]),
+    "psfd_test_fft": (_I, [_I, _I, _I, _I, _P]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once). Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2606_25541_b300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(status: int) -> str:
+    return load().psfd_strerror(status).decode()
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _c128(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def supported_length(n: int) -> bool:
+    return bool(load().psfd_supported_length(int(n)))
+
+
+def make_grid(nx, ny, nslab, nf, dx, dy, dz, wavelength, eps_bg=1.0) -> Grid:
+    return Grid(int(nx), int(ny), int(nslab), int(nf), float(dx), float(dy), float(dz), float(wavelength),
+                float(eps_bg))
+
+
+def workspace_bytes(grid: Grid, precision: int, max_rhs: int) -> int:
+    out = ctypes.c_size_t(0)
+    st = load().psfd_workspace_bytes(ctypes.byref(grid), int(precision), int(max_rhs), ctypes.byref(out))
+    if st != OK:
+        raise PsfdError(st, strerror(st))
+    return int(out.value)
+
+
+class Solver:
+    """One solver context (device state for one clip and up to max_rhs illuminations)."""
+
+    def __init__(self, grid: Grid, precision: int = FP32_REFINED, max_rhs: int = 1, hbm_budget: int = 0,
+                 stream=None):
+        self.lib = load()
+        self.grid = grid
+        self.precision = precision
+        self.max_rhs = max_rhs
+        self.ctx = ctypes.c_void_p()
+        st = self.lib.psfd_create(ctypes.byref(self.ctx), ctypes.byref(grid), int(precision), int(max_rhs),
+                                  ctypes.c_size_t(int(hbm_budget)), _stream_ptr(stream))
+        if st != OK:
+            raise PsfdError(st, strerror(st))
+        self.n_rhs = 0
+
+    @classmethod
+    def from_problem(cls, prob, precision=FP32_REFINED, max_rhs=None, hbm_budget=0, stream=None,
+                     set_inputs=True):
+        g = make_grid(prob.nx, prob.ny, prob.nslab, prob.nf, prob.dx, prob.dy, prob.dz, prob.wavelength,
+                      prob.eps_bg)
+        s = cls(g, precision, max_rhs or prob.n_rhs, hbm_budget, stream)
+        if set_inputs:
+            s.set_stack(prob.n_layers, prob.d_layers, prob.n_sub)
+            s.set_potential(prob.eps)
+            s.set_illumination(prob.theta_deg, prob.phi_deg, prob.pol)
+        return s
+
+    def _check(self, st):
+        if st != OK:
+            msg = self.lib.psfd_last_error(self.ctx).decode()
+            raise PsfdError(st, f"{strerror(st)}: {msg}")
+        return st
+
+    def close(self):
+        if self.ctx:
+            self.lib.psfd_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._check(self.lib.psfd_set_stream(self.ctx, _stream_ptr(stream)))
+
+    def set_stack(self, n_layers, thickness, n_sub):
+        n = _c128(n_layers).reshape(-1)
+        d = np.ascontiguousarray(thickness, dtype=np.float64).reshape(-1)
+        ns = np.array([complex(n_sub).real, complex(n_sub).imag], dtype=np.float64)
+        nn = n.view(np.float64) if n.size else np.zeros(2, np.float64)
+        self._check(self.lib.psfd_set_stack(self.ctx, int(n.size), _dptr(nn),
+                                            _dptr(d if d.size else np.zeros(1)), _dptr(ns)))
+
+    def set_potential(self, eps):
+        """eps: complex128 array (nslab, ny, nx) on the host, or a complex128 CUDA tensor."""
+        if hasattr(eps, "data_ptr"):
+            self._keep_eps = eps
+            self._check(self.lib.psfd_set_potential(self.ctx, ctypes.c_void_p(eps.data_ptr()), DEVICE))
+        else:
+            e = _c128(eps)
+            self._keep_eps = e
+            self._check(self.lib.psfd_set_potential(self.ctx, e.ctypes.data_as(ctypes.c_void_p), HOST))
+
+    def set_illumination(self, theta_deg, phi_deg, pol):
+        th = np.ascontiguousarray(theta_deg, dtype=np.float64).reshape(-1)
+        ph = np.ascontiguousarray(phi_deg, dtype=np.float64).reshape(-1)
+        po = np.ascontiguousarray(pol, dtype=np.int32).reshape(-1)
+        self._check(self.lib.psfd_set_illumination(self.ctx, int(th.size), _dptr(th), _dptr(ph),
+                                                   po.ctypes.data_as(_IP)))
+        self.n_rhs = int(th.size)
+
+    def solve(self, tol=1e-10, max_iter=500, max_outer=12, inner_tol=1e-4, check_every=4, raise_on_error=True):
+        o = SolveOpts(float(tol), int(max_iter), int(max_outer), float(inner_tol), int(check_every))
+        r = Report()
+        st = self.lib.psfd_solve(self.ctx, ctypes.byref(o), ctypes.byref(r))
+        rep = {"iterations": r.iterations, "outer": r.outer, "relres": r.relres, "seconds": r.seconds,
+               "status": st}
+        if raise_on_error and st != OK:
+            self._check(st)
+        return rep
+
+    def num_orders(self, rhs: int) -> int:
+        n = ctypes.c_int(0)
+        self._check(self.lib.psfd_num_orders(self.ctx, int(rhs), ctypes.byref(n)))
+        return n.value
+
+    def diffraction_orders(self, rhs: int = 0):
+        cap = self.num_orders(rhs)
+        n = ctypes.c_int(0)
+        mn = np.zeros(2 * max(cap, 1), np.int32)
+        amp = np.zeros(6 * max(cap, 1), np.float64)
+        sp = np.zeros(4 * max(cap, 1), np.float64)
+        eff = np.zeros(max(cap, 1), np.float64)
+        self._check(self.lib.psfd_diffraction_orders(self.ctx, int(rhs), cap, ctypes.byref(n), mn.ctypes.data_as(_IP),
+                                                     _dptr(amp), _dptr(sp), _dptr(eff)))
+        k = n.value
+        a = amp[:6 * k].view(np.complex128).reshape(k, 3)
+        s = sp[:4 * k].view(np.complex128).reshape(k, 2)
+        return {"m": mn[0:2 * k:2].copy(), "n": mn[1:2 * k:2].copy(), "amp": a.copy(), "a_s": s[:, 0].copy(),
+                "a_p": s[:, 1].copy(), "eff": eff[:k].copy()}
+
+    def apply(self, u, out, rhs0: int = 0, precision: int | None = None):
+        """out = A u on device tensors (complex128 for FP64, complex64 for FP32)."""
+        import torch
+        if precision is None:
+            precision = FP64 if u.dtype == torch.complex128 else FP32_REFINED
+        nrhs = u.shape[0]
+        self._check(self.lib.psfd_apply(self.ctx, int(precision), int(rhs0), int(nrhs),
+                                        ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def _field_shape(self):
+        g = self.grid
+        return (3, g.nslab, g.ny, g.nx)
+
+    def get_solution(self, rhs: int = 0) -> np.ndarray:
+        out = np.zeros(self._field_shape(), np.complex128)
+        self._check(self.lib.psfd_get_solution(self.ctx, int(rhs), out.ctypes.data_as(ctypes.c_void_p), HOST))
+        return out
+
+    def get_rhs(self, rhs: int = 0) -> np.ndarray:
+        out = np.zeros(self._field_shape(), np.complex128)
+        self._check(self.lib.psfd_get_rhs(self.ctx, int(rhs), out.ctypes.data_as(ctypes.c_void_p), HOST))
+        return out
+
+    def mode_tables(self, rhs: int = 0):
+        g = self.grid
+        beta = np.zeros((g.ny, g.nx), np.complex128)
+        rs = np.zeros_like(beta)
+        rp = np.zeros_like(beta)
+        self._check(self.lib.psfd_get_mode_tables(self.ctx, int(rhs), _dptr(beta.view(np.float64)),
+                                                  _dptr(rs.view(np.float64)), _dptr(rp.view(np.float64))))
+        return beta, rs, rp
+
+
+def fft_inplace(data, inverse: bool = False):
+    """In-place FFT of the rows of a (count, n) complex CUDA tensor with the library's kernels."""
+    import torch
+    fp64 = data.dtype == torch.complex128
+    st = load().psfd_test_fft(int(data.shape[-1]), int(data.numel() // data.shape[-1]), int(inverse), int(fp64),
+                              ctypes.c_void_p(data.data_ptr()))
+    if st != OK:
+        raise PsfdError(st, strerror(st))
+    return data
