@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark: solves/s of the LS-PSFD solver on the 128 x 128 x 60 line/space clip.
+
+One step solves one batch: the 128 x 128 nm line/space clip at 1 nm (60 absorber
+planes, nf = 128, Ru/40 x (Mo/Si) stack) under 18 illuminations (polar 0/4/8 deg x
+azimuth 0/45/90 deg x s/p). A step runs the whole hot path on the GPU: potential,
+per-mode stack tables and right-hand sides, the FP32 BiCGStab solves inside FP64
+defect correction (every operator application, Krylov update and FP64 residual), and
+the diffraction orders. A "solve" is one illumination solved to the FP64 relative
+residual --tol (1e-8 by default, which keeps the reflected orders within 1e-6 of the
+FP64 reference; the line reports the measured difference).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank solves its own seeded clip (independent replicas, weak
+scaling); timing is bracketed by a barrier and device synchronisation, and the
+maximum over ranks is reported. Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2606_25541_b300 import layouts  # noqa: E402
+
+METRIC = "solves/s at 1e-6 order error, FP32+refine vs FP64; p50/p99 latency; HBM %"
+UNIT = "solves/s"
+WORKLOAD = "line_space_128x128x60_nf128_18rhs"
+FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 vector rate, nominal
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
+    ap.add_argument("--profile-only", action="store_true", help="one profiled step, for ncu launch lists")
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Maximum of a float over all ranks (identity when world == 1)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (the baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_solve_seconds(prob, i: int, rtol: float) -> float:
+    """Wall time of one oracle solve of illumination i: set-up, GMRES, orders."""
+    import contextlib
+
+    import oracle
+    try:  # numpy's FFT and einsum are single threaded; pin BLAS (GMRES least squares) too
+        from threadpoolctl import threadpool_limits
+        limit = threadpool_limits(1)
+    except ImportError:
+        limit = contextlib.nullcontext()
+    with limit:
+        t0 = time.perf_counter()
+        oracle.solve(prob, i, rtol=rtol, maxiter=400)
+        return time.perf_counter() - t0
+
+
+def cpu_baseline(prob, rtol: float):
+    t = oracle_solve_seconds(prob, 5, rtol)
+    return {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one of the 18 illuminations (theta {prob.theta_deg[5]:g}, phi {prob.phi_deg[5]:g}, "
+                      f"pol {int(prob.pol[5])}) solved by the FP64 oracle (numpy FFT + GMRES to relative "
+                      f"residual {rtol:g}, orders included), single thread: {t:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    prob = layouts.line_space_clip(seed=2)
+    rtol = args.tol * 10.0
+    for w in range(args.warmup):
+        oracle_solve_seconds(prob, w % prob.n_rhs, rtol)
+    times = [oracle_solve_seconds(prob, (args.warmup + k) % prob.n_rhs, rtol) for k in range(args.steps)]
+    total = sum(times)
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference_step": "one illumination per step, oracle GMRES"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} single-illumination oracle solves (GMRES to {rtol:g}), "
+                                   f"one thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def orders_all(solver, n_rhs):
+    return [solver.diffraction_orders(i) for i in range(n_rhs)]
+
+
+def orders_rel_err(a, b):
+    num = sum(float(np.sum(np.abs(x["amp"] - y["amp"]) ** 2)) for x, y in zip(a, b))
+    den = sum(float(np.sum(np.abs(y["amp"]) ** 2)) for y in b)
+    return math.sqrt(num / den)
+
+
+def run_ours(args):
+    import torch
+    from paper_2606_25541_b300 import psfd
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    prob = layouts.line_space_clip(seed=2 + rank)
+    n_rhs = prob.n_rhs
+    solve_kw = dict(tol=args.tol, inner_tol=args.inner_tol, max_iter=400, max_outer=12, check_every=4)
+
+    solver = psfd.Solver.from_problem(prob, psfd.FP32_REFINED, stream=stream)
+    eps_dev = torch.from_numpy(prob.eps).to(dev)
+    th, ph, po = prob.theta_deg, prob.phi_deg, prob.pol
+
+    def step(s):
+        s.set_potential(eps_dev)
+        s.set_illumination(th, ph, po)
+        return s.solve(**solve_kw)
+
+    if args.profile_only:
+        step(solver)
+        torch.cuda.synchronize()
+        return 0
+
+    for _ in range(args.warmup):
+        rep = step(solver)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs ----
+    clocks = ClockSampler(torch.cuda.current_device())
+    if rank == 0:
+        clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    n0 = psfd.launch_count()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    reps = []
+    for k in range(args.steps):
+        reps.append(step(solver))
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = psfd.launch_count() - n0
+    clk = clocks.stop() if rank == 0 else None
+    per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    t_ms = reduce_max(ev[0].elapsed_time(ev[-1]), world, dev)
+    value = n_rhs * args.steps * world / (t_ms * 1e-3)
+
+    # ---- per-kernel timing of the same steps (CUDA events on the solver's stream) ----
+    psfd.profile_enable(True)
+    for _ in range(args.steps):
+        step(solver)
+    torch.cuda.synchronize()
+    psfd.profile_enable(False)
+    prof = psfd.profile_read()
+    total_prof_ms = sum(v["ms"] for v in prof.values())
+
+    # ---- end to end through the C ABI with host buffers ----
+    eps_host = torch.from_numpy(prob.eps).pin_memory()
+    e2e_solver = solver
+    d2h = 0
+
+    def e2e_step():
+        nonlocal d2h
+        e2e_solver.set_potential(eps_host)
+        e2e_solver.set_illumination(th, ph, po)
+        e2e_solver.solve(**solve_kw)
+        out = orders_all(e2e_solver, n_rhs)
+        d2h = sum(o["m"].nbytes + o["n"].nbytes + o["amp"].nbytes + o["a_s"].nbytes + o["a_p"].nbytes
+                  + o["eff"].nbytes for o in out)
+        return out
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orders32 = e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
+    h2d = prob.eps.nbytes + th.nbytes + ph.nbytes + po.nbytes
+
+    # ---- plain FP64 path on the same batch, and the order difference ----
+    fp64 = None
+    if not args.no_fp64:
+        s64 = psfd.Solver.from_problem(prob, psfd.FP64, stream=stream)
+        step(s64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep64 = step(s64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = reduce_max(e0.elapsed_time(e1), world, dev)
+        orders64 = orders_all(s64, n_rhs)
+        fp64 = {"value": n_rhs * world / (t64 * 1e-3), "unit": UNIT, "ms_per_step": t64,
+                "iterations": rep64["iterations"], "relres": rep64["relres"],
+                "order_rel_err_fp32_refined_vs_fp64": orders_rel_err(orders32, orders64)}
+        s64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(prob, rtol=args.tol * 10.0)
+
+    if rank != 0:
+        return 0
+
+    hbm_peak, peak_kind = measured_peaks()
+    kernels = {}
+    for name, v in prof.items():
+        if v["launches"] == 0:
+            continue
+        kernels[name] = {"launches": v["launches"], "ms": round(v["ms"], 4),
+                         "share_of_profiled": round(v["ms"] / total_prof_ms, 4),
+                         "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1),
+                         "GFLOPs": round(v["flops"] / (v["ms"] * 1e-3) / 1e9, 1)}
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    if dom.endswith("fp64"):
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                    "peak_kind": "nominal FP64 (148 SMs x 2 FP64 FMA/clk x 2.03 GHz class)"}
+    else:
+        achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind}
+    lat = sorted(per_step)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [prob.nx, prob.ny, prob.nslab, prob.nf], "dx_nm": prob.dx,
+                   "n_rhs": n_rhs, "precision": "FP32 BiCGStab inside FP64 defect correction",
+                   "tol": args.tol, "inner_tol": args.inner_tol, "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2: {solver_bytes(prob) / 1e9:.1f} GB working set per step"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "what": "per-step (18-illumination batch) device time"},
+        "iterations": reps[-1]["iterations"], "outer": reps[-1]["outer"], "relres": reps[-1]["relres"],
+        "roofline": roofline, "kernels": kernels,
+        "cpu_baseline": cpu,
+        "e2e": {"value": n_rhs * args.steps * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "fp64_plain": fp64,
+    }
+    print(json.dumps(line), flush=True)
+    solver.close()
+    return 0
+
+
+def solver_bytes(prob) -> float:
+    from paper_2606_25541_b300 import psfd
+    g = psfd.make_grid(prob.nx, prob.ny, prob.nslab, prob.nf, prob.dx, prob.dy, prob.dz, prob.wavelength,
+                       prob.eps_bg)
+    return float(psfd.workspace_bytes(g, psfd.FP32_REFINED, prob.n_rhs))
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -169,6 +169,21 @@ int psfd_get_rhs(psfd_ctx* ctx, int rhs, double* dst, int where);
  * beta (z wavenumber, Im >= 0) and the stack reflection coefficients r_s, r_p. */
 int psfd_get_mode_tables(psfd_ctx* ctx, int rhs, double* beta, double* r_s, double* r_p);
 
+/* Number of CUDA kernels the library has launched since it was loaded (all contexts). */
+int psfd_launch_count(unsigned long long* count);
+
+/* Per-pass timing for measurement: psfd_profile_enable(1) clears earlier records and
+ * brackets each operator pass (K1, K2, K3 in FP32 and FP64) and each BiCGStab vector
+ * update with CUDA events on the stream it runs on; psfd_profile_enable(0) stops.
+ * psfd_profile_get folds the finished records (synchronising on their events) into
+ * per-class totals: class name (static storage), launches, summed event time in ms,
+ * and the algorithmic bytes and flops of those launches (every vector read or written
+ * once; 5 N log2 N flops per complex FFT of length N). cls in [0, psfd_profile_classes()). */
+int psfd_profile_enable(int on);
+int psfd_profile_classes(void);
+int psfd_profile_get(int cls, const char** name, unsigned long long* launches, double* ms, double* bytes,
+                     double* flops);
+
 /* Test hook for the device FFT: `count` contiguous transforms of length n, in place, on
  * device data (complex double if fp64 else complex float). inverse = 1 applies the
  * unnormalised inverse. Runs on the legacy default stream and synchronises. */

@@ -85,6 +85,15 @@ int op_blocks_per_rhs(int nx, int ny, int nslab, bool fp64);
 // Whether the kernels are built for an FFT length.
 bool fft_length_supported(int n);
 
+// Kernel-launch accounting and optional per-class CUDA-event timing (psfd.cu).
+enum ProfClass {
+  PK_FWD32 = 0, PK_Z32, PK_INV32, PK_FWD64, PK_Z64, PK_INV64, PK_VEC32, PK_VEC64, PK_SCALAR, PK_SETUP, PK_N
+};
+void count_launch(int n = 1);
+bool prof_on();
+void prof_begin(int cls, cudaStream_t st);
+void prof_end(int cls, cudaStream_t st, double bytes, double flops);
+
 }  // namespace psfd
 
 namespace psfd {

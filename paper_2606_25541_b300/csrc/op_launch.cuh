@@ -1,6 +1,8 @@
 // op_launch.cuh -- host dispatch of the operator kernels (included once per precision).
 #pragma once
 
+#include <cmath>
+
 #include "op_kernels.cuh"
 #include "../../include/psfd.h"
 
@@ -39,8 +41,9 @@ inline int blocks_per_rhs_t(int nx, int ny, int nslab) {
   return 3 * nslab * (ny / row_block(nx, ny, Tune<C>::ROW_ELEMS));
 }
 
-#define PSFD_CHECK_LAUNCH()                                \
-  do {                                                     \
+#define PSFD_CHECK_LAUNCH()                                    \
+  do {                                                         \
+    count_launch();                                            \
     if (cudaGetLastError() != cudaSuccess) return PSFD_E_CUDA; \
   } while (0)
 
@@ -214,9 +217,40 @@ int dispatch_z(const OpCall<C>& a) {
   return PSFD_E_ARG;
 }
 
+// Algorithmic traffic and flops of the three passes, for the optional profiler: every
+// vector read or written once, V once per launch; 5 N log2 N flops per complex FFT.
+struct PassCost {
+  double bytes[3], flops[3];
+};
+template <typename C>
+PassCost pass_cost(const OpCall<C>& a) {
+  const double b = sizeof(C), plane = (double)a.nx * a.ny;
+  const double U = (double)a.nrhs * 3.0 * a.nslab * plane;
+  const double vec = U * b, Vb = a.nslab * plane * b;
+  PassCost c;
+  const double nin = a.in_mode == IN_PLAIN ? 1 : (a.in_mode == IN_PUPDATE ? 3 : 2);
+  const double nout = a.in_mode == IN_PLAIN ? 1 : 2;
+  c.bytes[0] = (nin + nout) * vec + Vb;
+  c.bytes[1] = 2 * vec + (double)a.nrhs * plane * sizeof(ModeEntry);
+  double ninv = 3;  // W, u, out
+  if (a.epi == EPI_RESID) ninv += 1;
+  if (a.dot_mask & DOT_R0_OUT) ninv += 1;
+  c.bytes[2] = ninv * vec;
+  const double nplanes = (double)a.nrhs * 3.0 * a.nslab;
+  c.flops[0] = nplanes * (5.0 * plane * std::log2(plane) + 6.0 * plane);
+  c.flops[1] = (double)a.nrhs * plane * (3.0 * 2.0 * 5.0 * a.nf * std::log2((double)a.nf) + 80.0 * a.nf);
+  c.flops[2] = nplanes * (5.0 * plane * std::log2(plane) + 2.0 * plane);
+  return c;
+}
+
 template <typename C>
 int op_apply_impl(const OpCall<C>& a) {
+  const bool f64 = sizeof(C) == 16;
+  const bool prof = prof_on();
+  PassCost cost;
+  if (prof) cost = pass_cost(a);
   int rc;
+  if (prof) prof_begin(f64 ? PK_FWD64 : PK_FWD32, a.stream);
   switch (a.in_mode) {
     case IN_PLAIN: rc = dispatch_fwd<C, IN_PLAIN>(a); break;
     case IN_PUPDATE: rc = dispatch_fwd<C, IN_PUPDATE>(a); break;
@@ -224,15 +258,20 @@ int op_apply_impl(const OpCall<C>& a) {
     default: return PSFD_E_ARG;
   }
   if (rc) return rc;
+  if (prof) prof_end(f64 ? PK_FWD64 : PK_FWD32, a.stream, cost.bytes[0], cost.flops[0]);
+  if (prof) prof_begin(f64 ? PK_Z64 : PK_Z32, a.stream);
   if ((rc = dispatch_z<C>(a))) return rc;
+  if (prof) prof_end(f64 ? PK_Z64 : PK_Z32, a.stream, cost.bytes[1], cost.flops[1]);
   if (a.epi == EPI_NONE) return blocks_per_rhs_t<C>(a.nx, a.ny, a.nslab);
   const C* uin = a.in_mode == IN_PLAIN ? a.u : a.ustore;
+  if (prof) prof_begin(f64 ? PK_INV64 : PK_INV32, a.stream);
   switch (a.epi) {
     case EPI_AU: rc = dispatch_inv<C, EPI_AU>(a, uin); break;
     case EPI_RESID: rc = dispatch_inv<C, EPI_RESID>(a, uin); break;
     default: return PSFD_E_ARG;
   }
   if (rc) return rc;
+  if (prof) prof_end(f64 ? PK_INV64 : PK_INV32, a.stream, cost.bytes[2], cost.flops[2]);
   return blocks_per_rhs_t<C>(a.nx, a.ny, a.nslab);
 }
 

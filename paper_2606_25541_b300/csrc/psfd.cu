@@ -1,6 +1,7 @@
 // psfd.cu -- the C ABI (include/psfd.h): solver context, device memory plan, set-up,
 // the FP64 and FP32-with-FP64-defect-correction solve drivers, and result read-back.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -14,6 +15,59 @@
 #include "tables.h"
 
 using namespace psfd;
+
+// ---------------------------------------------------------------------------
+// launch accounting and the optional per-class event profiler
+// ---------------------------------------------------------------------------
+namespace psfd {
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+bool g_prof = false;
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+  double bytes, flops;
+};
+std::vector<ProfRec> g_recs;
+std::vector<cudaEvent_t> g_pool;
+cudaEvent_t g_open[PK_N] = {};
+struct ProfTotal {
+  unsigned long long launches = 0;
+  double ms = 0, bytes = 0, flops = 0;
+};
+ProfTotal g_tot[PK_N];
+const char* kProfNames[PK_N] = {"k1_plane_fwd_fp32", "k2_zcol_fp32", "k3_plane_inv_fp32",
+                                "k1_plane_fwd_fp64", "k2_zcol_fp64", "k3_plane_inv_fp64",
+                                "vec_fp32",          "vec_fp64",     "scalar",
+                                "setup"};
+cudaEvent_t take_event() {
+  cudaEvent_t e = nullptr;
+  if (!g_pool.empty()) {
+    e = g_pool.back();
+    g_pool.pop_back();
+  } else {
+    cudaEventCreate(&e);
+  }
+  return e;
+}
+}  // namespace
+
+void count_launch(int n) { g_launches += (unsigned long long)n; }
+bool prof_on() { return g_prof; }
+void prof_begin(int cls, cudaStream_t st) {
+  if (!g_prof) return;
+  cudaEvent_t e = take_event();
+  cudaEventRecord(e, st);
+  g_open[cls] = e;
+}
+void prof_end(int cls, cudaStream_t st, double bytes, double flops) {
+  if (!g_prof || !g_open[cls]) return;
+  cudaEvent_t e = take_event();
+  cudaEventRecord(e, st);
+  g_recs.push_back({cls, g_open[cls], e, bytes, flops});
+  g_open[cls] = nullptr;
+}
+}  // namespace psfd
 
 namespace {
 
@@ -713,6 +767,55 @@ int psfd_get_mode_tables(psfd_ctx* ctx, int rhs, double* beta, double* r_s, doub
     if (r_s) { r_s[2 * i] = m[i].rs.x; r_s[2 * i + 1] = m[i].rs.y; }
     if (r_p) { r_p[2 * i] = m[i].rp.x; r_p[2 * i + 1] = m[i].rp.y; }
   }
+  return PSFD_OK;
+}
+
+int psfd_launch_count(unsigned long long* count) {
+  if (!count) return PSFD_E_ARG;
+  *count = g_launches.load();
+  return PSFD_OK;
+}
+
+int psfd_profile_enable(int on) {
+  if (on) {
+    for (auto& r : g_recs) {
+      g_pool.push_back(r.a);
+      g_pool.push_back(r.b);
+    }
+    g_recs.clear();
+    for (auto& t : g_tot) t = ProfTotal{};
+    g_prof = true;
+  } else {
+    g_prof = false;
+  }
+  return PSFD_OK;
+}
+
+int psfd_profile_classes(void) { return PK_N; }
+
+int psfd_profile_get(int cls, const char** name, unsigned long long* launches, double* ms, double* bytes,
+                     double* flops) {
+  if (cls < 0 || cls >= PK_N) return PSFD_E_ARG;
+  if (!g_recs.empty()) {  // fold finished records into the totals
+    for (auto& r : g_recs) {
+      if (cudaEventSynchronize(r.b) != cudaSuccess) return PSFD_E_CUDA;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, r.a, r.b);
+      ProfTotal& T = g_tot[r.cls];
+      T.launches += 1;
+      T.ms += t;
+      T.bytes += r.bytes;
+      T.flops += r.flops;
+      g_pool.push_back(r.a);
+      g_pool.push_back(r.b);
+    }
+    g_recs.clear();
+  }
+  if (name) *name = kProfNames[cls];
+  if (launches) *launches = g_tot[cls].launches;
+  if (ms) *ms = g_tot[cls].ms;
+  if (bytes) *bytes = g_tot[cls].bytes;
+  if (flops) *flops = g_tot[cls].flops;
   return PSFD_OK;
 }
 

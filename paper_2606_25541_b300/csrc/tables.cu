@@ -9,6 +9,12 @@
 
 namespace psfd {
 
+// Counts one kernel launch and reports whether it was accepted.
+static int launched() {
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+}
+
 // ---------------------------------------------------------------------------
 // V = k0^2 (eps - eps_bg) in FP64 and FP32 (Sec. 2, Eq. (1); Sec. 3, Eq. (10))
 // ---------------------------------------------------------------------------
@@ -24,7 +30,7 @@ __global__ void k_potential(size_t n, const double2* eps, double k02, double eps
 int launch_potential(size_t n, const double2* eps, double k02, double eps_bg, double2* V64, float2* V32,
                      cudaStream_t st) {
   k_potential<<<592, 256, 0, st>>>(n, eps, k02, eps_bg, V64, V32);
-  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+  return launched();
 }
 
 // ---------------------------------------------------------------------------
@@ -93,7 +99,7 @@ __global__ void k_modes(ModesArgs a) {
 int launch_modes(const ModesArgs& a, int n_slots, cudaStream_t st) {
   dim3 grid((a.nx + 127) / 128, a.ny, n_slots);
   k_modes<<<grid, 128, 0, st>>>(a);
-  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+  return launched();
 }
 
 // Bilinear triad of a mode: s = z x qhat, p+- = (-+beta qhat, |q|)/kb.
@@ -169,9 +175,9 @@ __global__ void k_build_rhs(int rhs0, int nrhs, const RhsParam* rp, int nslab, i
 int launch_rhs(int rhs0, int nrhs, RhsParam* rp, const ModeEntry* modes, int nx, int ny, int nslab, double dz,
                double kb, double2* b, cudaStream_t st) {
   k_rhs_params<<<(nrhs + 63) / 64, 64, 0, st>>>(rhs0, nrhs, rp, modes, nx, ny, kb);
-  if (cudaGetLastError() != cudaSuccess) return PSFD_E_CUDA;
+  if (launched() != PSFD_OK) return PSFD_E_CUDA;
   k_build_rhs<<<1184, 256, 0, st>>>(rhs0, nrhs, rp, nslab, nx * ny, dz, b);
-  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+  return launched();
 }
 
 // ---------------------------------------------------------------------------
@@ -222,7 +228,7 @@ __global__ void k_orders(OrdersArgs a) {
 int launch_orders(const OrdersArgs& a, int nrhs, cudaStream_t st) {
   dim3 grid((a.max_orders + 127) / 128, nrhs);
   k_orders<<<grid, 128, 0, st>>>(a);
-  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+  return launched();
 }
 
 // ---------------------------------------------------------------------------
@@ -259,10 +265,10 @@ int launch_norm(int n, int nblk, int rhs0, int nrhs, const double2* v, double2* 
                 double tol2, KScal* sc, int* act, cudaStream_t st) {
   if (v) {
     k_norm2_partials<<<dim3(nblk, nrhs), VEC_NT, 0, st>>>(n, nblk, rhs0, v, partials, maxblk);
-    if (cudaGetLastError() != cudaSuccess) return PSFD_E_CUDA;
+    if (launched() != PSFD_OK) return PSFD_E_CUDA;
   }
   k_norm_finish<<<nrhs, VEC_NT, 0, st>>>(rhs0, nblk, partials, maxblk, mode, tol2, sc, act);
-  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+  return launched();
 }
 
 // r32 = r64 / ||r64||  (only right-hand sides still active)
@@ -289,14 +295,14 @@ int launch_ref_scale(int n, int rhs0, int nrhs, const int* act, const KScal* sc,
                      cudaStream_t st) {
   const int bx = (n + 256 * 8 - 1) / (256 * 8);
   k_ref_scale<<<dim3(bx, nrhs), 256, 0, st>>>(n, rhs0, act, sc, r64, r32);
-  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+  return launched();
 }
 
 int launch_ref_update(int n, int rhs0, int nrhs, const int* act, const KScal* sc, double2* x64, const float2* x32,
                       cudaStream_t st) {
   const int bx = (n + 256 * 8 - 1) / (256 * 8);
   k_ref_update<<<dim3(bx, nrhs), 256, 0, st>>>(n, rhs0, act, sc, x64, x32);
-  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+  return launched();
 }
 
 // ---------------------------------------------------------------------------
@@ -332,7 +338,7 @@ int run_test_fft(C* data, int count, bool inv, const double2* tw) {
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<grid, 256, smem>>>(data, count, tw);
   }
-  return cudaGetLastError() == cudaSuccess ? PSFD_OK : PSFD_E_CUDA;
+  return launched();
 }
 
 int launch_test_fft(int n, int count, bool inv, bool fp64, void* data, const double2* tw) {

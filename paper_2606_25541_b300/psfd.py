@@ -69,7 +69,40 @@ _SIGS = {
     "psfd_get_rhs": (_I, [_P, _I, _P, _I]),
     "psfd_get_mode_tables": (_I, [_P, _I, _D, _D, _D]),
     "psfd_test_fft": (_I, [_I, _I, _I, _I, _P]),
+    "psfd_launch_count": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
+    "psfd_profile_enable": (_I, [_I]),
+    "psfd_profile_classes": (_I, []),
+    "psfd_profile_get": (_I, [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_ulonglong), _D, _D,
+                              _D]),
 }
+
+
+def launch_count() -> int:
+    """Kernels launched by the library since it was loaded."""
+    n = ctypes.c_ulonglong(0)
+    load().psfd_launch_count(ctypes.byref(n))
+    return int(n.value)
+
+
+def profile_enable(on: bool = True):
+    load().psfd_profile_enable(int(bool(on)))
+
+
+def profile_read():
+    """Per-class totals since profile_enable(True): {name: {launches, ms, bytes, flops}}."""
+    lib = load()
+    out = {}
+    for c in range(lib.psfd_profile_classes()):
+        name = ctypes.c_char_p()
+        n = ctypes.c_ulonglong(0)
+        ms, by, fl = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+        st = lib.psfd_profile_get(c, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by),
+                                  ctypes.byref(fl))
+        if st != OK:
+            raise PsfdError(st, strerror(st))
+        out[name.value.decode()] = {"launches": int(n.value), "ms": ms.value, "bytes": by.value,
+                                    "flops": fl.value}
+    return out
 
 
 def load(path: str = LIB_PATH):
@@ -182,10 +215,11 @@ class Solver:
                                             _dptr(d if d.size else np.zeros(1)), _dptr(ns)))
 
     def set_potential(self, eps):
-        """eps: complex128 array (nslab, ny, nx) on the host, or a complex128 CUDA tensor."""
+        """eps: complex128 (nslab, ny, nx) as a numpy array or torch tensor (CPU, e.g. pinned, or CUDA)."""
         if hasattr(eps, "data_ptr"):
             self._keep_eps = eps
-            self._check(self.lib.psfd_set_potential(self.ctx, ctypes.c_void_p(eps.data_ptr()), DEVICE))
+            where = DEVICE if eps.is_cuda else HOST
+            self._check(self.lib.psfd_set_potential(self.ctx, ctypes.c_void_p(eps.data_ptr()), where))
         else:
             e = _c128(eps)
             self._keep_eps = e
