@@ -184,6 +184,39 @@ int psfd_profile_classes(void);
 int psfd_profile_get(int cls, const char** name, unsigned long long* launches, double* ms, double* bytes,
                      double* flops);
 
+/* ---------------------------------------------------------------------------------
+ * Allocation-free operator application. The paper has no counterpart: this is a
+ * deployment variant of psfd_apply for callers that cannot call cudaMalloc -- systems
+ * whose device memory is fixed at start-up (real-time or certified deployments that
+ * forbid allocation after initialisation) and hosts whose own allocator owns the
+ * device, where an outside cudaMalloc/cudaFree would break its accounting or
+ * synchronise the device. Such callers cannot use psfd_create, which allocates.
+ *
+ * out = A u for one illumination, with the same FP32 kernels as psfd_apply(...,
+ * PSFD_FP32_REFINED, ...), computed without any context:
+ *   grid                   discretisation (same rules as psfd_create)
+ *   n_layers, n_complex, thickness_nm, n_sub   stack, as in psfd_set_stack (<= 256 layers)
+ *   theta_deg, phi_deg     illumination (polarisation does not enter A)
+ *   eps                    device, complex double [nslab][ny][nx] permittivity
+ *   u, out                 device, complex float [3][nslab][ny][nx]; must not alias
+ *   stream                 cudaStream_t (NULL = legacy default stream)
+ * It allocates nothing (no cudaMalloc, cudaFree or allocating library call): every
+ * intermediate lives in one static device array of PSFD_STATIC_SCRATCH_BYTES that the
+ * library holds on every GPU it is loaded on until the process exits. A grid needs
+ * about nx*ny*(64 + 32*nslab) + 12 KiB of it (128 x 128 x 60: 32.5 MB); larger grids
+ * are rejected with PSFD_E_BUDGET before any device work. The first call on each
+ * device looks the array's device address up (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture. All calls share the array
+ * and it keeps the previous call's contents: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller. The stack
+ * arrays are read before return; the call synchronises the stream once when
+ * n_layers > 0. Returns PSFD_OK, PSFD_E_ARG, PSFD_E_BUDGET, PSFD_E_ANOMALY or
+ * PSFD_E_CUDA. */
+#define PSFD_STATIC_SCRATCH_BYTES (48u * 1024u * 1024u)
+int psfd_apply_fp32_static(const psfd_grid* grid, int n_layers, const double* n_complex,
+                           const double* thickness_nm, const double* n_sub, double theta_deg,
+                           double phi_deg, const void* eps, const void* u, void* out, void* stream);
+
 /* Test hook for the device FFT: `count` contiguous transforms of length n, in place, on
  * device data (complex double if fp64 else complex float). inverse = 1 applies the
  * unnormalised inverse. Runs on the legacy default stream and synchronises. */

@@ -69,12 +69,28 @@ _SIGS = {
     "psfd_get_rhs": (_I, [_P, _I, _P, _I]),
     "psfd_get_mode_tables": (_I, [_P, _I, _D, _D, _D]),
     "psfd_test_fft": (_I, [_I, _I, _I, _I, _P]),
+    "psfd_apply_fp32_static": (_I, [ctypes.POINTER(Grid), _I, _D, _D, _D, ctypes.c_double, ctypes.c_double, _P,
+                                    _P, _P, _P]),
     "psfd_launch_count": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "psfd_profile_enable": (_I, [_I]),
     "psfd_profile_classes": (_I, []),
     "psfd_profile_get": (_I, [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_ulonglong), _D, _D,
                               _D]),
 }
+
+
+def apply_fp32_static(grid: Grid, n_layers, thickness, n_sub, theta_deg, phi_deg, eps, u, out, stream=None):
+    """out = A u through the allocation-free entry point (no context; the library's static
+    device scratch holds every intermediate). eps: complex128 CUDA tensor (nslab, ny, nx);
+    u, out: complex64 CUDA tensors (3, nslab, ny, nx). Returns the status code."""
+    n = _c128(n_layers).reshape(-1)
+    d = np.ascontiguousarray(thickness, dtype=np.float64).reshape(-1)
+    ns = np.array([complex(n_sub).real, complex(n_sub).imag], dtype=np.float64)
+    nn = n.view(np.float64) if n.size else np.zeros(2, np.float64)
+    return load().psfd_apply_fp32_static(ctypes.byref(grid), int(n.size), _dptr(nn), _dptr(d if d.size else np.zeros(1)),
+                                         _dptr(ns), float(theta_deg), float(phi_deg),
+                                         ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
 
 
 def launch_count() -> int:
