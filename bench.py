@@ -53,7 +53,46 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--profile-only", action="store_true", help="one profiled step, for ncu launch lists")
+    ap.add_argument("--apply", action="store_true",
+                    help="operator applications/s only (psfd_apply), for kernel captures")
+    ap.add_argument("--rhs", type=int, default=18, help="illuminations used by --apply")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "both"], default="both", help="--apply precision")
     return ap.parse_args(argv)
+
+
+def run_apply(args):
+    """Operator applications per second on the line/space clip (one application = K1, K2,
+    K3 over every illumination of the batch), with CUDA events on the current stream."""
+    import torch
+    from paper_2606_25541_b300 import psfd
+    prob = layouts.line_space_clip(seed=2)
+    sel = np.arange(args.rhs) % prob.n_rhs
+    prob = prob.with_illumination(prob.theta_deg[sel], prob.phi_deg[sel], prob.pol[sel])
+    stream = torch.cuda.current_stream()
+    out = {"mode": "apply", "workload": WORKLOAD.replace("18rhs", f"{args.rhs}rhs")}
+    precs = ["fp32", "fp64"] if args.precision == "both" else [args.precision]
+    for name in precs:
+        prec = psfd.FP32_REFINED if name == "fp32" else psfd.FP64
+        s = psfd.Solver.from_problem(prob, prec, stream=stream)
+        dt = torch.complex64 if name == "fp32" else torch.complex128
+        u = torch.tensor(layouts.random_field((args.rhs, 3, prob.nslab, prob.ny, prob.nx), seed=1), dtype=dt,
+                         device="cuda")
+        y = torch.empty_like(u)
+        for _ in range(args.warmup):
+            s.apply(u, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            s.apply(u, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(args.steps, 1)
+        out[name] = {"ms_per_application": ms, "applications_per_s": 1e3 / ms,
+                     "rhs_applications_per_s": args.rhs * 1e3 / ms}
+        s.close()
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def dist_env():
@@ -373,6 +412,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.apply:
+        return run_apply(args)
     return run_ours(args)
 
 

@@ -35,6 +35,14 @@ __host__ __device__ constexpr int fft_plan_stages(int n) {
   return s;
 }
 
+// Shared-memory layout of a transform: element i sits at fpad(i) = i + i/8 (times the
+// element stride), one spare slot after every eight elements. Without it the first
+// radix-8 stage stores with a stride of eight elements and eight lanes of a half-warp
+// hit the same bank pair; with it every stage's loads and stores are (nearly)
+// conflict free. A transform of length n occupies fft_phys(n) slots.
+__host__ __device__ constexpr int fft_phys(int n) { return n + (n >> 3); }
+__host__ __device__ __forceinline__ int fpad(int i) { return i + (i >> 3); }
+
 // Lanes per transform: N/8 rounded down to a power of two, clamped to [1, 32].
 __host__ __device__ constexpr int fft_group_lanes(int n) {
   int g = 1;
@@ -155,7 +163,7 @@ __device__ __forceinline__ void fft_stages(C* a, int es, int g, const C* tw, boo
       if (valid && (NB % G == 0 || b < NB)) {
         const int jj = b % NS;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[k][r] = a[(b + r * NB) * es];
+        for (int r = 0; r < R; ++r) v[k][r] = a[fpad(b + r * NB) * es];
         if constexpr (NS > 1) {
 #pragma unroll
           for (int r = 1; r < R; ++r) {
@@ -175,7 +183,7 @@ __device__ __forceinline__ void fft_stages(C* a, int es, int g, const C* tw, boo
         const int jj = b % NS;
         const int base = (b / NS) * NS * R + jj;
 #pragma unroll
-        for (int r = 0; r < R; ++r) a[(base + r * NS) * es] = v[k][r];
+        for (int r = 0; r < R; ++r) a[fpad(base + r * NS) * es] = v[k][r];
       }
     }
     __syncwarp();
@@ -192,8 +200,9 @@ __device__ __forceinline__ void group_fft(C* a, int es, int g, const C* tw, bool
 }
 
 // Batched transforms by a whole CTA: `count` transforms, transform f starting at
-// a + f * fs with element stride es. Each warp handles 32/G transforms at a time.
-template <typename C, int N, bool INV>
+// a + f' * fs with f' = fpad(f) if PADF (transforms along the second axis of a padded
+// 2-D tile) else f, element i at fpad(i) * es. Each warp handles 32/G transforms at a time.
+template <typename C, int N, bool INV, bool PADF = false>
 __device__ __forceinline__ void cta_fft(C* a, int count, int fs, int es, const C* tw) {
   constexpr int G = fft_group_lanes(N);
   constexpr int GPW = 32 / G;  // groups per warp
@@ -207,7 +216,8 @@ __device__ __forceinline__ void cta_fft(C* a, int count, int fs, int es, const C
   for (int it = 0; it < rounds; ++it) {
     const int f = gid + it * ngroups;
     const bool valid = f < count;
-    group_fft<C, N, INV>(a + (valid ? f : 0) * fs, es, g, tw, valid);
+    const int fo = valid ? (PADF ? fpad(f) : f) : 0;
+    group_fft<C, N, INV>(a + fo * fs, es, g, tw, valid);
   }
 }
 

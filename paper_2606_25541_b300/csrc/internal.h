@@ -26,6 +26,19 @@ struct ModeEntry {
   double2 rp;    // stack reflection coefficient, p (H-field)
 };
 
+// FP32 copy of what the z-column kernel needs per mode, prepared by the FP64 stack
+// kernel so that the FP32 hot path does no FP64 arithmetic.
+struct ModeF32 {
+  float qx, qy;     // transverse wavevector
+  float2 bh, bl;    // beta split into FP32 hi + lo (beta - kappa stays exact near kappa)
+  float2 ebL;       // exp(i beta L)
+  float2 bdz;       // beta dz
+  float2 rs, rp;    // stack reflection coefficients
+  float hx, hy;     // unit transverse direction (azimuth of the illumination at q = 0)
+  float qnk, pad;   // |q| / kb
+  float2 bq;        // beta / kb
+};
+
 // Krylov scalars per right-hand side (BiCGStab), all FP64.
 struct KScal {
   double2 rho, alpha, omega, beta;
@@ -54,6 +67,9 @@ struct OpCall {
   const double2 *twx, *twy, *twz;               // exp(-2 pi i t / n) tables (FP64)
   const RhsParam* rhsp;
   const ModeEntry* modes;
+  const ModeF32* modes32;  // FP32 column constants (used by the FP32 z-column kernel)
+  const float* ktab32;     // [3][nf]: |kz_l| hi, |kz_l| lo, signed kz_l (FP32)
+  const double* ktab64;    // [nf]: signed kz_l (FP64)
   const int* active;  // per global rhs, or null = all active
   // input stage: J = V * in, in = u | r + beta (u - omega v) | r - alpha v
   int in_mode;

@@ -46,6 +46,15 @@ __device__ __forceinline__ void split_hi_lo_r(double v, double& hi, double& lo) 
   lo = 0.0;
 }
 
+// a / b through one reciprocal of |b|^2; here |b| stays far from under- and overflow
+// (|kappa + beta| >= |beta| and |delta| >= 1/(2L) on this branch).
+__device__ __forceinline__ float2 cdiv_fast(float2 a, float2 b) {
+  return cscale(cmulc(b, a), __frcp_rn(b.x * b.x + b.y * b.y));
+}
+__device__ __forceinline__ double2 cdiv_fast(double2 a, double2 b) {
+  return cscale(cmulc(b, a), 1.0 / (b.x * b.x + b.y * b.y));
+}
+
 __device__ __forceinline__ float2 cexp_r(float2 z) {
   float s, c;
   sincosf(z.y, &s, &c);
@@ -153,12 +162,23 @@ __device__ __forceinline__ void zero_dots(Dots<C>& dt) {
 // ---------------------------------------------------------------------------
 // K1 / K3 for planes that fit in shared memory
 // ---------------------------------------------------------------------------
+// Shared tile of a whole plane: row y at fpad(y) * PITCH, element x of a row at fpad(x);
+// PITCH is odd so that column transforms (element stride PITCH) spread over the banks.
+template <int NX> __host__ __device__ constexpr int plane_pitch() { return fft_phys(NX) | 1; }
+template <int NX, int NY> __host__ __device__ constexpr int plane_tile_elems() {
+  return fft_phys(NY) * plane_pitch<NX>();
+}
+template <int NX>
+__device__ __forceinline__ int plane_slot(int i) {
+  return fpad(i / NX) * plane_pitch<NX>() + fpad(i % NX);
+}
+
 template <typename C, int NX, int NY, int IN, int NT>
 __global__ void __launch_bounds__(NT) k_plane_fwd(OpCall<C> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int PITCH = NX + 1;
+  constexpr int PITCH = plane_pitch<NX>();
   C* tile = reinterpret_cast<C*>(smem);
-  C* twx = tile + NY * PITCH;
+  C* twx = tile + plane_tile_elems<NX, NY>();
   C* twy = twx + NX;
   const int p = blockIdx.x, c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
@@ -169,22 +189,22 @@ __global__ void __launch_bounds__(NT) k_plane_fwd(OpCall<C> a) {
   const C* Vp = a.V + (size_t)p * (NX * NY);
   for (int i = threadIdx.x; i < NX * NY; i += NT) {
     C val = input_elem<C, IN>(a, plane + i, s);
-    tile[(i / NX) * PITCH + (i % NX)] = cmul(Vp[i], val);
+    tile[plane_slot<NX>(i)] = cmul(Vp[i], val);
   }
   __syncthreads();
-  cta_fft<C, NX, false>(tile, NY, PITCH, 1, twx);
+  cta_fft<C, NX, false, true>(tile, NY, PITCH, 1, twx);
   __syncthreads();
-  cta_fft<C, NY, false>(tile, NX, 1, PITCH, twy);
+  cta_fft<C, NY, false, true>(tile, NX, 1, PITCH, twy);
   __syncthreads();
-  for (int i = threadIdx.x; i < NX * NY; i += NT) a.work[plane + i] = tile[(i / NX) * PITCH + (i % NX)];
+  for (int i = threadIdx.x; i < NX * NY; i += NT) a.work[plane + i] = tile[plane_slot<NX>(i)];
 }
 
 template <typename C, int NX, int NY, int EPI, int NT>
 __global__ void __launch_bounds__(NT) k_plane_inv(OpCall<C> a, const C* uin) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int PITCH = NX + 1;
+  constexpr int PITCH = plane_pitch<NX>();
   C* tile = reinterpret_cast<C*>(smem);
-  C* twx = tile + NY * PITCH;
+  C* twx = tile + plane_tile_elems<NX, NY>();
   C* twy = twx + NX;
   double2* scratch = align16<double2>(twy + NY);
   const int p = blockIdx.x, c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
@@ -192,16 +212,16 @@ __global__ void __launch_bounds__(NT) k_plane_inv(OpCall<C> a, const C* uin) {
   for (int i = threadIdx.x; i < NX; i += NT) twx[i] = from_c64<C>(a.twx[i]);
   for (int i = threadIdx.x; i < NY; i += NT) twy[i] = from_c64<C>(a.twy[i]);
   const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
-  for (int i = threadIdx.x; i < NX * NY; i += NT) tile[(i / NX) * PITCH + (i % NX)] = a.work[plane + i];
+  for (int i = threadIdx.x; i < NX * NY; i += NT) tile[plane_slot<NX>(i)] = a.work[plane + i];
   __syncthreads();
-  cta_fft<C, NY, true>(tile, NX, 1, PITCH, twy);
+  cta_fft<C, NY, true, true>(tile, NX, 1, PITCH, twy);
   __syncthreads();
-  cta_fft<C, NX, true>(tile, NY, PITCH, 1, twx);
+  cta_fft<C, NX, true, true>(tile, NY, PITCH, 1, twx);
   __syncthreads();
   Dots<C> dt;
   zero_dots(dt);
   for (int i = threadIdx.x; i < NX * NY; i += NT)
-    epilogue_elem<C, EPI>(a, uin, plane + i, tile[(i / NX) * PITCH + (i % NX)], dt);
+    epilogue_elem<C, EPI>(a, uin, plane + i, tile[plane_slot<NX>(i)], dt);
   if (a.dot_mask) {
     const int blk = c * a.nslab + p;
     block_write_dots(dt, a.dot_mask, a.partials + ((size_t)g * NDOT) * a.maxblk + blk, a.maxblk, scratch);
@@ -215,8 +235,9 @@ __global__ void __launch_bounds__(NT) k_plane_inv(OpCall<C> a, const C* uin) {
 template <typename C, int NX, int IN, int NT>
 __global__ void __launch_bounds__(NT) k_rows_fwd(OpCall<C> a, int rb) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int RP = fft_phys(NX);  // row pitch of the tile
   C* tile = reinterpret_cast<C*>(smem);
-  C* tw = tile + rb * NX;
+  C* tw = tile + rb * RP;
   const int nrb = a.ny / rb;
   const int p = blockIdx.x / nrb, y0 = (blockIdx.x % nrb) * rb;
   const int c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
@@ -225,18 +246,20 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(OpCall<C> a, int rb) {
   const InScal<C> s = load_in_scalars<C, IN>(a, g);
   const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
   const C* Vp = a.V + ((size_t)p * a.ny + y0) * NX;
-  for (int i = threadIdx.x; i < rb * NX; i += NT) tile[i] = cmul(Vp[i], input_elem<C, IN>(a, base + i, s));
+  for (int i = threadIdx.x; i < rb * NX; i += NT)
+    tile[(i / NX) * RP + fpad(i % NX)] = cmul(Vp[i], input_elem<C, IN>(a, base + i, s));
   __syncthreads();
-  cta_fft<C, NX, false>(tile, rb, NX, 1, tw);
+  cta_fft<C, NX, false>(tile, rb, RP, 1, tw);
   __syncthreads();
-  for (int i = threadIdx.x; i < rb * NX; i += NT) a.work[base + i] = tile[i];
+  for (int i = threadIdx.x; i < rb * NX; i += NT) a.work[base + i] = tile[(i / NX) * RP + fpad(i % NX)];
 }
 
 template <typename C, int NX, int EPI, int NT>
 __global__ void __launch_bounds__(NT) k_rows_inv(OpCall<C> a, const C* uin, int rb) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int RP = fft_phys(NX);
   C* tile = reinterpret_cast<C*>(smem);
-  C* tw = tile + rb * NX;
+  C* tw = tile + rb * RP;
   double2* scratch = align16<double2>(tw + NX);
   const int nrb = a.ny / rb;
   const int p = blockIdx.x / nrb, y0 = (blockIdx.x % nrb) * rb;
@@ -244,13 +267,14 @@ __global__ void __launch_bounds__(NT) k_rows_inv(OpCall<C> a, const C* uin, int 
   if (a.active && !a.active[g]) return;
   for (int i = threadIdx.x; i < NX; i += NT) tw[i] = from_c64<C>(a.twx[i]);
   const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
-  for (int i = threadIdx.x; i < rb * NX; i += NT) tile[i] = a.work[base + i];
+  for (int i = threadIdx.x; i < rb * NX; i += NT) tile[(i / NX) * RP + fpad(i % NX)] = a.work[base + i];
   __syncthreads();
-  cta_fft<C, NX, true>(tile, rb, NX, 1, tw);
+  cta_fft<C, NX, true>(tile, rb, RP, 1, tw);
   __syncthreads();
   Dots<C> dt;
   zero_dots(dt);
-  for (int i = threadIdx.x; i < rb * NX; i += NT) epilogue_elem<C, EPI>(a, uin, base + i, tile[i], dt);
+  for (int i = threadIdx.x; i < rb * NX; i += NT)
+    epilogue_elem<C, EPI>(a, uin, base + i, tile[(i / NX) * RP + fpad(i % NX)], dt);
   if (a.dot_mask) {
     const int blk = (c * a.nslab + p) * nrb + (y0 / rb);
     block_write_dots(dt, a.dot_mask, a.partials + ((size_t)g * NDOT) * a.maxblk + blk, a.maxblk, scratch);
@@ -262,7 +286,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(OpCall<C> a, const C* uin, int 
 template <typename C, int NY, bool INV, int NT>
 __global__ void __launch_bounds__(NT) k_cols(OpCall<C> a, int tx) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int PITCH = NY + 1;
+  constexpr int PITCH = fft_phys(NY) | 1;  // odd column pitch: the transposing copies spread over the banks
   C* tile = reinterpret_cast<C*>(smem);
   C* tw = tile + tx * PITCH;
   const int ncb = a.nx / tx;
@@ -273,14 +297,14 @@ __global__ void __launch_bounds__(NT) k_cols(OpCall<C> a, int tx) {
   const size_t base = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)NY * a.nx + x0;
   for (int i = threadIdx.x; i < NY * tx; i += NT) {
     const int y = i / tx, xx = i % tx;
-    tile[xx * PITCH + y] = a.work[base + (size_t)y * a.nx + xx];
+    tile[xx * PITCH + fpad(y)] = a.work[base + (size_t)y * a.nx + xx];
   }
   __syncthreads();
   cta_fft<C, NY, INV>(tile, tx, PITCH, 1, tw);
   __syncthreads();
   for (int i = threadIdx.x; i < NY * tx; i += NT) {
     const int y = i / tx, xx = i % tx;
-    a.work[base + (size_t)y * a.nx + xx] = tile[xx * PITCH + y];
+    a.work[base + (size_t)y * a.nx + xx] = tile[xx * PITCH + fpad(y)];
   }
 }
 
@@ -314,9 +338,9 @@ __device__ __forceinline__ void green_apply(C& J0, C& J1, C& J2, typename RealOf
       C t = cmul(w, phi);
       phi = mk((R)1 + t.x / (R)k, t.y / (R)k);
     }
-    S = cdiv(mk(-phi.y * L, phi.x * L), kpb);  // i L phi1 / (kappa + beta)
+    S = cdiv_fast(mk(-phi.y * L, phi.x * L), kpb);  // i L phi1 / (kappa + beta)
   } else {
-    S = cdiv(mk(E.x - (R)1, E.y), cmul(d, kpb));
+    S = cdiv_fast(mk(E.x - (R)1, E.y), cmul(d, kpb));
   }
   S = cscale(S, scale);
   const C Es = cscale(E, cinv * scale);
@@ -335,7 +359,7 @@ template <typename C, int NF, int NT>
 __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
   using R = typename RealOf<C>::T;
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int P = NF + 1;
+  constexpr int P = fft_phys(NF) | 1;  // column pitch; element z of a column at fpad(z)
   C* col = reinterpret_cast<C*>(smem);
   C* tw = col + 3 * tx * P;
   R* kh = reinterpret_cast<R*>(tw + NF);
@@ -352,53 +376,71 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
   const int x0 = blockIdx.x * tx, y = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
   const int nx = a.nx, ny = a.ny, ns = a.nslab;
-  const RhsParam rp = a.rhsp[g];
-  const double two_pi = 6.283185307179586476925286766559;
+  constexpr bool F32 = sizeof(C) == sizeof(float2);
+  const int slot = a.rhsp[g].slot;
+  const size_t mbase = ((size_t)slot * ny + y) * nx + x0;
 
   for (int i = threadIdx.x; i < NF; i += NT) {
     tw[i] = from_c64<C>(a.twz[i]);
-    const int lf = fft_freq(i, NF);
-    const double kz64 = two_pi * (double)lf / ((double)NF * a.dz);
-    split_hi_lo_r(fabs(kz64), kh[i], kl[i]);
-    kzs[i] = (R)kz64;
+    if constexpr (F32) {
+      kh[i] = a.ktab32[i];
+      kl[i] = a.ktab32[NF + i];
+      kzs[i] = a.ktab32[2 * NF + i];
+    } else {
+      const double k = a.ktab64[i];
+      kh[i] = fabs(k);
+      kl[i] = 0.0;
+      kzs[i] = k;
+    }
   }
-  const int ni = fft_freq(y, ny);
-  const double qy64 = rp.qiy + two_pi * (double)ni / ((double)ny * a.dy);
+  const double two_pi = 6.283185307179586476925286766559;
   for (int t = threadIdx.x; t < tx; t += NT) {
-    const int x = x0 + t;
-    const int mi = fft_freq(x, nx);
-    const double qx64 = rp.qix + two_pi * (double)mi / ((double)nx * a.dx);
-    const ModeEntry me = a.modes[((size_t)rp.slot * ny + y) * nx + x];
-    split_hi_lo(me.beta, cb_h[t], cb_l[t]);
-    cebl[t] = from_c64<C>(me.ebL);
-    cbdz[t] = from_c64<C>(make_double2(me.beta.x * a.dz, me.beta.y * a.dz));
-    cqx[t] = (R)qx64;
-    cqy[t] = (R)qy64;
+    if constexpr (F32) {
+      const ModeF32 m = a.modes32[mbase + t];
+      cb_h[t] = m.bh;
+      cb_l[t] = m.bl;
+      cebl[t] = m.ebL;
+      cbdz[t] = m.bdz;
+      cqx[t] = m.qx;
+      cqy[t] = m.qy;
+    } else {
+      const RhsParam& rp = a.rhsp[g];
+      const double qx64 = rp.qix + two_pi * (double)fft_freq(x0 + t, nx) / ((double)nx * a.dx);
+      const double qy64 = rp.qiy + two_pi * (double)fft_freq(y, ny) / ((double)ny * a.dy);
+      const ModeEntry me = a.modes[mbase + t];
+      split_hi_lo(me.beta, cb_h[t], cb_l[t]);
+      cebl[t] = from_c64<C>(me.ebL);
+      cbdz[t] = from_c64<C>(make_double2(me.beta.x * a.dz, me.beta.y * a.dz));
+      cqx[t] = (R)qx64;
+      cqy[t] = (R)qy64;
+    }
   }
   // zero padding: plane 0 and planes ns+1 .. NF-1
   for (int i = threadIdx.x; i < 3 * tx * (NF - ns); i += NT) {
     const int cc = i / (NF - ns), zz = i % (NF - ns);
-    col[cc * P + (zz == 0 ? 0 : ns + zz)] = mk((R)0, (R)0);
+    col[cc * P + fpad(zz == 0 ? 0 : ns + zz)] = mk((R)0, (R)0);
   }
   const size_t rhs_base = (size_t)lr * 3 * ns * ny * nx;
   for (int i = threadIdx.x; i < 3 * ns * tx; i += NT) {
     const int t = i % tx, rest = i / tx, pl = rest % ns, cc = rest / ns;
-    col[(cc * tx + t) * P + pl + 1] = a.work[rhs_base + (((size_t)cc * ns + pl) * ny + y) * nx + x0 + t];
+    col[(cc * tx + t) * P + fpad(pl + 1)] = a.work[rhs_base + (((size_t)cc * ns + pl) * ny + y) * nx + x0 + t];
   }
   __syncthreads();
   cta_fft<C, NF, false>(col, 3 * tx, P, 1, tw);
   __syncthreads();
 
-  const R L = (R)(0.5 * NF * a.dz);
-  const R cinv = (R)(1.0 / (a.kb * a.kb));
-  const R scale = (R)(1.0 / ((double)NF * nx * ny));
+  // constants in the working precision (no FP64 arithmetic in the FP32 kernel)
+  const R L = (R)0.5 * (R)NF * (R)a.dz;
+  const R kbr = (R)a.kb;
+  const R cinv = (R)1 / (kbr * kbr);
+  const R scale = (R)1 / ((R)NF * (R)nx * (R)ny);
   for (int i = threadIdx.x; i < tx * NF; i += NT) {
     const int t = i / NF, l = i % NF;
     C E = cebl[t];
     if (fft_freq(l, NF) & 1) E = cneg(E);
-    C* c0 = col + (0 * tx + t) * P + l;
-    C* c1 = col + (1 * tx + t) * P + l;
-    C* c2 = col + (2 * tx + t) * P + l;
+    C* c0 = col + (0 * tx + t) * P + fpad(l);
+    C* c1 = col + (1 * tx + t) * P + fpad(l);
+    C* c2 = col + (2 * tx + t) * P + fpad(l);
     C J0 = *c0, J1 = *c1, J2 = *c2;
     green_apply(J0, J1, J2, cqx[t], cqy[t], kzs[l], kh[l], kl[l], cb_h[t], cb_l[t], E, L, cinv, scale);
     *c0 = J0;
@@ -415,16 +457,30 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
       const int cc = i / tx, t = i % tx;
       const size_t o = (((size_t)g * 2) * 3 + cc) * ny * nx + (size_t)y * nx + x0 + t;
       a.side[o] = col[(cc * tx + t) * P];
-      a.side[o + (size_t)3 * ny * nx] = col[(cc * tx + t) * P + ns + 1];
+      a.side[o + (size_t)3 * ny * nx] = col[(cc * tx + t) * P + fpad(ns + 1)];
     }
   }
   // stack reflection of the downgoing field on plane 0: R0 = T_R E0 (Eq. (9)),
   // T_R = r_s s s^T + r_p p+ p-^T with s = z x q/|q|, p+- = (-+beta qhat, |q|)/kb.
   for (int t = threadIdx.x; t < tx; t += NT) {
+    if constexpr (F32) {
+      const ModeF32 m = a.modes32[mbase + t];
+      const float2 e0 = col[(0 * tx + t) * P], e1 = col[(1 * tx + t) * P], e2 = col[(2 * tx + t) * P];
+      const float2 sE = mk(-m.hy * e0.x + m.hx * e1.x, -m.hy * e0.y + m.hx * e1.y);
+      const float2 tq = cadd(cscale(e0, m.hx), cscale(e1, m.hy));
+      const float2 pmE = cadd(cmul(m.bq, tq), cscale(e2, m.qnk));
+      const float2 as = cmul(m.rs, sE), ap = cmul(m.rp, pmE);
+      const float2 apb = cmul(ap, m.bq);
+      R0[0 * tx + t] = csub(cscale(as, -m.hy), cscale(apb, m.hx));
+      R0[1 * tx + t] = csub(cscale(as, m.hx), cscale(apb, m.hy));
+      R0[2 * tx + t] = cscale(ap, m.qnk);
+      continue;
+    }
     const int x = x0 + t;
-    const ModeEntry me = a.modes[((size_t)rp.slot * ny + y) * nx + x];
-    const int mi = fft_freq(x, nx);
-    const double qx64 = rp.qix + two_pi * (double)mi / ((double)nx * a.dx);
+    const RhsParam& rp = a.rhsp[g];
+    const ModeEntry me = a.modes[mbase + t];
+    const double qx64 = rp.qix + two_pi * (double)fft_freq(x, nx) / ((double)nx * a.dx);
+    const double qy64 = rp.qiy + two_pi * (double)fft_freq(y, ny) / ((double)ny * a.dy);
     const double qn = sqrt(qx64 * qx64 + qy64 * qy64);
     const double hx = qn > 0.0 ? qx64 / qn : rp.cphi;
     const double hy = qn > 0.0 ? qy64 / qn : rp.sphi;
@@ -455,14 +511,14 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
     const C ph = cexp_r(mk(-bdz.y * (R)pl, bdz.x * (R)pl));  // exp(i beta pl dz)
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
-      C* e = col + (cc * tx + t) * P + pl + 1;
+      C* e = col + (cc * tx + t) * P + fpad(pl + 1);
       *e = cadd(*e, cmul(R0[cc * tx + t], ph));
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 3 * ns * tx; i += NT) {
     const int t = i % tx, rest = i / tx, pl = rest % ns, cc = rest / ns;
-    a.work[rhs_base + (((size_t)cc * ns + pl) * ny + y) * nx + x0 + t] = col[(cc * tx + t) * P + pl + 1];
+    a.work[rhs_base + (((size_t)cc * ns + pl) * ny + y) * nx + x0 + t] = col[(cc * tx + t) * P + fpad(pl + 1)];
   }
 }
 

@@ -60,7 +60,7 @@ inline int set_smem(K kernel, size_t bytes) {
 template <typename C, int N, int IN>
 int launch_plane_fwd(const OpCall<C>& a) {
   constexpr int NT = N >= 128 ? 512 : 256;
-  const size_t smem = (size_t)(N * (N + 1) + 2 * N) * sizeof(C);
+  const size_t smem = (size_t)(plane_tile_elems<N, N>() + 2 * N) * sizeof(C);
   auto k = k_plane_fwd<C, N, N, IN, NT>;
   if (set_smem(k, smem)) return PSFD_E_CUDA;
   k<<<dim3(a.nslab, 3, a.nrhs), NT, smem, a.stream>>>(a);
@@ -71,7 +71,7 @@ int launch_plane_fwd(const OpCall<C>& a) {
 template <typename C, int N, int EPI>
 int launch_plane_inv(const OpCall<C>& a, const C* uin) {
   constexpr int NT = N >= 128 ? 512 : 256;
-  const size_t smem = (size_t)(N * (N + 1) + 2 * N) * sizeof(C) + 16 + NDOT * 32 * sizeof(double2);
+  const size_t smem = (size_t)(plane_tile_elems<N, N>() + 2 * N) * sizeof(C) + 16 + NDOT * 32 * sizeof(double2);
   auto k = k_plane_inv<C, N, N, EPI, NT>;
   if (set_smem(k, smem)) return PSFD_E_CUDA;
   k<<<dim3(a.nslab, 3, a.nrhs), NT, smem, a.stream>>>(a, uin);
@@ -83,7 +83,7 @@ template <typename C, int NX, int IN>
 int launch_rows_fwd(const OpCall<C>& a) {
   constexpr int NT = 256;
   const int rb = row_block(NX, a.ny, Tune<C>::ROW_ELEMS);
-  const size_t smem = (size_t)(rb * NX + NX) * sizeof(C);
+  const size_t smem = (size_t)(rb * fft_phys(NX) + NX) * sizeof(C);
   auto k = k_rows_fwd<C, NX, IN, NT>;
   if (set_smem(k, smem)) return PSFD_E_CUDA;
   k<<<dim3(a.nslab * (a.ny / rb), 3, a.nrhs), NT, smem, a.stream>>>(a, rb);
@@ -95,7 +95,7 @@ template <typename C, int NX, int EPI>
 int launch_rows_inv(const OpCall<C>& a, const C* uin) {
   constexpr int NT = 256;
   const int rb = row_block(NX, a.ny, Tune<C>::ROW_ELEMS);
-  const size_t smem = (size_t)(rb * NX + NX) * sizeof(C) + 16 + NDOT * 32 * sizeof(double2);
+  const size_t smem = (size_t)(rb * fft_phys(NX) + NX) * sizeof(C) + 16 + NDOT * 32 * sizeof(double2);
   auto k = k_rows_inv<C, NX, EPI, NT>;
   if (set_smem(k, smem)) return PSFD_E_CUDA;
   k<<<dim3(a.nslab * (a.ny / rb), 3, a.nrhs), NT, smem, a.stream>>>(a, uin, rb);
@@ -107,7 +107,7 @@ template <typename C, int NY, bool INV>
 int launch_cols(const OpCall<C>& a) {
   constexpr int NT = 256;
   const int tx = a.nx < Tune<C>::COL_TILE ? a.nx : Tune<C>::COL_TILE;
-  const size_t smem = (size_t)(tx * (NY + 1) + NY) * sizeof(C);
+  const size_t smem = (size_t)(tx * (fft_phys(NY) | 1) + NY) * sizeof(C);
   auto k = k_cols<C, NY, INV, NT>;
   if (set_smem(k, smem)) return PSFD_E_CUDA;
   k<<<dim3(a.nslab * (a.nx / tx), 3, a.nrhs), NT, smem, a.stream>>>(a, tx);
@@ -118,7 +118,7 @@ int launch_cols(const OpCall<C>& a) {
 template <typename C, int NF>
 size_t zcol_smem(int tx) {
   using R = typename RealOf<C>::T;
-  return (size_t)(3 * tx * (NF + 1) + NF) * sizeof(C) + 3 * NF * sizeof(R) + 7 * tx * sizeof(C) +
+  return (size_t)(3 * tx * (fft_phys(NF) | 1) + NF) * sizeof(C) + 3 * NF * sizeof(R) + 7 * tx * sizeof(C) +
          2 * tx * sizeof(R) + 16;
 }
 

@@ -96,8 +96,9 @@ Plan make_plan(const psfd_grid& g, int precision, int max_rhs) {
   size_t b = 0;
   b += p.plane * g.nslab * (16 + 8 + 16);                   // V64, V32, eps staging
   b += (size_t)(g.nx + g.ny + g.nf) * 16;                   // twiddles
-  b += R * (sizeof(RhsParam) + 2 * sizeof(double));         // illumination parameters
-  b += R * p.plane * sizeof(ModeEntry);                     // mode tables
+  b += R * (sizeof(RhsParam) + 4 * sizeof(double));         // illumination parameters
+  b += R * p.plane * (sizeof(ModeEntry) + sizeof(ModeF32)); // mode tables (FP64 and FP32)
+  b += (size_t)g.nf * (3 * sizeof(float) + sizeof(double));   // kz tables
   b += R * p.U * 16 * 4;                                    // b64, x64, r64, work64
   b += R * 6 * p.plane * 16;                                // side spectra
   if (precision == PSFD_FP64) b += R * p.U * 16 * 5;        // r0, p, v, s, t
@@ -138,8 +139,11 @@ struct psfd_ctx {
   double2 *V64 = nullptr, *eps_stage = nullptr, *twx = nullptr, *twy = nullptr, *twz = nullptr;
   float2* V32 = nullptr;
   RhsParam* rhsp = nullptr;
-  double *slot_qix = nullptr, *slot_qiy = nullptr;
+  double* slot_par = nullptr;  // [slot][4]: q_inc x, q_inc y, cos phi, sin phi
   ModeEntry* modes = nullptr;
+  ModeF32* modes32 = nullptr;
+  float* ktab32 = nullptr;
+  double* ktab64 = nullptr;
   double2* d_eps_l = nullptr;
   double* d_d_l = nullptr;
   int stack_cap = 0;
@@ -284,9 +288,11 @@ int psfd_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rh
   A(&ctx->twy, grid->ny);
   A(&ctx->twz, grid->nf);
   A(&ctx->rhsp, R);
-  A(&ctx->slot_qix, R);
-  A(&ctx->slot_qiy, R);
+  A(&ctx->slot_par, 4 * R);
   A(&ctx->modes, R * P.plane);
+  A(&ctx->modes32, R * P.plane);
+  A(&ctx->ktab32, 3 * (size_t)grid->nf);
+  A(&ctx->ktab64, grid->nf);
   A(&ctx->anomaly, 1);
   A(&ctx->b64, R * P.U);
   A(&ctx->x64, R * P.U);
@@ -326,6 +332,22 @@ int psfd_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rh
   cudaError_t e = cudaMemcpy(ctx->twx, tx.data(), tx.size() * 16, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ctx->twy, ty.data(), ty.size() * 16, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ctx->twz, tz.data(), tz.size() * 16, cudaMemcpyHostToDevice);
+  {
+    // signed z wavenumbers kz_l = 2 pi l / (nf dz), and |kz_l| split into FP32 hi + lo
+    std::vector<float> k32(3 * (size_t)grid->nf);
+    std::vector<double> k64(grid->nf);
+    for (int l = 0; l < grid->nf; ++l) {
+      const int lf = l < (grid->nf + 1) / 2 ? l : l - grid->nf;
+      const double k = 2.0 * kPi * (double)lf / ((double)grid->nf * grid->dz);
+      k64[l] = k;
+      const float hi = (float)std::fabs(k);
+      k32[l] = hi;
+      k32[grid->nf + l] = (float)(std::fabs(k) - (double)hi);
+      k32[2 * grid->nf + l] = (float)k;
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->ktab32, k32.data(), sizeof(float) * k32.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->ktab64, k64.data(), sizeof(double) * k64.size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMemset(ctx->sc, 0, sizeof(KScal) * R);
   if (e == cudaSuccess) e = cudaMemset(ctx->sc64, 0, sizeof(KScal) * R);
   if (e == cudaSuccess) e = cudaMemset(ctx->side64, 0, sizeof(double2) * R * 6 * P.plane);
@@ -409,13 +431,17 @@ static int build_tables(psfd_ctx* ctx) {
   m.k0 = ctx->k0;
   m.eps_bg = g.eps_bg;
   m.L = ctx->L;
-  m.slot_qix = ctx->slot_qix;
-  m.slot_qiy = ctx->slot_qiy;
+  m.dz = g.dz;
+  m.kb = ctx->kb;
+  m.slot_par = ctx->slot_par;
+  m.modes32 = ctx->modes32;
   m.stack.n_layers = ctx->n_layers;
   m.stack.reflect = ctx->have_stack ? 1 : 0;
   m.stack.eps = ctx->d_eps_l;
   m.stack.d = ctx->d_d_l;
   m.stack.eps_sub = ctx->eps_sub;
+  stack_dedup(m.stack, ctx->h_eps_l.data(), ctx->h_d_l.data(), ctx->n_layers, make_double2(g.eps_bg, 0.0),
+              ctx->eps_sub);
   m.modes = ctx->modes;
   m.anomaly = ctx->anomaly;
   RC(launch_modes(m, ctx->n_slots, ctx->stream));
@@ -433,7 +459,7 @@ int psfd_set_illumination(psfd_ctx* ctx, int n_rhs, const double* theta_deg, con
     return ctx->fail(PSFD_E_ARG, "invalid illumination arguments");
   const psfd_grid& g = ctx->g;
   std::map<std::pair<double, double>, int> slots;
-  std::vector<double> sqx, sqy;
+  std::vector<double> spar;
   ctx->h_rhsp.assign(n_rhs, RhsParam{});
   ctx->h_nord.assign(n_rhs, 0);
   ctx->h_mn.assign((size_t)n_rhs * ctx->plan.max_orders * 2, 0);
@@ -450,10 +476,9 @@ int psfd_set_illumination(psfd_ctx* ctx, int n_rhs, const double* theta_deg, con
     auto key = std::make_pair(theta_deg[i], phi_deg[i]);
     auto it = slots.find(key);
     if (it == slots.end()) {
-      const int s = (int)sqx.size();
+      const int s = (int)(spar.size() / 4);
       slots[key] = s;
-      sqx.push_back(p.qix);
-      sqy.push_back(p.qiy);
+      spar.insert(spar.end(), {p.qix, p.qiy, p.cphi, p.sphi});
       p.slot = s;
     } else {
       p.slot = it->second;
@@ -481,9 +506,8 @@ int psfd_set_illumination(psfd_ctx* ctx, int n_rhs, const double* theta_deg, con
     ctx->h_nord[i] = cnt;
   }
   ctx->n_rhs = n_rhs;
-  ctx->n_slots = (int)sqx.size();
-  CK(cudaMemcpyAsync(ctx->slot_qix, sqx.data(), sizeof(double) * sqx.size(), cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->slot_qiy, sqy.data(), sizeof(double) * sqy.size(), cudaMemcpyHostToDevice, ctx->stream));
+  ctx->n_slots = (int)(spar.size() / 4);
+  CK(cudaMemcpyAsync(ctx->slot_par, spar.data(), sizeof(double) * spar.size(), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_nord, ctx->h_nord.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_mn, ctx->h_mn.data(), sizeof(int) * ctx->h_mn.size(), cudaMemcpyHostToDevice,
                      ctx->stream));
@@ -512,6 +536,9 @@ static OpCall<C> base_call(psfd_ctx* ctx, int rhs0, int nrhs, const C* V) {
   a.twz = ctx->twz;
   a.rhsp = ctx->rhsp;
   a.modes = ctx->modes;
+  a.modes32 = ctx->modes32;
+  a.ktab32 = ctx->ktab32;
+  a.ktab64 = ctx->ktab64;
   a.partials = ctx->partials;
   a.maxblk = ctx->plan.maxblk;
   a.stream = ctx->stream;

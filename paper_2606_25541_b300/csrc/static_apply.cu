@@ -69,6 +69,21 @@ __global__ void k_static_params(RhsParam* rp, double* sq, double qix, double qiy
   *rp = p;
   sq[0] = qix;
   sq[1] = qiy;
+  sq[2] = cphi;
+  sq[3] = sphi;
+}
+
+// kz_l = 2 pi l / (nf dz): FP32 |kz| hi / lo and signed kz, FP64 signed kz.
+__global__ void k_static_ktab(float* k32, double* k64, int nf, double dz) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nf; l += gridDim.x * blockDim.x) {
+    const int lf = fft_freq(l, nf);
+    const double k = 6.283185307179586476925286766559 * (double)lf / ((double)nf * dz);
+    k64[l] = k;
+    const float hi = (float)fabs(k);
+    k32[l] = hi;
+    k32[nf + l] = (float)(fabs(k) - (double)hi);
+    k32[2 * nf + l] = (float)k;
+  }
 }
 
 // V = k0^2 (eps - eps_bg) formed in FP64 and rounded to FP32 (as psfd_set_potential does).
@@ -101,7 +116,10 @@ extern "C" int psfd_apply_fp32_static(const psfd_grid* g, int n_layers, const do
   const size_t o_twy = off; off = align256(off + g->ny * sizeof(double2));
   const size_t o_twz = off; off = align256(off + g->nf * sizeof(double2));
   const size_t o_rhs = off; off = align256(off + sizeof(RhsParam));
-  const size_t o_sq = off; off = align256(off + 2 * sizeof(double));
+  const size_t o_sq = off; off = align256(off + 4 * sizeof(double));
+  const size_t o_k32 = off; off = align256(off + 3 * (size_t)g->nf * sizeof(float));
+  const size_t o_k64 = off; off = align256(off + (size_t)g->nf * sizeof(double));
+  const size_t o_m32 = off; off = align256(off + plane * sizeof(ModeF32));
   const size_t o_epsl = off; off = align256(off + kMaxLayers * sizeof(double2));
   const size_t o_dl = off; off = align256(off + kMaxLayers * sizeof(double));
   const size_t o_anom = off; off = align256(off + sizeof(int));
@@ -157,10 +175,13 @@ extern "C" int psfd_apply_fp32_static(const psfd_grid* g, int n_layers, const do
   RhsParam* rhsp = reinterpret_cast<RhsParam*>(base + o_rhs);
   double* sq = reinterpret_cast<double*>(base + o_sq);
   k_static_params<<<1, 1, 0, st>>>(rhsp, sq, qix, qiy, std::cos(ph), std::sin(ph));
+  float* k32 = reinterpret_cast<float*>(base + o_k32);
+  double* k64 = reinterpret_cast<double*>(base + o_k64);
+  k_static_ktab<<<1, 256, 0, st>>>(k32, k64, g->nf, g->dz);
   float2* V32 = reinterpret_cast<float2*>(base + o_V);
   k_static_potential<<<592, 256, 0, st>>>((size_t)g->nslab * plane, static_cast<const double2*>(eps), k0 * k0,
                                           g->eps_bg, V32);
-  count_launch(5);
+  count_launch(6);
   if (cudaGetLastError() != cudaSuccess) return PSFD_E_CUDA;
 
   ModeEntry* modes = reinterpret_cast<ModeEntry*>(base + o_modes);
@@ -172,14 +193,17 @@ extern "C" int psfd_apply_fp32_static(const psfd_grid* g, int n_layers, const do
   m.k0 = k0;
   m.eps_bg = g->eps_bg;
   m.L = 0.5 * g->nf * g->dz;
-  m.slot_qix = sq;
-  m.slot_qiy = sq + 1;
+  m.dz = g->dz;
+  m.kb = kb;
+  m.slot_par = sq;
   m.stack.n_layers = n_layers;
   m.stack.reflect = 1;
   m.stack.eps = reinterpret_cast<const double2*>(base + o_epsl);
   m.stack.d = reinterpret_cast<const double*>(base + o_dl);
   m.stack.eps_sub = make_double2(n_sub[0] * n_sub[0] - n_sub[1] * n_sub[1], 2.0 * n_sub[0] * n_sub[1]);
+  stack_dedup(m.stack, eps_l, d_l, n_layers, make_double2(g->eps_bg, 0.0), m.stack.eps_sub);
   m.modes = modes;
+  m.modes32 = reinterpret_cast<ModeF32*>(base + o_m32);
   m.anomaly = reinterpret_cast<int*>(base + o_anom);
   if ((rc = launch_modes(m, 1, st))) return rc;
 
@@ -200,6 +224,9 @@ extern "C" int psfd_apply_fp32_static(const psfd_grid* g, int n_layers, const do
   a.twz = twz;
   a.rhsp = rhsp;
   a.modes = modes;
+  a.modes32 = m.modes32;
+  a.ktab32 = k32;
+  a.ktab64 = k64;
   a.active = nullptr;
   a.in_mode = IN_PLAIN;
   a.u = static_cast<const float2*>(u);

@@ -70,13 +70,85 @@ __device__ double2 parratt_d(double k02, double q2, double2 eps_amb, const Stack
   return gam;
 }
 
+// The same recursion for s and p at once, with the square roots, Fresnel coefficients
+// and layer phase factors taken once per distinct medium / interface / layer class.
+__device__ void parratt_dedup_d(double k02, double q2, const StackDev& st, double2& rs, double2& rp) {
+  double2 kz[kMaxMat], fs[kMaxIface], fp[kMaxIface], ph[kMaxPh];
+  for (int m = 0; m < st.n_mat; ++m) kz[m] = kz_of(k02, st.mat_eps[m], q2);
+  for (int i = 0; i < st.n_iface; ++i) {
+    const int ia = st.iface_a[i], ib = st.iface_b[i];
+    fs[i] = fresnel_d(kz[ia], kz[ib], st.mat_eps[ia], st.mat_eps[ib], 0);
+    fp[i] = fresnel_d(kz[ia], kz[ib], st.mat_eps[ia], st.mat_eps[ib], 1);
+  }
+  for (int p = 0; p < st.n_ph; ++p) {
+    const double2 k = kz[st.ph_mat[p]];
+    ph[p] = cexp_d(make_double2(-2.0 * k.y * st.ph_d[p], 2.0 * k.x * st.ph_d[p]));
+  }
+  const int M = st.n_layers;
+  double2 gs = fs[st.iface_of[M]], gp = fp[st.iface_of[M]];
+  const double2 one = make_double2(1.0, 0.0);
+  for (int j = M; j >= 1; --j) {
+    const double2 e = ph[st.layer_ph[j - 1]];
+    const int f = st.iface_of[j - 1];
+    const double2 ges = cmul(gs, e), gep = cmul(gp, e);
+    gs = cdiv(cadd(fs[f], ges), cadd(one, cmul(fs[f], ges)));
+    gp = cdiv(cadd(fp[f], gep), cadd(one, cmul(fp[f], gep)));
+  }
+  rs = gs;
+  rp = gp;
+}
+
+void stack_dedup(StackDev& st, const double2* eps_layers, const double* d_layers, int n_layers, double2 eps_amb,
+                 double2 eps_sub) {
+  st.n_mat = st.n_iface = st.n_ph = 0;
+  if (n_layers > kStackMaxLayers) return;
+  int med[kStackMaxLayers + 2];
+  auto mat_id = [&](double2 e) -> int {
+    for (int m = 0; m < st.n_mat; ++m)
+      if (st.mat_eps[m].x == e.x && st.mat_eps[m].y == e.y) return m;
+    if (st.n_mat == kMaxMat) return -1;
+    st.mat_eps[st.n_mat] = e;
+    return st.n_mat++;
+  };
+  for (int j = 0; j < n_layers + 2; ++j) {
+    const double2 e = j == 0 ? eps_amb : (j == n_layers + 1 ? eps_sub : eps_layers[j - 1]);
+    med[j] = mat_id(e);
+    if (med[j] < 0) { st.n_mat = 0; return; }
+  }
+  for (int j = 0; j <= n_layers; ++j) {
+    int id = -1;
+    for (int i = 0; i < st.n_iface; ++i)
+      if (st.iface_a[i] == med[j] && st.iface_b[i] == med[j + 1]) id = i;
+    if (id < 0) {
+      if (st.n_iface == kMaxIface) { st.n_mat = 0; return; }
+      id = st.n_iface++;
+      st.iface_a[id] = (unsigned char)med[j];
+      st.iface_b[id] = (unsigned char)med[j + 1];
+    }
+    st.iface_of[j] = (unsigned char)id;
+  }
+  for (int j = 0; j < n_layers; ++j) {
+    int id = -1;
+    for (int p = 0; p < st.n_ph; ++p)
+      if (st.ph_mat[p] == med[j + 1] && st.ph_d[p] == d_layers[j]) id = p;
+    if (id < 0) {
+      if (st.n_ph == kMaxPh) { st.n_mat = 0; return; }
+      id = st.n_ph++;
+      st.ph_mat[id] = (unsigned char)med[j + 1];
+      st.ph_d[id] = d_layers[j];
+    }
+    st.layer_ph[j] = (unsigned char)id;
+  }
+}
+
 // grid (ceil(nx / 128), ny, n_slots)
 __global__ void k_modes(ModesArgs a) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, slot = blockIdx.z;
   if (x >= a.nx) return;
   const double two_pi = 6.283185307179586476925286766559;
-  const double qx = a.slot_qix[slot] + two_pi * fft_freq(x, a.nx) / (a.nx * a.dx);
-  const double qy = a.slot_qiy[slot] + two_pi * fft_freq(y, a.ny) / (a.ny * a.dy);
+  const double* sp = a.slot_par + 4 * slot;
+  const double qx = sp[0] + two_pi * fft_freq(x, a.nx) / (a.nx * a.dx);
+  const double qy = sp[1] + two_pi * fft_freq(y, a.ny) / (a.ny * a.dy);
   const double q2 = qx * qx + qy * qy;
   const double kb2 = a.k0 * a.k0 * a.eps_bg;
   const double2 beta = csqrt_upper_d(make_double2(kb2 - q2, 0.0));
@@ -86,14 +158,34 @@ __global__ void k_modes(ModesArgs a) {
   m.ebL = cexp_d(make_double2(-beta.y * a.L, beta.x * a.L));
   const double k02 = a.k0 * a.k0;
   const double2 eb = make_double2(a.eps_bg, 0.0);
-  if (a.stack.reflect) {
-    m.rs = parratt_d(k02, q2, eb, a.stack, 0);
-    m.rp = parratt_d(k02, q2, eb, a.stack, 1);
-  } else {
+  if (!a.stack.reflect) {
     m.rs = make_double2(0.0, 0.0);
     m.rp = make_double2(0.0, 0.0);
+  } else if (a.stack.n_mat > 0) {
+    parratt_dedup_d(k02, q2, a.stack, m.rs, m.rp);
+  } else {
+    m.rs = parratt_d(k02, q2, eb, a.stack, 0);
+    m.rp = parratt_d(k02, q2, eb, a.stack, 1);
   }
-  a.modes[((size_t)slot * a.ny + y) * a.nx + x] = m;
+  const size_t idx = ((size_t)slot * a.ny + y) * a.nx + x;
+  a.modes[idx] = m;
+  if (a.modes32) {
+    ModeF32 f;
+    f.qx = (float)qx;
+    f.qy = (float)qy;
+    split_hi_lo(beta, f.bh, f.bl);
+    f.ebL = to_c32(m.ebL);
+    f.bdz = to_c32(cscale(beta, a.dz));
+    f.rs = to_c32(m.rs);
+    f.rp = to_c32(m.rp);
+    const double qn = sqrt(q2);
+    f.hx = (float)(qn > 0.0 ? qx / qn : sp[2]);
+    f.hy = (float)(qn > 0.0 ? qy / qn : sp[3]);
+    f.qnk = (float)(qn / a.kb);
+    f.pad = 0.f;
+    f.bq = to_c32(cscale(beta, 1.0 / a.kb));
+    a.modes32[idx] = f;
+  }
 }
 
 int launch_modes(const ModesArgs& a, int n_slots, cudaStream_t st) {
@@ -155,28 +247,30 @@ __global__ void k_rhs_params(int rhs0, int nrhs, RhsParam* rp, const ModeEntry* 
 
 // b = E_inc + R[E_inc] on the absorber planes (Eqs. (3), (9)): uniform in (x, y),
 // e exp(-i beta00 z_p) + T_R e exp(+i beta00 z_p), z_p = (p + 1/2) dz.
-__global__ void k_build_rhs(int rhs0, int nrhs, const RhsParam* rp, int nslab, int plane, double dz, double2* b) {
-  const size_t per = (size_t)3 * nslab * plane;
-  const size_t total = per * nrhs;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int lr = (int)(i / per);
-    const size_t k = i % per;
-    const int cp = (int)(k / plane);
-    const int c = cp / nslab, p = cp % nslab;
+// grid (3 nslab, nrhs): one CTA per (component, plane); the value is evaluated once.
+__global__ void k_build_rhs(int rhs0, const RhsParam* rp, int nslab, int plane, double dz, double2* b) {
+  __shared__ double2 val;
+  const int cp = blockIdx.x, lr = blockIdx.y;
+  const int c = cp / nslab, p = cp % nslab;
+  if (threadIdx.x == 0) {
     const RhsParam& q = rp[rhs0 + lr];
     const double z = (p + 0.5) * dz;
     const double2 bz = cscale(q.beta00, z);
     const double2 down = cexp_d(make_double2(bz.y, -bz.x));  // exp(-i beta00 z)
     const double2 up = cexp_d(make_double2(-bz.y, bz.x));    // exp(+i beta00 z)
-    b[i] = cadd(cmul(q.e_inc[c], down), cmul(q.r_inc[c], up));
+    val = cadd(cmul(q.e_inc[c], down), cmul(q.r_inc[c], up));
   }
+  __syncthreads();
+  const double2 v = val;
+  double2* dst = b + ((size_t)lr * 3 * nslab + cp) * plane;
+  for (int i = threadIdx.x; i < plane; i += blockDim.x) dst[i] = v;
 }
 
 int launch_rhs(int rhs0, int nrhs, RhsParam* rp, const ModeEntry* modes, int nx, int ny, int nslab, double dz,
                double kb, double2* b, cudaStream_t st) {
   k_rhs_params<<<(nrhs + 63) / 64, 64, 0, st>>>(rhs0, nrhs, rp, modes, nx, ny, kb);
   if (launched() != PSFD_OK) return PSFD_E_CUDA;
-  k_build_rhs<<<1184, 256, 0, st>>>(rhs0, nrhs, rp, nslab, nx * ny, dz, b);
+  k_build_rhs<<<dim3(3 * nslab, nrhs), 256, 0, st>>>(rhs0, rp, nslab, nx * ny, dz, b);
   return launched();
 }
 
@@ -313,21 +407,22 @@ __global__ void __launch_bounds__(256) k_test_fft(C* data, int count, const doub
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int B = N >= 2048 ? 1 : 2048 / N;
   C* tile = reinterpret_cast<C*>(smem);
-  C* tw = tile + B * N;
+  constexpr int PN = fft_phys(N);
+  C* tw = tile + B * PN;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = from_c64<C>(tw64[i]);
   const int f0 = blockIdx.x * B;
   const int nb = min(B, count - f0);
-  for (int i = threadIdx.x; i < nb * N; i += blockDim.x) tile[i] = data[(size_t)f0 * N + i];
+  for (int i = threadIdx.x; i < nb * N; i += blockDim.x) tile[(i / N) * PN + fpad(i % N)] = data[(size_t)f0 * N + i];
   __syncthreads();
-  cta_fft<C, N, INV>(tile, nb, N, 1, tw);
+  cta_fft<C, N, INV>(tile, nb, PN, 1, tw);
   __syncthreads();
-  for (int i = threadIdx.x; i < nb * N; i += blockDim.x) data[(size_t)f0 * N + i] = tile[i];
+  for (int i = threadIdx.x; i < nb * N; i += blockDim.x) data[(size_t)f0 * N + i] = tile[(i / N) * PN + fpad(i % N)];
 }
 
 template <typename C, int N>
 int run_test_fft(C* data, int count, bool inv, const double2* tw) {
   constexpr int B = N >= 2048 ? 1 : 2048 / N;
-  const size_t smem = (size_t)(B * N + N) * sizeof(C);
+  const size_t smem = (size_t)(B * fft_phys(N) + N) * sizeof(C);
   const int grid = (count + B - 1) / B;
   if (inv) {
     auto k = k_test_fft<C, N, true>;

@@ -5,21 +5,38 @@
 
 namespace psfd {
 
+constexpr int kStackMaxLayers = 256;
+constexpr int kMaxMat = 8, kMaxIface = 16, kMaxPh = 8;
+
 struct StackDev {
   int n_layers;
   int reflect;           // 0: no stack (R = 0)
   const double2* eps;    // [n_layers] permittivity, top to bottom
   const double* d;       // [n_layers] thickness, nm
   double2 eps_sub;
+  // A periodic stack has few distinct media, interfaces and (medium, thickness) layers;
+  // when they fit these tables (n_mat > 0) each is evaluated once per mode.
+  int n_mat, n_iface, n_ph;
+  double2 mat_eps[kMaxMat];                     // media: ambient, layers, substrate (deduplicated)
+  unsigned char iface_a[kMaxIface], iface_b[kMaxIface];  // upper / lower medium of an interface
+  unsigned char ph_mat[kMaxPh];
+  double ph_d[kMaxPh];
+  unsigned char iface_of[kStackMaxLayers + 1];  // interface between medium j and j+1
+  unsigned char layer_ph[kStackMaxLayers];      // (medium, thickness) class of layer j
 };
+
+// Fills the deduplication tables of st from host copies of the media (ambient first,
+// then the layers top to bottom, then the substrate); leaves n_mat = 0 if they do not fit.
+void stack_dedup(StackDev& st, const double2* eps_layers, const double* d_layers, int n_layers, double2 eps_amb,
+                 double2 eps_sub);
 
 struct ModesArgs {
   int nx, ny;
-  double dx, dy, k0, eps_bg, L;
-  const double* slot_qix;
-  const double* slot_qiy;
+  double dx, dy, dz, k0, kb, eps_bg, L;
+  const double* slot_par;  // [slot][4]: q_inc x, q_inc y, cos phi, sin phi
   StackDev stack;
-  ModeEntry* modes;  // [slot][ny][nx]
+  ModeEntry* modes;   // [slot][ny][nx]
+  ModeF32* modes32;   // [slot][ny][nx] or null
   int* anomaly;
 };
 
