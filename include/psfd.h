@@ -169,6 +169,53 @@ int psfd_get_rhs(psfd_ctx* ctx, int rhs, double* dst, int where);
  * beta (z wavenumber, Im >= 0) and the stack reflection coefficients r_s, r_p. */
 int psfd_get_mode_tables(psfd_ctx* ctx, int rhs, double* beta, double* r_s, double* r_p);
 
+/* ---------------------------------------------------------------------------------
+ * Serving loop: continuous batching of mask-clip solves (any number of clips, each with
+ * its own grid, stack, permittivity and 1..n illuminations).
+ *
+ * Requests are copied on submit and queued. Each psfd_server_progress call admits queued
+ * requests, in arrival order, into a context of the same grid (a "bucket" with
+ * slots_per_context illumination slots and as many potential slots) as soon as slots are
+ * free -- also while other requests of the bucket are mid-solve -- creating a bucket when
+ * its device footprint fits the HBM budget (idle buckets are released to make room);
+ * it then advances every bucket by one step of the solve engine (the FP32 / FP64 Krylov
+ * iterations, FP64 residuals and orders of all admitted illuminations share launches) and
+ * retires requests whose illuminations are all done. A request's orders do not depend on
+ * which other requests shared its bucket. Single threaded: the caller drives progress. */
+typedef struct psfd_server psfd_server;
+
+typedef struct {
+  psfd_grid grid;          /* discretisation (as for psfd_create) */
+  int n_layers;            /* stack, as for psfd_set_stack */
+  const double* n_complex;
+  const double* thickness_nm;
+  const double* n_sub;
+  const double* eps;       /* host, complex double [nslab][ny][nx] permittivity */
+  int n_rhs;               /* illuminations, as for psfd_set_illumination */
+  const double* theta_deg;
+  const double* phi_deg;
+  const int* pol;
+} psfd_request;
+
+/* precision: PSFD_FP64 or PSFD_FP32_REFINED; hbm_budget: bytes of all buckets (0 = no
+ * limit); opts: solve options for every request (NULL = defaults). */
+int psfd_server_create(psfd_server** out, int precision, size_t hbm_budget, int slots_per_context,
+                       const psfd_solve_opts* opts);
+int psfd_server_destroy(psfd_server* s);
+/* Queue a request (inputs copied); *ticket identifies it. */
+int psfd_server_submit(psfd_server* s, const psfd_request* req, long long* ticket);
+/* Admit, advance every bucket by one engine step, retire; *n_pending = queued + running. */
+int psfd_server_progress(psfd_server* s, int* n_pending);
+/* *state: 0 queued, 1 running, 2 done; *status: PSFD_OK or the request's failure. */
+int psfd_server_status(psfd_server* s, long long ticket, int* state, int* status);
+/* Orders of illumination rhs of a finished request (layout as psfd_diffraction_orders). */
+int psfd_server_orders(psfd_server* s, long long ticket, int rhs, int capacity, int* n_orders, int* mn,
+                       double* amp, double* sp, double* eff);
+/* Forget a finished request. */
+int psfd_server_release(psfd_server* s, long long ticket);
+/* Device bytes held by the buckets and their number. */
+int psfd_server_memory(psfd_server* s, size_t* used, int* n_contexts);
+
 /* Number of CUDA kernels the library has launched since it was loaded (all contexts). */
 int psfd_launch_count(unsigned long long* count);
 

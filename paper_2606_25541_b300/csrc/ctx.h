@@ -1,0 +1,162 @@
+// ctx.h -- the solver context shared by the C ABI (psfd.cu), the solve engine
+// (engine.cu) and the serving loop (server.cu). Private to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/psfd.h"
+#include "internal.h"
+#include "tables.h"
+
+namespace psfd {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+struct Plan {
+  size_t U = 0;      // complex elements per right-hand-side vector
+  size_t plane = 0;  // nx * ny
+  int maxblk = 1;
+  int max_orders = 1;
+  size_t bytes = 0;
+};
+Plan make_plan(const psfd_grid& g, int precision, int max_rhs, int max_clips);
+bool grid_ok(const psfd_grid* g, std::string& why);
+
+// Life cycle of one illumination in a context (see engine.cu).
+enum Phase { PH_FREE = 0, PH_NEW, PH_START, PH_INNER, PH_RESID, PH_DONE };
+
+struct StackHost {
+  std::vector<double2> eps;  // permittivity per layer, top to bottom
+  std::vector<double> d;     // thickness per layer, nm
+  double2 eps_sub{1.0, 0.0};
+  bool set = false;
+};
+
+}  // namespace psfd
+
+struct psfd_ctx {
+  psfd_grid g{};
+  int precision = PSFD_FP64;
+  int max_rhs = 0, max_clips = 1;
+  size_t budget = 0, allocated = 0;
+  cudaStream_t stream = nullptr;
+  psfd::Plan plan;
+  double k0 = 0, kb = 0, L = 0;
+  std::string err;
+  std::vector<void*> allocs;
+
+  // host state
+  bool have_potential = false, have_illum = false, orders_on_host = false;
+  int n_rhs = 0;                      // illuminations of the single-clip API (rhs 0 .. n_rhs-1)
+  psfd::StackHost stack;              // stack of the single-clip API
+  std::vector<psfd::RhsParam> h_rhsp;  // per rhs slot
+  std::vector<int> h_nord, h_mn;
+  std::vector<double> h_ordout;
+  std::vector<double> th, ph;  // angles per rhs slot (degrees)
+  std::vector<int> pol, clip;
+  // engine state per rhs slot
+  std::vector<int> phase, outer, iters, status;
+  std::vector<double> relres;
+  int* h_act = nullptr;      // pinned
+  int* h_act64 = nullptr;    // pinned
+  psfd::KScal* h_sc = nullptr;    // pinned
+  psfd::KScal* h_sc64 = nullptr;  // pinned
+  int* h_mask = nullptr;     // pinned staging for device masks
+
+  // device state
+  double2 *V64 = nullptr, *eps_stage = nullptr, *twx = nullptr, *twy = nullptr, *twz = nullptr;
+  float2* V32 = nullptr;
+  psfd::RhsParam* rhsp = nullptr;
+  double* slot_par = nullptr;  // [rhs][4]: q_inc x, q_inc y, cos phi, sin phi
+  psfd::ModeEntry* modes = nullptr;
+  psfd::ModeF32* modes32 = nullptr;
+  float* ktab32 = nullptr;
+  double* ktab64 = nullptr;
+  double2* d_eps_l = nullptr;
+  double* d_d_l = nullptr;
+  int* anomaly = nullptr;
+  double2 *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *work64 = nullptr, *side64 = nullptr;
+  double2* k64[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  float2 *x32 = nullptr, *r32 = nullptr, *r032 = nullptr, *p32 = nullptr, *v32 = nullptr, *s32 = nullptr,
+         *t32 = nullptr, *work32 = nullptr;
+  double2* partials = nullptr;
+  psfd::KScal *sc = nullptr, *sc64 = nullptr;
+  int *act = nullptr, *act64 = nullptr;
+  int* d_mask[4] = {nullptr, nullptr, nullptr, nullptr};  // per-phase selections
+  int *d_nord = nullptr, *d_mn = nullptr;
+  double* d_ordout = nullptr;
+
+  int fail(int code, const std::string& what) {
+    err = what;
+    return code;
+  }
+  int cuda_fail(cudaError_t e, const char* what) {
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return PSFD_E_CUDA;
+  }
+  template <typename T>
+  int dalloc(T** p, size_t count) {
+    const size_t bytes = (count > 0 ? count : 1) * sizeof(T);
+    if (budget && allocated + bytes > budget)
+      return fail(PSFD_E_BUDGET, "allocation of " + std::to_string(bytes) + " bytes exceeds the HBM budget");
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PSFD_E_NOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    allocs.push_back(q);
+    allocated += bytes;
+    *p = static_cast<T*>(q);
+    return PSFD_OK;
+  }
+  ~psfd_ctx() {
+    for (void* q : allocs) cudaFree(q);
+    for (void* q : {(void*)h_act, (void*)h_act64, (void*)h_sc, (void*)h_sc64, (void*)h_mask})
+      if (q) cudaFreeHost(q);
+  }
+};
+
+#define CK(call)                                             \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return ctx->cuda_fail(e_, #call); \
+  } while (0)
+#define RC(call)                              \
+  do {                                        \
+    int rc_ = (call);                         \
+    if (rc_ < 0) {                            \
+      if (ctx->err.empty()) ctx->err = #call; \
+      return rc_;                             \
+    }                                         \
+  } while (0)
+
+namespace psfd {
+
+// Context with room for max_rhs illuminations over up to max_clips potentials.
+int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs, int max_clips,
+               size_t hbm_budget, cudaStream_t stream);
+
+// Potential of clip `clip` from eps (host or device, complex double [nslab][ny][nx]).
+int ctx_set_potential(psfd_ctx* ctx, int clip, const double* eps, int where);
+
+// Illuminations for rhs slots g0 .. g0+n-1 seeing clip `clip` through the given stack:
+// host anomaly check and order lists, then per-mode tables and right-hand sides on the
+// device. The slots' phase becomes PH_NEW.
+int ctx_set_rhs(psfd_ctx* ctx, int g0, int n, const double* theta, const double* phi, const int* pol, int clip,
+                const StackHost& stack);
+
+// Solve engine: one tick advances every slot by one phase step (see engine.cu).
+int engine_tick(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active);
+psfd_solve_opts solve_defaults(const psfd_solve_opts* opts);
+
+// Copy the orders of the finished slots to the host cache (once per batch of finishes).
+int ctx_orders_to_host(psfd_ctx* ctx);
+
+OpCall<float2> base_call32(psfd_ctx* ctx, int rhs0, int nrhs);
+OpCall<double2> base_call64(psfd_ctx* ctx, int rhs0, int nrhs);
+
+}  // namespace psfd

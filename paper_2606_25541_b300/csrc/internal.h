@@ -14,8 +14,10 @@ struct RhsParam {
   double2 e_inc[3];   // incident polarisation vector (bilinear unit)
   double2 r_inc[3];   // T_R(q_00) e_inc: reflected incident amplitude at z_top
   double2 beta00;     // z wavenumber of the specular order
-  int slot;           // row of the mode tables (illuminations at one angle share it)
+  int slot;           // row of the mode tables
   int pol;
+  int clip;           // which potential (mask clip) of the context this illumination sees
+  int pad;
 };
 
 // Per transverse mode (m, n) and angle slot, computed in FP64 by the stack kernel.
@@ -129,6 +131,10 @@ struct KrylovCall {
   int max_iter;
   int check_every;
 };
-template <typename C> int bicgstab(const KrylovCall<C>& k);
+// Start BiCGStab for the right-hand sides selected by mask (device, per global rhs; null =
+// all): x = 0, r = r0 = b, scalars reset; others keep their state. No host synchronisation.
+template <typename C> int bicg_start(const KrylovCall<C>& k, const int* mask);
+// `iters` BiCGStab iterations for every right-hand side whose device flag act is set.
+template <typename C> int bicg_iterate(const KrylovCall<C>& k, int iters);
 
 }  // namespace psfd

@@ -51,12 +51,13 @@ __device__ __forceinline__ void vec_block_dots(typename Acc<C>::T d0, typename A
   block_write_dots(dt, mask, dst, stride, sh);
 }
 
-// x = 0, r = r0 = b, p = v = 0; partial ||b||^2 into slot 2.
+// x = 0, r = r0 = b, p = v = 0; partial ||b||^2 into slot 2 (right-hand sides in mask only).
 template <typename C>
-__global__ void __launch_bounds__(VEC_NT) k_bicg_init(int n, int nblk, int rhs0, const C* b, C* x, C* r, C* r0,
-                                                       C* p, C* v, double2* partials, int maxblk) {
+__global__ void __launch_bounds__(VEC_NT) k_bicg_init(int n, int nblk, int rhs0, const int* mask, const C* b, C* x,
+                                                       C* r, C* r0, C* p, C* v, double2* partials, int maxblk) {
   using R = typename RealOf<C>::T;
   const int blk = blockIdx.x, lr = blockIdx.y, g = rhs0 + lr;
+  if (mask && !mask[g]) return;
   const size_t off = (size_t)lr * n;
   const int chunk = (n + nblk - 1) / nblk;
   const int lo = blk * chunk, hi = min(n, lo + chunk);
@@ -103,11 +104,13 @@ __device__ __forceinline__ const double2* slot_ptr(const double2* partials, int 
   return partials + ((size_t)g * NDOT + slot) * maxblk;
 }
 
-// ||b||^2 -> scalars; activity from act_in (null = all) and b != 0.
+// ||b||^2 -> scalars and activity (b != 0) for the right-hand sides in mask (null = all);
+// the others keep their state.
 static __global__ void __launch_bounds__(VEC_NT) k_scal_init(int rhs0, int nblk, const double2* partials, int maxblk,
-                                                       const int* act_in, KScal* sc, int* act) {
+                                                       const int* mask, KScal* sc, int* act) {
   __shared__ double2 sh[33];
   const int g = rhs0 + blockIdx.x;
+  if (mask && !mask[g]) return;
   const double2 bb = block_sum_fixed(slot_ptr(partials, g, 2, maxblk), nblk, sh);
   if (threadIdx.x == 0) {
     KScal s;
@@ -120,7 +123,7 @@ static __global__ void __launch_bounds__(VEC_NT) k_scal_init(int rhs0, int nblk,
     s.scale = sc[g].scale;
     s.iters = 0;
     s.status = PSFD_OK;
-    s.active = ((act_in == nullptr) || act_in[g]) && bb.x > 0.0;
+    s.active = bb.x > 0.0;
     s.pad = 0;
     sc[g] = s;
     act[g] = s.active;

@@ -3,5 +3,10 @@
 
 namespace psfd {
 template <> int op_apply<float2>(const OpCall<float2>& a) { return op_apply_impl<float2>(a); }
-template <> int bicgstab<float2>(const KrylovCall<float2>& k) { return bicgstab_impl<float2>(k); }
+template <> int bicg_start<float2>(const KrylovCall<float2>& k, const int* mask) {
+  return bicg_start_impl<float2>(k, mask);
+}
+template <> int bicg_iterate<float2>(const KrylovCall<float2>& k, int iters) {
+  return bicg_iterate_impl<float2>(k, iters);
+}
 }  // namespace psfd

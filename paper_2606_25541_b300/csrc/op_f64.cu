@@ -3,7 +3,12 @@
 
 namespace psfd {
 template <> int op_apply<double2>(const OpCall<double2>& a) { return op_apply_impl<double2>(a); }
-template <> int bicgstab<double2>(const KrylovCall<double2>& k) { return bicgstab_impl<double2>(k); }
+template <> int bicg_start<double2>(const KrylovCall<double2>& k, const int* mask) {
+  return bicg_start_impl<double2>(k, mask);
+}
+template <> int bicg_iterate<double2>(const KrylovCall<double2>& k, int iters) {
+  return bicg_iterate_impl<double2>(k, iters);
+}
 
 int op_blocks_per_rhs(int nx, int ny, int nslab, bool fp64) {
   return fp64 ? blocks_per_rhs_t<double2>(nx, ny, nslab) : blocks_per_rhs_t<float2>(nx, ny, nslab);

@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(NT) k_plane_fwd(OpCall<C> a) {
   for (int i = threadIdx.x; i < NY; i += NT) twy[i] = from_c64<C>(a.twy[i]);
   const InScal<C> s = load_in_scalars<C, IN>(a, g);
   const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
-  const C* Vp = a.V + (size_t)p * (NX * NY);
+  const C* Vp = a.V + ((size_t)a.rhsp[g].clip * a.nslab + p) * (NX * NY);
   for (int i = threadIdx.x; i < NX * NY; i += NT) {
     C val = input_elem<C, IN>(a, plane + i, s);
     tile[plane_slot<NX>(i)] = cmul(Vp[i], val);
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(OpCall<C> a, int rb) {
   for (int i = threadIdx.x; i < NX; i += NT) tw[i] = from_c64<C>(a.twx[i]);
   const InScal<C> s = load_in_scalars<C, IN>(a, g);
   const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
-  const C* Vp = a.V + ((size_t)p * a.ny + y0) * NX;
+  const C* Vp = a.V + (((size_t)a.rhsp[g].clip * a.nslab + p) * a.ny + y0) * NX;
   for (int i = threadIdx.x; i < rb * NX; i += NT)
     tile[(i / NX) * RP + fpad(i % NX)] = cmul(Vp[i], input_elem<C, IN>(a, base + i, s));
   __syncthreads();

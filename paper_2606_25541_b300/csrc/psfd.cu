@@ -1,18 +1,15 @@
-// psfd.cu -- the C ABI (include/psfd.h): solver context, device memory plan, set-up,
-// the FP64 and FP32-with-FP64-defect-correction solve drivers, and result read-back.
+// psfd.cu -- the C ABI (include/psfd.h): solver context, device memory plan, set-up of
+// potentials and illuminations, one-application entry point, read-back, and the launch
+// accounting / event profiler. The solve itself is the engine in engine.cu.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
-#include <map>
 #include <string>
-#include <utility>
 #include <vector>
 
-#include "../../include/psfd.h"
-#include "internal.h"
-#include "tables.h"
+#include "ctx.h"
 
 using namespace psfd;
 
@@ -67,21 +64,11 @@ void prof_end(int cls, cudaStream_t st, double bytes, double flops) {
   g_recs.push_back({cls, g_open[cls], e, bytes, flops});
   g_open[cls] = nullptr;
 }
-}  // namespace psfd
 
-namespace {
-
-constexpr double kPi = 3.14159265358979323846264338327950288;
-
-struct Plan {
-  size_t U = 0;      // complex elements per right-hand-side vector
-  size_t plane = 0;  // nx * ny
-  int maxblk = 1;
-  int max_orders = 1;
-  size_t bytes = 0;
-};
-
-Plan make_plan(const psfd_grid& g, int precision, int max_rhs) {
+// ---------------------------------------------------------------------------
+// plan, validation, tables
+// ---------------------------------------------------------------------------
+Plan make_plan(const psfd_grid& g, int precision, int max_rhs, int max_clips) {
   Plan p;
   p.plane = (size_t)g.nx * g.ny;
   p.U = 3 * (size_t)g.nslab * p.plane;
@@ -92,118 +79,25 @@ Plan make_plan(const psfd_grid& g, int precision, int max_rhs) {
   const double ax = kb * g.nx * g.dx / (2 * kPi), ay = kb * g.ny * g.dy / (2 * kPi);
   const double bound = (2.0 * ax + 3.0) * (2.0 * ay + 3.0);
   p.max_orders = (int)std::min<double>((double)p.plane, bound);
-  const size_t R = (size_t)max_rhs;
+  const size_t R = (size_t)max_rhs, Cl = (size_t)max_clips;
   size_t b = 0;
-  b += p.plane * g.nslab * (16 + 8 + 16);                   // V64, V32, eps staging
-  b += (size_t)(g.nx + g.ny + g.nf) * 16;                   // twiddles
-  b += R * (sizeof(RhsParam) + 4 * sizeof(double));         // illumination parameters
-  b += R * p.plane * (sizeof(ModeEntry) + sizeof(ModeF32)); // mode tables (FP64 and FP32)
-  b += (size_t)g.nf * (3 * sizeof(float) + sizeof(double));   // kz tables
-  b += R * p.U * 16 * 4;                                    // b64, x64, r64, work64
-  b += R * 6 * p.plane * 16;                                // side spectra
-  if (precision == PSFD_FP64) b += R * p.U * 16 * 5;        // r0, p, v, s, t
-  else b += R * p.U * 8 * 8;                                // x, r, r0, p, v, s, t, work (FP32)
-  b += R * NDOT * (size_t)p.maxblk * 16;                    // partial sums
-  b += R * (2 * sizeof(KScal) + 2 * sizeof(int));           // scalars, flags
+  b += p.plane * g.nslab * (Cl * (16 + 8) + 16);             // V64, V32 per clip, eps staging
+  b += (size_t)(g.nx + g.ny + g.nf) * 16;                    // twiddles
+  b += R * (sizeof(RhsParam) + 4 * sizeof(double));          // illumination parameters
+  b += R * p.plane * (sizeof(ModeEntry) + sizeof(ModeF32));  // mode tables (FP64 and FP32)
+  b += (size_t)g.nf * (3 * sizeof(float) + sizeof(double));  // kz tables
+  b += R * p.U * 16 * 4;                                     // b64, x64, r64, work64
+  b += R * 6 * p.plane * 16;                                 // side spectra
+  if (precision == PSFD_FP64) b += R * p.U * 16 * 5;         // r0, p, v, s, t
+  else b += R * p.U * 8 * 8;                                 // x, r, r0, p, v, s, t, work (FP32)
+  b += R * NDOT * (size_t)p.maxblk * 16;                     // partial sums
+  b += R * (2 * sizeof(KScal) + 6 * sizeof(int));            // scalars, flags, masks
   b += R * (size_t)p.max_orders * (2 * sizeof(int) + 12 * sizeof(double)) + R * sizeof(int);
   p.bytes = b;
   return p;
 }
 
-}  // namespace
-
-struct psfd_ctx {
-  psfd_grid g{};
-  int precision = PSFD_FP64;
-  int max_rhs = 0;
-  size_t budget = 0, allocated = 0;
-  cudaStream_t stream = nullptr;
-  Plan plan;
-  double k0 = 0, kb = 0, L = 0;
-  std::string err;
-  std::vector<void*> allocs;
-
-  // host state
-  bool have_stack = false, have_potential = false, have_illum = false, solved = false, orders_on_host = false;
-  int n_layers = 0, n_rhs = 0, n_slots = 0;
-  std::vector<double2> h_eps_l;
-  std::vector<double> h_d_l;
-  double2 eps_sub{1.0, 0.0};
-  std::vector<RhsParam> h_rhsp;
-  std::vector<int> h_nord, h_mn;
-  std::vector<double> h_ordout;
-  int* h_act = nullptr;   // pinned
-  KScal* h_sc = nullptr;  // pinned
-
-  // device state
-  double2 *V64 = nullptr, *eps_stage = nullptr, *twx = nullptr, *twy = nullptr, *twz = nullptr;
-  float2* V32 = nullptr;
-  RhsParam* rhsp = nullptr;
-  double* slot_par = nullptr;  // [slot][4]: q_inc x, q_inc y, cos phi, sin phi
-  ModeEntry* modes = nullptr;
-  ModeF32* modes32 = nullptr;
-  float* ktab32 = nullptr;
-  double* ktab64 = nullptr;
-  double2* d_eps_l = nullptr;
-  double* d_d_l = nullptr;
-  int stack_cap = 0;
-  int* anomaly = nullptr;
-  double2 *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *work64 = nullptr, *side64 = nullptr;
-  double2* k64[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  float2 *x32 = nullptr, *r32 = nullptr, *r032 = nullptr, *p32 = nullptr, *v32 = nullptr, *s32 = nullptr,
-         *t32 = nullptr, *work32 = nullptr;
-  double2* partials = nullptr;
-  KScal *sc = nullptr, *sc64 = nullptr;
-  int *act = nullptr, *act64 = nullptr;
-  int *d_nord = nullptr, *d_mn = nullptr;
-  double* d_ordout = nullptr;
-
-  int fail(int code, const std::string& what) {
-    err = what;
-    return code;
-  }
-  int cuda_fail(cudaError_t e, const char* what) {
-    err = std::string(what) + ": " + cudaGetErrorString(e);
-    return PSFD_E_CUDA;
-  }
-  template <typename T>
-  int dalloc(T** p, size_t count) {
-    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-    if (budget && allocated + bytes > budget)
-      return fail(PSFD_E_BUDGET, "allocation of " + std::to_string(bytes) + " bytes exceeds the HBM budget");
-    void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(PSFD_E_NOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
-    }
-    allocs.push_back(q);
-    allocated += bytes;
-    *p = static_cast<T*>(q);
-    return PSFD_OK;
-  }
-  ~psfd_ctx() {
-    for (void* q : allocs) cudaFree(q);
-    if (h_act) cudaFreeHost(h_act);
-    if (h_sc) cudaFreeHost(h_sc);
-  }
-};
-
-#define CK(call)                                        \
-  do {                                                  \
-    cudaError_t e_ = (call);                            \
-    if (e_ != cudaSuccess) return ctx->cuda_fail(e_, #call); \
-  } while (0)
-#define RC(call)                                  \
-  do {                                            \
-    int rc_ = (call);                             \
-    if (rc_ < 0) {                                \
-      if (ctx->err.empty()) ctx->err = #call;     \
-      return rc_;                                 \
-    }                                             \
-  } while (0)
-
-static bool grid_ok(const psfd_grid* g, std::string& why) {
+bool grid_ok(const psfd_grid* g, std::string& why) {
   if (!g) { why = "grid is null"; return false; }
   if (!fft_length_supported(g->nx) || !fft_length_supported(g->ny)) { why = "unsupported nx or ny"; return false; }
   if (!fft_length_supported(g->nf)) { why = "unsupported nf"; return false; }
@@ -225,49 +119,22 @@ static std::vector<double2> twiddles(int n) {
   return t;
 }
 
-extern "C" {
-
-const char* psfd_strerror(int s) {
-  switch (s) {
-    case PSFD_OK: return "ok";
-    case PSFD_E_ARG: return "invalid argument";
-    case PSFD_E_NOMEM: return "device allocation failed";
-    case PSFD_E_BUDGET: return "HBM budget exceeded";
-    case PSFD_E_CUDA: return "CUDA error";
-    case PSFD_E_NOT_CONVERGED: return "not converged";
-    case PSFD_E_BREAKDOWN: return "Krylov breakdown";
-    case PSFD_E_ANOMALY: return "Rayleigh anomaly (a diffraction order has beta = 0)";
-    case PSFD_E_TIMEOUT: return "device wait timed out";
-    case PSFD_E_STATE: return "call out of order";
-  }
-  return "unknown status";
-}
-
-const char* psfd_last_error(const psfd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
-
-int psfd_supported_length(int n) { return fft_length_supported(n) ? 1 : 0; }
-
-int psfd_workspace_bytes(const psfd_grid* grid, int precision, int max_rhs, size_t* bytes) {
-  std::string why;
-  if (!bytes || !grid_ok(grid, why) || max_rhs < 1) return PSFD_E_ARG;
-  *bytes = make_plan(*grid, precision, max_rhs).bytes;
-  return PSFD_OK;
-}
-
-int psfd_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs, size_t hbm_budget,
-                void* stream) {
+int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs, int max_clips,
+               size_t hbm_budget, cudaStream_t stream) {
   if (!out) return PSFD_E_ARG;
   *out = nullptr;
   std::string why;
-  if (!grid_ok(grid, why) || max_rhs < 1 || (precision != PSFD_FP64 && precision != PSFD_FP32_REFINED))
+  if (!grid_ok(grid, why) || max_rhs < 1 || max_clips < 1 ||
+      (precision != PSFD_FP64 && precision != PSFD_FP32_REFINED))
     return PSFD_E_ARG;
   psfd_ctx* ctx = new psfd_ctx();
   ctx->g = *grid;
   ctx->precision = precision;
   ctx->max_rhs = max_rhs;
+  ctx->max_clips = max_clips;
   ctx->budget = hbm_budget;
-  ctx->stream = (cudaStream_t)stream;
-  ctx->plan = make_plan(*grid, precision, max_rhs);
+  ctx->stream = stream;
+  ctx->plan = make_plan(*grid, precision, max_rhs, max_clips);
   ctx->k0 = 2.0 * kPi / grid->wavelength;
   ctx->kb = ctx->k0 * std::sqrt(grid->eps_bg);
   ctx->L = 0.5 * grid->nf * grid->dz;
@@ -281,8 +148,8 @@ int psfd_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rh
   auto A = [&](auto** p, size_t n) {
     if (rc == PSFD_OK) rc = ctx->dalloc(p, n);
   };
-  A(&ctx->V64, P.plane * grid->nslab);
-  A(&ctx->V32, P.plane * grid->nslab);
+  A(&ctx->V64, P.plane * grid->nslab * max_clips);
+  A(&ctx->V32, P.plane * grid->nslab * max_clips);
   A(&ctx->eps_stage, P.plane * grid->nslab);
   A(&ctx->twx, grid->nx);
   A(&ctx->twy, grid->ny);
@@ -293,6 +160,8 @@ int psfd_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rh
   A(&ctx->modes32, R * P.plane);
   A(&ctx->ktab32, 3 * (size_t)grid->nf);
   A(&ctx->ktab64, grid->nf);
+  A(&ctx->d_eps_l, kStackMaxLayers);
+  A(&ctx->d_d_l, kStackMaxLayers);
   A(&ctx->anomaly, 1);
   A(&ctx->b64, R * P.U);
   A(&ctx->x64, R * P.U);
@@ -316,6 +185,7 @@ int psfd_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rh
   A(&ctx->sc64, R);
   A(&ctx->act, R);
   A(&ctx->act64, R);
+  for (int i = 0; i < 4; ++i) A(&ctx->d_mask[i], R);
   A(&ctx->d_nord, R);
   A(&ctx->d_mn, R * (size_t)P.max_orders * 2);
   A(&ctx->d_ordout, R * (size_t)P.max_orders * 12);
@@ -324,10 +194,25 @@ int psfd_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rh
     return rc;
   }
   if (cudaMallocHost(&ctx->h_act, sizeof(int) * R) != cudaSuccess ||
-      cudaMallocHost(&ctx->h_sc, sizeof(KScal) * R) != cudaSuccess) {
+      cudaMallocHost(&ctx->h_act64, sizeof(int) * R) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_sc, sizeof(KScal) * R) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_sc64, sizeof(KScal) * R) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_mask, sizeof(int) * 4 * R) != cudaSuccess) {
     delete ctx;
     return PSFD_E_NOMEM;
   }
+  ctx->h_rhsp.assign(R, RhsParam{});
+  ctx->h_nord.assign(R, 0);
+  ctx->h_mn.assign(R * (size_t)P.max_orders * 2, 0);
+  ctx->th.assign(R, 0.0);
+  ctx->ph.assign(R, 0.0);
+  ctx->pol.assign(R, 0);
+  ctx->clip.assign(R, 0);
+  ctx->phase.assign(R, PH_FREE);
+  ctx->outer.assign(R, 0);
+  ctx->iters.assign(R, 0);
+  ctx->status.assign(R, PSFD_OK);
+  ctx->relres.assign(R, 0.0);
   auto tx = twiddles(grid->nx), ty = twiddles(grid->ny), tz = twiddles(grid->nf);
   cudaError_t e = cudaMemcpy(ctx->twx, tx.data(), tx.size() * 16, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ctx->twy, ty.data(), ty.size() * 16, cudaMemcpyHostToDevice);
@@ -350,6 +235,8 @@ int psfd_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rh
   }
   if (e == cudaSuccess) e = cudaMemset(ctx->sc, 0, sizeof(KScal) * R);
   if (e == cudaSuccess) e = cudaMemset(ctx->sc64, 0, sizeof(KScal) * R);
+  if (e == cudaSuccess) e = cudaMemset(ctx->act, 0, sizeof(int) * R);
+  if (e == cudaSuccess) e = cudaMemset(ctx->act64, 0, sizeof(int) * R);
   if (e == cudaSuccess) e = cudaMemset(ctx->side64, 0, sizeof(double2) * R * 6 * P.plane);
   if (e != cudaSuccess) {
     delete ctx;
@@ -359,130 +246,41 @@ int psfd_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rh
   return PSFD_OK;
 }
 
-int psfd_destroy(psfd_ctx* ctx) {
-  if (!ctx) return PSFD_OK;
-  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  else cudaDeviceSynchronize();
-  delete ctx;
-  return PSFD_OK;
-}
-
-int psfd_set_stream(psfd_ctx* ctx, void* stream) {
-  if (!ctx) return PSFD_E_ARG;
-  ctx->stream = (cudaStream_t)stream;
-  return PSFD_OK;
-}
-
-static int build_tables(psfd_ctx* ctx);
-
-int psfd_set_stack(psfd_ctx* ctx, int n_layers, const double* n_complex, const double* thickness_nm,
-                   const double* n_sub) {
-  if (!ctx || n_layers < 0 || !n_sub || (n_layers > 0 && (!n_complex || !thickness_nm)))
-    return ctx ? ctx->fail(PSFD_E_ARG, "invalid stack arguments") : PSFD_E_ARG;
-  ctx->h_eps_l.resize(n_layers);
-  ctx->h_d_l.resize(n_layers);
-  for (int j = 0; j < n_layers; ++j) {
-    const double a = n_complex[2 * j], b = n_complex[2 * j + 1];
-    if (!(thickness_nm[j] >= 0.0)) return ctx->fail(PSFD_E_ARG, "negative layer thickness");
-    ctx->h_eps_l[j] = make_double2(a * a - b * b, 2.0 * a * b);
-    ctx->h_d_l[j] = thickness_nm[j];
-  }
-  ctx->eps_sub = make_double2(n_sub[0] * n_sub[0] - n_sub[1] * n_sub[1], 2.0 * n_sub[0] * n_sub[1]);
-  ctx->n_layers = n_layers;
-  if (n_layers > ctx->stack_cap) {
-    if (ctx->dalloc(&ctx->d_eps_l, n_layers) || ctx->dalloc(&ctx->d_d_l, n_layers)) return PSFD_E_NOMEM;
-    ctx->stack_cap = n_layers;
-  }
-  if (n_layers > 0) {
-    CK(cudaMemcpyAsync(ctx->d_eps_l, ctx->h_eps_l.data(), sizeof(double2) * n_layers, cudaMemcpyHostToDevice,
-                       ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d_d_l, ctx->h_d_l.data(), sizeof(double) * n_layers, cudaMemcpyHostToDevice,
-                       ctx->stream));
-  }
-  ctx->have_stack = true;
-  if (ctx->have_illum) return build_tables(ctx);
-  return PSFD_OK;
-}
-
-int psfd_set_potential(psfd_ctx* ctx, const double* eps_complex, int where) {
-  if (!ctx || !eps_complex || (where != PSFD_HOST && where != PSFD_DEVICE))
-    return ctx ? ctx->fail(PSFD_E_ARG, "invalid potential arguments") : PSFD_E_ARG;
+int ctx_set_potential(psfd_ctx* ctx, int clip, const double* eps_complex, int where) {
+  if (!eps_complex || clip < 0 || clip >= ctx->max_clips || (where != PSFD_HOST && where != PSFD_DEVICE))
+    return ctx->fail(PSFD_E_ARG, "invalid potential arguments");
   const size_t n = ctx->plan.plane * ctx->g.nslab;
   const double2* src = reinterpret_cast<const double2*>(eps_complex);
   if (where == PSFD_HOST) {
     CK(cudaMemcpyAsync(ctx->eps_stage, src, n * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
     src = ctx->eps_stage;
   }
-  RC(launch_potential(n, src, ctx->k0 * ctx->k0, ctx->g.eps_bg, ctx->V64, ctx->V32, ctx->stream));
-  ctx->have_potential = true;
-  ctx->solved = false;
+  RC(launch_potential(n, src, ctx->k0 * ctx->k0, ctx->g.eps_bg, ctx->V64 + (size_t)clip * n,
+                      ctx->V32 + (size_t)clip * n, ctx->stream));
   return PSFD_OK;
 }
 
-// Mode tables (stack reflection per transverse mode) and right-hand sides.
-static int build_tables(psfd_ctx* ctx) {
+int ctx_set_rhs(psfd_ctx* ctx, int g0, int n, const double* theta_deg, const double* phi_deg, const int* pol,
+                int clip, const StackHost& stack) {
   const psfd_grid& g = ctx->g;
-  CK(cudaMemsetAsync(ctx->anomaly, 0, sizeof(int), ctx->stream));
-  ModesArgs m;
-  m.nx = g.nx;
-  m.ny = g.ny;
-  m.dx = g.dx;
-  m.dy = g.dy;
-  m.k0 = ctx->k0;
-  m.eps_bg = g.eps_bg;
-  m.L = ctx->L;
-  m.dz = g.dz;
-  m.kb = ctx->kb;
-  m.slot_par = ctx->slot_par;
-  m.modes32 = ctx->modes32;
-  m.stack.n_layers = ctx->n_layers;
-  m.stack.reflect = ctx->have_stack ? 1 : 0;
-  m.stack.eps = ctx->d_eps_l;
-  m.stack.d = ctx->d_d_l;
-  m.stack.eps_sub = ctx->eps_sub;
-  stack_dedup(m.stack, ctx->h_eps_l.data(), ctx->h_d_l.data(), ctx->n_layers, make_double2(g.eps_bg, 0.0),
-              ctx->eps_sub);
-  m.modes = ctx->modes;
-  m.anomaly = ctx->anomaly;
-  RC(launch_modes(m, ctx->n_slots, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->rhsp, ctx->h_rhsp.data(), sizeof(RhsParam) * ctx->n_rhs, cudaMemcpyHostToDevice,
-                     ctx->stream));
-  RC(launch_rhs(0, ctx->n_rhs, ctx->rhsp, ctx->modes, g.nx, g.ny, g.nslab, g.dz, ctx->kb, ctx->b64, ctx->stream));
-  ctx->solved = false;
-  return PSFD_OK;
-}
-
-int psfd_set_illumination(psfd_ctx* ctx, int n_rhs, const double* theta_deg, const double* phi_deg,
-                          const int* pol) {
-  if (!ctx) return PSFD_E_ARG;
-  if (n_rhs < 1 || n_rhs > ctx->max_rhs || !theta_deg || !phi_deg || !pol)
-    return ctx->fail(PSFD_E_ARG, "invalid illumination arguments");
-  const psfd_grid& g = ctx->g;
-  std::map<std::pair<double, double>, int> slots;
-  std::vector<double> spar;
-  ctx->h_rhsp.assign(n_rhs, RhsParam{});
-  ctx->h_nord.assign(n_rhs, 0);
-  ctx->h_mn.assign((size_t)n_rhs * ctx->plan.max_orders * 2, 0);
-  for (int i = 0; i < n_rhs; ++i) {
+  if (g0 < 0 || n < 1 || g0 + n > ctx->max_rhs || clip < 0 || clip >= ctx->max_clips ||
+      (int)stack.eps.size() > kStackMaxLayers)
+    return ctx->fail(PSFD_E_ARG, "invalid illumination slots");
+  const int M = ctx->plan.max_orders;
+  std::vector<double> spar(4 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
     if (!std::isfinite(theta_deg[i]) || !std::isfinite(phi_deg[i]) || (pol[i] != 0 && pol[i] != 1))
       return ctx->fail(PSFD_E_ARG, "invalid angle or polarisation");
+    const int gi = g0 + i;
     const double th = theta_deg[i] * kPi / 180.0, ph = phi_deg[i] * kPi / 180.0;
-    RhsParam& p = ctx->h_rhsp[i];
+    RhsParam p{};
     p.qix = ctx->kb * std::sin(th) * std::cos(ph);
     p.qiy = ctx->kb * std::sin(th) * std::sin(ph);
     p.cphi = std::cos(ph);
     p.sphi = std::sin(ph);
     p.pol = pol[i];
-    auto key = std::make_pair(theta_deg[i], phi_deg[i]);
-    auto it = slots.find(key);
-    if (it == slots.end()) {
-      const int s = (int)(spar.size() / 4);
-      slots[key] = s;
-      spar.insert(spar.end(), {p.qix, p.qiy, p.cphi, p.sphi});
-      p.slot = s;
-    } else {
-      p.slot = it->second;
-    }
+    p.slot = gi;
+    p.clip = clip;
     // propagating orders (|q| < k_bg) and the anomaly check, in FFT order (y outer, x inner)
     int cnt = 0;
     for (int y = 0; y < g.ny; ++y) {
@@ -494,28 +292,85 @@ int psfd_set_illumination(psfd_ctx* ctx, int n_rhs, const double* theta_deg, con
         const double d = ctx->kb * ctx->kb - (qx * qx + qy * qy);
         if (std::sqrt(std::fabs(d)) < 1e-9 * ctx->k0)
           return ctx->fail(PSFD_E_ANOMALY, "order (" + std::to_string(mi) + ", " + std::to_string(ni) +
-                                               ") of illumination " + std::to_string(i) + " has beta = 0");
+                                               ") of illumination " + std::to_string(gi) + " has beta = 0");
         if (d > 0) {
-          if (cnt >= ctx->plan.max_orders) return ctx->fail(PSFD_E_ARG, "order capacity exceeded");
-          ctx->h_mn[((size_t)i * ctx->plan.max_orders + cnt) * 2] = mi;
-          ctx->h_mn[((size_t)i * ctx->plan.max_orders + cnt) * 2 + 1] = ni;
+          if (cnt >= M) return ctx->fail(PSFD_E_ARG, "order capacity exceeded");
+          ctx->h_mn[((size_t)gi * M + cnt) * 2] = mi;
+          ctx->h_mn[((size_t)gi * M + cnt) * 2 + 1] = ni;
           ++cnt;
         }
       }
     }
-    ctx->h_nord[i] = cnt;
+    ctx->h_nord[gi] = cnt;
+    ctx->h_rhsp[gi] = p;
+    ctx->th[gi] = theta_deg[i];
+    ctx->ph[gi] = phi_deg[i];
+    ctx->pol[gi] = pol[i];
+    ctx->clip[gi] = clip;
+    spar[4 * i] = p.qix;
+    spar[4 * i + 1] = p.qiy;
+    spar[4 * i + 2] = p.cphi;
+    spar[4 * i + 3] = p.sphi;
   }
-  ctx->n_rhs = n_rhs;
-  ctx->n_slots = (int)(spar.size() / 4);
-  CK(cudaMemcpyAsync(ctx->slot_par, spar.data(), sizeof(double) * spar.size(), cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->d_nord, ctx->h_nord.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->d_mn, ctx->h_mn.data(), sizeof(int) * ctx->h_mn.size(), cudaMemcpyHostToDevice,
-                     ctx->stream));
-  ctx->have_illum = true;
-  return build_tables(ctx);
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(ctx->slot_par + 4 * (size_t)g0, spar.data(), sizeof(double) * spar.size(),
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_nord + g0, ctx->h_nord.data() + g0, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_mn + (size_t)g0 * M * 2, ctx->h_mn.data() + (size_t)g0 * M * 2,
+                     sizeof(int) * (size_t)n * M * 2, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->rhsp + g0, ctx->h_rhsp.data() + g0, sizeof(RhsParam) * n, cudaMemcpyHostToDevice, st));
+  ModesArgs m;
+  m.slot0 = g0;
+  m.nx = g.nx;
+  m.ny = g.ny;
+  m.dx = g.dx;
+  m.dy = g.dy;
+  m.dz = g.dz;
+  m.k0 = ctx->k0;
+  m.kb = ctx->kb;
+  m.eps_bg = g.eps_bg;
+  m.L = ctx->L;
+  m.slot_par = ctx->slot_par;
+  m.stack.n_layers = (int)stack.eps.size();
+  m.stack.reflect = stack.set ? 1 : 0;
+  m.stack.eps = ctx->d_eps_l;
+  m.stack.d = ctx->d_d_l;
+  m.stack.eps_sub = stack.eps_sub;
+  stack_dedup(m.stack, stack.eps.data(), stack.d.data(), (int)stack.eps.size(), make_double2(g.eps_bg, 0.0),
+              stack.eps_sub);
+  if (m.stack.reflect && m.stack.n_mat == 0 && !stack.eps.empty()) {
+    // general stacks go through device copies (stream order keeps each copy for its launch)
+    CK(cudaMemcpyAsync(ctx->d_eps_l, stack.eps.data(), sizeof(double2) * stack.eps.size(), cudaMemcpyHostToDevice,
+                       st));
+    CK(cudaMemcpyAsync(ctx->d_d_l, stack.d.data(), sizeof(double) * stack.d.size(), cudaMemcpyHostToDevice, st));
+  }
+  m.modes = ctx->modes;
+  m.modes32 = ctx->modes32;
+  m.anomaly = ctx->anomaly;
+  RC(launch_modes(m, n, st));
+  RC(launch_rhs(g0, n, ctx->rhsp, ctx->modes, g.nx, g.ny, g.nslab, g.dz, ctx->kb, ctx->b64 + (size_t)g0 * ctx->plan.U,
+                st));
+  for (int i = 0; i < n; ++i) {
+    ctx->phase[g0 + i] = PH_NEW;
+    ctx->outer[g0 + i] = 0;
+    ctx->iters[g0 + i] = 0;
+    ctx->status[g0 + i] = PSFD_OK;
+    ctx->relres[g0 + i] = 0.0;
+  }
+  ctx->orders_on_host = false;
+  return PSFD_OK;
 }
 
-}  // extern "C"
+int ctx_orders_to_host(psfd_ctx* ctx) {
+  const size_t M = (size_t)ctx->plan.max_orders;
+  ctx->h_ordout.resize((size_t)ctx->max_rhs * M * 12);
+  CK(cudaMemcpyAsync(ctx->h_ordout.data(), ctx->d_ordout, sizeof(double) * ctx->h_ordout.size(),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->orders_on_host = true;
+  return PSFD_OK;
+}
+
 template <typename C>
 static OpCall<C> base_call(psfd_ctx* ctx, int rhs0, int nrhs, const C* V) {
   OpCall<C> a;
@@ -546,23 +401,124 @@ static OpCall<C> base_call(psfd_ctx* ctx, int rhs0, int nrhs, const C* V) {
   a.epi = EPI_AU;
   return a;
 }
+template OpCall<float2> base_call<float2>(psfd_ctx*, int, int, const float2*);
+template OpCall<double2> base_call<double2>(psfd_ctx*, int, int, const double2*);
 
+OpCall<float2> base_call32(psfd_ctx* ctx, int rhs0, int nrhs) { return base_call<float2>(ctx, rhs0, nrhs, ctx->V32); }
+OpCall<double2> base_call64(psfd_ctx* ctx, int rhs0, int nrhs) {
+  return base_call<double2>(ctx, rhs0, nrhs, ctx->V64);
+}
+
+}  // namespace psfd
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
 extern "C" {
+
+const char* psfd_strerror(int s) {
+  switch (s) {
+    case PSFD_OK: return "ok";
+    case PSFD_E_ARG: return "invalid argument";
+    case PSFD_E_NOMEM: return "device allocation failed";
+    case PSFD_E_BUDGET: return "HBM budget exceeded";
+    case PSFD_E_CUDA: return "CUDA error";
+    case PSFD_E_NOT_CONVERGED: return "not converged";
+    case PSFD_E_BREAKDOWN: return "Krylov breakdown";
+    case PSFD_E_ANOMALY: return "Rayleigh anomaly (a diffraction order has beta = 0)";
+    case PSFD_E_TIMEOUT: return "device wait timed out";
+    case PSFD_E_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* psfd_last_error(const psfd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int psfd_supported_length(int n) { return fft_length_supported(n) ? 1 : 0; }
+
+int psfd_workspace_bytes(const psfd_grid* grid, int precision, int max_rhs, size_t* bytes) {
+  std::string why;
+  if (!bytes || !grid_ok(grid, why) || max_rhs < 1) return PSFD_E_ARG;
+  *bytes = make_plan(*grid, precision, max_rhs, 1).bytes;
+  return PSFD_OK;
+}
+
+int psfd_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs, size_t hbm_budget,
+                void* stream) {
+  return ctx_create(out, grid, precision, max_rhs, 1, hbm_budget, (cudaStream_t)stream);
+}
+
+int psfd_destroy(psfd_ctx* ctx) {
+  if (!ctx) return PSFD_OK;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  delete ctx;
+  return PSFD_OK;
+}
+
+int psfd_set_stream(psfd_ctx* ctx, void* stream) {
+  if (!ctx) return PSFD_E_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return PSFD_OK;
+}
+
+int psfd_set_stack(psfd_ctx* ctx, int n_layers, const double* n_complex, const double* thickness_nm,
+                   const double* n_sub) {
+  if (!ctx) return PSFD_E_ARG;
+  if (n_layers < 0 || n_layers > kStackMaxLayers || !n_sub || (n_layers > 0 && (!n_complex || !thickness_nm)))
+    return ctx->fail(PSFD_E_ARG, "invalid stack arguments");
+  StackHost s;
+  s.eps.resize(n_layers);
+  s.d.resize(n_layers);
+  for (int j = 0; j < n_layers; ++j) {
+    const double a = n_complex[2 * j], b = n_complex[2 * j + 1];
+    if (!(thickness_nm[j] >= 0.0)) return ctx->fail(PSFD_E_ARG, "negative layer thickness");
+    s.eps[j] = make_double2(a * a - b * b, 2.0 * a * b);
+    s.d[j] = thickness_nm[j];
+  }
+  s.eps_sub = make_double2(n_sub[0] * n_sub[0] - n_sub[1] * n_sub[1], 2.0 * n_sub[0] * n_sub[1]);
+  s.set = true;
+  ctx->stack = s;
+  if (ctx->have_illum)
+    return ctx_set_rhs(ctx, 0, ctx->n_rhs, ctx->th.data(), ctx->ph.data(), ctx->pol.data(), 0, ctx->stack);
+  return PSFD_OK;
+}
+
+int psfd_set_potential(psfd_ctx* ctx, const double* eps_complex, int where) {
+  if (!ctx) return PSFD_E_ARG;
+  RC(ctx_set_potential(ctx, 0, eps_complex, where));
+  ctx->have_potential = true;
+  for (int i = 0; i < ctx->n_rhs; ++i)
+    if (ctx->phase[i] != PH_FREE) ctx->phase[i] = PH_NEW;
+  return PSFD_OK;
+}
+
+int psfd_set_illumination(psfd_ctx* ctx, int n_rhs, const double* theta_deg, const double* phi_deg,
+                          const int* pol) {
+  if (!ctx) return PSFD_E_ARG;
+  if (n_rhs < 1 || n_rhs > ctx->max_rhs || !theta_deg || !phi_deg || !pol)
+    return ctx->fail(PSFD_E_ARG, "invalid illumination arguments");
+  for (int i = 0; i < ctx->max_rhs; ++i) ctx->phase[i] = PH_FREE;
+  RC(ctx_set_rhs(ctx, 0, n_rhs, theta_deg, phi_deg, pol, 0, ctx->stack));
+  ctx->n_rhs = n_rhs;
+  ctx->have_illum = true;
+  return PSFD_OK;
+}
+
 int psfd_apply(psfd_ctx* ctx, int precision, int rhs0, int n_rhs, const void* u, void* out) {
   if (!ctx) return PSFD_E_ARG;
   if (!ctx->have_illum || !ctx->have_potential) return ctx->fail(PSFD_E_STATE, "apply before set_potential/illumination");
   if (!u || !out || rhs0 < 0 || n_rhs < 1 || rhs0 + n_rhs > ctx->n_rhs)
     return ctx->fail(PSFD_E_ARG, "invalid apply arguments");
-  const size_t U = ctx->plan.U;
   if (precision == PSFD_FP64) {
-    OpCall<double2> a = base_call<double2>(ctx, rhs0, n_rhs, ctx->V64);
+    OpCall<double2> a = base_call64(ctx, rhs0, n_rhs);
     a.u = (const double2*)u;
     a.out = (double2*)out;
     a.work = ctx->work64;
     RC(op_apply<double2>(a));
   } else if (precision == PSFD_FP32_REFINED) {
-    if (!ctx->work32) RC(ctx->dalloc(&ctx->work32, (size_t)ctx->max_rhs * U));
-    OpCall<float2> a = base_call<float2>(ctx, rhs0, n_rhs, ctx->V32);
+    if (!ctx->work32) RC(ctx->dalloc(&ctx->work32, (size_t)ctx->max_rhs * ctx->plan.U));
+    OpCall<float2> a = base_call32(ctx, rhs0, n_rhs);
     a.u = (const float2*)u;
     a.out = (float2*)out;
     a.work = ctx->work32;
@@ -573,153 +529,26 @@ int psfd_apply(psfd_ctx* ctx, int precision, int rhs0, int n_rhs, const void* u,
   return PSFD_OK;
 }
 
-// r64 = b - A x64 with side spectra, then ||r64||^2 into sc64 and act64.
-static int fp64_residual(psfd_ctx* ctx, double tol) {
-  OpCall<double2> a = base_call<double2>(ctx, 0, ctx->n_rhs, ctx->V64);
-  a.u = ctx->x64;
-  a.out = ctx->r64;
-  a.b = ctx->b64;
-  a.epi = EPI_RESID;
-  a.work = ctx->work64;
-  a.dot_mask = DOT_OUT_OUT;
-  a.side = ctx->side64;
-  const int nb = op_apply<double2>(a);
-  RC(nb);
-  RC(launch_norm((int)ctx->plan.U, nb, 0, ctx->n_rhs, nullptr, ctx->partials, ctx->plan.maxblk, 1, tol * tol,
-                 ctx->sc64, ctx->act64, ctx->stream));
-  return PSFD_OK;
-}
-
-}  // extern "C"
-template <typename C>
-static KrylovCall<C> krylov_call(psfd_ctx* ctx, const C* V, const psfd_solve_opts& o) {
-  KrylovCall<C> k;
-  std::memset(&k, 0, sizeof(k));
-  k.op = base_call<C>(ctx, 0, ctx->n_rhs, V);
-  k.n = (int)ctx->plan.U;
-  k.sc = ctx->sc;
-  k.act = ctx->act;
-  k.h_act = ctx->h_act;
-  k.max_iter = o.max_iter;
-  k.check_every = o.check_every;
-  return k;
-}
-
-extern "C" {
-static int read_scalars(psfd_ctx* ctx, const KScal* d) {
-  CK(cudaMemcpyAsync(ctx->h_sc, d, sizeof(KScal) * ctx->n_rhs, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  return PSFD_OK;
-}
-
-static int compute_orders(psfd_ctx* ctx) {
-  OrdersArgs o;
-  o.nx = ctx->g.nx;
-  o.ny = ctx->g.ny;
-  o.nslab = ctx->g.nslab;
-  o.dx = ctx->g.dx;
-  o.dy = ctx->g.dy;
-  o.dz = ctx->g.dz;
-  o.kb = ctx->kb;
-  o.n_orders = ctx->d_nord;
-  o.mn = ctx->d_mn;
-  o.max_orders = ctx->plan.max_orders;
-  o.rhsp = ctx->rhsp;
-  o.modes = ctx->modes;
-  o.side = ctx->side64;
-  o.out = ctx->d_ordout;
-  RC(launch_orders(o, ctx->n_rhs, ctx->stream));
-  ctx->orders_on_host = false;
-  return PSFD_OK;
-}
-
 int psfd_solve(psfd_ctx* ctx, const psfd_solve_opts* opts, psfd_report* report) {
   if (!ctx) return PSFD_E_ARG;
   if (!ctx->have_illum || !ctx->have_potential) return ctx->fail(PSFD_E_STATE, "solve before set_potential/illumination");
   const auto t0 = std::chrono::steady_clock::now();
-  psfd_solve_opts o{};
-  if (opts) o = *opts;
-  if (!(o.tol > 0)) o.tol = 1e-10;
-  if (o.max_iter <= 0) o.max_iter = 500;
-  if (o.max_outer <= 0) o.max_outer = 12;
-  if (!(o.inner_tol > 0)) o.inner_tol = 1e-4;
-  if (o.check_every <= 0) o.check_every = 4;
-  const size_t U = ctx->plan.U;
-  const int nr = ctx->n_rhs;
-  const int vblk = std::max(1, std::min(ctx->plan.maxblk, (int)((U + 8191) / 8192)));
-  int status = PSFD_OK, outer = 0, iters = 0;
-  CK(cudaMemsetAsync(ctx->side64, 0, sizeof(double2) * (size_t)nr * 6 * ctx->plan.plane, ctx->stream));
-  // ||b||^2 -> sc64.bnorm2
-  RC(launch_norm((int)U, vblk, 0, nr, ctx->b64, ctx->partials, ctx->plan.maxblk, 0, o.tol * o.tol, ctx->sc64,
-                 ctx->act64, ctx->stream));
-  if (ctx->precision == PSFD_FP64) {
-    KrylovCall<double2> k = krylov_call<double2>(ctx, ctx->V64, o);
-    k.b = ctx->b64;
-    k.x = ctx->x64;
-    k.r = ctx->r64;
-    k.r0 = ctx->k64[0];
-    k.p = ctx->k64[1];
-    k.v = ctx->k64[2];
-    k.s = ctx->k64[3];
-    k.t = ctx->k64[4];
-    k.work = ctx->work64;
-    k.tol = o.tol;
-    RC(bicgstab<double2>(k));
-    RC(read_scalars(ctx, ctx->sc));
-    for (int i = 0; i < nr; ++i) {
-      iters = std::max(iters, ctx->h_sc[i].iters);
-      if (ctx->h_sc[i].status != PSFD_OK && status == PSFD_OK) status = ctx->h_sc[i].status;
-    }
-    RC(fp64_residual(ctx, o.tol));
-  } else {
-    CK(cudaMemsetAsync(ctx->x64, 0, sizeof(double2) * U * nr, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->r64, ctx->b64, sizeof(double2) * U * nr, cudaMemcpyDeviceToDevice, ctx->stream));
-    std::vector<int> tot_iters(nr, 0);
-    for (outer = 0;; ++outer) {
-      CK(cudaMemcpyAsync(ctx->h_act, ctx->act64, sizeof(int) * nr, cudaMemcpyDeviceToHost, ctx->stream));
-      CK(cudaStreamSynchronize(ctx->stream));
-      bool any = false;
-      for (int i = 0; i < nr; ++i) any = any || ctx->h_act[i];
-      if (!any) break;
-      if (outer >= o.max_outer) {
-        status = PSFD_E_NOT_CONVERGED;
-        break;
-      }
-      std::vector<int> was_active(ctx->h_act, ctx->h_act + nr);
-      RC(launch_ref_scale((int)U, 0, nr, ctx->act64, ctx->sc64, ctx->r64, ctx->r32, ctx->stream));
-      // FP32 correction solve A d = r64 / ||r64||; the scaled residual is both b and the
-      // running residual of BiCGStab (its init copies b into r and r0 element by element)
-      KrylovCall<float2> k = krylov_call<float2>(ctx, ctx->V32, o);
-      k.b = ctx->r32;
-      k.r = ctx->r32;
-      k.x = ctx->x32;
-      k.r0 = ctx->r032;
-      k.p = ctx->p32;
-      k.v = ctx->v32;
-      k.s = ctx->s32;
-      k.t = ctx->t32;
-      k.work = ctx->work32;
-      k.act_in = ctx->act64;
-      k.tol = o.inner_tol;
-      RC(bicgstab<float2>(k));
-      RC(read_scalars(ctx, ctx->sc));
-      for (int i = 0; i < nr; ++i)
-        if (was_active[i]) tot_iters[i] += ctx->h_sc[i].iters;
-      RC(launch_ref_update((int)U, 0, nr, ctx->act64, ctx->sc64, ctx->x64, ctx->x32, ctx->stream));
-      RC(fp64_residual(ctx, o.tol));
-    }
-    for (int i = 0; i < nr; ++i) iters = std::max(iters, tot_iters[i]);
+  const psfd_solve_opts o = solve_defaults(opts);
+  for (int i = 0; i < ctx->n_rhs; ++i)
+    if (ctx->phase[i] == PH_DONE) ctx->phase[i] = PH_NEW;  // re-solve from scratch
+  for (;;) {
+    int active = 0;
+    RC(engine_tick(ctx, o, &active));
+    if (!active) break;
   }
-  RC(compute_orders(ctx));
-  RC(read_scalars(ctx, ctx->sc64));
+  int status = PSFD_OK, iters = 0, outer = 0;
   double relres = 0.0;
-  for (int i = 0; i < nr; ++i) {
-    const KScal& s = ctx->h_sc[i];
-    const double rr = s.bnorm2 > 0 ? std::sqrt(s.rnorm2 / s.bnorm2) : 0.0;
-    relres = std::max(relres, rr);
+  for (int i = 0; i < ctx->n_rhs; ++i) {
+    iters = std::max(iters, ctx->iters[i]);
+    outer = std::max(outer, ctx->outer[i]);
+    relres = std::max(relres, ctx->relres[i]);
+    if (ctx->status[i] != PSFD_OK && status == PSFD_OK) status = ctx->status[i];
   }
-  if (status == PSFD_OK && relres > o.tol) status = PSFD_E_NOT_CONVERGED;
-  ctx->solved = true;
   if (report) {
     report->iterations = iters;
     report->outer = outer;
@@ -740,22 +569,17 @@ int psfd_num_orders(psfd_ctx* ctx, int rhs, int* n_orders) {
 int psfd_diffraction_orders(psfd_ctx* ctx, int rhs, int capacity, int* n_orders, int* mn, double* amp, double* sp,
                             double* eff) {
   if (!ctx || !n_orders || !mn) return PSFD_E_ARG;
-  if (!ctx->solved) return ctx->fail(PSFD_E_STATE, "diffraction_orders before solve");
   if (rhs < 0 || rhs >= ctx->n_rhs) return ctx->fail(PSFD_E_ARG, "rhs out of range");
+  if (ctx->phase[rhs] != PH_DONE) return ctx->fail(PSFD_E_STATE, "diffraction_orders before solve");
   const int n = ctx->h_nord[rhs];
   *n_orders = n;
   if (capacity < n) return ctx->fail(PSFD_E_ARG, "capacity smaller than the number of orders");
-  if (!ctx->orders_on_host) {
-    ctx->h_ordout.resize((size_t)ctx->n_rhs * ctx->plan.max_orders * 12);
-    CK(cudaMemcpyAsync(ctx->h_ordout.data(), ctx->d_ordout, sizeof(double) * ctx->h_ordout.size(),
-                       cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    ctx->orders_on_host = true;
-  }
+  if (!ctx->orders_on_host) RC(ctx_orders_to_host(ctx));
+  const size_t M = (size_t)ctx->plan.max_orders;
   for (int k = 0; k < n; ++k) {
-    const double* o = ctx->h_ordout.data() + ((size_t)rhs * ctx->plan.max_orders + k) * 12;
-    mn[2 * k] = ctx->h_mn[((size_t)rhs * ctx->plan.max_orders + k) * 2];
-    mn[2 * k + 1] = ctx->h_mn[((size_t)rhs * ctx->plan.max_orders + k) * 2 + 1];
+    const double* o = ctx->h_ordout.data() + ((size_t)rhs * M + k) * 12;
+    mn[2 * k] = ctx->h_mn[((size_t)rhs * M + k) * 2];
+    mn[2 * k + 1] = ctx->h_mn[((size_t)rhs * M + k) * 2 + 1];
     if (amp) std::memcpy(amp + 6 * k, o, 6 * sizeof(double));
     if (sp) std::memcpy(sp + 4 * k, o + 6, 4 * sizeof(double));
     if (eff) eff[k] = o[10];
@@ -773,7 +597,7 @@ static int copy_vec(psfd_ctx* ctx, const double2* src, double* dst, int where) {
 
 int psfd_get_solution(psfd_ctx* ctx, int rhs, double* dst, int where) {
   if (!ctx || !dst || rhs < 0 || rhs >= ctx->n_rhs || (where != PSFD_HOST && where != PSFD_DEVICE)) return PSFD_E_ARG;
-  if (!ctx->solved) return ctx->fail(PSFD_E_STATE, "get_solution before solve");
+  if (ctx->phase[rhs] != PH_DONE) return ctx->fail(PSFD_E_STATE, "get_solution before solve");
   return copy_vec(ctx, ctx->x64 + (size_t)rhs * ctx->plan.U, dst, where);
 }
 

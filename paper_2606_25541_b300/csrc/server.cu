@@ -1,0 +1,342 @@
+// server.cu -- the serving loop: continuous batching of mask-clip solves.
+//
+// Requests (a clip: grid, stack, permittivity, 1..n illuminations) are queued on
+// submit. Each progress() call
+//   1. admits queued requests, in arrival order, into a context ("bucket") of the same
+//      grid: a free potential slot and a run of free illumination slots are claimed, the
+//      potential and the per-mode tables are built, and the slots enter the engine
+//      (engine.cu) -- while other requests of the bucket are mid-solve. A bucket is created
+//      when the request's grid has none and its device footprint fits the HBM budget;
+//      idle buckets are released when a queued request needs their memory;
+//   2. advances every bucket by one engine tick (shared launches over all its slots);
+//   3. retires requests whose illuminations are all done: their orders are copied to
+//      host memory, their slots freed for the next admissions.
+// A request's result does not depend on the other requests of its bucket: every kernel
+// masks per slot and every reduction is per slot and in a fixed order.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "ctx.h"
+
+using namespace psfd;
+
+namespace {
+
+bool same_grid(const psfd_grid& a, const psfd_grid& b) {
+  return a.nx == b.nx && a.ny == b.ny && a.nslab == b.nslab && a.nf == b.nf && a.dx == b.dx && a.dy == b.dy &&
+         a.dz == b.dz && a.wavelength == b.wavelength && a.eps_bg == b.eps_bg;
+}
+
+struct Bucket {
+  psfd_grid grid{};
+  psfd_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<long long> rhs_owner;   // request id per illumination slot, -1 free
+  std::vector<long long> clip_owner;  // request id per potential slot, -1 free
+  size_t bytes = 0;
+  int running = 0;
+};
+
+struct Request {
+  long long id = 0;
+  psfd_grid grid{};
+  StackHost stack;
+  std::vector<double2> eps;
+  std::vector<double> th, ph;
+  std::vector<int> pol;
+  int state = 0;  // 0 queued, 1 running, 2 done
+  int status = PSFD_OK;
+  Bucket* bucket = nullptr;
+  int clip = -1, g0 = -1;
+  std::vector<int> nord;
+  std::vector<std::vector<int>> mn;
+  std::vector<std::vector<double>> out;  // per illumination: orders x 12 doubles
+};
+
+}  // namespace
+
+struct psfd_server {
+  int precision = PSFD_FP32_REFINED;
+  size_t budget = 0, used = 0;
+  int slots = 18;
+  psfd_solve_opts opts{};
+  long long next_id = 1;
+  std::deque<long long> queue;
+  std::map<long long, std::unique_ptr<Request>> reqs;
+  std::vector<std::unique_ptr<Bucket>> buckets;
+};
+
+namespace {
+
+void destroy_bucket(psfd_server* s, Bucket* b) {
+  if (b->ctx) psfd_destroy(b->ctx);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  s->used -= b->bytes;
+  s->buckets.erase(std::remove_if(s->buckets.begin(), s->buckets.end(),
+                                  [&](const std::unique_ptr<Bucket>& p) { return p.get() == b; }),
+                   s->buckets.end());
+}
+
+// Create a bucket for grid g if the budget allows, releasing idle buckets if needed.
+Bucket* make_bucket(psfd_server* s, const psfd_grid& g, int cap, int* rc) {
+  const size_t need = make_plan(g, s->precision, cap, cap).bytes;
+  if (s->budget && s->used + need > s->budget) {
+    for (size_t i = 0; i < s->buckets.size();) {
+      Bucket* b = s->buckets[i].get();
+      if (b->running == 0 && s->used + need > s->budget) {
+        destroy_bucket(s, b);
+      } else {
+        ++i;
+      }
+    }
+  }
+  if (s->budget && s->used + need > s->budget) {
+    *rc = PSFD_E_BUDGET;
+    return nullptr;
+  }
+  auto b = std::make_unique<Bucket>();
+  b->grid = g;
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    *rc = PSFD_E_CUDA;
+    return nullptr;
+  }
+  *rc = ctx_create(&b->ctx, &g, s->precision, cap, cap, 0, b->stream);
+  if (*rc != PSFD_OK) {
+    cudaStreamDestroy(b->stream);
+    return nullptr;
+  }
+  b->bytes = need;
+  b->rhs_owner.assign(cap, -1);
+  b->clip_owner.assign(cap, -1);
+  s->used += need;
+  s->buckets.push_back(std::move(b));
+  return s->buckets.back().get();
+}
+
+// Claim a free potential slot and a run of n free illumination slots.
+bool find_slots(Bucket* b, int n, int* clip, int* g0) {
+  *clip = -1;
+  for (size_t c = 0; c < b->clip_owner.size(); ++c)
+    if (b->clip_owner[c] < 0) { *clip = (int)c; break; }
+  if (*clip < 0) return false;
+  const int R = (int)b->rhs_owner.size();
+  for (int start = 0; start + n <= R; ++start) {
+    bool ok = true;
+    for (int i = 0; i < n && ok; ++i) ok = b->rhs_owner[start + i] < 0;
+    if (ok) {
+      *g0 = start;
+      return true;
+    }
+  }
+  return false;
+}
+
+int admit(psfd_server* s, Request* r, bool* admitted) {
+  *admitted = false;
+  Bucket* b = nullptr;
+  int clip = -1, g0 = -1;
+  for (auto& bp : s->buckets)
+    if (same_grid(bp->grid, r->grid) && find_slots(bp.get(), (int)r->th.size(), &clip, &g0)) {
+      b = bp.get();
+      break;
+    }
+  if (!b) {
+    bool have_shape = false;
+    for (auto& bp : s->buckets) have_shape = have_shape || same_grid(bp->grid, r->grid);
+    if (have_shape && (int)r->th.size() <= s->slots) return PSFD_OK;  // wait for slots of that bucket
+    int rc = PSFD_OK;
+    b = make_bucket(s, r->grid, std::max(s->slots, (int)r->th.size()), &rc);
+    if (!b) return rc == PSFD_E_BUDGET ? PSFD_OK : rc;  // wait for memory
+    if (!find_slots(b, (int)r->th.size(), &clip, &g0)) return PSFD_E_ARG;
+  }
+  psfd_ctx* ctx = b->ctx;
+  int rc = ctx_set_potential(ctx, clip, reinterpret_cast<const double*>(r->eps.data()), PSFD_HOST);
+  if (rc == PSFD_OK)
+    rc = ctx_set_rhs(ctx, g0, (int)r->th.size(), r->th.data(), r->ph.data(), r->pol.data(), clip, r->stack);
+  if (rc != PSFD_OK) {
+    r->state = 2;
+    r->status = rc;
+    *admitted = true;
+    return PSFD_OK;
+  }
+  b->clip_owner[clip] = r->id;
+  for (size_t i = 0; i < r->th.size(); ++i) b->rhs_owner[g0 + i] = r->id;
+  b->running += 1;
+  r->bucket = b;
+  r->clip = clip;
+  r->g0 = g0;
+  r->state = 1;
+  *admitted = true;
+  return PSFD_OK;
+}
+
+int retire(psfd_server* s, Bucket* b) {
+  psfd_ctx* ctx = b->ctx;
+  bool copied = false;
+  for (auto& kv : s->reqs) {
+    Request* r = kv.second.get();
+    if (r->state != 1 || r->bucket != b) continue;
+    const int n = (int)r->th.size();
+    bool done = true;
+    for (int i = 0; i < n && done; ++i) done = ctx->phase[r->g0 + i] == PH_DONE;
+    if (!done) continue;
+    if (!copied) {
+      int rc = ctx_orders_to_host(ctx);
+      if (rc) return rc;
+      copied = true;
+    }
+    const size_t M = (size_t)ctx->plan.max_orders;
+    r->nord.assign(n, 0);
+    r->mn.assign(n, {});
+    r->out.assign(n, {});
+    for (int i = 0; i < n; ++i) {
+      const int g = r->g0 + i;
+      const int k = ctx->h_nord[g];
+      r->nord[i] = k;
+      r->mn[i].assign(ctx->h_mn.begin() + (ptrdiff_t)(g * M * 2), ctx->h_mn.begin() + (ptrdiff_t)(g * M * 2 + 2 * k));
+      r->out[i].assign(ctx->h_ordout.begin() + (ptrdiff_t)(g * M * 12),
+                       ctx->h_ordout.begin() + (ptrdiff_t)(g * M * 12 + 12 * k));
+      if (ctx->status[g] != PSFD_OK && r->status == PSFD_OK) r->status = ctx->status[g];
+      ctx->phase[g] = PH_FREE;
+      b->rhs_owner[g] = -1;
+    }
+    b->clip_owner[r->clip] = -1;
+    b->running -= 1;
+    r->state = 2;
+    r->bucket = nullptr;
+  }
+  return PSFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int psfd_server_create(psfd_server** out, int precision, size_t hbm_budget, int slots_per_context,
+                       const psfd_solve_opts* opts) {
+  if (!out || (precision != PSFD_FP64 && precision != PSFD_FP32_REFINED) || slots_per_context < 1)
+    return PSFD_E_ARG;
+  psfd_server* s = new psfd_server();
+  s->precision = precision;
+  s->budget = hbm_budget;
+  s->slots = slots_per_context;
+  s->opts = solve_defaults(opts);
+  *out = s;
+  return PSFD_OK;
+}
+
+int psfd_server_destroy(psfd_server* s) {
+  if (!s) return PSFD_OK;
+  while (!s->buckets.empty()) destroy_bucket(s, s->buckets.back().get());
+  delete s;
+  return PSFD_OK;
+}
+
+int psfd_server_submit(psfd_server* s, const psfd_request* q, long long* ticket) {
+  if (!s || !q || !ticket || !q->eps || !q->n_sub || q->n_rhs < 1 || !q->theta_deg || !q->phi_deg || !q->pol ||
+      q->n_layers < 0 || q->n_layers > kStackMaxLayers || (q->n_layers > 0 && (!q->n_complex || !q->thickness_nm)))
+    return PSFD_E_ARG;
+  std::string why;
+  if (!grid_ok(&q->grid, why)) return PSFD_E_ARG;
+  auto r = std::make_unique<Request>();
+  r->id = s->next_id++;
+  r->grid = q->grid;
+  r->stack.eps.resize(q->n_layers);
+  r->stack.d.assign(q->thickness_nm, q->thickness_nm + q->n_layers);
+  for (int j = 0; j < q->n_layers; ++j) {
+    const double a = q->n_complex[2 * j], b = q->n_complex[2 * j + 1];
+    r->stack.eps[j] = make_double2(a * a - b * b, 2.0 * a * b);
+  }
+  r->stack.eps_sub = make_double2(q->n_sub[0] * q->n_sub[0] - q->n_sub[1] * q->n_sub[1], 2.0 * q->n_sub[0] * q->n_sub[1]);
+  r->stack.set = true;
+  const size_t n = (size_t)q->grid.nx * q->grid.ny * q->grid.nslab;
+  r->eps.resize(n);
+  std::memcpy(r->eps.data(), q->eps, n * sizeof(double2));
+  r->th.assign(q->theta_deg, q->theta_deg + q->n_rhs);
+  r->ph.assign(q->phi_deg, q->phi_deg + q->n_rhs);
+  r->pol.assign(q->pol, q->pol + q->n_rhs);
+  *ticket = r->id;
+  s->queue.push_back(r->id);
+  s->reqs[r->id] = std::move(r);
+  return PSFD_OK;
+}
+
+int psfd_server_progress(psfd_server* s, int* n_pending) {
+  if (!s) return PSFD_E_ARG;
+  // 1. admissions, in arrival order; requests that do not fit yet stay queued
+  for (auto it = s->queue.begin(); it != s->queue.end();) {
+    Request* r = s->reqs[*it].get();
+    bool admitted = false;
+    const int rc = admit(s, r, &admitted);
+    if (rc != PSFD_OK) return rc;
+    it = admitted ? s->queue.erase(it) : std::next(it);
+  }
+  // 2. one engine tick per bucket with work; 3. retire finished requests
+  for (auto& bp : s->buckets) {
+    Bucket* b = bp.get();
+    if (b->running == 0) continue;
+    int active = 0;
+    int rc = engine_tick(b->ctx, s->opts, &active);
+    if (rc != PSFD_OK) return rc;
+    if ((rc = retire(s, b)) != PSFD_OK) return rc;
+  }
+  if (n_pending) {
+    int n = (int)s->queue.size();
+    for (auto& bp : s->buckets) n += bp->running;
+    *n_pending = n;
+  }
+  return PSFD_OK;
+}
+
+int psfd_server_status(psfd_server* s, long long ticket, int* state, int* status) {
+  if (!s || !state) return PSFD_E_ARG;
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return PSFD_E_ARG;
+  *state = it->second->state;
+  if (status) *status = it->second->status;
+  return PSFD_OK;
+}
+
+int psfd_server_orders(psfd_server* s, long long ticket, int rhs, int capacity, int* n_orders, int* mn, double* amp,
+                       double* sp, double* eff) {
+  if (!s || !n_orders || !mn) return PSFD_E_ARG;
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return PSFD_E_ARG;
+  Request* r = it->second.get();
+  if (r->state != 2 || r->nord.empty()) return PSFD_E_STATE;
+  if (rhs < 0 || rhs >= (int)r->nord.size()) return PSFD_E_ARG;
+  const int n = r->nord[rhs];
+  *n_orders = n;
+  if (capacity < n) return PSFD_E_ARG;
+  for (int k = 0; k < n; ++k) {
+    const double* o = r->out[rhs].data() + 12 * k;
+    mn[2 * k] = r->mn[rhs][2 * k];
+    mn[2 * k + 1] = r->mn[rhs][2 * k + 1];
+    if (amp) std::memcpy(amp + 6 * k, o, 6 * sizeof(double));
+    if (sp) std::memcpy(sp + 4 * k, o + 6, 4 * sizeof(double));
+    if (eff) eff[k] = o[10];
+  }
+  return PSFD_OK;
+}
+
+int psfd_server_release(psfd_server* s, long long ticket) {
+  if (!s) return PSFD_E_ARG;
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end() || it->second->state != 2) return PSFD_E_STATE;
+  s->reqs.erase(it);
+  return PSFD_OK;
+}
+
+int psfd_server_memory(psfd_server* s, size_t* used, int* n_contexts) {
+  if (!s) return PSFD_E_ARG;
+  if (used) *used = s->used;
+  if (n_contexts) *n_contexts = (int)s->buckets.size();
+  return PSFD_OK;
+}
+
+}  // extern "C"

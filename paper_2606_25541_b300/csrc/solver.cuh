@@ -1,9 +1,11 @@
-// solver.cuh -- host driver of the batched BiCGStab loop (one instantiation per precision).
+// solver.cuh -- host side of the batched BiCGStab loop (one instantiation per precision).
 //
 // Per iteration: v = A p with p = r + beta (p - omega v) formed inside K1; alpha;
 // t = A s with s = r - alpha v formed inside K1; omega; x and r updated with their dot
-// products; rho, beta and the convergence test. All scalars stay on the device; the
-// host reads the per-RHS activity flags every check_every iterations only.
+// products; rho, beta and the convergence test. All scalars and the per-RHS activity
+// flags stay on the device: iterations are enqueued without any host synchronisation,
+// and right-hand sides that converged (or were never started) are skipped by every
+// kernel, so illuminations at different stages of their solve can share the launches.
 #pragma once
 
 #include "krylov.cuh"
@@ -12,18 +14,31 @@
 namespace psfd {
 
 template <typename C>
-int bicgstab_impl(const KrylovCall<C>& k) {
+int vec_blocks(const KrylovCall<C>& k) {
+  int nblk = (k.n + 8191) / 8192;
+  if (nblk > k.op.maxblk) nblk = k.op.maxblk;
+  return nblk < 1 ? 1 : nblk;
+}
+
+template <typename C>
+int bicg_start_impl(const KrylovCall<C>& k, const int* mask) {
+  const OpCall<C>& base = k.op;
+  cudaStream_t st = base.stream;
+  const int nblk = vec_blocks(k);
+  k_bicg_init<C><<<dim3(nblk, base.nrhs), VEC_NT, 0, st>>>(k.n, nblk, base.rhs0, mask, k.b, k.x, k.r, k.r0, k.p,
+                                                            k.v, base.partials, base.maxblk);
+  PSFD_CHECK_LAUNCH();
+  k_scal_init<<<base.nrhs, VEC_NT, 0, st>>>(base.rhs0, nblk, base.partials, base.maxblk, mask, k.sc, k.act);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+template <typename C>
+int bicg_iterate_impl(const KrylovCall<C>& k, int iters) {
   const OpCall<C>& base = k.op;
   cudaStream_t st = base.stream;
   const int nrhs = base.nrhs, rhs0 = base.rhs0;
-  int nblk = (k.n + 8191) / 8192;
-  if (nblk > base.maxblk) nblk = base.maxblk;
-  if (nblk < 1) nblk = 1;
-  k_bicg_init<C><<<dim3(nblk, nrhs), VEC_NT, 0, st>>>(k.n, nblk, rhs0, k.b, k.x, k.r, k.r0, k.p, k.v,
-                                                       base.partials, base.maxblk);
-  PSFD_CHECK_LAUNCH();
-  k_scal_init<<<nrhs, VEC_NT, 0, st>>>(rhs0, nblk, base.partials, base.maxblk, k.act_in, k.sc, k.act);
-  PSFD_CHECK_LAUNCH();
+  const int nblk = vec_blocks(k);
 
   OpCall<C> pv = base;  // v = A p
   pv.active = k.act;
@@ -48,8 +63,7 @@ int bicgstab_impl(const KrylovCall<C>& k) {
   ts.dot_mask = DOT_OUT_U | DOT_OUT_OUT;
 
   const double tol2 = k.tol * k.tol;
-  const int every = k.check_every > 0 ? k.check_every : 4;
-  for (int it = 0; it < k.max_iter; ++it) {
+  for (int it = 0; it < iters; ++it) {
     int nb = op_apply_impl<C>(pv);
     if (nb < 0) return nb;
     k_scal_alpha<<<nrhs, VEC_NT, 0, st>>>(rhs0, nb, base.partials, base.maxblk, k.sc, k.act);
@@ -67,15 +81,6 @@ int bicgstab_impl(const KrylovCall<C>& k) {
     prof_end(vcls, st, 7.0 * nrhs * (double)k.n * sizeof(C), 24.0 * nrhs * (double)k.n);
     k_scal_rho<<<nrhs, VEC_NT, 0, st>>>(rhs0, nblk, base.partials, base.maxblk, tol2, k.max_iter, k.sc, k.act);
     PSFD_CHECK_LAUNCH();
-    if ((it + 1) % every == 0 || it + 1 == k.max_iter) {
-      if (cudaMemcpyAsync(k.h_act + rhs0, k.act + rhs0, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st) !=
-          cudaSuccess)
-        return PSFD_E_CUDA;
-      if (cudaStreamSynchronize(st) != cudaSuccess) return PSFD_E_CUDA;
-      bool any = false;
-      for (int i = 0; i < nrhs; ++i) any = any || k.h_act[rhs0 + i];
-      if (!any) break;
-    }
   }
   return PSFD_OK;
 }

@@ -186,6 +186,7 @@ extern "C" int psfd_apply_fp32_static(const psfd_grid* g, int n_layers, const do
 
   ModeEntry* modes = reinterpret_cast<ModeEntry*>(base + o_modes);
   ModesArgs m;
+  m.slot0 = 0;
   m.nx = g->nx;
   m.ny = g->ny;
   m.dx = g->dx;

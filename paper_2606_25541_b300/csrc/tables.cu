@@ -143,7 +143,7 @@ void stack_dedup(StackDev& st, const double2* eps_layers, const double* d_layers
 
 // grid (ceil(nx / 128), ny, n_slots)
 __global__ void k_modes(ModesArgs a) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, slot = blockIdx.z;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, slot = a.slot0 + blockIdx.z;
   if (x >= a.nx) return;
   const double two_pi = 6.283185307179586476925286766559;
   const double* sp = a.slot_par + 4 * slot;
@@ -282,7 +282,7 @@ int launch_rhs(int rhs0, int nrhs, RhsParam* rp, const ModeEntry* modes, int nx,
 // ---------------------------------------------------------------------------
 __global__ void k_orders(OrdersArgs a) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x, g = blockIdx.y;
-  if (k >= a.n_orders[g]) return;
+  if (k >= a.n_orders[g] || (a.mask && !a.mask[g])) return;
   const int mi = a.mn[((size_t)g * a.max_orders + k) * 2], ni = a.mn[((size_t)g * a.max_orders + k) * 2 + 1];
   const int x = (mi + a.nx) % a.nx, y = (ni + a.ny) % a.ny;
   const RhsParam p = a.rhsp[g];
@@ -329,9 +329,10 @@ int launch_orders(const OrdersArgs& a, int nrhs, cudaStream_t st) {
 // defect correction helpers (FP64 outer loop around the FP32 Krylov solve)
 // ---------------------------------------------------------------------------
 // partial ||v||^2 per block into slot 2
-__global__ void __launch_bounds__(VEC_NT) k_norm2_partials(int n, int nblk, int rhs0, const double2* v,
-                                                            double2* partials, int maxblk) {
+__global__ void __launch_bounds__(VEC_NT) k_norm2_partials(int n, int nblk, int rhs0, const int* mask,
+                                                            const double2* v, double2* partials, int maxblk) {
   const int blk = blockIdx.x, lr = blockIdx.y, g = rhs0 + lr;
+  if (mask && !mask[g]) return;
   const size_t off = (size_t)lr * n;
   const int chunk = (n + nblk - 1) / nblk;
   const int lo = blk * chunk, hi = min(n, lo + chunk);
@@ -342,11 +343,12 @@ __global__ void __launch_bounds__(VEC_NT) k_norm2_partials(int n, int nblk, int 
 }
 
 // mode 0: bnorm2 = rnorm2 = sum (initial residual = b); mode 1: rnorm2 = sum.
-// act = rnorm2 > tol2 * bnorm2.
-__global__ void __launch_bounds__(VEC_NT) k_norm_finish(int rhs0, int nblk, const double2* partials, int maxblk,
-                                                         int mode, double tol2, KScal* sc, int* act) {
+// act = rnorm2 > tol2 * bnorm2. Right-hand sides outside mask (null = all) are untouched.
+__global__ void __launch_bounds__(VEC_NT) k_norm_finish(int rhs0, int nblk, const int* mask, const double2* partials,
+                                                         int maxblk, int mode, double tol2, KScal* sc, int* act) {
   __shared__ double2 sh[33];
   const int g = rhs0 + blockIdx.x;
+  if (mask && !mask[g]) return;
   const double2 s = block_sum_fixed(slot_ptr(partials, g, 2, maxblk), nblk, sh);
   if (threadIdx.x == 0) {
     if (mode == 0) sc[g].bnorm2 = s.x;
@@ -355,13 +357,13 @@ __global__ void __launch_bounds__(VEC_NT) k_norm_finish(int rhs0, int nblk, cons
   }
 }
 
-int launch_norm(int n, int nblk, int rhs0, int nrhs, const double2* v, double2* partials, int maxblk, int mode,
-                double tol2, KScal* sc, int* act, cudaStream_t st) {
+int launch_norm(int n, int nblk, int rhs0, int nrhs, const int* mask, const double2* v, double2* partials,
+                int maxblk, int mode, double tol2, KScal* sc, int* act, cudaStream_t st) {
   if (v) {
-    k_norm2_partials<<<dim3(nblk, nrhs), VEC_NT, 0, st>>>(n, nblk, rhs0, v, partials, maxblk);
+    k_norm2_partials<<<dim3(nblk, nrhs), VEC_NT, 0, st>>>(n, nblk, rhs0, mask, v, partials, maxblk);
     if (launched() != PSFD_OK) return PSFD_E_CUDA;
   }
-  k_norm_finish<<<nrhs, VEC_NT, 0, st>>>(rhs0, nblk, partials, maxblk, mode, tol2, sc, act);
+  k_norm_finish<<<nrhs, VEC_NT, 0, st>>>(rhs0, nblk, mask, partials, maxblk, mode, tol2, sc, act);
   return launched();
 }
 

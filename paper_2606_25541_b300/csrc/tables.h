@@ -31,6 +31,7 @@ void stack_dedup(StackDev& st, const double2* eps_layers, const double* d_layers
                  double2 eps_sub);
 
 struct ModesArgs {
+  int slot0;  // first table row written (one launch covers rows slot0 .. slot0 + n_slots - 1)
   int nx, ny;
   double dx, dy, dz, k0, kb, eps_bg, L;
   const double* slot_par;  // [slot][4]: q_inc x, q_inc y, cos phi, sin phi
@@ -50,6 +51,7 @@ struct OrdersArgs {
   const ModeEntry* modes;
   const double2* side;  // [rhs][2][3][ny][nx]
   double* out;          // [rhs][max_orders][12]
+  const int* mask;      // right-hand sides to evaluate (null = all)
 };
 
 int launch_potential(size_t n, const double2* eps, double k02, double eps_bg, double2* V64, float2* V32,
@@ -58,8 +60,8 @@ int launch_modes(const ModesArgs& a, int n_slots, cudaStream_t st);
 int launch_rhs(int rhs0, int nrhs, RhsParam* rp, const ModeEntry* modes, int nx, int ny, int nslab, double dz,
                double kb, double2* b, cudaStream_t st);
 int launch_orders(const OrdersArgs& a, int nrhs, cudaStream_t st);
-int launch_norm(int n, int nblk, int rhs0, int nrhs, const double2* v, double2* partials, int maxblk, int mode,
-                double tol2, KScal* sc, int* act, cudaStream_t st);
+int launch_norm(int n, int nblk, int rhs0, int nrhs, const int* mask, const double2* v, double2* partials,
+                int maxblk, int mode, double tol2, KScal* sc, int* act, cudaStream_t st);
 int launch_ref_scale(int n, int rhs0, int nrhs, const int* act, const KScal* sc, const double2* r64, float2* r32,
                      cudaStream_t st);
 int launch_ref_update(int n, int rhs0, int nrhs, const int* act, const KScal* sc, double2* x64, const float2* x32,

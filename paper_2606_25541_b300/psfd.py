@@ -38,6 +38,14 @@ class Report(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("status", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("grid", Grid), ("n_layers", ctypes.c_int), ("n_complex", ctypes.POINTER(ctypes.c_double)),
+                ("thickness_nm", ctypes.POINTER(ctypes.c_double)), ("n_sub", ctypes.POINTER(ctypes.c_double)),
+                ("eps", ctypes.POINTER(ctypes.c_double)), ("n_rhs", ctypes.c_int),
+                ("theta_deg", ctypes.POINTER(ctypes.c_double)), ("phi_deg", ctypes.POINTER(ctypes.c_double)),
+                ("pol", ctypes.POINTER(ctypes.c_int))]
+
+
 class PsfdError(RuntimeError):
     def __init__(self, status, msg=""):
         super().__init__(f"psfd status {status}: {msg}")
@@ -71,6 +79,14 @@ _SIGS = {
     "psfd_test_fft": (_I, [_I, _I, _I, _I, _P]),
     "psfd_apply_fp32_static": (_I, [ctypes.POINTER(Grid), _I, _D, _D, _D, ctypes.c_double, ctypes.c_double, _P,
                                     _P, _P, _P]),
+    "psfd_server_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _I, ctypes.POINTER(SolveOpts)]),
+    "psfd_server_destroy": (_I, [_P]),
+    "psfd_server_submit": (_I, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)]),
+    "psfd_server_progress": (_I, [_P, _IP]),
+    "psfd_server_status": (_I, [_P, ctypes.c_longlong, _IP, _IP]),
+    "psfd_server_orders": (_I, [_P, ctypes.c_longlong, _I, _I, _IP, _IP, _D, _D, _D]),
+    "psfd_server_release": (_I, [_P, ctypes.c_longlong]),
+    "psfd_server_memory": (_I, [_P, ctypes.POINTER(ctypes.c_size_t), _IP]),
     "psfd_launch_count": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "psfd_profile_enable": (_I, [_I]),
     "psfd_profile_classes": (_I, []),
@@ -322,3 +338,91 @@ def fft_inplace(data, inverse: bool = False):
     if st != OK:
         raise PsfdError(st, strerror(st))
     return data
+
+
+class Server:
+    """Serving loop: queue mask-clip requests, drive progress(), collect orders per request."""
+
+    def __init__(self, precision: int = FP32_REFINED, hbm_budget: int = 0, slots_per_context: int = 18,
+                 tol=1e-8, max_iter=400, max_outer=12, inner_tol=1e-4, check_every=4):
+        self.lib = load()
+        self.h = ctypes.c_void_p()
+        o = SolveOpts(float(tol), int(max_iter), int(max_outer), float(inner_tol), int(check_every))
+        st = self.lib.psfd_server_create(ctypes.byref(self.h), int(precision), ctypes.c_size_t(int(hbm_budget)),
+                                         int(slots_per_context), ctypes.byref(o))
+        if st != OK:
+            raise PsfdError(st, strerror(st))
+
+    def _check(self, st):
+        if st != OK:
+            raise PsfdError(st, strerror(st))
+
+    def close(self):
+        if self.h:
+            self.lib.psfd_server_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, prob, theta=None, phi=None, pol=None) -> int:
+        """Queue one clip (a layouts.Problem); illuminations default to the problem's."""
+        th = np.ascontiguousarray(prob.theta_deg if theta is None else theta, dtype=np.float64).reshape(-1)
+        ph = np.ascontiguousarray(prob.phi_deg if phi is None else phi, dtype=np.float64).reshape(-1)
+        po = np.ascontiguousarray(prob.pol if pol is None else pol, dtype=np.int32).reshape(-1)
+        n = _c128(prob.n_layers).reshape(-1)
+        nn = n.view(np.float64) if n.size else np.zeros(2, np.float64)
+        d = np.ascontiguousarray(prob.d_layers, dtype=np.float64).reshape(-1)
+        d = d if d.size else np.zeros(1)
+        ns = np.array([complex(prob.n_sub).real, complex(prob.n_sub).imag], dtype=np.float64)
+        eps = _c128(prob.eps)
+        g = make_grid(prob.nx, prob.ny, prob.nslab, prob.nf, prob.dx, prob.dy, prob.dz, prob.wavelength,
+                      prob.eps_bg)
+        q = Request(g, int(n.size), _dptr(nn), _dptr(d), _dptr(ns), _dptr(eps.view(np.float64)), int(th.size),
+                    _dptr(th), _dptr(ph), po.ctypes.data_as(_IP))
+        t = ctypes.c_longlong(0)
+        self._check(self.lib.psfd_server_submit(self.h, ctypes.byref(q), ctypes.byref(t)))
+        return int(t.value)
+
+    def progress(self) -> int:
+        n = ctypes.c_int(0)
+        self._check(self.lib.psfd_server_progress(self.h, ctypes.byref(n)))
+        return n.value
+
+    def status(self, ticket: int):
+        state, status = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self.lib.psfd_server_status(self.h, ctypes.c_longlong(ticket), ctypes.byref(state),
+                                                ctypes.byref(status)))
+        return state.value, status.value
+
+    def orders(self, ticket: int, rhs: int = 0, capacity: int = 65536):
+        n = ctypes.c_int(0)
+        mn = np.zeros(2 * capacity, np.int32)
+        amp = np.zeros(6 * capacity, np.float64)
+        sp = np.zeros(4 * capacity, np.float64)
+        eff = np.zeros(capacity, np.float64)
+        self._check(self.lib.psfd_server_orders(self.h, ctypes.c_longlong(ticket), int(rhs), int(capacity),
+                                                ctypes.byref(n), mn.ctypes.data_as(_IP), _dptr(amp), _dptr(sp),
+                                                _dptr(eff)))
+        k = n.value
+        a = amp[:6 * k].view(np.complex128).reshape(k, 3)
+        s = sp[:4 * k].view(np.complex128).reshape(k, 2)
+        return {"m": mn[0:2 * k:2].copy(), "n": mn[1:2 * k:2].copy(), "amp": a.copy(), "a_s": s[:, 0].copy(),
+                "a_p": s[:, 1].copy(), "eff": eff[:k].copy()}
+
+    def release(self, ticket: int):
+        self._check(self.lib.psfd_server_release(self.h, ctypes.c_longlong(ticket)))
+
+    def memory(self):
+        used, n = ctypes.c_size_t(0), ctypes.c_int(0)
+        self._check(self.lib.psfd_server_memory(self.h, ctypes.byref(used), ctypes.byref(n)))
+        return int(used.value), n.value
+
+    def run_until_done(self, max_steps: int = 100000) -> int:
+        for k in range(max_steps):
+            if self.progress() == 0:
+                return k + 1
+        raise RuntimeError("server did not finish")

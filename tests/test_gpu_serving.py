@@ -1,0 +1,111 @@
+"""Serving loop: continuous batching of mask-clip requests through psfd_server_*.
+
+A request's diffraction orders must be identical (bitwise) whether it is solved alone or
+admitted into a bucket where other requests are already mid-solve, and must match the
+oracle within the FP32-with-FP64-refinement tolerance (1e-6).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_25541_b300 import layouts
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def psfd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_25541_b300 import psfd as m
+    m.load()
+    return m
+
+
+def _clips():
+    st = layouts.ru_mosi_stack(40)
+    a = layouts.small_clip(nx=16, ny=16, nslab=5, seed=1, stack=st, theta=(6.0, 2.0), phi=(0.0, 30.0), pol=(0, 1))
+    b = layouts.small_clip(nx=16, ny=16, nslab=5, seed=2, stack=st, theta=(4.0,), phi=(45.0,), pol=(1,))
+    c = layouts.small_clip(nx=8, ny=8, nslab=4, seed=3, stack=layouts.ru_mosi_stack(5), theta=(6.0, 6.0),
+                           phi=(0.0, 0.0), pol=(0, 1))
+    d = layouts.small_clip(nx=16, ny=16, nslab=5, seed=4, stack=st, theta=(0.0, 3.0, 8.0), phi=(0.0, 90.0, 10.0),
+                           pol=(1, 0, 1))
+    return [a, b, c, d]
+
+
+def _solve_alone(psfd, prob, precision):
+    srv = psfd.Server(precision, slots_per_context=6, tol=1e-9)
+    t = srv.submit(prob)
+    srv.run_until_done()
+    state, status = srv.status(t)
+    assert state == 2 and status == psfd.OK
+    out = [srv.orders(t, i) for i in range(prob.n_rhs)]
+    srv.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_results_are_identical_alone_and_in_the_mix(psfd, precision):
+    clips = _clips()
+    alone = [_solve_alone(psfd, p, precision) for p in clips]
+
+    srv = psfd.Server(precision, slots_per_context=6, tol=1e-9)
+    t0 = srv.submit(clips[0])
+    t1 = srv.submit(clips[1])
+    for _ in range(3):
+        srv.progress()
+    assert srv.status(t0)[0] == 1 and srv.status(t1)[0] == 1
+    # late arrivals: admitted next to the running requests (same grid) or into a new bucket
+    t2 = srv.submit(clips[2])
+    t3 = srv.submit(clips[3])
+    srv.progress()
+    assert srv.status(t3)[0] >= 1
+    assert srv.status(t0)[0] == 1, "the late request should overlap the running ones"
+    used, n_ctx = srv.memory()
+    assert n_ctx == 2 and used > 0
+    srv.run_until_done()
+    for t, p, ref in zip((t0, t1, t2, t3), clips, alone):
+        state, status = srv.status(t)
+        assert state == 2 and status == psfd.OK
+        for i in range(p.n_rhs):
+            got = srv.orders(t, i)
+            np.testing.assert_array_equal(got["m"], ref[i]["m"])
+            np.testing.assert_array_equal(got["amp"], ref[i]["amp"])
+        srv.release(t)
+    srv.close()
+
+
+def test_served_orders_match_the_oracle(psfd):
+    p = _clips()[3]
+    srv = psfd.Server(psfd.FP32_REFINED, slots_per_context=4, tol=1e-9)
+    t = srv.submit(p)
+    srv.run_until_done()
+    for i in range(p.n_rhs):
+        got = srv.orders(t, i)
+        ref, _, _ = oracle.solve(p, i, rtol=1e-13)
+        key = {(m, n): k for k, (m, n) in enumerate(zip(ref["m"], ref["n"]))}
+        idx = [key[(m, n)] for m, n in zip(got["m"], got["n"])]
+        err = np.linalg.norm(got["amp"] - ref["amp"][idx]) / np.linalg.norm(ref["amp"])
+        assert err < 1e-6, (i, err)
+    srv.close()
+
+
+def test_budget_admits_one_bucket_at_a_time(psfd):
+    clips = _clips()
+    probe = psfd.Server(psfd.FP32_REFINED, slots_per_context=4, tol=1e-9)
+    probe.submit(clips[0])
+    probe.progress()
+    one_bucket, _ = probe.memory()
+    probe.close()
+    srv = psfd.Server(psfd.FP32_REFINED, hbm_budget=int(one_bucket * 1.05), slots_per_context=4, tol=1e-9)
+    ta = srv.submit(clips[0])
+    tc = srv.submit(clips[2])  # other grid: waits for the first bucket to drain
+    srv.progress()
+    assert srv.status(ta)[0] == 1 and srv.status(tc)[0] == 0
+    assert srv.memory()[1] == 1
+    srv.run_until_done()
+    assert srv.status(ta)[0] == 2 and srv.status(tc)[0] == 2
+    ref = _solve_alone(psfd, clips[2], psfd.FP32_REFINED)
+    np.testing.assert_array_equal(srv.orders(tc, 1)["amp"], ref[1]["amp"])
+    srv.close()
