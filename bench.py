@@ -57,7 +57,74 @@ def parse_args(argv=None):
                     help="operator applications/s only (psfd_apply), for kernel captures")
     ap.add_argument("--rhs", type=int, default=18, help="illuminations used by --apply")
     ap.add_argument("--precision", choices=["fp32", "fp64", "both"], default="both", help="--apply precision")
+    ap.add_argument("--serve", type=int, default=24,
+                    help="requests in the serving-loop sample (0 = skip); --serve-only prints only that")
+    ap.add_argument("--serve-only", action="store_true")
+    ap.add_argument("--serve-sizes", type=str, default="64,128")
     return ap.parse_args(argv)
+
+
+def run_serving(n_req: int, sizes, tol: float, inner_tol: float, seed: int = 4, slots: int = 18,
+                budget_gb: float = 120.0):
+    """Seeded Poisson stream of mixed-size Manhattan clips through the continuous-batching server.
+
+    Every request is first solved alone (its isolated service time); the arrival rate is then set
+    to 0.8 of the one-at-a-time capacity and the stream is replayed through psfd_server_*. The
+    one-at-a-time latency under the same arrivals is the FIFO recursion over the isolated
+    service times. Latency = completion - arrival, wall clock."""
+    from paper_2606_25541_b300 import psfd
+    reqs = layouts.serving_requests(n_req, seed=seed, sizes=sizes)
+    kw = dict(hbm_budget=int(budget_gb * 2 ** 30), slots_per_context=slots, tol=tol, inner_tol=inner_tol)
+    service = []
+    srv = psfd.Server(psfd.FP32_REFINED, **kw)
+    srv.submit(reqs[0])
+    srv.run_until_done()  # warm-up
+    for p in reqs:
+        t0 = time.perf_counter()
+        t = srv.submit(p)
+        srv.run_until_done()
+        service.append(time.perf_counter() - t0)
+        srv.release(t)
+    srv.close()
+    rng = np.random.default_rng(seed + 1)
+    rate = 0.8 / float(np.mean(service))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    fifo, done = [], 0.0
+    for a, s in zip(arrivals, service):
+        done = max(a, done) + s
+        fifo.append(done - a)
+    srv = psfd.Server(psfd.FP32_REFINED, **kw)
+    pending, lat, i, peak_ctx = {}, [], 0, 0
+    start = time.perf_counter()
+    while i < n_req or pending:
+        now = time.perf_counter() - start
+        while i < n_req and arrivals[i] <= now:
+            pending[srv.submit(reqs[i])] = arrivals[i]
+            i += 1
+        if not pending:
+            time.sleep(max(0.0, arrivals[i] - now))
+            continue
+        srv.progress()
+        peak_ctx = max(peak_ctx, srv.memory()[1])
+        now = time.perf_counter() - start
+        for t in list(pending):
+            state, status = srv.status(t)
+            if state == 2:
+                if status != psfd.OK:
+                    raise RuntimeError(f"request {t} failed: {psfd.strerror(status)}")
+                lat.append(now - pending.pop(t))
+                srv.release(t)
+    makespan = time.perf_counter() - start
+    srv.close()
+    n_rhs = int(sum(p.n_rhs for p in reqs))
+    return {"requests": n_req, "illuminations": n_rhs, "sizes_nm": list(sizes), "offered_load": 0.8,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "solves_per_s": n_rhs / makespan, "peak_contexts": peak_ctx,
+            "one_at_a_time": {"p50_ms": 1e3 * float(np.percentile(fifo, 50)),
+                              "p99_ms": 1e3 * float(np.percentile(fifo, 99)),
+                              "solves_per_s": n_rhs / float(np.sum(service))},
+            "stream": "seeded Poisson arrivals; 1-18 illuminations, 50-70 nm Manhattan absorber, "
+                      "z from {64,96,128} nm, slab rounded up to 8 planes"}
 
 
 def run_apply(args):
@@ -349,6 +416,11 @@ def run_ours(args):
                 "order_rel_err_fp32_refined_vs_fp64": orders_rel_err(orders32, orders64)}
         s64.close()
 
+    serving = None
+    if args.serve > 0 and world == 1:
+        sizes = tuple(int(s) for s in args.serve_sizes.split(","))
+        serving = run_serving(args.serve, sizes, args.tol, args.inner_tol)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob, rtol=args.tol * 10.0)
@@ -395,6 +467,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "fp64_plain": fp64,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     solver.close()
@@ -414,6 +487,10 @@ def main(argv=None):
         return run_reference(args)
     if args.apply:
         return run_apply(args)
+    if args.serve_only:
+        sizes = tuple(int(s) for s in args.serve_sizes.split(","))
+        print(json.dumps({"mode": "serving", **run_serving(args.serve, sizes, args.tol, args.inner_tol)}), flush=True)
+        return 0
     return run_ours(args)
 
 

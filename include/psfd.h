@@ -74,8 +74,17 @@ typedef struct {
   int max_outer;    /* refinement sweep cap for PSFD_FP32_REFINED [12] */
   double inner_tol; /* relative tolerance of each FP32 inner solve [1e-4] */
   int check_every;  /* iterations between host reads of the device convergence flags [4] */
-  int reserved[4];
+  int krylov;       /* PSFD_BICGSTAB [default] or PSFD_GMRES */
+  int restart;      /* GMRES basis size per sweep [PSFD_KRYLOV_MAX] (<= PSFD_KRYLOV_MAX) */
+  int reserved[2];
 } psfd_solve_opts;
+
+/* Krylov methods. GMRES(m) (classical Gram-Schmidt, Givens rotations) needs fewer operator
+ * applications; BiCGStab needs no growing basis, and on B300 its two cheap vector passes
+ * per iteration make it the faster of the two at the bench sizes. */
+#define PSFD_BICGSTAB 0
+#define PSFD_GMRES 1
+#define PSFD_KRYLOV_MAX 24 /* Krylov vectors a context reserves per illumination */
 
 typedef struct {
   int iterations;   /* Krylov iterations (operator applications / 2), max over RHS */

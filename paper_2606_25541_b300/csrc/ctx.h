@@ -59,6 +59,7 @@ struct psfd_ctx {
   std::vector<int> pol, clip;
   // engine state per rhs slot
   std::vector<int> phase, outer, iters, status;
+  int enq_hi = 0;  // slots covered by the work enqueued by engine_enqueue
   std::vector<double> relres;
   int* h_act = nullptr;      // pinned
   int* h_act64 = nullptr;    // pinned
@@ -79,9 +80,14 @@ struct psfd_ctx {
   double* d_d_l = nullptr;
   int* anomaly = nullptr;
   double2 *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *work64 = nullptr, *side64 = nullptr;
-  double2* k64[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  float2 *x32 = nullptr, *r32 = nullptr, *r032 = nullptr, *p32 = nullptr, *v32 = nullptr, *s32 = nullptr,
-         *t32 = nullptr, *work32 = nullptr;
+  // Krylov vectors in the context's working precision: rs = r64 / ||r64|| (the system each
+  // sweep solves), xc = its solution, pool = KMAX + 1 GMRES basis vectors, z and w (BiCGStab
+  // uses the first six pool vectors); each vector is [max_rhs][U].
+  double2 *rs64 = nullptr, *xc64 = nullptr, *pool64 = nullptr;
+  float2 *x32 = nullptr, *r32 = nullptr, *work32 = nullptr, *pool32 = nullptr;
+  psfd::GmState* gm = nullptr;
+  double2* gpart = nullptr;  // [rhs][KMAX + 1][gblk]
+  int gblk = 1;
   double2* partials = nullptr;
   psfd::KScal *sc = nullptr, *sc64 = nullptr;
   int *act = nullptr, *act64 = nullptr;
@@ -151,6 +157,9 @@ int ctx_set_rhs(psfd_ctx* ctx, int g0, int n, const double* theta, const double*
 
 // Solve engine: one tick advances every slot by one phase step (see engine.cu).
 int engine_tick(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active);
+// The two halves of a tick: enqueue the work (no host wait), then wait and transition.
+int engine_enqueue(psfd_ctx* ctx, const psfd_solve_opts& o, bool* pending);
+int engine_complete(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active);
 psfd_solve_opts solve_defaults(const psfd_solve_opts* opts);
 
 // Copy the orders of the finished slots to the host cache (once per batch of finishes).

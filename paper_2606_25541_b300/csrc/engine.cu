@@ -1,19 +1,25 @@
 // engine.cu -- the solve engine: every illumination ("rhs slot") of a context moves
 // through its own phases, and one tick advances all of them with shared launches.
 //
-//   PH_NEW    right-hand side just built: ||b|| is taken, x = 0, r = b
-//   PH_START  start a Krylov solve: FP32 path -> r32 = r64 / ||r64||, BiCGStab init on r32;
-//             FP64 path -> BiCGStab init on b
-//   PH_INNER  BiCGStab iterating (check_every iterations per tick; the device flag of a slot
-//             drops when its relative residual reaches the inner tolerance)
-//   PH_RESID  FP64 residual r64 = b - A x64 (and the spectra for the orders); the FP32 path
-//             stops when ||r64|| <= tol ||b|| or after max_outer sweeps, else starts again
+//   PH_NEW    right-hand side just built: ||b|| is taken, x64 = 0, r64 = b
+//   PH_START  a refinement sweep starts: rs = r64 / ||r64|| in the working precision (FP32
+//             for PSFD_FP32_REFINED, FP64 for PSFD_FP64) and a Krylov solve of A xc = rs
+//             (GMRES by default, or BiCGStab) is initialised
+//   PH_INNER  Krylov iterations (check_every per tick; the device flag of a slot drops when
+//             its residual estimate reaches the sweep's tolerance, its GMRES cycle is full,
+//             or it breaks down); then x64 += ||r64|| xc
+//   PH_RESID  FP64 residual r64 = b - A x64 (and the spectra for the orders); done when
+//             ||r64|| <= tol ||b||, else a new sweep (at most max_outer)
 //   PH_DONE   orders computed
+// The FP64 path is the same loop with an FP64 Krylov solve to tol/2, so one sweep normally
+// suffices; the FP32 path solves each sweep to inner_tol.
 //
 // Slots in different phases coexist in one batch: every kernel takes a per-slot mask or
 // activity flag, and all reductions are per slot and in a fixed order, so a slot's result
 // does not depend on which other slots share the context or when they were admitted.
-// One host synchronisation per tick reads the per-slot scalars.
+// A tick is split in two so that a caller driving several contexts can overlap them:
+// engine_enqueue puts the tick's work and the read-back of the per-slot scalars on the
+// context's stream; engine_complete waits for it and applies the phase transitions.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -23,9 +29,6 @@
 #include "ctx.h"
 
 namespace psfd {
-
-OpCall<float2> base_call32(psfd_ctx* ctx, int rhs0, int nrhs);
-OpCall<double2> base_call64(psfd_ctx* ctx, int rhs0, int nrhs);
 
 psfd_solve_opts solve_defaults(const psfd_solve_opts* opts) {
   psfd_solve_opts o{};
@@ -46,61 +49,86 @@ int upload_mask(psfd_ctx* ctx, int which, const std::vector<int>& sel) {
   return PSFD_OK;
 }
 
+// The Krylov solve of one refinement sweep: rs x = rs-system in the context's working
+// precision; b = rs, x = xc, GMRES basis / z / w in the pool (BiCGStab uses pool vectors 0-5).
 template <typename C>
-KrylovCall<C> krylov_of(psfd_ctx* ctx, const psfd_solve_opts& o);
-
-template <>
-KrylovCall<float2> krylov_of<float2>(psfd_ctx* ctx, const psfd_solve_opts& o) {
-  KrylovCall<float2> k;
+KrylovCall<C> krylov_common(psfd_ctx* ctx, const psfd_solve_opts& o, OpCall<C> op, C* rs, C* xc, C* work, C* pool,
+                            double tol) {
+  KrylovCall<C> k;
   std::memset(&k, 0, sizeof(k));
-  k.op = base_call32(ctx, 0, ctx->max_rhs);
+  k.op = op;
   k.n = (int)ctx->plan.U;
-  // the scaled FP64 residual is both b and the running residual (init copies b into r)
-  k.b = ctx->r32;
-  k.r = ctx->r32;
-  k.x = ctx->x32;
-  k.r0 = ctx->r032;
-  k.p = ctx->p32;
-  k.v = ctx->v32;
-  k.s = ctx->s32;
-  k.t = ctx->t32;
-  k.work = ctx->work32;
+  const size_t bs = (size_t)ctx->max_rhs * ctx->plan.U;
+  k.b = rs;
+  k.x = xc;
+  k.work = work;
+  k.basis = pool;
+  k.bstride = bs;
+  k.z = pool + (size_t)(KMAX + 1) * bs;
+  k.w = k.z + bs;
+  k.r = pool;
+  k.r0 = pool + bs;
+  k.p = pool + 2 * bs;
+  k.v = pool + 3 * bs;
+  k.s = pool + 4 * bs;
+  k.t = pool + 5 * bs;
+  k.gm = ctx->gm;
+  k.gpart = ctx->gpart;
+  k.gblk = ctx->gblk;
+  k.m = (o.restart > 0 && o.restart < KMAX) ? o.restart : KMAX;
   k.sc = ctx->sc;
   k.act = ctx->act;
   k.h_act = ctx->h_act;
-  k.tol = o.inner_tol;
+  k.tol = tol;
   k.max_iter = o.max_iter;
   k.check_every = o.check_every;
   return k;
 }
 
+template <typename C>
+KrylovCall<C> krylov_of(psfd_ctx* ctx, const psfd_solve_opts& o, int hi);
+
 template <>
-KrylovCall<double2> krylov_of<double2>(psfd_ctx* ctx, const psfd_solve_opts& o) {
-  KrylovCall<double2> k;
-  std::memset(&k, 0, sizeof(k));
-  k.op = base_call64(ctx, 0, ctx->max_rhs);
-  k.n = (int)ctx->plan.U;
-  k.b = ctx->b64;
-  k.x = ctx->x64;
-  k.r = ctx->r64;
-  k.r0 = ctx->k64[0];
-  k.p = ctx->k64[1];
-  k.v = ctx->k64[2];
-  k.s = ctx->k64[3];
-  k.t = ctx->k64[4];
-  k.work = ctx->work64;
-  k.sc = ctx->sc;
-  k.act = ctx->act;
-  k.h_act = ctx->h_act;
-  k.tol = o.tol;
-  k.max_iter = o.max_iter;
-  k.check_every = o.check_every;
-  return k;
+KrylovCall<float2> krylov_of<float2>(psfd_ctx* ctx, const psfd_solve_opts& o, int hi) {
+  return krylov_common<float2>(ctx, o, base_call32(ctx, 0, hi), ctx->r32, ctx->x32, ctx->work32, ctx->pool32,
+                               o.inner_tol);
+}
+
+template <>
+KrylovCall<double2> krylov_of<double2>(psfd_ctx* ctx, const psfd_solve_opts& o, int hi) {
+  // the FP64 path converges in one sweep: inner target below the outer one
+  return krylov_common<double2>(ctx, o, base_call64(ctx, 0, hi), ctx->rs64, ctx->xc64, ctx->work64, ctx->pool64,
+                                0.5 * o.tol);
+}
+
+template <typename C>
+int krylov_start(psfd_ctx* ctx, const psfd_solve_opts& o, int hi, const int* mask) {
+  const KrylovCall<C> k = krylov_of<C>(ctx, o, hi);
+  C* rs = const_cast<C*>(k.b);
+  RC(launch_ref_scale<C>((int)ctx->plan.U, 0, hi, mask, ctx->sc64, ctx->r64, rs, ctx->stream));
+  if (o.krylov == PSFD_BICGSTAB) return bicg_start<C>(k, mask);
+  return gmres_start<C>(k, mask);
+}
+
+template <typename C>
+int krylov_iterate(psfd_ctx* ctx, const psfd_solve_opts& o, int hi) {
+  const KrylovCall<C> k = krylov_of<C>(ctx, o, hi);
+  if (o.krylov == PSFD_BICGSTAB) return bicg_iterate<C>(k, o.check_every);
+  return gmres_iterate<C>(k, o.check_every);
+}
+
+// End of a sweep for the rhs in mask: xc (GMRES: V y), then x64 += ||r64|| xc.
+template <typename C>
+int krylov_finish(psfd_ctx* ctx, const psfd_solve_opts& o, int hi, const int* mask) {
+  const KrylovCall<C> k = krylov_of<C>(ctx, o, hi);
+  if (o.krylov != PSFD_BICGSTAB) RC(gmres_finish<C>(k, mask));
+  RC(launch_ref_update<C>((int)ctx->plan.U, 0, hi, mask, ctx->sc64, ctx->x64, k.x, ctx->stream));
+  return PSFD_OK;
 }
 
 // r64 = b - A x64 with the side spectra, then ||r64||^2 into sc64 / act64, for the slots in mask.
-int fp64_residual(psfd_ctx* ctx, const int* mask, double tol) {
-  OpCall<double2> a = base_call64(ctx, 0, ctx->max_rhs);
+int fp64_residual(psfd_ctx* ctx, const int* mask, double tol, int hi) {
+  OpCall<double2> a = base_call64(ctx, 0, hi);
   a.active = mask;
   a.u = ctx->x64;
   a.out = ctx->r64;
@@ -111,12 +139,12 @@ int fp64_residual(psfd_ctx* ctx, const int* mask, double tol) {
   a.side = ctx->side64;
   const int nb = op_apply<double2>(a);
   RC(nb);
-  RC(launch_norm((int)ctx->plan.U, nb, 0, ctx->max_rhs, mask, nullptr, ctx->partials, ctx->plan.maxblk, 1,
-                 tol * tol, ctx->sc64, ctx->act64, ctx->stream));
+  RC(launch_norm((int)ctx->plan.U, nb, 0, hi, mask, nullptr, ctx->partials, ctx->plan.maxblk, 1, tol * tol,
+                 ctx->sc64, ctx->act64, ctx->stream));
   return PSFD_OK;
 }
 
-int compute_orders(psfd_ctx* ctx, const int* mask) {
+int compute_orders(psfd_ctx* ctx, const int* mask, int hi) {
   OrdersArgs o;
   o.nx = ctx->g.nx;
   o.ny = ctx->g.ny;
@@ -133,19 +161,30 @@ int compute_orders(psfd_ctx* ctx, const int* mask) {
   o.side = ctx->side64;
   o.out = ctx->d_ordout;
   o.mask = mask;
-  RC(launch_orders(o, ctx->max_rhs, ctx->stream));
+  RC(launch_orders(o, hi, ctx->stream));
   ctx->orders_on_host = false;
   return PSFD_OK;
 }
 
 }  // namespace
 
-int engine_tick(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
-  const int R = ctx->max_rhs;
+// Launches of a tick cover slots [0, hi): hi is one past the last slot with work.
+static int busy_hi(const psfd_ctx* ctx) {
+  int hi = 0;
+  for (int g = 0; g < ctx->max_rhs; ++g)
+    if (ctx->phase[g] != PH_FREE && ctx->phase[g] != PH_DONE) hi = g + 1;
+  return hi;
+}
+
+int engine_enqueue(psfd_ctx* ctx, const psfd_solve_opts& o, bool* pending) {
+  const int R = busy_hi(ctx);
   const size_t U = ctx->plan.U;
   const bool f32 = ctx->precision == PSFD_FP32_REFINED;
   cudaStream_t st = ctx->stream;
   const int vblk = std::max(1, std::min(ctx->plan.maxblk, (int)((U + 8191) / 8192)));
+  *pending = false;
+  ctx->enq_hi = R;
+  if (R == 0) return PSFD_OK;
   std::vector<int> sel(R);
   auto select = [&](int ph) {
     int n = 0;
@@ -155,9 +194,6 @@ int engine_tick(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
     }
     return n;
   };
-
-  // ---- A: enqueue the work of every phase ------------------------------------------
-  bool enqueued = false;
   if (select(PH_NEW)) {
     RC(upload_mask(ctx, 0, sel));
     RC(launch_norm((int)U, vblk, 0, R, ctx->d_mask[0], ctx->b64, ctx->partials, ctx->plan.maxblk, 0,
@@ -170,119 +206,113 @@ int engine_tick(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
       CK(cudaMemsetAsync(ctx->side64 + (size_t)g * 6 * ctx->plan.plane, 0, sizeof(double2) * 6 * ctx->plan.plane,
                          st));
     }
-    enqueued = true;
+    *pending = true;
   }
   if (select(PH_RESID)) {
     RC(upload_mask(ctx, 1, sel));
-    RC(fp64_residual(ctx, ctx->d_mask[1], o.tol));
-    enqueued = true;
+    RC(fp64_residual(ctx, ctx->d_mask[1], o.tol, R));
+    *pending = true;
   }
-  bool any_inner = false;
-  for (int g = 0; g < R; ++g) any_inner = any_inner || ctx->phase[g] == PH_INNER;
-  if (any_inner) {
-    if (f32) RC(bicg_iterate<float2>(krylov_of<float2>(ctx, o), o.check_every));
-    else RC(bicg_iterate<double2>(krylov_of<double2>(ctx, o), o.check_every));
-    enqueued = true;
+  if (select(PH_INNER)) {
+    if (f32) RC(krylov_iterate<float2>(ctx, o, R));
+    else RC(krylov_iterate<double2>(ctx, o, R));
+    *pending = true;
   }
-  if (!enqueued) {
-    int n = 0;
-    for (int g = 0; g < R; ++g) n += ctx->phase[g] != PH_FREE && ctx->phase[g] != PH_DONE;
-    *n_active = n;
-    return PSFD_OK;
+  if (*pending) {  // read-back of the per-slot scalars, waited for in engine_complete
+    CK(cudaMemcpyAsync(ctx->h_sc64, ctx->sc64, sizeof(KScal) * R, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(KScal) * R, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->h_act, ctx->act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
   }
+  return PSFD_OK;
+}
 
-  // ---- B: one synchronisation, read the per-slot scalars --------------------------
-  CK(cudaMemcpyAsync(ctx->h_sc64, ctx->sc64, sizeof(KScal) * R, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(KScal) * R, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(ctx->h_act, ctx->act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-
-  // ---- C: transitions -------------------------------------------------------------
-  std::vector<int> to_update(R, 0), to_start(R, 0), to_done(R, 0);
-  const double tol2 = o.tol * o.tol;
-  for (int g = 0; g < R; ++g) {
-    const KScal& s64 = ctx->h_sc64[g];
-    switch (ctx->phase[g]) {
-      case PH_NEW:
-        ctx->outer[g] = 0;
-        ctx->iters[g] = 0;
-        ctx->status[g] = PSFD_OK;
-        if (!(s64.bnorm2 > 0.0)) {  // zero right-hand side: x = 0 is exact
-          ctx->relres[g] = 0.0;
-          to_done[g] = 1;
-        } else {
-          to_start[g] = 1;
-        }
-        break;
-      case PH_RESID: {
-        const double rel = std::sqrt(s64.rnorm2 / s64.bnorm2);
-        ctx->relres[g] = rel;
-        if (!f32) {
-          if (!(s64.rnorm2 <= tol2 * s64.bnorm2) && ctx->status[g] == PSFD_OK) ctx->status[g] = PSFD_E_NOT_CONVERGED;
-          to_done[g] = 1;
-        } else if (s64.rnorm2 <= tol2 * s64.bnorm2) {
-          ctx->status[g] = PSFD_OK;
-          to_done[g] = 1;
-        } else if (ctx->outer[g] >= o.max_outer || !std::isfinite(rel)) {
-          ctx->status[g] = std::isfinite(rel) ? PSFD_E_NOT_CONVERGED : PSFD_E_BREAKDOWN;
-          to_done[g] = 1;
-        } else {
-          to_start[g] = 1;
-        }
-        break;
-      }
-      case PH_INNER:
-        if (!ctx->h_act[g]) {
-          ctx->iters[g] += ctx->h_sc[g].iters;
-          if (!f32 && ctx->h_sc[g].status != PSFD_OK) ctx->status[g] = ctx->h_sc[g].status;
-          to_update[g] = 1;
-        }
-        break;
-      default:
-        break;
-    }
-  }
-
-  // ---- D: enqueue sweep updates and starts -----------------------------------------
-  bool any = false;
-  for (int g = 0; g < R; ++g) any = any || to_update[g];
-  if (any) {
-    if (f32) {
-      RC(upload_mask(ctx, 2, to_update));
-      RC(launch_ref_update((int)U, 0, R, ctx->d_mask[2], ctx->sc64, ctx->x64, ctx->x32, st));
-    }
-    for (int g = 0; g < R; ++g)
-      if (to_update[g]) ctx->phase[g] = PH_RESID;
-  }
-  any = false;
-  for (int g = 0; g < R; ++g) any = any || to_start[g];
-  if (any) {
-    RC(upload_mask(ctx, 3, to_start));
-    if (f32) {
-      RC(launch_ref_scale((int)U, 0, R, ctx->d_mask[3], ctx->sc64, ctx->r64, ctx->r32, st));
-      RC(bicg_start<float2>(krylov_of<float2>(ctx, o), ctx->d_mask[3]));
-    } else {
-      RC(bicg_start<double2>(krylov_of<double2>(ctx, o), ctx->d_mask[3]));
-    }
+int engine_complete(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
+  const int R = ctx->enq_hi;
+  const size_t U = ctx->plan.U;
+  const bool f32 = ctx->precision == PSFD_FP32_REFINED;
+  cudaStream_t st = ctx->stream;
+  if (R > 0) {
+    CK(cudaStreamSynchronize(st));
+    std::vector<int> to_update(R, 0), to_start(R, 0), to_done(R, 0);
+    const double tol2 = o.tol * o.tol;
+    bool any_update = false, any_start = false, any_done = false;
     for (int g = 0; g < R; ++g) {
-      if (!to_start[g]) continue;
-      if (f32) ctx->outer[g] += 1;  // sweeps started
-      ctx->phase[g] = PH_INNER;
+      const KScal& s64 = ctx->h_sc64[g];
+      switch (ctx->phase[g]) {
+        case PH_NEW:
+          ctx->outer[g] = 0;
+          ctx->iters[g] = 0;
+          ctx->status[g] = PSFD_OK;
+          if (!(s64.bnorm2 > 0.0)) {  // zero right-hand side: x = 0 is exact
+            ctx->relres[g] = 0.0;
+            to_done[g] = 1;
+          } else {
+            to_start[g] = 1;
+          }
+          break;
+        case PH_RESID: {
+          const double rel = std::sqrt(s64.rnorm2 / s64.bnorm2);
+          ctx->relres[g] = rel;
+          if (s64.rnorm2 <= tol2 * s64.bnorm2) {
+            ctx->status[g] = PSFD_OK;
+            to_done[g] = 1;
+          } else if (ctx->outer[g] >= o.max_outer || !std::isfinite(rel)) {
+            ctx->status[g] = std::isfinite(rel) ? PSFD_E_NOT_CONVERGED : PSFD_E_BREAKDOWN;
+            to_done[g] = 1;
+          } else {
+            to_start[g] = 1;
+          }
+          break;
+        }
+        case PH_INNER:
+          if (!ctx->h_act[g]) {  // sweep ended (converged, cycle full or breakdown): correct x64
+            ctx->iters[g] += ctx->h_sc[g].iters;
+            to_update[g] = 1;
+          }
+          break;
+        default:
+          break;
+      }
+      any_update = any_update || to_update[g];
+      any_start = any_start || to_start[g];
+      any_done = any_done || to_done[g];
     }
-  }
-  // ---- E: orders of the slots that finished ----------------------------------------
-  any = false;
-  for (int g = 0; g < R; ++g) any = any || to_done[g];
-  if (any) {
-    RC(upload_mask(ctx, 0, to_done));
-    RC(compute_orders(ctx, ctx->d_mask[0]));
-    for (int g = 0; g < R; ++g)
-      if (to_done[g]) ctx->phase[g] = PH_DONE;
+    // sweep updates, then Krylov starts, then orders of the finished slots
+    if (any_update) {
+      RC(upload_mask(ctx, 2, to_update));
+      if (f32) RC(krylov_finish<float2>(ctx, o, R, ctx->d_mask[2]));
+      else RC(krylov_finish<double2>(ctx, o, R, ctx->d_mask[2]));
+      for (int g = 0; g < R; ++g)
+        if (to_update[g]) ctx->phase[g] = PH_RESID;
+    }
+    if (any_start) {
+      RC(upload_mask(ctx, 3, to_start));
+      if (f32) RC(krylov_start<float2>(ctx, o, R, ctx->d_mask[3]));
+      else RC(krylov_start<double2>(ctx, o, R, ctx->d_mask[3]));
+      for (int g = 0; g < R; ++g) {
+        if (!to_start[g]) continue;
+        ctx->outer[g] += 1;  // sweeps started
+        ctx->phase[g] = PH_INNER;
+      }
+    }
+    if (any_done) {
+      RC(upload_mask(ctx, 0, to_done));
+      RC(compute_orders(ctx, ctx->d_mask[0], R));
+      for (int g = 0; g < R; ++g)
+        if (to_done[g]) ctx->phase[g] = PH_DONE;
+    }
+    ctx->enq_hi = 0;
   }
   int n = 0;
-  for (int g = 0; g < R; ++g) n += ctx->phase[g] != PH_FREE && ctx->phase[g] != PH_DONE;
+  for (int g = 0; g < ctx->max_rhs; ++g) n += ctx->phase[g] != PH_FREE && ctx->phase[g] != PH_DONE;
   *n_active = n;
   return PSFD_OK;
+}
+
+int engine_tick(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
+  bool pending = false;
+  RC(engine_enqueue(ctx, o, &pending));
+  return engine_complete(ctx, o, n_active);
 }
 
 }  // namespace psfd

@@ -53,6 +53,24 @@ struct KScal {
   int pad;
 };
 
+// GMRES state per right-hand side (FP64; the Hessenberg matrix is tiny).
+constexpr int KMAX = 24;  // basis vectors per cycle (PSFD_KRYLOV_MAX)
+struct GmState {
+  int j;       // vectors in the basis of this cycle (the newest is v_j)
+  int m;       // cycle length
+  int status;
+  int pad;
+  double beta;   // ||b|| of the system of this cycle
+  double tol;    // relative residual target
+  double inv_h;  // 1 / ||w|| for the normalisation of the newest vector
+  double resid;  // current residual estimate |g_j| / beta
+  double2 g[KMAX + 1];
+  double cs[KMAX];
+  double2 sn[KMAX];
+  double2 H[(KMAX + 1) * KMAX];  // column j at H[j * (KMAX + 1) + i]
+  double2 y[KMAX];
+};
+
 enum InMode { IN_PLAIN = 0, IN_PUPDATE = 1, IN_SUPDATE = 2 };
 enum EpiMode { EPI_AU = 0, EPI_RESID = 1, EPI_NONE = 2 };
 enum DotBits { DOT_R0_OUT = 1, DOT_OUT_U = 2, DOT_OUT_OUT = 4 };
@@ -91,6 +109,7 @@ struct OpCall {
   int dot_mask;
   C* side;  // [global rhs][2][3][ny][nx] normalised spectra of G*(V u), planes 0, nslab+1
   cudaStream_t stream;
+  unsigned* ctac;  // profiling only: counts the CTAs that did work (null otherwise)
 };
 
 // Runs K1 (V multiply + forward xy FFT), K2 (z column) and K3 (inverse xy + epilogue).
@@ -109,8 +128,12 @@ enum ProfClass {
 };
 void count_launch(int n = 1);
 bool prof_on();
-void prof_begin(int cls, cudaStream_t st);
-void prof_end(int cls, cudaStream_t st, double bytes, double flops);
+// Opens a profiled launch of class cls on stream st; returns a device counter that the
+// launch's CTAs increment when they do work (null when profiling is off).
+unsigned* prof_begin(int cls, cudaStream_t st);
+// Closes it: bytes / flops are the algorithmic figures of a launch in which all ctas_full
+// CTAs work; the profile scales them by the counted fraction.
+void prof_end(int cls, cudaStream_t st, double bytes, double flops, double ctas_full);
 
 }  // namespace psfd
 
@@ -130,11 +153,25 @@ struct KrylovCall {
   double tol;
   int max_iter;
   int check_every;
+  // GMRES: basis vector i of global rhs g at basis + i * bstride + g * n; z = newest basis
+  // vector (operator input), w = operator output; gpart = [rhs][KMAX + 1][gblk] partials
+  C* basis;
+  size_t bstride;
+  C *z, *w;
+  GmState* gm;
+  double2* gpart;
+  int gblk;
+  int m;
 };
 // Start BiCGStab for the right-hand sides selected by mask (device, per global rhs; null =
 // all): x = 0, r = r0 = b, scalars reset; others keep their state. No host synchronisation.
 template <typename C> int bicg_start(const KrylovCall<C>& k, const int* mask);
 // `iters` BiCGStab iterations for every right-hand side whose device flag act is set.
 template <typename C> int bicg_iterate(const KrylovCall<C>& k, int iters);
+// GMRES(m) with classical Gram-Schmidt: start a cycle on b for the rhs in mask, iterate the
+// active ones, and form x = V y for the rhs in mask once their cycle has ended.
+template <typename C> int gmres_start(const KrylovCall<C>& k, const int* mask);
+template <typename C> int gmres_iterate(const KrylovCall<C>& k, int iters);
+template <typename C> int gmres_finish(const KrylovCall<C>& k, const int* mask);
 
 }  // namespace psfd

@@ -79,10 +79,12 @@ __global__ void __launch_bounds__(VEC_NT) k_bicg_init(int n, int nblk, int rhs0,
 template <typename C>
 __global__ void __launch_bounds__(VEC_NT) k_bicg_xr(int n, int nblk, int rhs0, const int* act, const KScal* sc,
                                                      C* x, const C* p, const C* s, const C* t, C* r,
-                                                     const C* r0, double2* partials, int maxblk) {
+                                                     const C* r0, double2* partials, int maxblk,
+                                                     unsigned* ctac) {
   using R = typename RealOf<C>::T;
   const int blk = blockIdx.x, lr = blockIdx.y, g = rhs0 + lr;
   if (!act[g]) return;
+  if (ctac && threadIdx.x == 0) atomicAdd(ctac, 1u);
   const size_t off = (size_t)lr * n;
   const int chunk = (n + nblk - 1) / nblk;
   const int lo = blk * chunk, hi = min(n, lo + chunk);

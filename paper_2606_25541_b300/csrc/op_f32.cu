@@ -1,4 +1,5 @@
-// op_f32.cu -- complex FP32 instantiation of the operator and BiCGStab (bulk path).
+// op_f32.cu -- complex FP32 instantiation of the operator and the Krylov solvers (bulk path).
+#include "gmres.cuh"
 #include "solver.cuh"
 
 namespace psfd {
@@ -8,5 +9,14 @@ template <> int bicg_start<float2>(const KrylovCall<float2>& k, const int* mask)
 }
 template <> int bicg_iterate<float2>(const KrylovCall<float2>& k, int iters) {
   return bicg_iterate_impl<float2>(k, iters);
+}
+template <> int gmres_start<float2>(const KrylovCall<float2>& k, const int* mask) {
+  return gmres_start_impl<float2>(k, mask);
+}
+template <> int gmres_iterate<float2>(const KrylovCall<float2>& k, int iters) {
+  return gmres_iterate_impl<float2>(k, iters);
+}
+template <> int gmres_finish<float2>(const KrylovCall<float2>& k, const int* mask) {
+  return gmres_finish_impl<float2>(k, mask);
 }
 }  // namespace psfd

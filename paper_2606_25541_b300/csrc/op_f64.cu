@@ -1,4 +1,5 @@
-// op_f64.cu -- complex FP64 instantiation of the operator and BiCGStab.
+// op_f64.cu -- complex FP64 instantiation of the operator and the Krylov solvers.
+#include "gmres.cuh"
 #include "solver.cuh"
 
 namespace psfd {
@@ -8,6 +9,15 @@ template <> int bicg_start<double2>(const KrylovCall<double2>& k, const int* mas
 }
 template <> int bicg_iterate<double2>(const KrylovCall<double2>& k, int iters) {
   return bicg_iterate_impl<double2>(k, iters);
+}
+template <> int gmres_start<double2>(const KrylovCall<double2>& k, const int* mask) {
+  return gmres_start_impl<double2>(k, mask);
+}
+template <> int gmres_iterate<double2>(const KrylovCall<double2>& k, int iters) {
+  return gmres_iterate_impl<double2>(k, iters);
+}
+template <> int gmres_finish<double2>(const KrylovCall<double2>& k, const int* mask) {
+  return gmres_finish_impl<double2>(k, mask);
 }
 
 int op_blocks_per_rhs(int nx, int ny, int nslab, bool fp64) {

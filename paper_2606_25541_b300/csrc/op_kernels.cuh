@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(NT) k_plane_fwd(OpCall<C> a) {
   C* twy = twx + NX;
   const int p = blockIdx.x, c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
+  if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
   for (int i = threadIdx.x; i < NX; i += NT) twx[i] = from_c64<C>(a.twx[i]);
   for (int i = threadIdx.x; i < NY; i += NT) twy[i] = from_c64<C>(a.twy[i]);
   const InScal<C> s = load_in_scalars<C, IN>(a, g);
@@ -209,6 +210,7 @@ __global__ void __launch_bounds__(NT) k_plane_inv(OpCall<C> a, const C* uin) {
   double2* scratch = align16<double2>(twy + NY);
   const int p = blockIdx.x, c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
+  if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
   for (int i = threadIdx.x; i < NX; i += NT) twx[i] = from_c64<C>(a.twx[i]);
   for (int i = threadIdx.x; i < NY; i += NT) twy[i] = from_c64<C>(a.twy[i]);
   const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
@@ -242,6 +244,7 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(OpCall<C> a, int rb) {
   const int p = blockIdx.x / nrb, y0 = (blockIdx.x % nrb) * rb;
   const int c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
+  if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
   for (int i = threadIdx.x; i < NX; i += NT) tw[i] = from_c64<C>(a.twx[i]);
   const InScal<C> s = load_in_scalars<C, IN>(a, g);
   const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
@@ -265,6 +268,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(OpCall<C> a, const C* uin, int 
   const int p = blockIdx.x / nrb, y0 = (blockIdx.x % nrb) * rb;
   const int c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
+  if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
   for (int i = threadIdx.x; i < NX; i += NT) tw[i] = from_c64<C>(a.twx[i]);
   const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
   for (int i = threadIdx.x; i < rb * NX; i += NT) tile[(i / NX) * RP + fpad(i % NX)] = a.work[base + i];
@@ -293,6 +297,7 @@ __global__ void __launch_bounds__(NT) k_cols(OpCall<C> a, int tx) {
   const int p = blockIdx.x / ncb, x0 = (blockIdx.x % ncb) * tx;
   const int c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
+  if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
   for (int i = threadIdx.x; i < NY; i += NT) tw[i] = from_c64<C>(a.twy[i]);
   const size_t base = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)NY * a.nx + x0;
   for (int i = threadIdx.x; i < NY * tx; i += NT) {
@@ -375,6 +380,7 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
 
   const int x0 = blockIdx.x * tx, y = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
+  if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
   const int nx = a.nx, ny = a.ny, ns = a.nslab;
   constexpr bool F32 = sizeof(C) == sizeof(float2);
   const int slot = a.rhsp[g].slot;

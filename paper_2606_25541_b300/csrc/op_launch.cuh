@@ -243,14 +243,33 @@ PassCost pass_cost(const OpCall<C>& a) {
   return c;
 }
 
+// CTAs the xy passes (K1 or K3) and the z pass (K2) launch when every rhs is active.
 template <typename C>
-int op_apply_impl(const OpCall<C>& a) {
+void pass_ctas(const OpCall<C>& a, double* xy, double* z) {
+  const double planes = (double)a.nslab * 3.0 * a.nrhs;
+  const int tx = a.nx < Tune<C>::COL_TILE ? a.nx : Tune<C>::COL_TILE;
+  if (use_fused<C>(a.nx, a.ny)) {
+    *xy = planes;
+  } else {
+    const int rb = row_block(a.nx, a.ny, Tune<C>::ROW_ELEMS);
+    *xy = planes * ((double)(a.ny / rb) + (double)(a.nx / tx));
+  }
+  *z = (double)(a.nx / tx) * a.ny * a.nrhs;
+}
+
+template <typename C>
+int op_apply_impl(const OpCall<C>& a0) {
   const bool f64 = sizeof(C) == 16;
   const bool prof = prof_on();
+  OpCall<C> a = a0;
   PassCost cost;
-  if (prof) cost = pass_cost(a);
+  double cx = 0, cz = 0;
+  if (prof) {
+    cost = pass_cost(a);
+    pass_ctas(a, &cx, &cz);
+  }
   int rc;
-  if (prof) prof_begin(f64 ? PK_FWD64 : PK_FWD32, a.stream);
+  a.ctac = prof ? prof_begin(f64 ? PK_FWD64 : PK_FWD32, a.stream) : nullptr;
   switch (a.in_mode) {
     case IN_PLAIN: rc = dispatch_fwd<C, IN_PLAIN>(a); break;
     case IN_PUPDATE: rc = dispatch_fwd<C, IN_PUPDATE>(a); break;
@@ -258,20 +277,20 @@ int op_apply_impl(const OpCall<C>& a) {
     default: return PSFD_E_ARG;
   }
   if (rc) return rc;
-  if (prof) prof_end(f64 ? PK_FWD64 : PK_FWD32, a.stream, cost.bytes[0], cost.flops[0]);
-  if (prof) prof_begin(f64 ? PK_Z64 : PK_Z32, a.stream);
+  if (prof) prof_end(f64 ? PK_FWD64 : PK_FWD32, a.stream, cost.bytes[0], cost.flops[0], cx);
+  a.ctac = prof ? prof_begin(f64 ? PK_Z64 : PK_Z32, a.stream) : nullptr;
   if ((rc = dispatch_z<C>(a))) return rc;
-  if (prof) prof_end(f64 ? PK_Z64 : PK_Z32, a.stream, cost.bytes[1], cost.flops[1]);
+  if (prof) prof_end(f64 ? PK_Z64 : PK_Z32, a.stream, cost.bytes[1], cost.flops[1], cz);
   if (a.epi == EPI_NONE) return blocks_per_rhs_t<C>(a.nx, a.ny, a.nslab);
   const C* uin = a.in_mode == IN_PLAIN ? a.u : a.ustore;
-  if (prof) prof_begin(f64 ? PK_INV64 : PK_INV32, a.stream);
+  a.ctac = prof ? prof_begin(f64 ? PK_INV64 : PK_INV32, a.stream) : nullptr;
   switch (a.epi) {
     case EPI_AU: rc = dispatch_inv<C, EPI_AU>(a, uin); break;
     case EPI_RESID: rc = dispatch_inv<C, EPI_RESID>(a, uin); break;
     default: return PSFD_E_ARG;
   }
   if (rc) return rc;
-  if (prof) prof_end(f64 ? PK_INV64 : PK_INV32, a.stream, cost.bytes[2], cost.flops[2]);
+  if (prof) prof_end(f64 ? PK_INV64 : PK_INV32, a.stream, cost.bytes[2], cost.flops[2], cx);
   return blocks_per_rhs_t<C>(a.nx, a.ny, a.nslab);
 }
 

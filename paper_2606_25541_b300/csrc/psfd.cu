@@ -23,9 +23,14 @@ bool g_prof = false;
 struct ProfRec {
   int cls;
   cudaEvent_t a, b;
-  double bytes, flops;
+  double bytes, flops, ctas;
+  int counter;
 };
 std::vector<ProfRec> g_recs;
+constexpr int kMaxCounters = 1 << 18;
+unsigned* g_counters = nullptr;  // device, one per profiled launch
+int g_next_counter = 0;
+int g_open_counter[PK_N] = {};
 std::vector<cudaEvent_t> g_pool;
 cudaEvent_t g_open[PK_N] = {};
 struct ProfTotal {
@@ -51,17 +56,19 @@ cudaEvent_t take_event() {
 
 void count_launch(int n) { g_launches += (unsigned long long)n; }
 bool prof_on() { return g_prof; }
-void prof_begin(int cls, cudaStream_t st) {
-  if (!g_prof) return;
+unsigned* prof_begin(int cls, cudaStream_t st) {
+  if (!g_prof || !g_counters || g_next_counter >= kMaxCounters) return nullptr;
   cudaEvent_t e = take_event();
   cudaEventRecord(e, st);
   g_open[cls] = e;
+  g_open_counter[cls] = g_next_counter++;
+  return g_counters + g_open_counter[cls];
 }
-void prof_end(int cls, cudaStream_t st, double bytes, double flops) {
+void prof_end(int cls, cudaStream_t st, double bytes, double flops, double ctas) {
   if (!g_prof || !g_open[cls]) return;
   cudaEvent_t e = take_event();
   cudaEventRecord(e, st);
-  g_recs.push_back({cls, g_open[cls], e, bytes, flops});
+  g_recs.push_back({cls, g_open[cls], e, bytes, flops, ctas, g_open_counter[cls]});
   g_open[cls] = nullptr;
 }
 
@@ -88,9 +95,11 @@ Plan make_plan(const psfd_grid& g, int precision, int max_rhs, int max_clips) {
   b += (size_t)g.nf * (3 * sizeof(float) + sizeof(double));  // kz tables
   b += R * p.U * 16 * 4;                                     // b64, x64, r64, work64
   b += R * 6 * p.plane * 16;                                 // side spectra
-  if (precision == PSFD_FP64) b += R * p.U * 16 * 5;         // r0, p, v, s, t
-  else b += R * p.U * 8 * 8;                                 // x, r, r0, p, v, s, t, work (FP32)
+  const size_t kvec = precision == PSFD_FP64 ? 16 : 8;       // Krylov working precision
+  b += R * p.U * kvec * (2 + KMAX + 3);                      // rs, xc, basis, z, w
+  if (precision != PSFD_FP64) b += R * p.U * 8;              // FP32 spectral work
   b += R * NDOT * (size_t)p.maxblk * 16;                     // partial sums
+  b += R * (sizeof(GmState) + (size_t)(KMAX + 1) * p.maxblk * 16);  // GMRES state and partials
   b += R * (2 * sizeof(KScal) + 6 * sizeof(int));            // scalars, flags, masks
   b += R * (size_t)p.max_orders * (2 * sizeof(int) + 12 * sizeof(double)) + R * sizeof(int);
   p.bytes = b;
@@ -169,17 +178,18 @@ int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs
   A(&ctx->work64, R * P.U);
   A(&ctx->side64, R * 6 * P.plane);
   if (precision == PSFD_FP64) {
-    for (int i = 0; i < 5; ++i) A(&ctx->k64[i], R * P.U);
+    A(&ctx->rs64, R * P.U);
+    A(&ctx->xc64, R * P.U);
+    A(&ctx->pool64, R * P.U * (KMAX + 3));
   } else {
     A(&ctx->x32, R * P.U);
     A(&ctx->r32, R * P.U);
-    A(&ctx->r032, R * P.U);
-    A(&ctx->p32, R * P.U);
-    A(&ctx->v32, R * P.U);
-    A(&ctx->s32, R * P.U);
-    A(&ctx->t32, R * P.U);
     A(&ctx->work32, R * P.U);
+    A(&ctx->pool32, R * P.U * (KMAX + 3));
   }
+  ctx->gblk = std::max(1, std::min(P.maxblk, (int)((P.U + 8191) / 8192)));
+  A(&ctx->gm, R);
+  A(&ctx->gpart, R * (size_t)(KMAX + 1) * ctx->gblk);
   A(&ctx->partials, R * NDOT * (size_t)P.maxblk);
   A(&ctx->sc, R);
   A(&ctx->sc64, R);
@@ -635,6 +645,12 @@ int psfd_profile_enable(int on) {
     }
     g_recs.clear();
     for (auto& t : g_tot) t = ProfTotal{};
+    if (!g_counters && cudaMalloc(&g_counters, sizeof(unsigned) * kMaxCounters) != cudaSuccess) {
+      g_counters = nullptr;
+      return PSFD_E_NOMEM;
+    }
+    if (cudaMemset(g_counters, 0, sizeof(unsigned) * kMaxCounters) != cudaSuccess) return PSFD_E_CUDA;
+    g_next_counter = 0;
     g_prof = true;
   } else {
     g_prof = false;
@@ -648,15 +664,20 @@ int psfd_profile_get(int cls, const char** name, unsigned long long* launches, d
                      double* flops) {
   if (cls < 0 || cls >= PK_N) return PSFD_E_ARG;
   if (!g_recs.empty()) {  // fold finished records into the totals
+    std::vector<unsigned> cnt(g_next_counter > 0 ? g_next_counter : 1, 0u);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(cnt.data(), g_counters, sizeof(unsigned) * cnt.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return PSFD_E_CUDA;
     for (auto& r : g_recs) {
       if (cudaEventSynchronize(r.b) != cudaSuccess) return PSFD_E_CUDA;
       float t = 0.f;
       cudaEventElapsedTime(&t, r.a, r.b);
       ProfTotal& T = g_tot[r.cls];
+      const double frac = r.ctas > 0 ? (double)cnt[r.counter] / r.ctas : 1.0;  // share of CTAs that worked
       T.launches += 1;
       T.ms += t;
-      T.bytes += r.bytes;
-      T.flops += r.flops;
+      T.bytes += r.bytes * frac;
+      T.flops += r.flops * frac;
       g_pool.push_back(r.a);
       g_pool.push_back(r.b);
     }

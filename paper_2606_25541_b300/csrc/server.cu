@@ -276,12 +276,20 @@ int psfd_server_progress(psfd_server* s, int* n_pending) {
     if (rc != PSFD_OK) return rc;
     it = admitted ? s->queue.erase(it) : std::next(it);
   }
-  // 2. one engine tick per bucket with work; 3. retire finished requests
+  // 2. one engine tick per bucket with work: all buckets enqueue first (each on its own
+  //    stream, so their kernels overlap on the device), then each is completed;
+  // 3. retire finished requests
+  for (auto& bp : s->buckets) {
+    if (bp->running == 0) continue;
+    bool pending = false;
+    const int rc = engine_enqueue(bp->ctx, s->opts, &pending);
+    if (rc != PSFD_OK) return rc;
+  }
   for (auto& bp : s->buckets) {
     Bucket* b = bp.get();
     if (b->running == 0) continue;
     int active = 0;
-    int rc = engine_tick(b->ctx, s->opts, &active);
+    int rc = engine_complete(b->ctx, s->opts, &active);
     if (rc != PSFD_OK) return rc;
     if ((rc = retire(s, b)) != PSFD_OK) return rc;
   }

@@ -73,12 +73,12 @@ int bicg_iterate_impl(const KrylovCall<C>& k, int iters) {
     k_scal_omega<<<nrhs, VEC_NT, 0, st>>>(rhs0, nb, base.partials, base.maxblk, k.sc, k.act);
     PSFD_CHECK_LAUNCH();
     const int vcls = sizeof(C) == 16 ? PK_VEC64 : PK_VEC32;
-    prof_begin(vcls, st);
+    unsigned* ctac = prof_begin(vcls, st);
     k_bicg_xr<C><<<dim3(nblk, nrhs), VEC_NT, 0, st>>>(k.n, nblk, rhs0, k.act, k.sc, k.x, k.p, k.s, k.t, k.r,
-                                                       k.r0, base.partials, base.maxblk);
+                                                       k.r0, base.partials, base.maxblk, ctac);
     PSFD_CHECK_LAUNCH();
     // reads x, p, s, t, r0; writes x, r
-    prof_end(vcls, st, 7.0 * nrhs * (double)k.n * sizeof(C), 24.0 * nrhs * (double)k.n);
+    prof_end(vcls, st, 7.0 * nrhs * (double)k.n * sizeof(C), 24.0 * nrhs * (double)k.n, (double)nblk * nrhs);
     k_scal_rho<<<nrhs, VEC_NT, 0, st>>>(rhs0, nblk, base.partials, base.maxblk, tol2, k.max_iter, k.sc, k.act);
     PSFD_CHECK_LAUNCH();
   }

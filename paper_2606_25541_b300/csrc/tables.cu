@@ -367,39 +367,50 @@ int launch_norm(int n, int nblk, int rhs0, int nrhs, const int* mask, const doub
   return launched();
 }
 
-// r32 = r64 / ||r64||  (only right-hand sides still active)
-__global__ void k_ref_scale(int n, int rhs0, const int* act, const KScal* sc, const double2* r64, float2* r32) {
+// rs = r64 / ||r64|| in the Krylov precision (right-hand sides selected by act)
+template <typename C>
+__global__ void k_ref_scale(int n, int rhs0, const int* act, const KScal* sc, const double2* r64, C* rs) {
   const int lr = blockIdx.y, g = rhs0 + lr;
   if (!act[g]) return;
   const double inv = 1.0 / sqrt(sc[g].rnorm2);
   const size_t off = (size_t)lr * n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    r32[off + i] = to_c32(cscale(r64[off + i], inv));
+    rs[off + i] = from_c64<C>(cscale(r64[off + i], inv));
 }
 
-// x64 += ||r64|| x32
-__global__ void k_ref_update(int n, int rhs0, const int* act, const KScal* sc, double2* x64, const float2* x32) {
+// x64 += ||r64|| xc
+template <typename C>
+__global__ void k_ref_update(int n, int rhs0, const int* act, const KScal* sc, double2* x64, const C* xc) {
   const int lr = blockIdx.y, g = rhs0 + lr;
   if (!act[g]) return;
   const double s = sqrt(sc[g].rnorm2);
   const size_t off = (size_t)lr * n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    x64[off + i] = cadd(x64[off + i], cscale(to_c64(x32[off + i]), s));
+    x64[off + i] = cadd(x64[off + i], cscale(as_c64(xc[off + i]), s));
 }
 
-int launch_ref_scale(int n, int rhs0, int nrhs, const int* act, const KScal* sc, const double2* r64, float2* r32,
+template <typename C>
+int launch_ref_scale(int n, int rhs0, int nrhs, const int* act, const KScal* sc, const double2* r64, C* rs,
                      cudaStream_t st) {
   const int bx = (n + 256 * 8 - 1) / (256 * 8);
-  k_ref_scale<<<dim3(bx, nrhs), 256, 0, st>>>(n, rhs0, act, sc, r64, r32);
+  k_ref_scale<C><<<dim3(bx, nrhs), 256, 0, st>>>(n, rhs0, act, sc, r64, rs);
   return launched();
 }
 
-int launch_ref_update(int n, int rhs0, int nrhs, const int* act, const KScal* sc, double2* x64, const float2* x32,
+template <typename C>
+int launch_ref_update(int n, int rhs0, int nrhs, const int* act, const KScal* sc, double2* x64, const C* xc,
                       cudaStream_t st) {
   const int bx = (n + 256 * 8 - 1) / (256 * 8);
-  k_ref_update<<<dim3(bx, nrhs), 256, 0, st>>>(n, rhs0, act, sc, x64, x32);
+  k_ref_update<C><<<dim3(bx, nrhs), 256, 0, st>>>(n, rhs0, act, sc, x64, xc);
   return launched();
 }
+template int launch_ref_scale<float2>(int, int, int, const int*, const KScal*, const double2*, float2*, cudaStream_t);
+template int launch_ref_scale<double2>(int, int, int, const int*, const KScal*, const double2*, double2*,
+                                       cudaStream_t);
+template int launch_ref_update<float2>(int, int, int, const int*, const KScal*, double2*, const float2*,
+                                       cudaStream_t);
+template int launch_ref_update<double2>(int, int, int, const int*, const KScal*, double2*, const double2*,
+                                        cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // FFT test hook: `count` contiguous length-N transforms, B per CTA.

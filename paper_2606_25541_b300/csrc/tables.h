@@ -62,9 +62,11 @@ int launch_rhs(int rhs0, int nrhs, RhsParam* rp, const ModeEntry* modes, int nx,
 int launch_orders(const OrdersArgs& a, int nrhs, cudaStream_t st);
 int launch_norm(int n, int nblk, int rhs0, int nrhs, const int* mask, const double2* v, double2* partials,
                 int maxblk, int mode, double tol2, KScal* sc, int* act, cudaStream_t st);
-int launch_ref_scale(int n, int rhs0, int nrhs, const int* act, const KScal* sc, const double2* r64, float2* r32,
+template <typename C>
+int launch_ref_scale(int n, int rhs0, int nrhs, const int* act, const KScal* sc, const double2* r64, C* rs,
                      cudaStream_t st);
-int launch_ref_update(int n, int rhs0, int nrhs, const int* act, const KScal* sc, double2* x64, const float2* x32,
+template <typename C>
+int launch_ref_update(int n, int rhs0, int nrhs, const int* act, const KScal* sc, double2* x64, const C* xc,
                       cudaStream_t st);
 int launch_test_fft(int n, int count, bool inv, bool fp64, void* data, const double2* tw);
 

@@ -272,3 +272,37 @@ def random_field(shape, seed: int, dtype=np.complex128) -> np.ndarray:
     """Seeded complex Gaussian test vector (for operator-level parity checks)."""
     rng = np.random.default_rng(seed)
     return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(dtype)
+
+
+def serving_requests(n: int, seed: int = 4, sizes=(64, 128), z_choices=(64, 96, 128), max_rhs: int = 18,
+                     slab_quantum: int = 8):
+    """Seeded stream of mask-clip requests for the serving loop.
+
+    Transverse sizes from `sizes` (independently in x and y) at 1 nm, a z extent from
+    `z_choices`, an absorber of U{50..70} nm with a Manhattan layout (30-50 % fill, 4 nm snap,
+    +-2 % index jitter) placed on the lowest planes of a slab rounded up to a multiple of
+    `slab_quantum` planes (vacuum above; requests of similar thickness then share a grid),
+    and 1..max_rhs illuminations (polar 0..8 deg, azimuth 0..90 deg, s or p).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    stack = ru_mosi_stack()
+    for k in range(n):
+        nx = int(sizes[rng.integers(len(sizes))])
+        ny = int(sizes[rng.integers(len(sizes))])
+        nz = int(z_choices[rng.integers(len(z_choices))])
+        thick = int(rng.integers(50, 71))
+        nslab = slab_quantum * ((thick + slab_quantum - 1) // slab_quantum)
+        mask, labels = manhattan_mask(nx, ny, rng)
+        nfeat = int(labels.max()) + 1
+        scale = 1.0 + rng.uniform(-0.02, 0.02, size=max(nfeat, 1))
+        n_map = np.where(labels >= 0, N_ABSORBER * scale[np.maximum(labels, 0)], 1.0)
+        eps = extrude(mask, nslab, n_map=n_map)
+        eps[thick:] = 1.0
+        n_rhs = int(rng.integers(1, max_rhs + 1))
+        th = np.round(rng.uniform(0.0, 8.0, n_rhs), 1)
+        ph = np.round(rng.uniform(0.0, 90.0, n_rhs), 0)
+        po = rng.integers(0, 2, n_rhs)
+        out.append(_problem(nx, ny, nslab, padded_nf(nslab, nz), 1.0, 1.0, eps, stack, th, ph, po,
+                            f"request_{k}_{nx}x{ny}x{nslab}_{n_rhs}rhs"))
+    return out

@@ -27,10 +27,13 @@ class Grid(ctypes.Structure):
                 ("wavelength", ctypes.c_double), ("eps_bg", ctypes.c_double)]
 
 
+BICGSTAB, GMRES = 0, 1
+
+
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_outer", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int), ("krylov", ctypes.c_int),
+                ("restart", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class Report(ctypes.Structure):
@@ -265,8 +268,10 @@ class Solver:
                                                    po.ctypes.data_as(_IP)))
         self.n_rhs = int(th.size)
 
-    def solve(self, tol=1e-10, max_iter=500, max_outer=12, inner_tol=1e-4, check_every=4, raise_on_error=True):
-        o = SolveOpts(float(tol), int(max_iter), int(max_outer), float(inner_tol), int(check_every))
+    def solve(self, tol=1e-10, max_iter=500, max_outer=12, inner_tol=1e-4, check_every=4, raise_on_error=True,
+              krylov=BICGSTAB, restart=0):
+        o = SolveOpts(float(tol), int(max_iter), int(max_outer), float(inner_tol), int(check_every), int(krylov),
+                      int(restart))
         r = Report()
         st = self.lib.psfd_solve(self.ctx, ctypes.byref(o), ctypes.byref(r))
         rep = {"iterations": r.iterations, "outer": r.outer, "relres": r.relres, "seconds": r.seconds,
@@ -344,10 +349,11 @@ class Server:
     """Serving loop: queue mask-clip requests, drive progress(), collect orders per request."""
 
     def __init__(self, precision: int = FP32_REFINED, hbm_budget: int = 0, slots_per_context: int = 18,
-                 tol=1e-8, max_iter=400, max_outer=12, inner_tol=1e-4, check_every=4):
+                 tol=1e-8, max_iter=400, max_outer=12, inner_tol=1e-4, check_every=4, krylov=BICGSTAB, restart=0):
         self.lib = load()
         self.h = ctypes.c_void_p()
-        o = SolveOpts(float(tol), int(max_iter), int(max_outer), float(inner_tol), int(check_every))
+        o = SolveOpts(float(tol), int(max_iter), int(max_outer), float(inner_tol), int(check_every), int(krylov),
+                      int(restart))
         st = self.lib.psfd_server_create(ctypes.byref(self.h), int(precision), ctypes.c_size_t(int(hbm_budget)),
                                          int(slots_per_context), ctypes.byref(o))
         if st != OK:

@@ -157,20 +157,22 @@ def contact_hole_reference():
     return prob, orders, x
 
 
-def test_solve_fp64_matches_oracle_orders(psfd, contact_hole_reference):
+@pytest.mark.parametrize("krylov", [0, 1])
+def test_solve_fp64_matches_oracle_orders(psfd, contact_hole_reference, krylov):
     prob, ref, xref = contact_hole_reference
     s = _solver(psfd, prob, psfd.FP64)
-    rep = s.solve(tol=1e-12, max_iter=400)
+    rep = s.solve(tol=1e-12, max_iter=400, krylov=krylov)
     assert rep["relres"] <= 1e-12
     got = s.diffraction_orders(0)
     assert _orders_err(got, ref) < 1e-9
     assert _rel(s.get_solution(0), xref) < 1e-9
 
 
-def test_solve_fp32_refined_matches_oracle_orders(psfd, contact_hole_reference):
+@pytest.mark.parametrize("krylov", [0, 1])
+def test_solve_fp32_refined_matches_oracle_orders(psfd, contact_hole_reference, krylov):
     prob, ref, xref = contact_hole_reference
     s = _solver(psfd, prob, psfd.FP32_REFINED)
-    rep = s.solve(tol=1e-8, inner_tol=1e-4, max_iter=200, max_outer=10)
+    rep = s.solve(tol=1e-8, inner_tol=1e-4, max_iter=200, max_outer=10, krylov=krylov)
     assert rep["relres"] <= 1e-8
     assert rep["outer"] >= 2
     got = s.diffraction_orders(0)
