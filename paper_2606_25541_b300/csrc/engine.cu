@@ -72,6 +72,7 @@ KrylovCall<C> krylov_common(psfd_ctx* ctx, const psfd_solve_opts& o, OpCall<C> o
   k.v = pool + 3 * bs;
   k.s = pool + 4 * bs;
   k.t = pool + 5 * bs;
+  k.pn = pool + 6 * bs;
   k.gm = ctx->gm;
   k.gpart = ctx->gpart;
   k.gblk = ctx->gblk;

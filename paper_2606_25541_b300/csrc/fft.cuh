@@ -144,35 +144,93 @@ template <typename C, bool INV> struct Dft<C, 5, INV> {
   }
 };
 
+// Radix-R DFT of inputs whose upper half is zero (v[r] = 0 for r >= R/2; only v[0..R/2)
+// are read), as the first stage of a transform whose input is zero on [N/2, N).
+template <typename C, int R, bool INV> struct DftHalf;
+
+template <typename C, bool INV> struct DftHalf<C, 2, INV> {
+  __device__ __forceinline__ static void run(C* v) { v[1] = v[0]; }
+};
+
+template <typename C, bool INV> struct DftHalf<C, 4, INV> {
+  __device__ __forceinline__ static void run(C* v) {
+    const C a = v[0], b = v[1];
+    const C jb = INV ? cmul_i(b) : cmul_mi(b);  // exp(-+ i pi / 2) b
+    v[0] = cadd(a, b);
+    v[1] = cadd(a, jb);
+    v[2] = csub(a, b);
+    v[3] = csub(a, jb);
+  }
+};
+
+// X[2j] = DFT4(v)[j], X[2j+1] = DFT4(v_n w8^n)[j] for the four nonzero inputs.
+template <typename C, bool INV> struct DftHalf<C, 8, INV> {
+  __device__ __forceinline__ static void run(C* v) {
+    using R = typename RealOf<C>::T;
+    const R h = (R)0.70710678118654752440;  // 1/sqrt(2)
+    C e0 = v[0], e1 = v[1], e2 = v[2], e3 = v[3];
+    C o0 = v[0], o1, o2, o3;
+    if (INV) {
+      o1 = mk((v[1].x - v[1].y) * h, (v[1].x + v[1].y) * h);
+      o2 = cmul_i(v[2]);
+      o3 = mk(-(v[3].x + v[3].y) * h, (v[3].x - v[3].y) * h);
+    } else {
+      o1 = mk((v[1].x + v[1].y) * h, (v[1].y - v[1].x) * h);
+      o2 = cmul_mi(v[2]);
+      o3 = mk((v[3].y - v[3].x) * h, -(v[3].x + v[3].y) * h);
+    }
+    dft4<C, INV>(e0, e1, e2, e3);
+    dft4<C, INV>(o0, o1, o2, o3);
+    v[0] = e0; v[2] = e1; v[4] = e2; v[6] = e3;
+    v[1] = o0; v[3] = o1; v[5] = o2; v[7] = o3;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Stockham stages. Butterfly b of a radix-R stage (after stages whose radices multiply
 // to NS) reads elements b + r N/R, twiddles them by exp(-2 pi i r (b mod NS)/(NS R)),
 // and writes element r of its DFT to (b / NS) NS R + (b mod NS) + r NS.
+// Element i sits at fpad(i) * ES. Whenever the R elements of a butterfly stay inside one
+// run of eight (or are spaced by a multiple of eight) their padded offsets differ by
+// compile-time constants, so only the first address of a butterfly is computed.
+// HALF_IN: the input is zero on [N/2, N) and only its lower half is read.
 // ---------------------------------------------------------------------------
-template <typename C, int N, int G, bool INV, int S, int NS>
-__device__ __forceinline__ void fft_stages(C* a, int es, int g, const C* tw, bool valid) {
+template <typename C, int N, int G, bool INV, int S, int NS, int ES, bool HALF_IN>
+__device__ __forceinline__ void fft_stages(C* a, int g, const C* tw, bool valid) {
   if constexpr (S < fft_plan_stages(N)) {
     constexpr int R = fft_plan_radix(N, S);
     constexpr int NB = N / R;
     constexpr int K = (NB + G - 1) / G;
     constexpr int TWS = N / (NS * R);
+    constexpr bool HIN = HALF_IN && S == 0 && (R == 2 || R == 4 || R == 8);
+    constexpr int RL = HIN ? R / 2 : R;  // inputs read per butterfly
     C v[K][R];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int b = g + k * G;
       if (valid && (NB % G == 0 || b < NB)) {
-        const int jj = b % NS;
+        if constexpr (NB % 8 == 0) {
+          const C* src = a + fpad(b) * ES;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[k][r] = a[fpad(b + r * NB) * es];
+          for (int r = 0; r < RL; ++r) v[k][r] = src[r * fft_phys(NB) * ES];
+        } else {
+#pragma unroll
+          for (int r = 0; r < RL; ++r) v[k][r] = a[fpad(b + r * NB) * ES];
+        }
         if constexpr (NS > 1) {
+          const int jt = (b % NS) * TWS;
 #pragma unroll
           for (int r = 1; r < R; ++r) {
-            C w = tw[r * jj * TWS];
+            C w = tw[r * jt];
             if (INV) w = cconj(w);
             v[k][r] = cmul(v[k][r], w);
           }
         }
-        Dft<C, R, INV>::run(v[k]);
+        if constexpr (HIN) {
+          DftHalf<C, R, INV>::run(v[k]);
+        } else {
+          Dft<C, R, INV>::run(v[k]);
+        }
       }
     }
     __syncwarp();
@@ -182,28 +240,38 @@ __device__ __forceinline__ void fft_stages(C* a, int es, int g, const C* tw, boo
       if (valid && (NB % G == 0 || b < NB)) {
         const int jj = b % NS;
         const int base = (b / NS) * NS * R + jj;
+        if constexpr (NS % 8 == 0) {
+          C* dst = a + fpad(base) * ES;
 #pragma unroll
-        for (int r = 0; r < R; ++r) a[fpad(base + r * NS) * es] = v[k][r];
+          for (int r = 0; r < R; ++r) dst[r * fft_phys(NS) * ES] = v[k][r];
+        } else if constexpr (NS == 1 && 8 % R == 0) {
+          C* dst = a + fpad(base) * ES;
+#pragma unroll
+          for (int r = 0; r < R; ++r) dst[r * ES] = v[k][r];
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) a[fpad(base + r * NS) * ES] = v[k][r];
+        }
       }
     }
     __syncwarp();
-    fft_stages<C, N, G, INV, S + 1, NS * R>(a, es, g, tw, valid);
+    fft_stages<C, N, G, INV, S + 1, NS * R, ES, HALF_IN>(a, g, tw, valid);
   }
 }
 
 // One length-N transform per group of G lanes. Every lane of the warp must call this
 // (lanes of groups without work pass valid = false) because stages end in __syncwarp.
-template <typename C, int N, bool INV>
-__device__ __forceinline__ void group_fft(C* a, int es, int g, const C* tw, bool valid) {
+template <typename C, int N, bool INV, int ES = 1, bool HALF_IN = false>
+__device__ __forceinline__ void group_fft(C* a, int g, const C* tw, bool valid) {
   constexpr int G = fft_group_lanes(N);
-  fft_stages<C, N, G, INV, 0, 1>(a, es, g, tw, valid);
+  fft_stages<C, N, G, INV, 0, 1, ES, HALF_IN>(a, g, tw, valid);
 }
 
 // Batched transforms by a whole CTA: `count` transforms, transform f starting at
 // a + f' * fs with f' = fpad(f) if PADF (transforms along the second axis of a padded
-// 2-D tile) else f, element i at fpad(i) * es. Each warp handles 32/G transforms at a time.
-template <typename C, int N, bool INV, bool PADF = false>
-__device__ __forceinline__ void cta_fft(C* a, int count, int fs, int es, const C* tw) {
+// 2-D tile) else f, element i at fpad(i) * ES. Each warp handles 32/G transforms at a time.
+template <typename C, int N, bool INV, bool PADF = false, int ES = 1, bool HALF_IN = false>
+__device__ __forceinline__ void cta_fft(C* a, int count, int fs, const C* tw) {
   constexpr int G = fft_group_lanes(N);
   constexpr int GPW = 32 / G;  // groups per warp
   const int lane = threadIdx.x & 31;
@@ -217,7 +285,7 @@ __device__ __forceinline__ void cta_fft(C* a, int count, int fs, int es, const C
     const int f = gid + it * ngroups;
     const bool valid = f < count;
     const int fo = valid ? (PADF ? fpad(f) : f) : 0;
-    group_fft<C, N, INV>(a + fo * fs, es, g, tw, valid);
+    group_fft<C, N, INV, ES, HALF_IN>(a + fo * fs, g, tw, valid);
   }
 }
 

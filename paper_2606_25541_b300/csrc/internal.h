@@ -146,6 +146,7 @@ struct KrylovCall {
   int n;         // complex elements per right-hand side
   const C* b;
   C *x, *r, *r0, *p, *v, *s, *t, *work;
+  C* pn;  // BiCGStab: the updated p when the operator's input stage may not write p in place
   KScal* sc;           // per global rhs
   int* act;            // per global rhs, device
   const int* act_in;   // initial activity (device) or null

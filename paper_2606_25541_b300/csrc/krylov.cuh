@@ -76,9 +76,10 @@ __global__ void __launch_bounds__(VEC_NT) k_bicg_init(int n, int nblk, int rhs0,
 }
 
 // x += alpha p + omega s; r = s - omega t; partials <r0, r> (slot 0) and ||r||^2 (slot 2).
+// The current p is read from pn; when pn is not p it is also copied into p.
 template <typename C>
 __global__ void __launch_bounds__(VEC_NT) k_bicg_xr(int n, int nblk, int rhs0, const int* act, const KScal* sc,
-                                                     C* x, const C* p, const C* s, const C* t, C* r,
+                                                     C* x, const C* pn, C* p, const C* s, const C* t, C* r,
                                                      const C* r0, double2* partials, int maxblk,
                                                      unsigned* ctac) {
   using R = typename RealOf<C>::T;
@@ -92,8 +93,9 @@ __global__ void __launch_bounds__(VEC_NT) k_bicg_xr(int n, int nblk, int rhs0, c
   typename Acc<C>::T d0 = mk((R)0, (R)0), d2 = d0;
   for (int i = lo + threadIdx.x; i < hi; i += VEC_NT) {
     const size_t k = off + i;
-    const C si = s[k];
-    x[k] = cadd(x[k], cadd(cmul(al, p[k]), cmul(om, si)));
+    const C si = s[k], pk = pn[k];
+    if (pn != p) p[k] = pk;
+    x[k] = cadd(x[k], cadd(cmul(al, pk), cmul(om, si)));
     const C ri = csub(si, cmul(om, t[k]));
     r[k] = ri;
     d0 = cadd(d0, cmulc(r0[k], ri));

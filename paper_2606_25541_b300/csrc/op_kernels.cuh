@@ -193,9 +193,9 @@ __global__ void __launch_bounds__(NT) k_plane_fwd(OpCall<C> a) {
     tile[plane_slot<NX>(i)] = cmul(Vp[i], val);
   }
   __syncthreads();
-  cta_fft<C, NX, false, true>(tile, NY, PITCH, 1, twx);
+  cta_fft<C, NX, false, true, 1>(tile, NY, PITCH, twx);
   __syncthreads();
-  cta_fft<C, NY, false, true>(tile, NX, 1, PITCH, twy);
+  cta_fft<C, NY, false, true, PITCH>(tile, NX, 1, twy);
   __syncthreads();
   for (int i = threadIdx.x; i < NX * NY; i += NT) a.work[plane + i] = tile[plane_slot<NX>(i)];
 }
@@ -216,9 +216,9 @@ __global__ void __launch_bounds__(NT) k_plane_inv(OpCall<C> a, const C* uin) {
   const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
   for (int i = threadIdx.x; i < NX * NY; i += NT) tile[plane_slot<NX>(i)] = a.work[plane + i];
   __syncthreads();
-  cta_fft<C, NY, true, true>(tile, NX, 1, PITCH, twy);
+  cta_fft<C, NY, true, true, PITCH>(tile, NX, 1, twy);
   __syncthreads();
-  cta_fft<C, NX, true, true>(tile, NY, PITCH, 1, twx);
+  cta_fft<C, NX, true, true, 1>(tile, NY, PITCH, twx);
   __syncthreads();
   Dots<C> dt;
   zero_dots(dt);
@@ -226,6 +226,116 @@ __global__ void __launch_bounds__(NT) k_plane_inv(OpCall<C> a, const C* uin) {
     epilogue_elem<C, EPI>(a, uin, plane + i, tile[plane_slot<NX>(i)], dt);
   if (a.dot_mask) {
     const int blk = c * a.nslab + p;
+    block_write_dots(dt, a.dot_mask, a.partials + ((size_t)g * NDOT) * a.maxblk + blk, a.maxblk, scratch);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K1 / K3 on half planes: two CTAs per plane, each holding NY/2 rows, so that two
+// planes' worth of CTAs share one SM and one CTA's loads overlap the other's FFTs.
+// The y transform is split by one radix-2 decimation-in-frequency step done while
+// loading: with H = NY/2 and w = exp(-2 pi i / NY),
+//   Y[2m + h] = sum_{r<H} [(x_r + (-1)^h x_{r+H}) w^{r h}] exp(-2 pi i r m / H),
+// so CTA h reads the whole plane (the second read of each element hits L2), forms the
+// H combined rows, and transforms them along x (length NX) and along y (length H),
+// giving the spectral rows of parity h. The inverse uses the conjugate identity
+//   y[2m + h] = sum_{k<H} [(Y_k + (-1)^h Y_{k+H}) w^{-k h}] exp(+2 pi i k m / H)
+// and applies the epilogue to the output rows of parity h.
+// ---------------------------------------------------------------------------
+template <typename C, int IN>
+__device__ __forceinline__ C input_elem_owned(const OpCall<C>& a, size_t idx, const InScal<C>& s, bool own) {
+  if constexpr (IN == IN_PLAIN) {
+    return a.u[idx];
+  } else if constexpr (IN == IN_PUPDATE) {
+    C p = a.u[idx], r = a.r[idx], v = a.v[idx];
+    C val = cadd(r, cmul(s.a, csub(p, cmul(s.b, v))));
+    if (own) a.ustore[idx] = val;
+    return val;
+  } else {
+    C val = csub(a.r[idx], cmul(s.a, a.v[idx]));
+    if (own) a.ustore[idx] = val;
+    return val;
+  }
+}
+
+template <int NX, int NY> __host__ __device__ constexpr int half_tile_elems() {
+  return fft_phys(NY / 2) * plane_pitch<NX>();
+}
+
+template <typename C, int NX, int NY, int IN, int NT>
+__global__ void __launch_bounds__(NT, 2) k_half_fwd(OpCall<C> a) {
+  constexpr int H = NY / 2, PITCH = plane_pitch<NX>();
+  extern __shared__ __align__(16) unsigned char smem[];
+  C* tile = reinterpret_cast<C*>(smem);
+  C* twx = tile + half_tile_elems<NX, NY>();
+  C* twy = twx + NX;  // exp(-2 pi i r / NY), r < H
+  C* twh = twy + H;   // exp(-2 pi i t / H), t < H
+  const int p = blockIdx.x >> 1, h = blockIdx.x & 1, c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
+  if (a.active && !a.active[g]) return;
+  if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
+  for (int i = threadIdx.x; i < NX; i += NT) twx[i] = from_c64<C>(a.twx[i]);
+  for (int i = threadIdx.x; i < H; i += NT) {
+    twy[i] = from_c64<C>(a.twy[i]);
+    twh[i] = from_c64<C>(a.twy[2 * i]);
+  }
+  __syncthreads();
+  const InScal<C> s = load_in_scalars<C, IN>(a, g);
+  const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
+  const C* Vp = a.V + ((size_t)a.rhsp[g].clip * a.nslab + p) * (NX * NY);
+  for (int i = threadIdx.x; i < H * NX; i += NT) {
+    const int r = i / NX;
+    const C v0 = cmul(Vp[i], input_elem_owned<C, IN>(a, plane + i, s, h == 0));
+    const C v1 = cmul(Vp[i + H * NX], input_elem_owned<C, IN>(a, plane + i + H * NX, s, h == 1));
+    tile[fpad(r) * PITCH + fpad(i % NX)] = h ? cmul(csub(v0, v1), twy[r]) : cadd(v0, v1);
+  }
+  __syncthreads();
+  cta_fft<C, NX, false, true, 1>(tile, H, PITCH, twx);
+  __syncthreads();
+  cta_fft<C, H, false, true, PITCH>(tile, NX, 1, twh);
+  __syncthreads();
+  for (int i = threadIdx.x; i < H * NX; i += NT) {
+    const int m = i / NX, x = i % NX;
+    a.work[plane + (size_t)(2 * m + h) * NX + x] = tile[fpad(m) * PITCH + fpad(x)];
+  }
+}
+
+template <typename C, int NX, int NY, int EPI, int NT>
+__global__ void __launch_bounds__(NT, 2) k_half_inv(OpCall<C> a, const C* uin) {
+  constexpr int H = NY / 2, PITCH = plane_pitch<NX>();
+  extern __shared__ __align__(16) unsigned char smem[];
+  C* tile = reinterpret_cast<C*>(smem);
+  C* twx = tile + half_tile_elems<NX, NY>();
+  C* twy = twx + NX;
+  C* twh = twy + H;
+  double2* scratch = align16<double2>(twh + H);
+  const int p = blockIdx.x >> 1, h = blockIdx.x & 1, c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
+  if (a.active && !a.active[g]) return;
+  if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
+  for (int i = threadIdx.x; i < NX; i += NT) twx[i] = from_c64<C>(a.twx[i]);
+  for (int i = threadIdx.x; i < H; i += NT) {
+    twy[i] = from_c64<C>(a.twy[i]);
+    twh[i] = from_c64<C>(a.twy[2 * i]);
+  }
+  __syncthreads();
+  const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
+  for (int i = threadIdx.x; i < H * NX; i += NT) {
+    const int k = i / NX;
+    const C y0 = a.work[plane + i], y1 = a.work[plane + i + H * NX];
+    tile[fpad(k) * PITCH + fpad(i % NX)] = h ? cmul(csub(y0, y1), cconj(twy[k])) : cadd(y0, y1);
+  }
+  __syncthreads();
+  cta_fft<C, H, true, true, PITCH>(tile, NX, 1, twh);
+  __syncthreads();
+  cta_fft<C, NX, true, true, 1>(tile, H, PITCH, twx);
+  __syncthreads();
+  Dots<C> dt;
+  zero_dots(dt);
+  for (int i = threadIdx.x; i < H * NX; i += NT) {
+    const int m = i / NX, x = i % NX;
+    epilogue_elem<C, EPI>(a, uin, plane + (size_t)(2 * m + h) * NX + x, tile[fpad(m) * PITCH + fpad(x)], dt);
+  }
+  if (a.dot_mask) {
+    const int blk = (c * a.nslab + p) * 2 + h;
     block_write_dots(dt, a.dot_mask, a.partials + ((size_t)g * NDOT) * a.maxblk + blk, a.maxblk, scratch);
   }
 }
@@ -252,7 +362,7 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(OpCall<C> a, int rb) {
   for (int i = threadIdx.x; i < rb * NX; i += NT)
     tile[(i / NX) * RP + fpad(i % NX)] = cmul(Vp[i], input_elem<C, IN>(a, base + i, s));
   __syncthreads();
-  cta_fft<C, NX, false>(tile, rb, RP, 1, tw);
+  cta_fft<C, NX, false>(tile, rb, RP, tw);
   __syncthreads();
   for (int i = threadIdx.x; i < rb * NX; i += NT) a.work[base + i] = tile[(i / NX) * RP + fpad(i % NX)];
 }
@@ -273,7 +383,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(OpCall<C> a, const C* uin, int 
   const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
   for (int i = threadIdx.x; i < rb * NX; i += NT) tile[(i / NX) * RP + fpad(i % NX)] = a.work[base + i];
   __syncthreads();
-  cta_fft<C, NX, true>(tile, rb, RP, 1, tw);
+  cta_fft<C, NX, true>(tile, rb, RP, tw);
   __syncthreads();
   Dots<C> dt;
   zero_dots(dt);
@@ -300,17 +410,12 @@ __global__ void __launch_bounds__(NT) k_cols(OpCall<C> a, int tx) {
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
   for (int i = threadIdx.x; i < NY; i += NT) tw[i] = from_c64<C>(a.twy[i]);
   const size_t base = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)NY * a.nx + x0;
-  for (int i = threadIdx.x; i < NY * tx; i += NT) {
-    const int y = i / tx, xx = i % tx;
-    tile[xx * PITCH + fpad(y)] = a.work[base + (size_t)y * a.nx + xx];
-  }
+  const int t0 = threadIdx.x % tx, y0 = threadIdx.x / tx, ystep = NT / tx;
+  for (int y = y0; y < NY; y += ystep) tile[t0 * PITCH + fpad(y)] = a.work[base + (size_t)y * a.nx + t0];
   __syncthreads();
-  cta_fft<C, NY, INV>(tile, tx, PITCH, 1, tw);
+  cta_fft<C, NY, INV>(tile, tx, PITCH, tw);
   __syncthreads();
-  for (int i = threadIdx.x; i < NY * tx; i += NT) {
-    const int y = i / tx, xx = i % tx;
-    a.work[base + (size_t)y * a.nx + xx] = tile[xx * PITCH + fpad(y)];
-  }
+  for (int y = y0; y < NY; y += ystep) a.work[base + (size_t)y * a.nx + t0] = tile[t0 * PITCH + fpad(y)];
 }
 
 // ---------------------------------------------------------------------------
@@ -324,40 +429,49 @@ __global__ void __launch_bounds__(NT) k_cols(OpCall<C> a, int tx) {
 // phi1(w) = (e^w - 1)/w. Near the removable singularity (|delta L| < 1/2) phi1 is summed
 // as its Taylor series; elsewhere S = (E - 1)/(delta (kappa + beta)) with E from the FP64
 // table exp(i beta L). delta is formed from hi/lo splits of beta and kappa so that it
-// stays accurate in FP32 when beta ~ kappa.
+// stays accurate in FP32 when beta ~ kappa. S and E depend on l only through kappa and
+// the parity of l, so one evaluation serves l and nf - l.
 template <typename C>
-__device__ __forceinline__ void green_apply(C& J0, C& J1, C& J2, typename RealOf<C>::T qx,
-                                            typename RealOf<C>::T qy, typename RealOf<C>::T kz,
-                                            typename RealOf<C>::T kh, typename RealOf<C>::T kl, C bh, C bl,
-                                            C E, typename RealOf<C>::T L, typename RealOf<C>::T cinv,
-                                            typename RealOf<C>::T scale) {
+__device__ __forceinline__ void green_scalars(typename RealOf<C>::T kh, typename RealOf<C>::T kl, C bh, C bl, C E,
+                                              typename RealOf<C>::T L, typename RealOf<C>::T cinv,
+                                              typename RealOf<C>::T scale, C& S, C& Es) {
   using R = typename RealOf<C>::T;
   const C d = mk((bh.x - kh) + (bl.x - kl), bh.y + bl.y);
   const C kpb = mk((kh + bh.x) + (kl + bl.x), bh.y + bl.y);
   const C w = mk(-d.y * L, d.x * L);
-  C S;
   if (w.x * w.x + w.y * w.y < (R)0.25) {
+    // phi1(w) = 1 + w/2 (1 + w/3 (1 + ...)), Horner from the innermost term
     C phi = mk((R)1, (R)0);
 #pragma unroll
     for (int k = Prec<C>::PHI_TERMS; k >= 2; --k) {
-      C t = cmul(w, phi);
-      phi = mk((R)1 + t.x / (R)k, t.y / (R)k);
+      const R ik = (R)1 / (R)k;
+      const C t = cmul(w, phi);
+      phi = mk((R)1 + t.x * ik, t.y * ik);
     }
     S = cdiv_fast(mk(-phi.y * L, phi.x * L), kpb);  // i L phi1 / (kappa + beta)
   } else {
     S = cdiv_fast(mk(E.x - (R)1, E.y), cmul(d, kpb));
   }
   S = cscale(S, scale);
-  const C Es = cscale(E, cinv * scale);
+  Es = cscale(E, cinv * scale);
+}
+
+// W = S (J - k (k.J) / kb^2) - (E / kb^2) z (z.J) for k = (qx, qy, kz), in place.
+template <typename C>
+__device__ __forceinline__ void dyadic_apply(C* c0, C* c1, C* c2, typename RealOf<C>::T qx, typename RealOf<C>::T qy,
+                                             typename RealOf<C>::T kz, C S, C Es, typename RealOf<C>::T cinv) {
+  const C J0 = *c0, J1 = *c1, J2 = *c2;
   const C kJ = cadd(cadd(cscale(J0, qx), cscale(J1, qy)), cscale(J2, kz));
   const C ckJ = cscale(kJ, cinv);
-  const C W0 = cmul(S, csub(J0, cscale(ckJ, qx)));
-  const C W1 = cmul(S, csub(J1, cscale(ckJ, qy)));
-  const C W2 = csub(cmul(S, csub(J2, cscale(ckJ, kz))), cmul(Es, J2));
-  J0 = W0;
-  J1 = W1;
-  J2 = W2;
+  *c0 = cmul(S, csub(J0, cscale(ckJ, qx)));
+  *c1 = cmul(S, csub(J1, cscale(ckJ, qy)));
+  *c2 = csub(cmul(S, csub(J2, cscale(ckJ, kz))), cmul(Es, J2));
 }
+
+// Entries of the per-column reflection phase table exp(i beta dz j): j < 8 (fine
+// steps) and 8 j' for j' < NF/16 (coarse steps); the phase of plane pl is the
+// product of entries pl % 8 and 8 + pl / 8 (pl < nslab <= nf/2 - 1).
+template <int NF> __host__ __device__ constexpr int phase_entries() { return 8 + (NF + 15) / 16; }
 
 // grid (nx / tx, ny, nrhs); dynamic shared memory: 3 tx (NF + 1) columns + tables.
 template <typename C, int NF, int NT>
@@ -375,7 +489,8 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
   C* cebl = cb_l + tx;                        // exp(i beta L)
   C* cbdz = cebl + tx;                        // beta dz
   C* R0 = cbdz + tx;                          // 3 tx: T_R E(plane 0)
-  R* cqx = reinterpret_cast<R*>(R0 + 3 * tx);
+  C* ptab = R0 + 3 * tx;                      // tx phase_entries<NF>(): exp(i beta dz j)
+  R* cqx = reinterpret_cast<R*>(ptab + tx * phase_entries<NF>());
   R* cqy = cqx + tx;
 
   const int x0 = blockIdx.x * tx, y = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
@@ -421,18 +536,26 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
       cqy[t] = (R)qy64;
     }
   }
-  // zero padding: plane 0 and planes ns+1 .. NF-1
-  for (int i = threadIdx.x; i < 3 * tx * (NF - ns); i += NT) {
-    const int cc = i / (NF - ns), zz = i % (NF - ns);
+  // The forward transform reads only planes 0 .. NF/2-1 (its input vanishes above, as
+  // ns + 1 <= NF/2): zero plane 0 and planes ns+1 .. NF/2-1, copy planes 1 .. ns.
+  constexpr int HF = NF / 2;
+  const int nz = HF - ns;
+  for (int i = threadIdx.x; i < 3 * tx * nz; i += NT) {
+    const int cc = i / nz, zz = i % nz;
     col[cc * P + fpad(zz == 0 ? 0 : ns + zz)] = mk((R)0, (R)0);
   }
-  const size_t rhs_base = (size_t)lr * 3 * ns * ny * nx;
-  for (int i = threadIdx.x; i < 3 * ns * tx; i += NT) {
-    const int t = i % tx, rest = i / tx, pl = rest % ns, cc = rest / ns;
-    col[(cc * tx + t) * P + fpad(pl + 1)] = a.work[rhs_base + (((size_t)cc * ns + pl) * ny + y) * nx + x0 + t];
+  // thread -> (column t0, planes p0, p0 + pstep, ...): no divisions inside the copy loops
+  const int t0 = threadIdx.x % tx, p0 = threadIdx.x / tx, pstep = NT / tx;
+  const size_t pstride = (size_t)ny * nx;
+  C* gcol = a.work + (size_t)lr * 3 * ns * pstride + (size_t)y * nx + x0 + t0;
+#pragma unroll
+  for (int cc = 0; cc < 3; ++cc) {
+#pragma unroll 4
+    for (int pl = p0; pl < ns; pl += pstep)
+      col[(cc * tx + t0) * P + fpad(pl + 1)] = gcol[((size_t)cc * ns + pl) * pstride];
   }
   __syncthreads();
-  cta_fft<C, NF, false>(col, 3 * tx, P, 1, tw);
+  cta_fft<C, NF, false, false, 1, true>(col, 3 * tx, P, tw);
   __syncthreads();
 
   // constants in the working precision (no FP64 arithmetic in the FP32 kernel)
@@ -440,21 +563,30 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
   const R kbr = (R)a.kb;
   const R cinv = (R)1 / (kbr * kbr);
   const R scale = (R)1 / ((R)NF * (R)nx * (R)ny);
-  for (int i = threadIdx.x; i < tx * NF; i += NT) {
-    const int t = i / NF, l = i % NF;
+  // pairs (l, nf - l) share S and E; l = 0 stands alone, l = nf/2 follows below
+  for (int i = threadIdx.x; i < tx * HF; i += NT) {
+    const int t = i / HF, l = i % HF;
     C E = cebl[t];
-    if (fft_freq(l, NF) & 1) E = cneg(E);
-    C* c0 = col + (0 * tx + t) * P + fpad(l);
-    C* c1 = col + (1 * tx + t) * P + fpad(l);
-    C* c2 = col + (2 * tx + t) * P + fpad(l);
-    C J0 = *c0, J1 = *c1, J2 = *c2;
-    green_apply(J0, J1, J2, cqx[t], cqy[t], kzs[l], kh[l], kl[l], cb_h[t], cb_l[t], E, L, cinv, scale);
-    *c0 = J0;
-    *c1 = J1;
-    *c2 = J2;
+    if (l & 1) E = cneg(E);
+    C S, Es;
+    green_scalars(kh[l], kl[l], cb_h[t], cb_l[t], E, L, cinv, scale, S, Es);
+    const R qx = cqx[t], qy = cqy[t];
+    C* c0 = col + (0 * tx + t) * P;
+    C* c1 = col + (1 * tx + t) * P;
+    C* c2 = col + (2 * tx + t) * P;
+    dyadic_apply(c0 + fpad(l), c1 + fpad(l), c2 + fpad(l), qx, qy, kzs[l], S, Es, cinv);
+    if (l) dyadic_apply(c0 + fpad(NF - l), c1 + fpad(NF - l), c2 + fpad(NF - l), qx, qy, kzs[NF - l], S, Es, cinv);
+  }
+  for (int t = threadIdx.x; t < tx; t += NT) {
+    C E = cebl[t];
+    if (HF & 1) E = cneg(E);
+    C S, Es;
+    green_scalars(kh[HF], kl[HF], cb_h[t], cb_l[t], E, L, cinv, scale, S, Es);
+    dyadic_apply(col + (0 * tx + t) * P + fpad(HF), col + (1 * tx + t) * P + fpad(HF),
+                 col + (2 * tx + t) * P + fpad(HF), cqx[t], cqy[t], kzs[HF], S, Es, cinv);
   }
   __syncthreads();
-  cta_fft<C, NF, true>(col, 3 * tx, P, 1, tw);
+  cta_fft<C, NF, true>(col, 3 * tx, P, tw);
   __syncthreads();
 
   // normalised spectra of G*(V u) on plane 0 and plane ns+1
@@ -510,21 +642,28 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
     R0[1 * tx + t] = from_c64<C>(Ry);
     R0[2 * tx + t] = from_c64<C>(Rz);
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < tx * ns; i += NT) {
-    const int t = i % tx, pl = i / tx;
+  constexpr int PE = phase_entries<NF>();
+  for (int i = threadIdx.x; i < tx * PE; i += NT) {
+    const int t = i / PE, j = i % PE;
+    const R m = j < 8 ? (R)j : (R)(8 * (j - 8));
     const C bdz = cbdz[t];
-    const C ph = cexp_r(mk(-bdz.y * (R)pl, bdz.x * (R)pl));  // exp(i beta pl dz)
+    ptab[i] = cexp_r(mk(-bdz.y * m, bdz.x * m));  // exp(i beta m dz)
+  }
+  __syncthreads();
+  for (int pl = p0; pl < ns; pl += pstep) {
+    const C ph = cmul(ptab[t0 * PE + (pl & 7)], ptab[t0 * PE + 8 + (pl >> 3)]);  // exp(i beta pl dz)
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
-      C* e = col + (cc * tx + t) * P + fpad(pl + 1);
-      *e = cadd(*e, cmul(R0[cc * tx + t], ph));
+      C* e = col + (cc * tx + t0) * P + fpad(pl + 1);
+      *e = cadd(*e, cmul(R0[cc * tx + t0], ph));
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 3 * ns * tx; i += NT) {
-    const int t = i % tx, rest = i / tx, pl = rest % ns, cc = rest / ns;
-    a.work[rhs_base + (((size_t)cc * ns + pl) * ny + y) * nx + x0 + t] = col[(cc * tx + t) * P + fpad(pl + 1)];
+#pragma unroll
+  for (int cc = 0; cc < 3; ++cc) {
+#pragma unroll 4
+    for (int pl = p0; pl < ns; pl += pstep)
+      gcol[((size_t)cc * ns + pl) * pstride] = col[(cc * tx + t0) * P + fpad(pl + 1)];
   }
 }
 

@@ -14,12 +14,14 @@ namespace psfd {
 
 template <typename C> struct Tune;
 template <> struct Tune<float2> {
-  static constexpr int FUSED_MAX = 128;   // largest square plane transformed in one CTA
+  static constexpr int FUSED_MAX = 128;   // largest square plane transformed in shared memory
+  static constexpr int HALF_MIN = 128;    // from this size on, two CTAs per plane (half planes)
   static constexpr int COL_TILE = 16;     // columns per CTA (128-byte segments)
   static constexpr int ROW_ELEMS = 4096;  // row-pass tile size in elements
 };
 template <> struct Tune<double2> {
   static constexpr int FUSED_MAX = 64;
+  static constexpr int HALF_MIN = 1 << 20;  // FP64 planes are FP64-pipe bound: no split
   static constexpr int COL_TILE = 8;
   static constexpr int ROW_ELEMS = 2048;
 };
@@ -27,6 +29,11 @@ template <> struct Tune<double2> {
 template <typename C>
 inline bool use_fused(int nx, int ny) {
   return nx == ny && nx <= Tune<C>::FUSED_MAX && (nx & (nx - 1)) == 0 && nx >= 4;
+}
+
+template <typename C>
+inline bool use_half(int nx, int ny) {
+  return use_fused<C>(nx, ny) && nx >= Tune<C>::HALF_MIN;
 }
 
 inline int row_block(int nx, int ny, int max_elems) {
@@ -37,7 +44,7 @@ inline int row_block(int nx, int ny, int max_elems) {
 
 template <typename C>
 inline int blocks_per_rhs_t(int nx, int ny, int nslab) {
-  if (use_fused<C>(nx, ny)) return 3 * nslab;
+  if (use_fused<C>(nx, ny)) return (use_half<C>(nx, ny) ? 6 : 3) * nslab;
   return 3 * nslab * (ny / row_block(nx, ny, Tune<C>::ROW_ELEMS));
 }
 
@@ -75,6 +82,28 @@ int launch_plane_inv(const OpCall<C>& a, const C* uin) {
   auto k = k_plane_inv<C, N, N, EPI, NT>;
   if (set_smem(k, smem)) return PSFD_E_CUDA;
   k<<<dim3(a.nslab, 3, a.nrhs), NT, smem, a.stream>>>(a, uin);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+template <typename C, int N, int IN>
+int launch_half_fwd(const OpCall<C>& a) {
+  constexpr int NT = 512;
+  const size_t smem = (size_t)(half_tile_elems<N, N>() + 2 * N) * sizeof(C);
+  auto k = k_half_fwd<C, N, N, IN, NT>;
+  if (set_smem(k, smem)) return PSFD_E_CUDA;
+  k<<<dim3(2 * a.nslab, 3, a.nrhs), NT, smem, a.stream>>>(a);
+  PSFD_CHECK_LAUNCH();
+  return PSFD_OK;
+}
+
+template <typename C, int N, int EPI>
+int launch_half_inv(const OpCall<C>& a, const C* uin) {
+  constexpr int NT = 512;
+  const size_t smem = (size_t)(half_tile_elems<N, N>() + 2 * N) * sizeof(C) + 16 + NDOT * 32 * sizeof(double2);
+  auto k = k_half_inv<C, N, N, EPI, NT>;
+  if (set_smem(k, smem)) return PSFD_E_CUDA;
+  k<<<dim3(2 * a.nslab, 3, a.nrhs), NT, smem, a.stream>>>(a, uin);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -118,8 +147,8 @@ int launch_cols(const OpCall<C>& a) {
 template <typename C, int NF>
 size_t zcol_smem(int tx) {
   using R = typename RealOf<C>::T;
-  return (size_t)(3 * tx * (fft_phys(NF) | 1) + NF) * sizeof(C) + 3 * NF * sizeof(R) + 7 * tx * sizeof(C) +
-         2 * tx * sizeof(R) + 16;
+  return (size_t)(3 * tx * (fft_phys(NF) | 1) + NF) * sizeof(C) + 3 * NF * sizeof(R) +
+         (7 + phase_entries<NF>()) * tx * sizeof(C) + 2 * tx * sizeof(R) + 16;
 }
 
 template <typename C, int NF>
@@ -141,7 +170,10 @@ int dispatch_fwd(const OpCall<C>& a) {
     switch (a.nx) {
 #define X(n) \
   case n:    \
-    if constexpr (n <= Tune<C>::FUSED_MAX && (n & (n - 1)) == 0) return launch_plane_fwd<C, n, IN>(a); \
+    if constexpr (n >= Tune<C>::HALF_MIN && n <= Tune<C>::FUSED_MAX && (n & (n - 1)) == 0) \
+      return launch_half_fwd<C, n, IN>(a);                                                   \
+    else if constexpr (n <= Tune<C>::FUSED_MAX && (n & (n - 1)) == 0)                        \
+      return launch_plane_fwd<C, n, IN>(a);                                                  \
     break;
       PSFD_FOR_EACH_LENGTH(X)
 #undef X
@@ -176,7 +208,10 @@ int dispatch_inv(const OpCall<C>& a, const C* uin) {
     switch (a.nx) {
 #define X(n) \
   case n:    \
-    if constexpr (n <= Tune<C>::FUSED_MAX && (n & (n - 1)) == 0) return launch_plane_inv<C, n, EPI>(a, uin); \
+    if constexpr (n >= Tune<C>::HALF_MIN && n <= Tune<C>::FUSED_MAX && (n & (n - 1)) == 0) \
+      return launch_half_inv<C, n, EPI>(a, uin);                                             \
+    else if constexpr (n <= Tune<C>::FUSED_MAX && (n & (n - 1)) == 0)                        \
+      return launch_plane_inv<C, n, EPI>(a, uin);                                            \
     break;
       PSFD_FOR_EACH_LENGTH(X)
 #undef X
@@ -249,7 +284,7 @@ void pass_ctas(const OpCall<C>& a, double* xy, double* z) {
   const double planes = (double)a.nslab * 3.0 * a.nrhs;
   const int tx = a.nx < Tune<C>::COL_TILE ? a.nx : Tune<C>::COL_TILE;
   if (use_fused<C>(a.nx, a.ny)) {
-    *xy = planes;
+    *xy = use_half<C>(a.nx, a.ny) ? 2 * planes : planes;
   } else {
     const int rb = row_block(a.nx, a.ny, Tune<C>::ROW_ELEMS);
     *xy = planes * ((double)(a.ny / rb) + (double)(a.nx / tx));

@@ -44,7 +44,9 @@ int bicg_iterate_impl(const KrylovCall<C>& k, int iters) {
   pv.active = k.act;
   pv.in_mode = IN_PUPDATE;
   pv.u = k.p;
-  pv.ustore = k.p;
+  // Half-plane K1 kernels read every element of p from two CTAs: the updated p goes to
+  // pn there, and the x/r update copies it back into p.
+  pv.ustore = use_half<C>(base.nx, base.ny) ? k.pn : k.p;
   pv.r = k.r;
   pv.v = k.v;
   pv.sc = k.sc;
@@ -74,11 +76,12 @@ int bicg_iterate_impl(const KrylovCall<C>& k, int iters) {
     PSFD_CHECK_LAUNCH();
     const int vcls = sizeof(C) == 16 ? PK_VEC64 : PK_VEC32;
     unsigned* ctac = prof_begin(vcls, st);
-    k_bicg_xr<C><<<dim3(nblk, nrhs), VEC_NT, 0, st>>>(k.n, nblk, rhs0, k.act, k.sc, k.x, k.p, k.s, k.t, k.r,
-                                                       k.r0, base.partials, base.maxblk, ctac);
+    k_bicg_xr<C><<<dim3(nblk, nrhs), VEC_NT, 0, st>>>(k.n, nblk, rhs0, k.act, k.sc, k.x, pv.ustore, k.p, k.s, k.t,
+                                                       k.r, k.r0, base.partials, base.maxblk, ctac);
     PSFD_CHECK_LAUNCH();
-    // reads x, p, s, t, r0; writes x, r
-    prof_end(vcls, st, 7.0 * nrhs * (double)k.n * sizeof(C), 24.0 * nrhs * (double)k.n, (double)nblk * nrhs);
+    // reads x, p, s, t, r0; writes x, r (and p when the update went to pn)
+    const double nvec = pv.ustore == k.p ? 7.0 : 8.0;
+    prof_end(vcls, st, nvec * nrhs * (double)k.n * sizeof(C), 24.0 * nrhs * (double)k.n, (double)nblk * nrhs);
     k_scal_rho<<<nrhs, VEC_NT, 0, st>>>(rhs0, nblk, base.partials, base.maxblk, tol2, k.max_iter, k.sc, k.act);
     PSFD_CHECK_LAUNCH();
   }

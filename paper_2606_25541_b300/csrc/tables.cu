@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(256) k_test_fft(C* data, int count, const doub
   const int nb = min(B, count - f0);
   for (int i = threadIdx.x; i < nb * N; i += blockDim.x) tile[(i / N) * PN + fpad(i % N)] = data[(size_t)f0 * N + i];
   __syncthreads();
-  cta_fft<C, N, INV>(tile, nb, PN, 1, tw);
+  cta_fft<C, N, INV>(tile, nb, PN, tw);
   __syncthreads();
   for (int i = threadIdx.x; i < nb * N; i += blockDim.x) data[(size_t)f0 * N + i] = tile[(i / N) * PN + fpad(i % N)];
 }

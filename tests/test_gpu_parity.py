@@ -179,6 +179,18 @@ def test_solve_fp32_refined_matches_oracle_orders(psfd, contact_hole_reference, 
     assert _orders_err(got, ref) < 1e-6
 
 
+@pytest.mark.parametrize("krylov", [0, 1])
+def test_solve_fp32_half_plane_path_matches_oracle_orders(psfd, krylov):
+    """128 x 128 planes: FP32 K1/K3 run on half planes (two CTAs read every element of the
+    operator input, so the BiCGStab update of p must not be written in place)."""
+    prob = layouts.small_clip(nx=128, ny=128, nslab=4, dx=2.0, dz=2.0, seed=21, stack=layouts.ru_mosi_stack(10))
+    ref, _, _ = oracle.solve(prob, 0, rtol=1e-11)
+    s = _solver(psfd, prob, psfd.FP32_REFINED)
+    rep = s.solve(tol=1e-8, inner_tol=1e-4, max_iter=300, max_outer=10, krylov=krylov)
+    assert rep["relres"] <= 1e-8
+    assert _orders_err(s.diffraction_orders(0), ref) < 1e-6
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_result_is_the_same_alone_and_in_a_batch(psfd, precision):
     prob = _multi_rhs_problem(nx=16, ny=16, nslab=5, seed=9)
