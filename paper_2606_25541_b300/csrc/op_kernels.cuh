@@ -82,25 +82,6 @@ __device__ __forceinline__ InScal<C> load_in_scalars(const OpCall<C>& a, int g) 
   return s;
 }
 
-// The vector the operator is applied to, element idx; updates p or s on the way.
-template <typename C, int IN>
-__device__ __forceinline__ C input_elem(const OpCall<C>& a, size_t idx, const InScal<C>& s) {
-  if constexpr (IN == IN_PLAIN) {
-    return a.u[idx];
-  } else if constexpr (IN == IN_PUPDATE) {
-    // p = r + beta (p - omega v)
-    C p = a.u[idx], r = a.r[idx], v = a.v[idx];
-    C val = cadd(r, cmul(s.a, csub(p, cmul(s.b, v))));
-    a.ustore[idx] = val;
-    return val;
-  } else {
-    // s = r - alpha v
-    C val = csub(a.r[idx], cmul(s.a, a.v[idx]));
-    a.ustore[idx] = val;
-    return val;
-  }
-}
-
 template <typename C> struct Acc;
 template <> struct Acc<float2> { using T = float2; };
 template <> struct Acc<double2> { using T = double2; };
@@ -110,16 +91,107 @@ struct Dots {
   typename Acc<C>::T d[NDOT];
 };
 
+// Split forms of the two element operations: all operands of a few elements are loaded
+// first (so that their loads are in flight together), then combined and stored.
+template <typename C, int IN> struct InVals { C p, r, v; };
+
+template <typename C, int IN>
+__device__ __forceinline__ InVals<C, IN> load_in(const OpCall<C>& a, size_t idx) {
+  InVals<C, IN> o;
+  if constexpr (IN == IN_PLAIN) {
+    o.p = a.u[idx];
+  } else if constexpr (IN == IN_PUPDATE) {
+    o.p = a.u[idx];
+    o.r = a.r[idx];
+    o.v = a.v[idx];
+  } else {
+    o.r = a.r[idx];
+    o.v = a.v[idx];
+  }
+  return o;
+}
+
+// p = r + beta (p - omega v), s = r - alpha v, or the plain input
+template <typename C, int IN>
+__device__ __forceinline__ C combine_in(const InVals<C, IN>& o, const InScal<C>& s) {
+  if constexpr (IN == IN_PLAIN) return o.p;
+  else if constexpr (IN == IN_PUPDATE) return cadd(o.r, cmul(s.a, csub(o.p, cmul(s.b, o.v))));
+  else return csub(o.r, cmul(s.a, o.v));
+}
+
+template <typename C> struct EpiVals { C u, b, r0; };
+
 template <typename C, int EPI>
-__device__ __forceinline__ C epilogue_elem(const OpCall<C>& a, const C* uin, size_t idx, C w, Dots<C>& dt) {
-  C u = uin[idx];
-  C out = csub(u, w);
-  if constexpr (EPI == EPI_RESID) out = csub(a.b[idx], out);
+__device__ __forceinline__ EpiVals<C> load_epi(const OpCall<C>& a, const C* uin, size_t idx) {
+  EpiVals<C> e;
+  e.u = uin[idx];
+  e.b = e.r0 = mk((typename RealOf<C>::T)0, (typename RealOf<C>::T)0);
+  if constexpr (EPI == EPI_RESID) e.b = a.b[idx];
+  if (a.dot_mask & DOT_R0_OUT) e.r0 = a.r0[idx];
+  return e;
+}
+
+template <typename C, int EPI>
+__device__ __forceinline__ void store_epi(const OpCall<C>& a, size_t idx, const EpiVals<C>& e, C w, Dots<C>& dt) {
+  C out = csub(e.u, w);
+  if constexpr (EPI == EPI_RESID) out = csub(e.b, out);
   a.out[idx] = out;
-  if (a.dot_mask & DOT_R0_OUT) dt.d[0] = cadd(dt.d[0], cmulc(a.r0[idx], out));
-  if (a.dot_mask & DOT_OUT_U) dt.d[1] = cadd(dt.d[1], cmulc(out, u));
+  if (a.dot_mask & DOT_R0_OUT) dt.d[0] = cadd(dt.d[0], cmulc(e.r0, out));
+  if (a.dot_mask & DOT_OUT_U) dt.d[1] = cadd(dt.d[1], cmulc(out, e.u));
   if (a.dot_mask & DOT_OUT_OUT) dt.d[2].x += out.x * out.x + out.y * out.y;
-  return out;
+}
+
+// Elements whose loads a thread keeps in flight together (input stage / epilogue).
+template <typename C> struct Batch {
+  static constexpr int IN = sizeof(C) == 8 ? 2 : 1;
+  static constexpr int OUT = sizeof(C) == 8 ? 4 : 2;
+};
+
+// Input stage of n consecutive elements starting at base: tile[slot(i)] = V[i] * input(i),
+// updating p or s in place on the way.
+template <typename C, int IN, int NT, typename Slot>
+__device__ __forceinline__ void stage_in(const OpCall<C>& a, const InScal<C>& s, size_t base, const C* Vp, int n,
+                                         C* tile, Slot slot) {
+  constexpr int BT = Batch<C>::IN;
+  for (int i0 = threadIdx.x; i0 < n; i0 += BT * NT) {
+    InVals<C, IN> in[BT];
+    C vv[BT];
+#pragma unroll
+    for (int j = 0; j < BT; ++j) {
+      const int i = i0 + j * NT;
+      if (i < n) {
+        vv[j] = Vp[i];
+        in[j] = load_in<C, IN>(a, base + i);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < BT; ++j) {
+      const int i = i0 + j * NT;
+      if (i < n) {
+        const C u = combine_in<C, IN>(in[j], s);
+        if constexpr (IN != IN_PLAIN) a.ustore[base + i] = u;
+        tile[slot(i)] = cmul(vv[j], u);
+      }
+    }
+  }
+}
+
+// Epilogue of n consecutive elements starting at base, w(i) = tile[slot(i)].
+template <typename C, int EPI, int NT, typename Slot>
+__device__ __forceinline__ void stage_out(const OpCall<C>& a, const C* uin, size_t base, int n, const C* tile,
+                                          Slot slot, Dots<C>& dt) {
+  constexpr int BT = Batch<C>::OUT;
+  for (int i0 = threadIdx.x; i0 < n; i0 += BT * NT) {
+    EpiVals<C> e[BT];
+#pragma unroll
+    for (int j = 0; j < BT; ++j)
+      if (i0 + j * NT < n) e[j] = load_epi<C, EPI>(a, uin, base + i0 + j * NT);
+#pragma unroll
+    for (int j = 0; j < BT; ++j) {
+      const int i = i0 + j * NT;
+      if (i < n) store_epi<C, EPI>(a, base + i, e[j], tile[slot(i)], dt);
+    }
+  }
 }
 
 __device__ __forceinline__ double2 shfl_down_d2(double2 v, int o) {
@@ -188,10 +260,7 @@ __global__ void __launch_bounds__(NT) k_plane_fwd(OpCall<C> a) {
   const InScal<C> s = load_in_scalars<C, IN>(a, g);
   const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
   const C* Vp = a.V + ((size_t)a.rhsp[g].clip * a.nslab + p) * (NX * NY);
-  for (int i = threadIdx.x; i < NX * NY; i += NT) {
-    C val = input_elem<C, IN>(a, plane + i, s);
-    tile[plane_slot<NX>(i)] = cmul(Vp[i], val);
-  }
+  stage_in<C, IN, NT>(a, s, plane, Vp, NX * NY, tile, [](int i) { return plane_slot<NX>(i); });
   __syncthreads();
   cta_fft<C, NX, false, true, 1>(tile, NY, PITCH, twx);
   __syncthreads();
@@ -222,8 +291,7 @@ __global__ void __launch_bounds__(NT) k_plane_inv(OpCall<C> a, const C* uin) {
   __syncthreads();
   Dots<C> dt;
   zero_dots(dt);
-  for (int i = threadIdx.x; i < NX * NY; i += NT)
-    epilogue_elem<C, EPI>(a, uin, plane + i, tile[plane_slot<NX>(i)], dt);
+  stage_out<C, EPI, NT>(a, uin, plane, NX * NY, tile, [](int i) { return plane_slot<NX>(i); }, dt);
   if (a.dot_mask) {
     const int blk = c * a.nslab + p;
     block_write_dots(dt, a.dot_mask, a.partials + ((size_t)g * NDOT) * a.maxblk + blk, a.maxblk, scratch);
@@ -242,22 +310,6 @@ __global__ void __launch_bounds__(NT) k_plane_inv(OpCall<C> a, const C* uin) {
 //   y[2m + h] = sum_{k<H} [(Y_k + (-1)^h Y_{k+H}) w^{-k h}] exp(+2 pi i k m / H)
 // and applies the epilogue to the output rows of parity h.
 // ---------------------------------------------------------------------------
-template <typename C, int IN>
-__device__ __forceinline__ C input_elem_owned(const OpCall<C>& a, size_t idx, const InScal<C>& s, bool own) {
-  if constexpr (IN == IN_PLAIN) {
-    return a.u[idx];
-  } else if constexpr (IN == IN_PUPDATE) {
-    C p = a.u[idx], r = a.r[idx], v = a.v[idx];
-    C val = cadd(r, cmul(s.a, csub(p, cmul(s.b, v))));
-    if (own) a.ustore[idx] = val;
-    return val;
-  } else {
-    C val = csub(a.r[idx], cmul(s.a, a.v[idx]));
-    if (own) a.ustore[idx] = val;
-    return val;
-  }
-}
-
 template <int NX, int NY> __host__ __device__ constexpr int half_tile_elems() {
   return fft_phys(NY / 2) * plane_pitch<NX>();
 }
@@ -282,11 +334,28 @@ __global__ void __launch_bounds__(NT, 2) k_half_fwd(OpCall<C> a) {
   const InScal<C> s = load_in_scalars<C, IN>(a, g);
   const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
   const C* Vp = a.V + ((size_t)a.rhsp[g].clip * a.nslab + p) * (NX * NY);
-  for (int i = threadIdx.x; i < H * NX; i += NT) {
-    const int r = i / NX;
-    const C v0 = cmul(Vp[i], input_elem_owned<C, IN>(a, plane + i, s, h == 0));
-    const C v1 = cmul(Vp[i + H * NX], input_elem_owned<C, IN>(a, plane + i + H * NX, s, h == 1));
-    tile[fpad(r) * PITCH + fpad(i % NX)] = h ? cmul(csub(v0, v1), twy[r]) : cadd(v0, v1);
+  constexpr int TOT = H * NX;
+  constexpr int BT = TOT % (2 * NT) == 0 ? 2 : 1;  // elements per thread whose loads overlap
+  static_assert(TOT % NT == 0, "half plane must be a multiple of the CTA size");
+  for (int i0 = threadIdx.x; i0 < TOT; i0 += BT * NT) {
+    InVals<C, IN> in0[BT], in1[BT];
+    C va[BT], vb[BT];
+#pragma unroll
+    for (int j = 0; j < BT; ++j) {
+      const int i = i0 + j * NT;
+      va[j] = Vp[i];
+      vb[j] = Vp[i + TOT];
+      in0[j] = load_in<C, IN>(a, plane + i);
+      in1[j] = load_in<C, IN>(a, plane + i + TOT);
+    }
+#pragma unroll
+    for (int j = 0; j < BT; ++j) {
+      const int i = i0 + j * NT, r = i / NX;
+      const C u0 = combine_in<C, IN>(in0[j], s), u1 = combine_in<C, IN>(in1[j], s);
+      if constexpr (IN != IN_PLAIN) a.ustore[plane + i + (h ? TOT : 0)] = h ? u1 : u0;  // owner's half
+      const C v0 = cmul(va[j], u0), v1 = cmul(vb[j], u1);
+      tile[fpad(r) * PITCH + fpad(i % NX)] = h ? cmul(csub(v0, v1), twy[r]) : cadd(v0, v1);
+    }
   }
   __syncthreads();
   cta_fft<C, NX, false, true, 1>(tile, H, PITCH, twx);
@@ -330,9 +399,21 @@ __global__ void __launch_bounds__(NT, 2) k_half_inv(OpCall<C> a, const C* uin) {
   __syncthreads();
   Dots<C> dt;
   zero_dots(dt);
-  for (int i = threadIdx.x; i < H * NX; i += NT) {
-    const int m = i / NX, x = i % NX;
-    epilogue_elem<C, EPI>(a, uin, plane + (size_t)(2 * m + h) * NX + x, tile[fpad(m) * PITCH + fpad(x)], dt);
+  constexpr int TOT = H * NX;
+  constexpr int BT = TOT % (4 * NT) == 0 ? 4 : 1;
+  static_assert(TOT % NT == 0, "half plane must be a multiple of the CTA size");
+  for (int i0 = threadIdx.x; i0 < TOT; i0 += BT * NT) {
+    EpiVals<C> e[BT];
+#pragma unroll
+    for (int j = 0; j < BT; ++j) {
+      const int i = i0 + j * NT;
+      e[j] = load_epi<C, EPI>(a, uin, plane + (size_t)(2 * (i / NX) + h) * NX + i % NX);
+    }
+#pragma unroll
+    for (int j = 0; j < BT; ++j) {
+      const int i = i0 + j * NT, m = i / NX, x = i % NX;
+      store_epi<C, EPI>(a, plane + (size_t)(2 * m + h) * NX + x, e[j], tile[fpad(m) * PITCH + fpad(x)], dt);
+    }
   }
   if (a.dot_mask) {
     const int blk = (c * a.nslab + p) * 2 + h;
@@ -359,8 +440,7 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(OpCall<C> a, int rb) {
   const InScal<C> s = load_in_scalars<C, IN>(a, g);
   const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
   const C* Vp = a.V + (((size_t)a.rhsp[g].clip * a.nslab + p) * a.ny + y0) * NX;
-  for (int i = threadIdx.x; i < rb * NX; i += NT)
-    tile[(i / NX) * RP + fpad(i % NX)] = cmul(Vp[i], input_elem<C, IN>(a, base + i, s));
+  stage_in<C, IN, NT>(a, s, base, Vp, rb * NX, tile, [](int i) { return (i / NX) * RP + fpad(i % NX); });
   __syncthreads();
   cta_fft<C, NX, false>(tile, rb, RP, tw);
   __syncthreads();
@@ -387,8 +467,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(OpCall<C> a, const C* uin, int 
   __syncthreads();
   Dots<C> dt;
   zero_dots(dt);
-  for (int i = threadIdx.x; i < rb * NX; i += NT)
-    epilogue_elem<C, EPI>(a, uin, base + i, tile[(i / NX) * RP + fpad(i % NX)], dt);
+  stage_out<C, EPI, NT>(a, uin, base, rb * NX, tile, [](int i) { return (i / NX) * RP + fpad(i % NX); }, dt);
   if (a.dot_mask) {
     const int blk = (c * a.nslab + p) * nrb + (y0 / rb);
     block_write_dots(dt, a.dot_mask, a.partials + ((size_t)g * NDOT) * a.maxblk + blk, a.maxblk, scratch);
