@@ -57,6 +57,8 @@ def parse_args(argv=None):
                     help="operator applications/s only (psfd_apply), for kernel captures")
     ap.add_argument("--rhs", type=int, default=18, help="illuminations used by --apply")
     ap.add_argument("--precision", choices=["fp32", "fp64", "both"], default="both", help="--apply precision")
+    ap.add_argument("--sweep", action="store_true",
+                    help="precision sweep on the 256 x 256 x 60 Manhattan clip (FP64 vs FP32 + FP64 refinement)")
     ap.add_argument("--serve", type=int, default=24,
                     help="requests in the serving-loop sample (0 = skip); --serve-only prints only that")
     ap.add_argument("--serve-only", action="store_true")
@@ -158,6 +160,56 @@ def run_apply(args):
         out[name] = {"ms_per_application": ms, "applications_per_s": 1e3 / ms,
                      "rhs_applications_per_s": args.rhs * 1e3 / ms}
         s.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_sweep(args):
+    """Precision sweep on the 256 x 256 x 60 Manhattan clip (nf = 128, 6 deg s and p): the plain
+    FP64 path and the FP32 path with FP64 defect correction, each timed over whole solves of
+    both illuminations, with the order error of every variant against the FP64 solution."""
+    import torch
+    from paper_2606_25541_b300 import psfd
+    prob = layouts.manhattan_clip(256, seed=3)
+    stream = torch.cuda.current_stream()
+    eps_dev = torch.from_numpy(prob.eps).cuda()
+    out = {"mode": "precision_sweep", "workload": f"manhattan_256x256x60_nf{prob.nf}_2rhs",
+           "n_rhs": prob.n_rhs, "tol": args.tol}
+    orders = {}
+    for name, prec, kw in (("fp64", psfd.FP64, dict(tol=args.tol, max_iter=600)),
+                           ("fp32_refined", psfd.FP32_REFINED,
+                            dict(tol=args.tol, inner_tol=args.inner_tol, max_iter=400, max_outer=12))):
+        s = psfd.Solver.from_problem(prob, prec, stream=stream)
+
+        def step():
+            s.set_potential(eps_dev)
+            s.set_illumination(prob.theta_deg, prob.phi_deg, prob.pol)
+            return s.solve(**kw)
+
+        for _ in range(max(args.warmup, 1)):
+            rep = step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            rep = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        orders[name] = [s.diffraction_orders(i) for i in range(prob.n_rhs)]
+        out[name] = {"solves_per_s": prob.n_rhs * 1e3 / ms, "ms_per_batch": ms, "iterations": rep["iterations"],
+                     "outer": rep["outer"], "relres": rep["relres"]}
+        s.close()
+
+    def err(a, b):
+        key = {(m, n): k for k, (m, n) in enumerate(zip(b["m"], b["n"]))}
+        idx = [key[(m, n)] for m, n in zip(a["m"], a["n"])]
+        return float(np.linalg.norm(a["amp"] - b["amp"][idx]) / np.linalg.norm(b["amp"]))
+
+    out["fp32_refined"]["order_rel_err_vs_fp64"] = max(
+        err(a, b) for a, b in zip(orders["fp32_refined"], orders["fp64"]))
+    out["fp32_refined"]["speedup_vs_fp64"] = out["fp32_refined"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    out["bf16x3"] = {"status": "not built", "why": "split-BF16 tensor-core DFT stages are not implemented"}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -442,12 +494,14 @@ def run_ours(args):
     if dom.endswith("fp64"):
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
+                    "traffic": ncu_traffic(dom, d["bytes"] / max(d["launches"], 1)),
                     "peak_kind": "nominal FP64 (148 SMs x 2 FP64 FMA/clk x 2.03 GHz class)"}
     else:
         achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
         roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind}
+                    "frac": achieved / hbm_peak, "traffic": ncu_traffic(dom, d["bytes"] / max(d["launches"], 1)),
+                    "peak_kind": peak_kind}
     lat = sorted(per_step)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -474,6 +528,27 @@ def run_ours(args):
     return 0
 
 
+def ncu_traffic(kernel: str, alg_bytes_per_launch: float):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture (profiles/ncu_traffic.json),
+    scaled from the captured launch by algorithmic bytes; None if absent or if the kernel sources
+    changed since the capture."""
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    h = hashlib.sha256()
+    for src in rec["sources"]:
+        with open(os.path.join(here, src), "rb") as f:
+            h.update(f.read())
+    k = rec["kernels"].get(kernel)
+    if k is None or h.hexdigest()[:16] != rec["sources_sha256_16"]:
+        return None
+    return k["dram_bytes"] / k["algorithmic_bytes"] * alg_bytes_per_launch
+
+
 def solver_bytes(prob) -> float:
     from paper_2606_25541_b300 import psfd
     g = psfd.make_grid(prob.nx, prob.ny, prob.nslab, prob.nf, prob.dx, prob.dy, prob.dz, prob.wavelength,
@@ -487,6 +562,8 @@ def main(argv=None):
         return run_reference(args)
     if args.apply:
         return run_apply(args)
+    if args.sweep:
+        return run_sweep(args)
     if args.serve_only:
         sizes = tuple(int(s) for s in args.serve_sizes.split(","))
         print(json.dumps({"mode": "serving", **run_serving(args.serve, sizes, args.tol, args.inner_tol)}), flush=True)

@@ -45,7 +45,8 @@ __all__ = [
     "upper_sqrt", "fft_integers", "parratt_reflection", "tmm_reflection", "triad",
     "green_scalar", "green_dyadic", "RhsContext", "setup_rhs", "apply_operator",
     "apply_operator_dft", "rhs_vector", "gmres", "dense_operator", "diffraction_orders",
-    "transmitted_orders", "solve", "solve_all", "AnomalyError",
+    "transmitted_orders", "solve", "solve_all", "AnomalyError", "full_domain_problem",
+    "orders_at_old_reference",
 ]
 
 
@@ -447,6 +448,75 @@ def solve(prob, i: int = 0, rtol: float = 1e-13, maxiter: int = 500, direct: boo
     _, E0, Etop = apply_operator(ctx, x, return_side=True)
     orders = diffraction_orders(ctx, E0, Etop)
     return orders, x, {"iterations": its, "relres": res, "ctx": ctx, "E0": E0, "Etop": Etop}
+
+
+# ---------------------------------------------------------------------------
+# conventional PSFD with the stack inside the domain (cross-check of the decomposition)
+# ---------------------------------------------------------------------------
+def _smooth_length(n: int) -> int:
+    """Smallest 2^a 3^b 5^c >= n."""
+    m = n
+    while True:
+        k = m
+        for f in (2, 3, 5):
+            while k % f == 0:
+                k //= f
+        if k == 1:
+            return m
+        m += 1
+
+
+def full_domain_problem(prob, nf: int | None = None):
+    """The clip with its multilayer stack meshed into the domain (Sec. 4's comparison).
+
+    The stack of total thickness T below z_top is covered by M = ceil(T/dz) cells that
+    extend the domain downward; each cell's permittivity is the thickness-weighted mean
+    of the layers (and the substrate) it overlaps. Below the new bottom only the
+    substrate remains, so its reflection is the single Fresnel interface background /
+    substrate (an empty stack). Returns (problem, D) with D = M dz, the depth of the
+    new reference plane below the old z_top.
+    """
+    d = np.asarray(prob.d_layers, np.float64)
+    eps_l = np.asarray(prob.n_layers, np.complex128) ** 2
+    eps_s = complex(prob.n_sub) ** 2
+    T = float(d.sum())
+    M = int(math.ceil(T / prob.dz - 1e-9))
+    D = M * prob.dz
+    tops = -np.concatenate([[0.0], np.cumsum(d)])  # layer j spans [tops[j+1], tops[j]]
+    cells = np.empty(M, np.complex128)
+    for p in range(M):  # cell p (from the bottom) spans [lo, hi]
+        lo, hi = -D + p * prob.dz, -D + (p + 1) * prob.dz
+        acc, covered = 0.0 + 0.0j, 0.0
+        for j in range(len(d)):
+            ov = max(0.0, min(hi, tops[j]) - max(lo, tops[j + 1]))
+            acc += ov * eps_l[j]
+            covered += ov
+        acc += (prob.dz - covered) * eps_s  # what is left of the cell lies in the substrate
+        cells[p] = acc / prob.dz
+    stack_eps = np.broadcast_to(cells[:, None, None], (M, prob.ny, prob.nx))
+    eps = np.concatenate([stack_eps, np.asarray(prob.eps, np.complex128)], axis=0)
+    nslab = prob.nslab + M
+    if nf is None:
+        nf = _smooth_length(max(prob.nf, 2 * nslab + 2))
+    full = dataclasses.replace(prob, nslab=nslab, nf=nf, eps=eps, n_layers=np.zeros(0, np.complex128),
+                               d_layers=np.zeros(0, np.float64), name=prob.name + "_full_domain")
+    return full, D
+
+
+def orders_at_old_reference(orders_full: dict, ctx_full: RhsContext, D: float) -> dict:
+    """Reflected amplitudes of the full-domain solve referred to the decomposition's z_top.
+
+    The full-domain solve references the incident wave and the upgoing orders to z = -D;
+    moving both references up by D multiplies each order by exp(i (beta_mn + beta00) D).
+    """
+    out = dict(orders_full)
+    beta = np.array([ctx_full.beta[(ctx_full.ni == n).argmax(), (ctx_full.mi == m).argmax()]
+                     for m, n in zip(orders_full["m"], orders_full["n"])])
+    ph = np.exp(1j * (beta + ctx_full.beta00) * D)
+    out["amp"] = orders_full["amp"] * ph[:, None]
+    out["a_s"] = orders_full["a_s"] * ph
+    out["a_p"] = orders_full["a_p"] * ph
+    return out
 
 
 def solve_all(prob, rtol: float = 1e-13):
