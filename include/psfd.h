@@ -101,10 +101,14 @@ const char* psfd_strerror(int status);
 /* Description of the last failure on this context ("" if none). */
 const char* psfd_last_error(const psfd_ctx* ctx);
 
-/* 1 if n is an FFT length the kernels are built for, else 0. */
+/* 1 if n is an FFT length the kernels are built for, else 0: 4, 8, 16, 32, 64, 96, 128, 160,
+ * 192, 256, 320, 384, 512, 640, 768, 1024. */
 int psfd_supported_length(int n);
 
-/* Device bytes psfd_create would allocate for this grid, precision and RHS capacity. */
+/* Device bytes psfd_create would allocate for this grid, precision and RHS capacity. The
+ * Krylov pool is sized for BiCGStab (7 vectors per illumination); the first PSFD_GMRES solve
+ * on a context grows it to restart + 3 vectors (and fails with PSFD_E_BUDGET or
+ * PSFD_E_NOMEM if that does not fit). */
 int psfd_workspace_bytes(const psfd_grid* grid, int precision, int max_rhs, size_t* bytes);
 
 /* Create a solver context on the current CUDA device.

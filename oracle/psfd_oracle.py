@@ -46,7 +46,7 @@ __all__ = [
     "green_scalar", "green_dyadic", "RhsContext", "setup_rhs", "apply_operator",
     "apply_operator_dft", "rhs_vector", "gmres", "dense_operator", "diffraction_orders",
     "transmitted_orders", "solve", "solve_all", "AnomalyError", "full_domain_problem",
-    "orders_at_old_reference",
+    "orders_at_old_reference", "scattered_spectrum_mode",
 ]
 
 
@@ -231,18 +231,17 @@ class RhsContext:
     ni: np.ndarray  # signed order index along y, (ny,)
 
 
-def setup_rhs(prob, i: int, reflection: bool = True) -> RhsContext:
-    """Mode wavevectors, stack tables, Green's function and potential for one illumination."""
+def _mode_tables(prob, i: int, mi: np.ndarray, ni: np.ndarray, reflection: bool = True):
+    """Wavevectors, beta, stack reflection and triad of the transverse modes (ni, mi) (2-D
+    arrays of signed order indices) for illumination i."""
     k0 = 2.0 * math.pi / prob.wavelength
     kb = k0 * math.sqrt(prob.eps_bg)
     th = math.radians(float(prob.theta_deg[i]))
     ph = math.radians(float(prob.phi_deg[i]))
     qix = kb * math.sin(th) * math.cos(ph)
     qiy = kb * math.sin(th) * math.sin(ph)
-    mi = fft_integers(prob.nx)
-    ni = fft_integers(prob.ny)
-    qx = qix + 2.0 * math.pi * mi[None, :] / (prob.nx * prob.dx) + 0.0 * ni[:, None]
-    qy = qiy + 2.0 * math.pi * ni[:, None] / (prob.ny * prob.dy) + 0.0 * mi[None, :]
+    qx = qix + 2.0 * math.pi * mi / (prob.nx * prob.dx)
+    qy = qiy + 2.0 * math.pi * ni / (prob.ny * prob.dy)
     q2 = qx * qx + qy * qy
     beta = upper_sqrt(kb * kb - q2)
     if np.any(np.abs(beta) < 1e-9 * k0):
@@ -258,6 +257,15 @@ def setup_rhs(prob, i: int, reflection: bool = True) -> RhsContext:
     s_hat, p_up, p_dn = triad(qx, qy, beta, kb, ph)
     TR = r_s[None, None] * s_hat[:, None] * s_hat[None, :] \
         + r_p[None, None] * p_up[:, None] * p_dn[None, :]
+    return k0, kb, qx, qy, beta, r_s, r_p, s_hat, p_up, p_dn, TR
+
+
+def setup_rhs(prob, i: int, reflection: bool = True) -> RhsContext:
+    """Mode wavevectors, stack tables, Green's function and potential for one illumination."""
+    mi = fft_integers(prob.nx)
+    ni = fft_integers(prob.ny)
+    k0, kb, qx, qy, beta, r_s, r_p, s_hat, p_up, p_dn, TR = _mode_tables(
+        prob, i, mi[None, :] + 0 * ni[:, None], ni[:, None] + 0 * mi[None, :], reflection)
     e_inc = s_hat[:, 0, 0] if int(prob.pol[i]) == 0 else p_dn[:, 0, 0]
     V = k0 * k0 * (np.asarray(prob.eps, np.complex128) - prob.eps_bg)
     G = green_dyadic(qx, qy, beta, prob.nf, prob.dz, kb)
@@ -517,6 +525,32 @@ def orders_at_old_reference(orders_full: dict, ctx_full: RhsContext, D: float) -
     out["a_s"] = orders_full["a_s"] * ph
     out["a_p"] = orders_full["a_p"] * ph
     return out
+
+
+def scattered_spectrum_mode(prob, i: int, u: np.ndarray, m: int, n: int) -> np.ndarray:
+    """xy Fourier coefficient (unnormalised DFT) at the single transverse mode (m, n) of the
+    scattered part (I + R) G*(V u) = u - A u on the absorber planes; shape (3, nslab).
+
+    The steps of apply_operator restricted to one mode, for grids too large for the full
+    oracle: the xy transform of V u at (m, n) is written as a direct sum over the plane,
+    then zero padding and the z transform, the dyadic Green's function of that mode, the
+    inverse z transform and the reflection of the plane-0 field (Eqs. (9), (18)).
+    """
+    mi = np.array([[m]])
+    ni = np.array([[n]])
+    k0, kb, qx, qy, beta, r_s, r_p, s_hat, p_up, p_dn, TR = _mode_tables(prob, i, mi, ni)
+    V = k0 * k0 * (np.asarray(prob.eps, np.complex128) - prob.eps_bg)
+    x = np.arange(prob.nx)
+    y = np.arange(prob.ny)
+    phase = np.exp(-2j * math.pi * (n * y[:, None] / prob.ny + m * x[None, :] / prob.nx))
+    J = np.zeros((3, prob.nf), np.complex128)
+    for p in range(prob.nslab):
+        J[:, p + 1] = np.einsum("cyx,yx->c", V[p][None] * u[:, p], phase)
+    G = green_dyadic(qx, qy, beta, prob.nf, prob.dz, kb)[:, :, :, 0, 0]  # (3, 3, nf)
+    Wt = np.fft.ifft(np.einsum("abl,bl->al", G, np.fft.fft(J, axis=1)), axis=1)
+    R0 = TR[:, :, 0, 0] @ Wt[:, 0]
+    steps = np.arange(prob.nslab, dtype=np.float64)
+    return Wt[:, 1:prob.nslab + 1] + R0[:, None] * np.exp(1j * beta[0, 0] * prob.dz * steps)[None]
 
 
 def solve_all(prob, rtol: float = 1e-13):

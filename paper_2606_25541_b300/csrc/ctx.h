@@ -22,6 +22,9 @@ struct Plan {
   int max_orders = 1;
   size_t bytes = 0;
 };
+// Krylov pool vectors a context starts with: BiCGStab's r, r0, p, v, s, t and pn. GMRES(m)
+// needs m + 1 basis vectors plus z and w; the pool grows to that on the first GMRES solve.
+constexpr int kPoolBicg = 7;
 Plan make_plan(const psfd_grid& g, int precision, int max_rhs, int max_clips);
 bool grid_ok(const psfd_grid* g, std::string& why);
 
@@ -46,7 +49,7 @@ struct psfd_ctx {
   psfd::Plan plan;
   double k0 = 0, kb = 0, L = 0;
   std::string err;
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> allocs;  // device buffers and their sizes
 
   // host state
   bool have_potential = false, have_illum = false, orders_on_host = false;
@@ -81,10 +84,13 @@ struct psfd_ctx {
   int* anomaly = nullptr;
   double2 *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *work64 = nullptr, *side64 = nullptr;
   // Krylov vectors in the context's working precision: rs = r64 / ||r64|| (the system each
-  // sweep solves), xc = its solution, pool = KMAX + 1 GMRES basis vectors, z and w (BiCGStab
-  // uses the first six pool vectors); each vector is [max_rhs][U].
+  // sweep solves), xc = its solution, pool = pool_vecs vectors (BiCGStab: r, r0, p, v, s, t,
+  // pn; GMRES(m): m + 1 basis vectors, z, w); each vector is [max_rhs][U]. The FP32 spectral
+  // work buffer work32 lives inside work64: FP32 and FP64 applications never overlap on a
+  // context's stream.
   double2 *rs64 = nullptr, *xc64 = nullptr, *pool64 = nullptr;
   float2 *x32 = nullptr, *r32 = nullptr, *work32 = nullptr, *pool32 = nullptr;
+  int pool_vecs = 0;
   psfd::GmState* gm = nullptr;
   double2* gpart = nullptr;  // [rhs][KMAX + 1][gblk]
   int gblk = 1;
@@ -114,13 +120,22 @@ struct psfd_ctx {
       cudaGetLastError();
       return fail(PSFD_E_NOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
     }
-    allocs.push_back(q);
+    allocs.push_back({q, bytes});
     allocated += bytes;
     *p = static_cast<T*>(q);
     return PSFD_OK;
   }
+  void dfree(void* q) {
+    for (size_t i = 0; i < allocs.size(); ++i)
+      if (allocs[i].first == q) {
+        cudaFree(q);
+        allocated -= allocs[i].second;
+        allocs.erase(allocs.begin() + (long)i);
+        return;
+      }
+  }
   ~psfd_ctx() {
-    for (void* q : allocs) cudaFree(q);
+    for (auto& q : allocs) cudaFree(q.first);
     for (void* q : {(void*)h_act, (void*)h_act64, (void*)h_sc, (void*)h_sc64, (void*)h_mask})
       if (q) cudaFreeHost(q);
   }
@@ -145,6 +160,9 @@ namespace psfd {
 // Context with room for max_rhs illuminations over up to max_clips potentials.
 int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs, int max_clips,
                size_t hbm_budget, cudaStream_t stream);
+// Grow the Krylov pool to what opts.krylov needs; extra bytes that takes for a plan.
+int ensure_pool(psfd_ctx* ctx, const psfd_solve_opts& o);
+size_t pool_extra_bytes(const Plan& p, int precision, int max_rhs, const psfd_solve_opts& o);
 
 // Potential of clip `clip` from eps (host or device, complex double [nslab][ny][nx]).
 int ctx_set_potential(psfd_ctx* ctx, int clip, const double* eps, int where);

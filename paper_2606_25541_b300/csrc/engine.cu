@@ -64,7 +64,8 @@ KrylovCall<C> krylov_common(psfd_ctx* ctx, const psfd_solve_opts& o, OpCall<C> o
   k.work = work;
   k.basis = pool;
   k.bstride = bs;
-  k.z = pool + (size_t)(KMAX + 1) * bs;
+  k.m = (o.restart > 0 && o.restart < KMAX) ? o.restart : KMAX;
+  k.z = pool + (size_t)(k.m + 1) * bs;
   k.w = k.z + bs;
   k.r = pool;
   k.r0 = pool + bs;
@@ -76,7 +77,6 @@ KrylovCall<C> krylov_common(psfd_ctx* ctx, const psfd_solve_opts& o, OpCall<C> o
   k.gm = ctx->gm;
   k.gpart = ctx->gpart;
   k.gblk = ctx->gblk;
-  k.m = (o.restart > 0 && o.restart < KMAX) ? o.restart : KMAX;
   k.sc = ctx->sc;
   k.act = ctx->act;
   k.h_act = ctx->h_act;

@@ -43,11 +43,26 @@ __host__ __device__ constexpr int fft_plan_stages(int n) {
 __host__ __device__ constexpr int fft_phys(int n) { return n + (n >> 3); }
 __host__ __device__ __forceinline__ int fpad(int i) { return i + (i >> 3); }
 
-// Lanes per transform: N/8 rounded down to a power of two, clamped to [1, 32].
+// Lanes per transform: N/8 rounded down to a power of two, clamped to [1, 32] up to
+// N = 512. Longer transforms span several warps (64 lanes, or 128 in FP64) so that a lane
+// holds at most 16 complex values per stage; such groups synchronise with a named barrier.
+template <typename C>
 __host__ __device__ constexpr int fft_group_lanes(int n) {
+  const int cap = n <= 512 ? 32 : (sizeof(C) == 16 ? 128 : 64);
   int g = 1;
-  while (g * 2 <= n / 8 && g * 2 <= 32) g *= 2;
+  while (g * 2 <= n / 8 && g * 2 <= cap) g *= 2;
   return g;
+}
+
+// Barrier between the load and store phases of a stage: the warp, or the G threads of a
+// multi-warp group (named barrier `bar`, 1..15).
+template <int G>
+__device__ __forceinline__ void group_sync(int bar) {
+  if constexpr (G <= 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(G) : "memory");
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -196,7 +211,7 @@ template <typename C, bool INV> struct DftHalf<C, 8, INV> {
 // HALF_IN: the input is zero on [N/2, N) and only its lower half is read.
 // ---------------------------------------------------------------------------
 template <typename C, int N, int G, bool INV, int S, int NS, int ES, bool HALF_IN>
-__device__ __forceinline__ void fft_stages(C* a, int g, const C* tw, bool valid) {
+__device__ __forceinline__ void fft_stages(C* a, int g, const C* tw, bool valid, int bar) {
   if constexpr (S < fft_plan_stages(N)) {
     constexpr int R = fft_plan_radix(N, S);
     constexpr int NB = N / R;
@@ -233,7 +248,7 @@ __device__ __forceinline__ void fft_stages(C* a, int g, const C* tw, bool valid)
         }
       }
     }
-    __syncwarp();
+    group_sync<G>(bar);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int b = g + k * G;
@@ -254,38 +269,43 @@ __device__ __forceinline__ void fft_stages(C* a, int g, const C* tw, bool valid)
         }
       }
     }
-    __syncwarp();
-    fft_stages<C, N, G, INV, S + 1, NS * R, ES, HALF_IN>(a, g, tw, valid);
+    group_sync<G>(bar);
+    fft_stages<C, N, G, INV, S + 1, NS * R, ES, HALF_IN>(a, g, tw, valid, bar);
   }
 }
 
 // One length-N transform per group of G lanes. Every lane of the warp must call this
 // (lanes of groups without work pass valid = false) because stages end in __syncwarp.
 template <typename C, int N, bool INV, int ES = 1, bool HALF_IN = false>
-__device__ __forceinline__ void group_fft(C* a, int g, const C* tw, bool valid) {
-  constexpr int G = fft_group_lanes(N);
-  fft_stages<C, N, G, INV, 0, 1, ES, HALF_IN>(a, g, tw, valid);
+__device__ __forceinline__ void group_fft(C* a, int g, const C* tw, bool valid, int bar = 0) {
+  constexpr int G = fft_group_lanes<C>(N);
+  fft_stages<C, N, G, INV, 0, 1, ES, HALF_IN>(a, g, tw, valid, bar);
 }
 
 // Batched transforms by a whole CTA: `count` transforms, transform f starting at
 // a + f' * fs with f' = fpad(f) if PADF (transforms along the second axis of a padded
-// 2-D tile) else f, element i at fpad(i) * ES. Each warp handles 32/G transforms at a time.
+// 2-D tile) else f, element i at fpad(i) * ES. Groups of G <= 32 lanes share a warp
+// (32/G transforms per warp at a time); larger groups are G consecutive threads with
+// named barrier 1 + (thread / G), so the CTA size must be a multiple of G and below 16 G.
 template <typename C, int N, bool INV, bool PADF = false, int ES = 1, bool HALF_IN = false>
 __device__ __forceinline__ void cta_fft(C* a, int count, int fs, const C* tw) {
-  constexpr int G = fft_group_lanes(N);
-  constexpr int GPW = 32 / G;  // groups per warp
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  const int gid = warp * GPW + lane / G;
-  const int g = lane % G;
-  const int ngroups = nwarps * GPW;
+  constexpr int G = fft_group_lanes<C>(N);
+  int gid, ngroups, bar = 0;
+  if constexpr (G <= 32) {
+    gid = (threadIdx.x >> 5) * (32 / G) + (threadIdx.x & 31) / G;
+    ngroups = (blockDim.x >> 5) * (32 / G);
+  } else {
+    gid = threadIdx.x / G;
+    ngroups = blockDim.x / G;
+    bar = 1 + gid;
+  }
+  const int g = threadIdx.x % G;
   const int rounds = (count + ngroups - 1) / ngroups;
   for (int it = 0; it < rounds; ++it) {
     const int f = gid + it * ngroups;
     const bool valid = f < count;
     const int fo = valid ? (PADF ? fpad(f) : f) : 0;
-    group_fft<C, N, INV, ES, HALF_IN>(a + fo * fs, g, tw, valid);
+    group_fft<C, N, INV, ES, HALF_IN>(a + fo * fs, g, tw, valid, bar);
   }
 }
 

@@ -10,7 +10,7 @@ namespace psfd {
 
 // FFT lengths the kernels are instantiated for.
 #define PSFD_FOR_EACH_LENGTH(X) \
-  X(4) X(8) X(16) X(32) X(64) X(96) X(128) X(160) X(192) X(256) X(320) X(384) X(512)
+  X(4) X(8) X(16) X(32) X(64) X(96) X(128) X(160) X(192) X(256) X(320) X(384) X(512) X(640) X(768) X(1024)
 
 template <typename C> struct Tune;
 template <> struct Tune<float2> {
@@ -18,12 +18,16 @@ template <> struct Tune<float2> {
   static constexpr int HALF_MIN = 128;    // from this size on, two CTAs per plane (half planes)
   static constexpr int COL_TILE = 16;     // columns per CTA (128-byte segments)
   static constexpr int ROW_ELEMS = 4096;  // row-pass tile size in elements
+  static constexpr size_t COLS_SMEM = 64 * 1024;  // column-pass tile bound (long columns: fewer per CTA)
+  static constexpr size_t ZCOL_SMEM = 80 * 1024;  // z-column tile bound
 };
 template <> struct Tune<double2> {
   static constexpr int FUSED_MAX = 64;
   static constexpr int HALF_MIN = 1 << 20;  // FP64 planes are FP64-pipe bound: no split
   static constexpr int COL_TILE = 8;
   static constexpr int ROW_ELEMS = 2048;
+  static constexpr size_t COLS_SMEM = 64 * 1024;
+  static constexpr size_t ZCOL_SMEM = 80 * 1024;
 };
 
 template <typename C>
@@ -132,11 +136,38 @@ int launch_rows_inv(const OpCall<C>& a, const C* uin) {
   return PSFD_OK;
 }
 
+// Columns per CTA of the column pass: COL_TILE, halved while the tile exceeds COLS_SMEM.
+template <typename C>
+inline size_t cols_smem_bytes(int ny, int tx) {
+  return (size_t)(tx * (fft_phys(ny) | 1) + ny) * sizeof(C);
+}
+template <typename C>
+inline int cols_tile(int nx, int ny) {
+  int tx = nx < Tune<C>::COL_TILE ? nx : Tune<C>::COL_TILE;
+  while (tx > 1 && cols_smem_bytes<C>(ny, tx) > Tune<C>::COLS_SMEM) tx >>= 1;
+  return tx;
+}
+
+// Columns per CTA of the z pass: COL_TILE, halved while the tile exceeds ZCOL_SMEM.
+template <typename C>
+inline size_t zcol_smem_bytes(int nf, int tx) {
+  using R = typename RealOf<C>::T;
+  const int pe = 8 + (nf + 15) / 16;  // phase_entries
+  return (size_t)(3 * tx * (fft_phys(nf) | 1) + nf) * sizeof(C) + 3 * (size_t)nf * sizeof(R) +
+         (size_t)(7 + pe) * tx * sizeof(C) + 2 * (size_t)tx * sizeof(R) + 16;
+}
+template <typename C>
+inline int zcol_tile(int nx, int nf) {
+  int tx = nx < Tune<C>::COL_TILE ? nx : Tune<C>::COL_TILE;
+  while (tx > 1 && zcol_smem_bytes<C>(nf, tx) > Tune<C>::ZCOL_SMEM) tx >>= 1;
+  return tx;
+}
+
 template <typename C, int NY, bool INV>
 int launch_cols(const OpCall<C>& a) {
   constexpr int NT = 256;
-  const int tx = a.nx < Tune<C>::COL_TILE ? a.nx : Tune<C>::COL_TILE;
-  const size_t smem = (size_t)(tx * (fft_phys(NY) | 1) + NY) * sizeof(C);
+  const int tx = cols_tile<C>(a.nx, NY);
+  const size_t smem = cols_smem_bytes<C>(NY, tx);
   auto k = k_cols<C, NY, INV, NT>;
   if (set_smem(k, smem)) return PSFD_E_CUDA;
   k<<<dim3(a.nslab * (a.nx / tx), 3, a.nrhs), NT, smem, a.stream>>>(a, tx);
@@ -145,17 +176,11 @@ int launch_cols(const OpCall<C>& a) {
 }
 
 template <typename C, int NF>
-size_t zcol_smem(int tx) {
-  using R = typename RealOf<C>::T;
-  return (size_t)(3 * tx * (fft_phys(NF) | 1) + NF) * sizeof(C) + 3 * NF * sizeof(R) +
-         (7 + phase_entries<NF>()) * tx * sizeof(C) + 2 * tx * sizeof(R) + 16;
-}
-
-template <typename C, int NF>
 int launch_zcol(const OpCall<C>& a) {
   constexpr int NT = 256;
-  const int tx = a.nx < Tune<C>::COL_TILE ? a.nx : Tune<C>::COL_TILE;
-  const size_t smem = zcol_smem<C, NF>(tx);
+  static_assert(8 + (NF + 15) / 16 == phase_entries<NF>(), "phase table size");
+  const int tx = zcol_tile<C>(a.nx, NF);
+  const size_t smem = zcol_smem_bytes<C>(NF, tx);
   auto k = k_zcol<C, NF, NT>;
   if (set_smem(k, smem)) return PSFD_E_CUDA;
   k<<<dim3(a.nx / tx, a.ny, a.nrhs), NT, smem, a.stream>>>(a, tx);
@@ -282,14 +307,13 @@ PassCost pass_cost(const OpCall<C>& a) {
 template <typename C>
 void pass_ctas(const OpCall<C>& a, double* xy, double* z) {
   const double planes = (double)a.nslab * 3.0 * a.nrhs;
-  const int tx = a.nx < Tune<C>::COL_TILE ? a.nx : Tune<C>::COL_TILE;
   if (use_fused<C>(a.nx, a.ny)) {
     *xy = use_half<C>(a.nx, a.ny) ? 2 * planes : planes;
   } else {
     const int rb = row_block(a.nx, a.ny, Tune<C>::ROW_ELEMS);
-    *xy = planes * ((double)(a.ny / rb) + (double)(a.nx / tx));
+    *xy = planes * ((double)(a.ny / rb) + (double)(a.nx / cols_tile<C>(a.nx, a.ny)));
   }
-  *z = (double)(a.nx / tx) * a.ny * a.nrhs;
+  *z = (double)(a.nx / zcol_tile<C>(a.nx, a.nf)) * a.ny * a.nrhs;
 }
 
 template <typename C>

@@ -96,8 +96,7 @@ Plan make_plan(const psfd_grid& g, int precision, int max_rhs, int max_clips) {
   b += R * p.U * 16 * 4;                                     // b64, x64, r64, work64
   b += R * 6 * p.plane * 16;                                 // side spectra
   const size_t kvec = precision == PSFD_FP64 ? 16 : 8;       // Krylov working precision
-  b += R * p.U * kvec * (2 + KMAX + 3);                      // rs, xc, basis, z, w
-  if (precision != PSFD_FP64) b += R * p.U * 8;              // FP32 spectral work
+  b += R * p.U * kvec * (2 + kPoolBicg);                     // rs, xc, BiCGStab pool
   b += R * NDOT * (size_t)p.maxblk * 16;                     // partial sums
   b += R * (sizeof(GmState) + (size_t)(KMAX + 1) * p.maxblk * 16);  // GMRES state and partials
   b += R * (2 * sizeof(KScal) + 6 * sizeof(int));            // scalars, flags, masks
@@ -180,13 +179,14 @@ int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs
   if (precision == PSFD_FP64) {
     A(&ctx->rs64, R * P.U);
     A(&ctx->xc64, R * P.U);
-    A(&ctx->pool64, R * P.U * (KMAX + 3));
+    A(&ctx->pool64, R * P.U * kPoolBicg);
   } else {
     A(&ctx->x32, R * P.U);
     A(&ctx->r32, R * P.U);
-    A(&ctx->work32, R * P.U);
-    A(&ctx->pool32, R * P.U * (KMAX + 3));
+    A(&ctx->pool32, R * P.U * kPoolBicg);
   }
+  ctx->pool_vecs = kPoolBicg;
+  ctx->work32 = reinterpret_cast<float2*>(ctx->work64);
   ctx->gblk = std::max(1, std::min(P.maxblk, (int)((P.U + 8191) / 8192)));
   A(&ctx->gm, R);
   A(&ctx->gpart, R * (size_t)(KMAX + 1) * ctx->gblk);
@@ -419,6 +419,37 @@ OpCall<double2> base_call64(psfd_ctx* ctx, int rhs0, int nrhs) {
   return base_call<double2>(ctx, rhs0, nrhs, ctx->V64);
 }
 
+static int pool_need(const psfd_solve_opts& o) {
+  if (o.krylov != PSFD_GMRES) return kPoolBicg;
+  const int m = (o.restart > 0 && o.restart < KMAX) ? o.restart : KMAX;
+  return std::max(kPoolBicg, m + 3);
+}
+
+size_t pool_extra_bytes(const Plan& p, int precision, int max_rhs, const psfd_solve_opts& o) {
+  const size_t kvec = precision == PSFD_FP64 ? 16 : 8;
+  return (size_t)max_rhs * p.U * kvec * (size_t)(pool_need(o) - kPoolBicg);
+}
+
+// Grow the Krylov pool to what the requested method needs (GMRES(m): m + 3 vectors). Runs
+// before any work of the solve is enqueued; waits for the context's stream first.
+int ensure_pool(psfd_ctx* ctx, const psfd_solve_opts& o) {
+  const int need = pool_need(o);
+  if (need <= ctx->pool_vecs) return PSFD_OK;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return ctx->cuda_fail(cudaGetLastError(), "pool resize");
+  const size_t n = (size_t)ctx->max_rhs * ctx->plan.U * need;
+  if (ctx->precision == PSFD_FP64) {
+    ctx->dfree(ctx->pool64);
+    ctx->pool64 = nullptr;
+    RC(ctx->dalloc(&ctx->pool64, n));
+  } else {
+    ctx->dfree(ctx->pool32);
+    ctx->pool32 = nullptr;
+    RC(ctx->dalloc(&ctx->pool32, n));
+  }
+  ctx->pool_vecs = need;
+  return PSFD_OK;
+}
+
 }  // namespace psfd
 
 // ---------------------------------------------------------------------------
@@ -527,7 +558,6 @@ int psfd_apply(psfd_ctx* ctx, int precision, int rhs0, int n_rhs, const void* u,
     a.work = ctx->work64;
     RC(op_apply<double2>(a));
   } else if (precision == PSFD_FP32_REFINED) {
-    if (!ctx->work32) RC(ctx->dalloc(&ctx->work32, (size_t)ctx->max_rhs * ctx->plan.U));
     OpCall<float2> a = base_call32(ctx, rhs0, n_rhs);
     a.u = (const float2*)u;
     a.out = (float2*)out;
@@ -544,6 +574,7 @@ int psfd_solve(psfd_ctx* ctx, const psfd_solve_opts* opts, psfd_report* report) 
   if (!ctx->have_illum || !ctx->have_potential) return ctx->fail(PSFD_E_STATE, "solve before set_potential/illumination");
   const auto t0 = std::chrono::steady_clock::now();
   const psfd_solve_opts o = solve_defaults(opts);
+  RC(ensure_pool(ctx, o));
   for (int i = 0; i < ctx->n_rhs; ++i)
     if (ctx->phase[i] == PH_DONE) ctx->phase[i] = PH_NEW;  // re-solve from scratch
   for (;;) {

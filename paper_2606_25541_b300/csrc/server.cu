@@ -84,7 +84,8 @@ void destroy_bucket(psfd_server* s, Bucket* b) {
 
 // Create a bucket for grid g if the budget allows, releasing idle buckets if needed.
 Bucket* make_bucket(psfd_server* s, const psfd_grid& g, int cap, int* rc) {
-  const size_t need = make_plan(g, s->precision, cap, cap).bytes;
+  const Plan plan = make_plan(g, s->precision, cap, cap);
+  const size_t need = plan.bytes + pool_extra_bytes(plan, s->precision, cap, s->opts);
   if (s->budget && s->used + need > s->budget) {
     for (size_t i = 0; i < s->buckets.size();) {
       Bucket* b = s->buckets[i].get();
@@ -106,7 +107,9 @@ Bucket* make_bucket(psfd_server* s, const psfd_grid& g, int cap, int* rc) {
     return nullptr;
   }
   *rc = ctx_create(&b->ctx, &g, s->precision, cap, cap, 0, b->stream);
+  if (*rc == PSFD_OK) *rc = ensure_pool(b->ctx, s->opts);
   if (*rc != PSFD_OK) {
+    if (b->ctx) psfd_destroy(b->ctx);
     cudaStreamDestroy(b->stream);
     return nullptr;
   }

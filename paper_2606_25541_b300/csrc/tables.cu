@@ -455,7 +455,7 @@ int launch_test_fft(int n, int count, bool inv, bool fp64, void* data, const dou
   case v:                                                                                 \
     return fp64 ? run_test_fft<double2, v>((double2*)data, count, inv, tw)                \
                 : run_test_fft<float2, v>((float2*)data, count, inv, tw);
-    X(4) X(8) X(16) X(32) X(64) X(96) X(128) X(160) X(192) X(256) X(320) X(384) X(512)
+    X(4) X(8) X(16) X(32) X(64) X(96) X(128) X(160) X(192) X(256) X(320) X(384) X(512) X(640) X(768) X(1024)
 #undef X
   }
   return PSFD_E_ARG;

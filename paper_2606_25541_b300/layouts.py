@@ -77,7 +77,7 @@ class Problem:
 # z padding
 # ---------------------------------------------------------------------------
 # FFT lengths the CUDA kernels are instantiated for (psfd_supported_length).
-SUPPORTED_LENGTHS = (4, 8, 16, 32, 64, 96, 128, 160, 192, 256, 320, 384, 512)
+SUPPORTED_LENGTHS = (4, 8, 16, 32, 64, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768, 1024)
 
 
 def padded_nf(nslab: int, nz_min: int = 0) -> int:
@@ -250,6 +250,18 @@ def manhattan_clip(n: int = 256, seed: int = 3, nslab: int = 60, nz: int = 128,
     eps = extrude(mask, nslab, n_map=n_map)
     return _problem(n, n, nslab, padded_nf(nslab, nz), 1.0, 1.0, eps, ru_mosi_stack(),
                     [6.0, 6.0], [0.0, 0.0], [0, 1], f"manhattan_{n}x{n}x{nslab}")
+
+
+def curvilinear_clip(n: int = 1024, seed: int = 5, nslab: int = 60, nf: int = 160) -> Problem:
+    """n x n curvilinear (ILT-like) clip at 1 nm: a thresholded smooth random field extruded
+    over 60 absorber planes (n = 0.94 + 0.04i), nf = 160; 4 polar angles (0, 3, 6, 9 deg at
+    azimuth 0) times s/p polarisation."""
+    rng = np.random.default_rng(seed)
+    eps = extrude(curvilinear_mask(n, n, rng, corr_cells=12.0, fill=0.4), nslab)
+    th = [t for t in (0.0, 3.0, 6.0, 9.0) for _ in (0, 1)]
+    po = [s for _ in range(4) for s in (0, 1)]
+    return _problem(n, n, nslab, padded_nf(nslab, nf), 1.0, 1.0, eps, ru_mosi_stack(), th,
+                    [0.0] * 8, po, f"curvilinear_{n}x{n}x{nslab}")
 
 
 def small_clip(nx=8, ny=8, nslab=4, dx=4.0, dz=2.0, seed=0, stack=None, theta=(6.0,), phi=(0.0,),

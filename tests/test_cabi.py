@@ -42,9 +42,9 @@ def test_host_side_entry_points():
     build_mod.build()
     lib = psfd.load()
     assert psfd.strerror(psfd.E_ANOMALY).startswith("Rayleigh")
-    for n in (4, 8, 64, 96, 128, 160, 384, 512):
+    for n in (4, 8, 64, 96, 128, 160, 384, 512, 640, 768, 1024):
         assert psfd.supported_length(n)
-    for n in (0, 2, 7, 100, 1000):
+    for n in (0, 2, 7, 100, 1000, 2048):
         assert not psfd.supported_length(n)
     g = psfd.make_grid(128, 128, 60, 128, 1.0, 1.0, 1.0, 13.5)
     b32 = psfd.workspace_bytes(g, psfd.FP32_REFINED, 18)

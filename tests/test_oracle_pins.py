@@ -327,3 +327,17 @@ def test_stack_in_the_domain_converges_to_the_decomposition(pol, theta):
     errs = [_full_domain_error(dz, pol, theta) for dz in (0.5, 0.25, 0.125)]
     assert errs[1] < errs[0] / 2 and errs[2] < errs[1] / 1.8, errs
     assert errs[2] < 1.5e-3, errs
+
+
+def test_single_mode_restriction_equals_the_full_operator():
+    """The one-mode form used to check large grids mode by mode reproduces the xy spectrum
+    of u - A u of the full (pinned) operator, including the Nyquist index and modes whose
+    signed indices wrap around."""
+    p = layouts.small_clip(nx=16, ny=8, nslab=5, dx=2.0, dz=1.5, seed=3, stack=layouts.ru_mosi_stack(10))
+    p = p.with_illumination([7.0], [20.0], [1])
+    u = layouts.random_field((3, 5, 8, 16), seed=2)
+    W = np.fft.fft2(u - oracle.apply_operator(oracle.setup_rhs(p, 0), u), axes=(2, 3))
+    for m, n in [(0, 0), (3, -2), (-8, 3), (7, -4), (-1, -4)]:
+        got = oracle.scattered_spectrum_mode(p, 0, u, m, n)
+        ref = W[:, :, n % 8, m % 16]
+        assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
