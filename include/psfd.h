@@ -190,11 +190,17 @@ int psfd_get_mode_tables(psfd_ctx* ctx, int rhs, double* beta, double* r_s, doub
  * requests, in arrival order, into a context of the same grid (a "bucket" with
  * slots_per_context illumination slots and as many potential slots) as soon as slots are
  * free -- also while other requests of the bucket are mid-solve -- creating a bucket when
- * its device footprint fits the HBM budget (idle buckets are released to make room);
- * it then advances every bucket by one step of the solve engine (the FP32 / FP64 Krylov
- * iterations, FP64 residuals and orders of all admitted illuminations share launches) and
- * retires requests whose illuminations are all done. A request's orders do not depend on
- * which other requests shared its bucket. Single threaded: the caller drives progress. */
+ * its device footprint fits the HBM budget (idle buckets are released to make room).
+ * Buckets advance independently: each has its own streams, and progress enqueues the next
+ * step of the solve engine for every bucket whose previous step has finished (the FP32 /
+ * FP64 Krylov iterations, FP64 residuals and orders of all its admitted illuminations share
+ * launches), completes the steps that have finished and retires requests whose
+ * illuminations are all done; it never waits for a bucket's running step (it polls for at
+ * most 2 ms when nothing can move). The bucket holding the oldest running request runs on
+ * the highest-priority stream, the next oldest on the next level, so the device serves
+ * requests in arrival order and younger ones fill idle SMs. A request's orders do not
+ * depend on which other requests shared its bucket. Single threaded: the caller drives
+ * progress. */
 typedef struct psfd_server psfd_server;
 
 typedef struct {
@@ -217,7 +223,8 @@ int psfd_server_create(psfd_server** out, int precision, size_t hbm_budget, int 
 int psfd_server_destroy(psfd_server* s);
 /* Queue a request (inputs copied); *ticket identifies it. */
 int psfd_server_submit(psfd_server* s, const psfd_request* req, long long* ticket);
-/* Admit, advance every bucket by one engine step, retire; *n_pending = queued + running. */
+/* Complete finished engine steps, admit, enqueue the next step of idle buckets, retire;
+ * *n_pending = queued + running. */
 int psfd_server_progress(psfd_server* s, int* n_pending);
 /* *state: 0 queued, 1 running, 2 done; *status: PSFD_OK or the request's failure. */
 int psfd_server_status(psfd_server* s, long long ticket, int* state, int* status);

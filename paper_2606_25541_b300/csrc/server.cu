@@ -32,10 +32,18 @@ bool same_grid(const psfd_grid& a, const psfd_grid& b) {
          a.dz == b.dz && a.wavelength == b.wavelength && a.eps_bg == b.eps_bg;
 }
 
+// Stream priority levels a bucket can run at (rank 0 = the bucket holding the oldest
+// running request).
+constexpr int kPrioLevels = 4;
+
 struct Bucket {
   psfd_grid grid{};
   psfd_ctx* ctx = nullptr;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;             // the stream the context currently runs on
+  cudaStream_t prio[kPrioLevels] = {};       // one stream per priority level, highest first
+  cudaEvent_t handoff = nullptr;             // orders work across a stream change
+  cudaEvent_t tick_done = nullptr;           // end of the bucket's enqueued engine step
+  bool in_flight = false;                    // an engine step is enqueued and not completed
   std::vector<long long> rhs_owner;   // request id per illumination slot, -1 free
   std::vector<long long> clip_owner;  // request id per potential slot, -1 free
   size_t bytes = 0;
@@ -75,7 +83,10 @@ namespace {
 
 void destroy_bucket(psfd_server* s, Bucket* b) {
   if (b->ctx) psfd_destroy(b->ctx);
-  if (b->stream) cudaStreamDestroy(b->stream);
+  for (cudaStream_t st : b->prio)
+    if (st) cudaStreamDestroy(st);
+  if (b->handoff) cudaEventDestroy(b->handoff);
+  if (b->tick_done) cudaEventDestroy(b->tick_done);
   s->used -= b->bytes;
   s->buckets.erase(std::remove_if(s->buckets.begin(), s->buckets.end(),
                                   [&](const std::unique_ptr<Bucket>& p) { return p.get() == b; }),
@@ -102,15 +113,30 @@ Bucket* make_bucket(psfd_server* s, const psfd_grid& g, int cap, int* rc) {
   }
   auto b = std::make_unique<Bucket>();
   b->grid = g;
-  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  bool ok = cudaEventCreateWithFlags(&b->handoff, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->tick_done, cudaEventDisableTiming) == cudaSuccess;
+  for (int l = 0; l < kPrioLevels && ok; ++l) {
+    const int prio = std::min(least, greatest + l);  // greatest = highest priority
+    ok = cudaStreamCreateWithPriority(&b->prio[l], cudaStreamNonBlocking, prio) == cudaSuccess;
+  }
+  if (!ok) {
+    for (cudaStream_t st : b->prio)
+      if (st) cudaStreamDestroy(st);
+    if (b->handoff) cudaEventDestroy(b->handoff);
+    if (b->tick_done) cudaEventDestroy(b->tick_done);
     *rc = PSFD_E_CUDA;
     return nullptr;
   }
+  b->stream = b->prio[kPrioLevels - 1];
   *rc = ctx_create(&b->ctx, &g, s->precision, cap, cap, 0, b->stream);
   if (*rc == PSFD_OK) *rc = ensure_pool(b->ctx, s->opts);
   if (*rc != PSFD_OK) {
     if (b->ctx) psfd_destroy(b->ctx);
-    cudaStreamDestroy(b->stream);
+    for (cudaStream_t st : b->prio) cudaStreamDestroy(st);
+    cudaEventDestroy(b->handoff);
+    cudaEventDestroy(b->tick_done);
     return nullptr;
   }
   b->bytes = need;
@@ -144,7 +170,7 @@ int admit(psfd_server* s, Request* r, bool* admitted) {
   Bucket* b = nullptr;
   int clip = -1, g0 = -1;
   for (auto& bp : s->buckets)
-    if (same_grid(bp->grid, r->grid) && find_slots(bp.get(), (int)r->th.size(), &clip, &g0)) {
+    if (!bp->in_flight && same_grid(bp->grid, r->grid) && find_slots(bp.get(), (int)r->th.size(), &clip, &g0)) {
       b = bp.get();
       break;
     }
@@ -216,6 +242,72 @@ int retire(psfd_server* s, Bucket* b) {
   return PSFD_OK;
 }
 
+// One non-blocking pass: complete the buckets whose engine step has finished, admit queued
+// requests into buckets between steps, then enqueue the next step of every idle bucket with
+// work on its priority stream. Returns whether anything completed or was admitted.
+static int progress_pass(psfd_server* s, bool* moved) {
+  *moved = false;
+  // 1. completions: buckets whose last step has finished on the device
+  for (auto& bp : s->buckets) {
+    Bucket* b = bp.get();
+    if (!b->in_flight) continue;
+    const cudaError_t q = cudaEventQuery(b->tick_done);
+    if (q == cudaErrorNotReady) continue;
+    if (q != cudaSuccess) return PSFD_E_CUDA;
+    b->in_flight = false;
+    *moved = true;
+    int active = 0;
+    int rc = engine_complete(b->ctx, s->opts, &active);
+    if (rc != PSFD_OK) return rc;
+    if ((rc = retire(s, b)) != PSFD_OK) return rc;
+  }
+  // 2. admissions, in arrival order; requests that do not fit yet stay queued
+  for (auto it = s->queue.begin(); it != s->queue.end();) {
+    Request* r = s->reqs[*it].get();
+    bool admitted = false;
+    const int rc = admit(s, r, &admitted);
+    if (rc != PSFD_OK) return rc;
+    *moved = *moved || admitted;
+    it = admitted ? s->queue.erase(it) : std::next(it);
+  }
+  // 3. stream priorities by age: the bucket holding the oldest running request runs at the
+  //    highest priority, the next at the next level, and so on, so the block scheduler
+  //    serves requests in arrival order while younger ones fill the idle SMs; then the next
+  //    engine step of every idle bucket with work is enqueued (buckets advance
+  //    independently: none waits for a slower one)
+  std::vector<std::pair<long long, Bucket*>> order;
+  for (auto& bp : s->buckets) {
+    if (bp->running == 0) continue;
+    long long oldest = -1;
+    for (long long id : bp->rhs_owner)
+      if (id >= 0 && (oldest < 0 || id < oldest)) oldest = id;
+    order.push_back({oldest, bp.get()});
+  }
+  std::sort(order.begin(), order.end(),
+            [](const std::pair<long long, Bucket*>& a, const std::pair<long long, Bucket*>& b) {
+              return a.first < b.first;
+            });
+  for (size_t r = 0; r < order.size(); ++r) {
+    Bucket* b = order[r].second;
+    if (b->in_flight) continue;
+    cudaStream_t want = b->prio[std::min<size_t>(r, kPrioLevels - 1)];
+    if (want != b->stream) {
+      // whatever the context queued on its previous stream (admission uploads) comes first
+      if (cudaEventRecord(b->handoff, b->stream) != cudaSuccess ||
+          cudaStreamWaitEvent(want, b->handoff, 0) != cudaSuccess)
+        return PSFD_E_CUDA;
+      b->stream = want;
+      psfd_set_stream(b->ctx, want);
+    }
+    bool pending = false;
+    const int rc = engine_enqueue(b->ctx, s->opts, &pending);
+    if (rc != PSFD_OK) return rc;
+    if (cudaEventRecord(b->tick_done, b->stream) != cudaSuccess) return PSFD_E_CUDA;
+    b->in_flight = true;
+  }
+  return PSFD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -271,30 +363,17 @@ int psfd_server_submit(psfd_server* s, const psfd_request* q, long long* ticket)
 
 int psfd_server_progress(psfd_server* s, int* n_pending) {
   if (!s) return PSFD_E_ARG;
-  // 1. admissions, in arrival order; requests that do not fit yet stay queued
-  for (auto it = s->queue.begin(); it != s->queue.end();) {
-    Request* r = s->reqs[*it].get();
-    bool admitted = false;
-    const int rc = admit(s, r, &admitted);
+  // repeat non-blocking passes until something moves (or briefly, 2 ms, if nothing can)
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    bool moved = false;
+    const int rc = progress_pass(s, &moved);
     if (rc != PSFD_OK) return rc;
-    it = admitted ? s->queue.erase(it) : std::next(it);
-  }
-  // 2. one engine tick per bucket with work: all buckets enqueue first (each on its own
-  //    stream, so their kernels overlap on the device), then each is completed;
-  // 3. retire finished requests
-  for (auto& bp : s->buckets) {
-    if (bp->running == 0) continue;
-    bool pending = false;
-    const int rc = engine_enqueue(bp->ctx, s->opts, &pending);
-    if (rc != PSFD_OK) return rc;
-  }
-  for (auto& bp : s->buckets) {
-    Bucket* b = bp.get();
-    if (b->running == 0) continue;
-    int active = 0;
-    int rc = engine_complete(b->ctx, s->opts, &active);
-    if (rc != PSFD_OK) return rc;
-    if ((rc = retire(s, b)) != PSFD_OK) return rc;
+    bool any_in_flight = false;
+    for (auto& bp : s->buckets) any_in_flight = any_in_flight || bp->in_flight;
+    if (moved || !any_in_flight ||
+        std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(2000))
+      break;
   }
   if (n_pending) {
     int n = (int)s->queue.size();
