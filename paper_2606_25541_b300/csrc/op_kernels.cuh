@@ -387,10 +387,19 @@ __global__ void __launch_bounds__(NT, 2) k_half_inv(OpCall<C> a, const C* uin) {
   }
   __syncthreads();
   const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
-  for (int i = threadIdx.x; i < H * NX; i += NT) {
-    const int k = i / NX;
-    const C y0 = a.work[plane + i], y1 = a.work[plane + i + H * NX];
-    tile[fpad(k) * PITCH + fpad(i % NX)] = h ? cmul(csub(y0, y1), cconj(twy[k])) : cadd(y0, y1);
+  constexpr int BL = (H * NX) % (4 * NT) == 0 ? 4 : 1;  // elements per thread whose loads overlap
+  for (int i0 = threadIdx.x; i0 < H * NX; i0 += BL * NT) {
+    C y0[BL], y1[BL];
+#pragma unroll
+    for (int j = 0; j < BL; ++j) {
+      y0[j] = a.work[plane + i0 + j * NT];
+      y1[j] = a.work[plane + i0 + j * NT + H * NX];
+    }
+#pragma unroll
+    for (int j = 0; j < BL; ++j) {
+      const int i = i0 + j * NT, k = i / NX;
+      tile[fpad(k) * PITCH + fpad(i % NX)] = h ? cmul(csub(y0[j], y1[j]), cconj(twy[k])) : cadd(y0[j], y1[j]);
+    }
   }
   __syncthreads();
   cta_fft<C, H, true, true, PITCH>(tile, NX, 1, twh);

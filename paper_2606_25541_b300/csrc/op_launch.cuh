@@ -19,6 +19,8 @@ template <> struct Tune<float2> {
   static constexpr int COL_TILE = 16;     // columns per CTA (128-byte segments)
   static constexpr int ROW_ELEMS = 4096;  // row-pass tile size in elements
   static constexpr size_t COLS_SMEM = 64 * 1024;  // column-pass tile bound (long columns: fewer per CTA)
+  static constexpr int ZCOL_TILE = 8;             // x-modes per z-column CTA (4 warps: 7 CTAs per SM)
+  static constexpr int ZCOL_NT = 128;
   static constexpr size_t ZCOL_SMEM = 80 * 1024;  // z-column tile bound
 };
 template <> struct Tune<double2> {
@@ -27,6 +29,8 @@ template <> struct Tune<double2> {
   static constexpr int COL_TILE = 8;
   static constexpr int ROW_ELEMS = 2048;
   static constexpr size_t COLS_SMEM = 64 * 1024;
+  static constexpr int ZCOL_TILE = 8;
+  static constexpr int ZCOL_NT = 256;
   static constexpr size_t ZCOL_SMEM = 80 * 1024;
 };
 
@@ -148,7 +152,7 @@ inline int cols_tile(int nx, int ny) {
   return tx;
 }
 
-// Columns per CTA of the z pass: COL_TILE, halved while the tile exceeds ZCOL_SMEM.
+// Columns per CTA of the z pass: ZCOL_TILE, halved while the tile exceeds ZCOL_SMEM.
 template <typename C>
 inline size_t zcol_smem_bytes(int nf, int tx) {
   using R = typename RealOf<C>::T;
@@ -158,7 +162,7 @@ inline size_t zcol_smem_bytes(int nf, int tx) {
 }
 template <typename C>
 inline int zcol_tile(int nx, int nf) {
-  int tx = nx < Tune<C>::COL_TILE ? nx : Tune<C>::COL_TILE;
+  int tx = nx < Tune<C>::ZCOL_TILE ? nx : Tune<C>::ZCOL_TILE;
   while (tx > 1 && zcol_smem_bytes<C>(nf, tx) > Tune<C>::ZCOL_SMEM) tx >>= 1;
   return tx;
 }
@@ -177,7 +181,7 @@ int launch_cols(const OpCall<C>& a) {
 
 template <typename C, int NF>
 int launch_zcol(const OpCall<C>& a) {
-  constexpr int NT = 256;
+  constexpr int NT = Tune<C>::ZCOL_NT;
   static_assert(8 + (NF + 15) / 16 == phase_entries<NF>(), "phase table size");
   const int tx = zcol_tile<C>(a.nx, NF);
   const size_t smem = zcol_smem_bytes<C>(NF, tx);
