@@ -270,7 +270,7 @@ int psfd_profile_get(int cls, const char** name, unsigned long long* launches, d
  * It allocates nothing (no cudaMalloc, cudaFree or allocating library call): every
  * intermediate lives in one static device array of PSFD_STATIC_SCRATCH_BYTES that the
  * library holds on every GPU it is loaded on until the process exits. A grid needs
- * about nx*ny*(144 + 32*nslab) + 16 KiB of it (128 x 128 x 60: 33.8 MB); larger grids
+ * about nx*ny*(152 + 32*nslab) + 16 KiB of it (128 x 128 x 60: 34.0 MB); larger grids
  * are rejected with PSFD_E_BUDGET before any device work. The first call on each
  * device looks the array's device address up (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture. All calls share the array

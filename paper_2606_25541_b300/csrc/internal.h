@@ -34,7 +34,7 @@ struct ModeF32 {
   float qx, qy;     // transverse wavevector
   float2 bh, bl;    // beta split into FP32 hi + lo (beta - kappa stays exact near kappa)
   float2 ebL;       // exp(i beta L)
-  float2 bdz;       // beta dz
+  float2 e1, e8;    // exp(i beta dz), exp(i beta 8 dz) (reflection phase table steps)
   float2 rs, rp;    // stack reflection coefficients
   float hx, hy;     // unit transverse direction (azimuth of the illumination at q = 0)
   float qnk, pad;   // |q| / kb

@@ -55,13 +55,6 @@ __device__ __forceinline__ double2 cdiv_fast(double2 a, double2 b) {
   return cscale(cmulc(b, a), 1.0 / (b.x * b.x + b.y * b.y));
 }
 
-__device__ __forceinline__ float2 cexp_r(float2 z) {
-  float s, c;
-  sincosf(z.y, &s, &c);
-  float e = expf(z.x);
-  return make_float2(e * c, e * s);
-}
-__device__ __forceinline__ double2 cexp_r(double2 z) { return cexp_d(z); }
 
 // ---------------------------------------------------------------------------
 // input stage (K1) and epilogue (K3) element operations
@@ -575,8 +568,9 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
   C* cb_h = reinterpret_cast<C*>(kzs + NF);  // per column: beta hi
   C* cb_l = cb_h + tx;                        // beta lo
   C* cebl = cb_l + tx;                        // exp(i beta L)
-  C* cbdz = cebl + tx;                        // beta dz
-  C* R0 = cbdz + tx;                          // 3 tx: T_R E(plane 0)
+  C* ce1 = cebl + tx;                         // exp(i beta dz)
+  C* ce8 = ce1 + tx;                          // exp(i beta 8 dz)
+  C* R0 = ce8 + tx;                           // 3 tx: T_R E(plane 0)
   C* ptab = R0 + 3 * tx;                      // tx phase_entries<NF>(): exp(i beta dz j)
   R* cqx = reinterpret_cast<R*>(ptab + tx * phase_entries<NF>());
   R* cqy = cqx + tx;
@@ -609,7 +603,8 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
       cb_h[t] = m.bh;
       cb_l[t] = m.bl;
       cebl[t] = m.ebL;
-      cbdz[t] = m.bdz;
+      ce1[t] = m.e1;
+      ce8[t] = m.e8;
       cqx[t] = m.qx;
       cqy[t] = m.qy;
     } else {
@@ -619,7 +614,8 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
       const ModeEntry me = a.modes[mbase + t];
       split_hi_lo(me.beta, cb_h[t], cb_l[t]);
       cebl[t] = from_c64<C>(me.ebL);
-      cbdz[t] = from_c64<C>(make_double2(me.beta.x * a.dz, me.beta.y * a.dz));
+      ce1[t] = from_c64<C>(cexp_d(make_double2(-me.beta.y * a.dz, me.beta.x * a.dz)));
+      ce8[t] = from_c64<C>(cexp_d(make_double2(-8.0 * me.beta.y * a.dz, 8.0 * me.beta.x * a.dz)));
       cqx[t] = (R)qx64;
       cqy[t] = (R)qy64;
     }
@@ -730,12 +726,20 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
     R0[1 * tx + t] = from_c64<C>(Ry);
     R0[2 * tx + t] = from_c64<C>(Rz);
   }
+  // phase table: powers of exp(i beta dz) (fine, j < 8) and of exp(i beta 8 dz) (coarse),
+  // both evaluated in FP64; every entry by binary powering in its own thread
   constexpr int PE = phase_entries<NF>();
   for (int i = threadIdx.x; i < tx * PE; i += NT) {
     const int t = i / PE, j = i % PE;
-    const R m = j < 8 ? (R)j : (R)(8 * (j - 8));
-    const C bdz = cbdz[t];
-    ptab[i] = cexp_r(mk(-bdz.y * m, bdz.x * m));  // exp(i beta m dz)
+    C w = j < 8 ? ce1[t] : ce8[t];
+    int e = j < 8 ? j : j - 8;
+    C r = mk((R)1, (R)0);
+    while (e) {
+      if (e & 1) r = cmul(r, w);
+      e >>= 1;
+      if (e) w = cmul(w, w);
+    }
+    ptab[i] = r;
   }
   __syncthreads();
   for (int pl = p0; pl < ns; pl += pstep) {

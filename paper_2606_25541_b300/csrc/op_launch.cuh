@@ -158,7 +158,7 @@ inline size_t zcol_smem_bytes(int nf, int tx) {
   using R = typename RealOf<C>::T;
   const int pe = 8 + (nf + 15) / 16;  // phase_entries
   return (size_t)(3 * tx * (fft_phys(nf) | 1) + nf) * sizeof(C) + 3 * (size_t)nf * sizeof(R) +
-         (size_t)(7 + pe) * tx * sizeof(C) + 2 * (size_t)tx * sizeof(R) + 16;
+         (size_t)(8 + pe) * tx * sizeof(C) + 2 * (size_t)tx * sizeof(R) + 16;
 }
 template <typename C>
 inline int zcol_tile(int nx, int nf) {

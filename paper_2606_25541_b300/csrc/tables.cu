@@ -70,6 +70,35 @@ __device__ double2 parratt_d(double k02, double q2, double2 eps_amb, const Stack
   return gam;
 }
 
+// 2 x 2 complex matrices acting on the reflection coefficient as Moebius maps.
+struct Mobius2 {
+  double2 a, b, c, d;  // G -> (a G + b) / (c G + d)
+};
+__device__ __forceinline__ Mobius2 mobius_layer(double2 e, double2 r) {
+  return {e, r, cmul(r, e), make_double2(1.0, 0.0)};
+}
+__device__ __forceinline__ Mobius2 mobius_mul(const Mobius2& x, const Mobius2& y) {
+  return {cadd(cmul(x.a, y.a), cmul(x.b, y.c)), cadd(cmul(x.a, y.b), cmul(x.b, y.d)),
+          cadd(cmul(x.c, y.a), cmul(x.d, y.c)), cadd(cmul(x.c, y.b), cmul(x.d, y.d))};
+}
+__device__ __forceinline__ Mobius2 mobius_rescale(const Mobius2& x) {
+  const double m = fmax(fmax(cabs2(x.a), cabs2(x.b)), fmax(cabs2(x.c), cabs2(x.d)));
+  const double s = m > 0.0 ? 1.0 / sqrt(m) : 1.0;
+  return {cscale(x.a, s), cscale(x.b, s), cscale(x.c, s), cscale(x.d, s)};
+}
+__device__ __forceinline__ Mobius2 mobius_pow(Mobius2 x, int k) {
+  Mobius2 r = {make_double2(1.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(1.0, 0.0)};
+  while (k > 0) {
+    if (k & 1) r = mobius_rescale(mobius_mul(r, x));
+    k >>= 1;
+    if (k) x = mobius_rescale(mobius_mul(x, x));
+  }
+  return r;
+}
+__device__ __forceinline__ double2 mobius_apply(const Mobius2& m, double2 g) {
+  return cdiv(cadd(cmul(m.a, g), m.b), cadd(cmul(m.c, g), m.d));
+}
+
 // The same recursion for s and p at once, with the square roots, Fresnel coefficients
 // and layer phase factors taken once per distinct medium / interface / layer class.
 __device__ void parratt_dedup_d(double k02, double q2, const StackDev& st, double2& rs, double2& rp) {
@@ -87,13 +116,30 @@ __device__ void parratt_dedup_d(double k02, double q2, const StackDev& st, doubl
   const int M = st.n_layers;
   double2 gs = fs[st.iface_of[M]], gp = fp[st.iface_of[M]];
   const double2 one = make_double2(1.0, 0.0);
-  for (int j = M; j >= 1; --j) {
+  // one recursion step through layer j: G <- (r + G e) / (1 + r G e)
+  auto step = [&](int j) {
     const double2 e = ph[st.layer_ph[j - 1]];
     const int f = st.iface_of[j - 1];
     const double2 ges = cmul(gs, e), gep = cmul(gp, e);
     gs = cdiv(cadd(fs[f], ges), cadd(one, cmul(fs[f], ges)));
     gp = cdiv(cadd(fp[f], gep), cadd(one, cmul(fp[f], gep)));
+  };
+  const int rb = st.run_k ? st.run_top + 2 * st.run_k - 1 : 0;  // bottom layer of the run
+  for (int j = M; j > rb; --j) step(j);
+  if (st.run_k) {
+    // The step through layer j is the Moebius map of [[e, r], [r e, 1]]; a unit (upper
+    // layer a, lower layer b) is their product, and run_k units are its run_k-th power
+    // (by squaring, rescaled to unit max entry: the map ignores a common factor).
+    const int ja = st.run_top, jb = st.run_top + 1;
+    const double2 ea = ph[st.layer_ph[ja - 1]], eb = ph[st.layer_ph[jb - 1]];
+    const int fa = st.iface_of[ja - 1], fb = st.iface_of[jb - 1];
+    Mobius2 qs = mobius_mul(mobius_layer(ea, fs[fa]), mobius_layer(eb, fs[fb]));
+    Mobius2 qp = mobius_mul(mobius_layer(ea, fp[fa]), mobius_layer(eb, fp[fb]));
+    gs = mobius_apply(mobius_pow(qs, st.run_k), gs);
+    gp = mobius_apply(mobius_pow(qp, st.run_k), gp);
   }
+  if (st.run_k)
+    for (int j = st.run_top - 1; j >= 1; --j) step(j);
   rs = gs;
   rp = gp;
 }
@@ -101,6 +147,7 @@ __device__ void parratt_dedup_d(double k02, double q2, const StackDev& st, doubl
 void stack_dedup(StackDev& st, const double2* eps_layers, const double* d_layers, int n_layers, double2 eps_amb,
                  double2 eps_sub) {
   st.n_mat = st.n_iface = st.n_ph = 0;
+  st.run_top = st.run_k = 0;
   if (n_layers > kStackMaxLayers) return;
   int med[kStackMaxLayers + 2];
   auto mat_id = [&](double2 e) -> int {
@@ -139,6 +186,22 @@ void stack_dedup(StackDev& st, const double2* eps_layers, const double* d_layers
     }
     st.layer_ph[j] = (unsigned char)id;
   }
+  // longest periodic two-layer run: 1-based layers top .. top + 2k - 1 with layer j and j + 2
+  // alike for every j in the run, and medium top - 1 alike medium top + 1 (so that every
+  // unit of the run sits below the same interface)
+  auto same = [&](int j1, int j2) {  // 1-based layers j1, j2 <= n_layers: medium and thickness
+    return med[j1] == med[j2] && d_layers[j1 - 1] == d_layers[j2 - 1];
+  };
+  for (int top = 1; top + 3 <= n_layers; ++top) {
+    if (med[top - 1] != med[top + 1]) continue;
+    int k = 0;
+    while (top + 2 * k + 1 <= n_layers && same(top + 2 * k, top) && same(top + 2 * k + 1, top + 1)) ++k;
+    if (k > st.run_k) {
+      st.run_k = k;
+      st.run_top = top;
+    }
+  }
+  if (st.run_k < 3) st.run_k = 0;
 }
 
 // grid (ceil(nx / 128), ny, n_slots)
@@ -175,7 +238,8 @@ __global__ void k_modes(ModesArgs a) {
     f.qy = (float)qy;
     split_hi_lo(beta, f.bh, f.bl);
     f.ebL = to_c32(m.ebL);
-    f.bdz = to_c32(cscale(beta, a.dz));
+    f.e1 = to_c32(cexp_d(make_double2(-beta.y * a.dz, beta.x * a.dz)));
+    f.e8 = to_c32(cexp_d(make_double2(-8.0 * beta.y * a.dz, 8.0 * beta.x * a.dz)));
     f.rs = to_c32(m.rs);
     f.rp = to_c32(m.rp);
     const double qn = sqrt(q2);

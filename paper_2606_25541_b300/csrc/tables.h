@@ -23,6 +23,10 @@ struct StackDev {
   double ph_d[kMaxPh];
   unsigned char iface_of[kStackMaxLayers + 1];  // interface between medium j and j+1
   unsigned char layer_ph[kStackMaxLayers];      // (medium, thickness) class of layer j
+  // Periodic run: layers run_top .. run_top + 2 run_k - 1 (1-based, top to bottom) are run_k
+  // copies of one two-layer unit whose upper interface is the unit's own (the medium above
+  // run_top equals the unit's second layer); run_k = 0 if there is none.
+  int run_top, run_k;
 };
 
 // Fills the deduplication tables of st from host copies of the media (ambient first,
