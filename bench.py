@@ -57,6 +57,9 @@ def parse_args(argv=None):
                     help="operator applications/s only (psfd_apply), for kernel captures")
     ap.add_argument("--rhs", type=int, default=18, help="illuminations used by --apply")
     ap.add_argument("--precision", choices=["fp32", "fp64", "both"], default="both", help="--apply precision")
+    ap.add_argument("--krylov", choices=["bicgstab", "gmres"], default="bicgstab",
+                    help="inner Krylov method of the refined solve")
+    ap.add_argument("--restart", type=int, default=0, help="GMRES basis size per sweep (0 = maximum)")
     ap.add_argument("--sweep", action="store_true",
                     help="precision sweep on the 256 x 256 x 60 Manhattan clip (FP64 vs FP32 + FP64 refinement)")
     ap.add_argument("--large", action="store_true",
@@ -449,7 +452,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     prob = layouts.line_space_clip(seed=2 + rank)
     n_rhs = prob.n_rhs
-    solve_kw = dict(tol=args.tol, inner_tol=args.inner_tol, max_iter=400, max_outer=12, check_every=4)
+    solve_kw = dict(tol=args.tol, inner_tol=args.inner_tol, max_iter=400, max_outer=12, check_every=4,
+                    krylov=psfd.GMRES if args.krylov == "gmres" else psfd.BICGSTAB, restart=args.restart)
 
     solver = psfd.Solver.from_problem(prob, psfd.FP32_REFINED, stream=stream)
     eps_dev = torch.from_numpy(prob.eps).to(dev)
@@ -583,7 +587,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [prob.nx, prob.ny, prob.nslab, prob.nf], "dx_nm": prob.dx,
-                   "n_rhs": n_rhs, "precision": "FP32 BiCGStab inside FP64 defect correction",
+                   "n_rhs": n_rhs, "precision": f"FP32 {'GMRES' if args.krylov == 'gmres' else 'BiCGStab'} inside FP64 defect correction",
                    "tol": args.tol, "inner_tol": args.inner_tol, "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2: {solver_bytes(prob) / 1e9:.1f} GB working set per step"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),

@@ -85,42 +85,25 @@ __global__ void k_gm_scale(int n, const int* mask, const int* act, const GmState
   }
 }
 
-// partial projections <v_i, w>, i = 0..j, into slots i.
+// partial projection <v_i, w> of one chunk into slot i: grid (nblk, rhs, m + 1), one basis
+// vector per block (blocks with i > j exit), so every active (vector, chunk) pair is its own
+// block and w's chunk is re-read from L2.
 template <typename C>
 __global__ void __launch_bounds__(VEC_NT) k_gm_dots(int n, int nblk, const int* act, const GmState* st,
                                                      const C* basis, size_t bstride, const C* w, double2* gpart,
                                                      int gblk) {
   using R = typename RealOf<C>::T;
-  __shared__ double2 sh[32];
-  const int blk = blockIdx.x, g = blockIdx.y;
-  if (!act[g]) return;
-  const int j = st[g].j;
+  const int blk = blockIdx.x, g = blockIdx.y, i = blockIdx.z;
+  if (!act[g] || i > st[g].j) return;
   const size_t off = (size_t)g * n;
   const int chunk = (n + nblk - 1) / nblk;
   const int lo = blk * chunk, hi = min(n, lo + chunk);
-  typename Acc<C>::T acc[KMAX + 1];
-#pragma unroll
-  for (int i = 0; i <= KMAX; ++i) acc[i] = mk((R)0, (R)0);
-  for (int e = lo + threadIdx.x; e < hi; e += VEC_NT) {
-    const C we = w[off + e];
-#pragma unroll
-    for (int i = 0; i <= KMAX; ++i)
-      if (i <= j) acc[i] = cadd(acc[i], cmulc(basis[(size_t)i * bstride + off + e], we));
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = VEC_NT / 32;
-  for (int i = 0; i <= j; ++i) {
-    double2 v = as_c64(acc[i]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = cadd(v, shfl_down_d2(v, o));
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double2 t = make_double2(0.0, 0.0);
-      for (int k = 0; k < nw; ++k) t = cadd(t, sh[k]);
-      gpart_ptr(gpart, g, i, gblk)[blk] = t;
-    }
-  }
+  const C* v = basis + (size_t)i * bstride + off;
+  const C* ww = w + off;
+  typename Acc<C>::T acc = mk((R)0, (R)0);
+#pragma unroll 4
+  for (int e = lo + threadIdx.x; e < hi; e += VEC_NT) acc = cadd(acc, cmulc(v[e], ww[e]));
+  vec_block_dots<C>(acc, acc, DOT_R0_OUT, gpart_ptr(gpart, g, i, gblk) + blk, gblk);
 }
 
 // Hessenberg column j: H[i][j] = sum of the partial projections (fixed order).
@@ -274,8 +257,8 @@ int gmres_iterate_impl(const KrylovCall<C>& k, int iters) {
     const int nb = op_apply_impl<C>(a);
     if (nb < 0) return nb;
     unsigned* ctac = prof_begin(vcls, st);
-    k_gm_dots<C><<<dim3(k.gblk, R), VEC_NT, 0, st>>>(k.n, k.gblk, k.act, k.gm, k.basis, k.bstride, k.w, k.gpart,
-                                                      k.gblk);
+    k_gm_dots<C><<<dim3(k.gblk, R, k.m + 1), VEC_NT, 0, st>>>(k.n, k.gblk, k.act, k.gm, k.basis, k.bstride, k.w,
+                                                               k.gpart, k.gblk);
     PSFD_CHECK_LAUNCH();
     k_gm_hcol<<<R, VEC_NT, 0, st>>>(k.gblk, k.act, k.gpart, k.gblk, k.gm);
     PSFD_CHECK_LAUNCH();
