@@ -477,38 +477,16 @@ def _smooth_length(n: int) -> int:
 def full_domain_problem(prob, nf: int | None = None):
     """The clip with its multilayer stack meshed into the domain (Sec. 4's comparison).
 
-    The stack of total thickness T below z_top is covered by M = ceil(T/dz) cells that
-    extend the domain downward; each cell's permittivity is the thickness-weighted mean
-    of the layers (and the substrate) it overlaps. Below the new bottom only the
-    substrate remains, so its reflection is the single Fresnel interface background /
-    substrate (an empty stack). Returns (problem, D) with D = M dz, the depth of the
-    new reference plane below the old z_top.
+    The voxelisation (thickness-weighted permittivity per cell, substrate-only reflection
+    below the new bottom) is input construction and comes from the seeded input module;
+    this picks the z length (smallest 2^a 3^b 5^c >= 2 nslab + 2 unless given). Returns
+    (problem, D) with D the depth of the new reference plane below the old z_top.
     """
-    d = np.asarray(prob.d_layers, np.float64)
-    eps_l = np.asarray(prob.n_layers, np.complex128) ** 2
-    eps_s = complex(prob.n_sub) ** 2
-    T = float(d.sum())
-    M = int(math.ceil(T / prob.dz - 1e-9))
-    D = M * prob.dz
-    tops = -np.concatenate([[0.0], np.cumsum(d)])  # layer j spans [tops[j+1], tops[j]]
-    cells = np.empty(M, np.complex128)
-    for p in range(M):  # cell p (from the bottom) spans [lo, hi]
-        lo, hi = -D + p * prob.dz, -D + (p + 1) * prob.dz
-        acc, covered = 0.0 + 0.0j, 0.0
-        for j in range(len(d)):
-            ov = max(0.0, min(hi, tops[j]) - max(lo, tops[j + 1]))
-            acc += ov * eps_l[j]
-            covered += ov
-        acc += (prob.dz - covered) * eps_s  # what is left of the cell lies in the substrate
-        cells[p] = acc / prob.dz
-    stack_eps = np.broadcast_to(cells[:, None, None], (M, prob.ny, prob.nx))
-    eps = np.concatenate([stack_eps, np.asarray(prob.eps, np.complex128)], axis=0)
-    nslab = prob.nslab + M
+    from paper_2606_25541_b300 import layouts
+    m = int(math.ceil(float(np.sum(prob.d_layers)) / prob.dz - 1e-9))
     if nf is None:
-        nf = _smooth_length(max(prob.nf, 2 * nslab + 2))
-    full = dataclasses.replace(prob, nslab=nslab, nf=nf, eps=eps, n_layers=np.zeros(0, np.complex128),
-                               d_layers=np.zeros(0, np.float64), name=prob.name + "_full_domain")
-    return full, D
+        nf = _smooth_length(max(prob.nf, 2 * (prob.nslab + m) + 2))
+    return layouts.stack_in_domain(prob, nf)
 
 
 def orders_at_old_reference(orders_full: dict, ctx_full: RhsContext, D: float) -> dict:

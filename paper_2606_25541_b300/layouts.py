@@ -280,6 +280,38 @@ def small_clip(nx=8, ny=8, nslab=4, dx=4.0, dz=2.0, seed=0, stack=None, theta=(6
                     stack, theta, phi, pol, f"small_{nx}x{ny}x{nslab}_s{seed}")
 
 
+def stack_in_domain(prob: Problem, nf: int | None = None):
+    """The clip with its multilayer stack meshed into the domain (the conventional PSFD of
+    the paper's comparison): the stack of total thickness T below z_top is covered by
+    M = ceil(T/dz) cells that extend the domain downward, each with the thickness-weighted
+    mean permittivity of the layers (and substrate) it overlaps; below the new bottom only
+    the substrate remains (an empty stack). nf defaults to the smallest supported length.
+    Returns (problem, D) with D = M dz, the depth of the new reference plane."""
+    d = np.asarray(prob.d_layers, np.float64)
+    eps_l = np.asarray(prob.n_layers, np.complex128) ** 2
+    eps_s = complex(prob.n_sub) ** 2
+    M = int(math.ceil(float(d.sum()) / prob.dz - 1e-9))
+    D = M * prob.dz
+    tops = -np.concatenate([[0.0], np.cumsum(d)])  # layer j spans [tops[j+1], tops[j]]
+    cells = np.empty(M, np.complex128)
+    for p in range(M):  # cell p (from the bottom) spans [lo, hi]
+        lo, hi = -D + p * prob.dz, -D + (p + 1) * prob.dz
+        acc, covered = 0.0 + 0.0j, 0.0
+        for j in range(len(d)):
+            ov = max(0.0, min(hi, tops[j]) - max(lo, tops[j + 1]))
+            acc += ov * eps_l[j]
+            covered += ov
+        acc += (prob.dz - covered) * eps_s  # what is left of the cell lies in the substrate
+        cells[p] = acc / prob.dz
+    eps = np.concatenate([np.broadcast_to(cells[:, None, None], (M, prob.ny, prob.nx)),
+                          np.asarray(prob.eps, np.complex128)], axis=0)
+    nslab = prob.nslab + M
+    full = dataclasses.replace(prob, nslab=nslab, nf=nf or padded_nf(nslab), eps=eps,
+                               n_layers=np.zeros(0, np.complex128), d_layers=np.zeros(0, np.float64),
+                               name=prob.name + "_stack_in_domain")
+    return full, D
+
+
 def random_field(shape, seed: int, dtype=np.complex128) -> np.ndarray:
     """Seeded complex Gaussian test vector (for operator-level parity checks)."""
     rng = np.random.default_rng(seed)
