@@ -201,6 +201,114 @@ template <typename C, bool INV> struct DftHalf<C, 8, INV> {
   }
 };
 
+// v * exp(-+ 2 pi i e / 16) for a compile-time e (after unrolling), INV: conjugate.
+template <typename C, bool INV>
+__device__ __forceinline__ C mulw16(C v, int e) {
+  using R = typename RealOf<C>::T;
+  e &= 15;
+  if (e == 0) return v;
+  if (e == 4) return INV ? cmul_i(v) : cmul_mi(v);
+  if (e == 8) return cneg(v);
+  if (e == 12) return INV ? cmul_mi(v) : cmul_i(v);
+  // cos and sin of 2 pi e / 16 from c(r) = cos(r pi / 8), r = 1, 2, 3 (e is not a multiple of 4)
+  auto c = [](int r) -> R {
+    return r == 1 ? (R)0.92387953251128675613 : (r == 2 ? (R)0.70710678118654752440 : (R)0.38268343236508977173);
+  };
+  const int q = e >> 2, r = e & 3;
+  R cs = q == 0 ? c(r) : (q == 1 ? -c(4 - r) : (q == 2 ? -c(r) : c(4 - r)));
+  R sn = q == 0 ? c(4 - r) : (q == 1 ? c(r) : (q == 2 ? -c(4 - r) : -c(r)));
+  if (!INV) sn = -sn;
+  return cmul(v, mk(cs, sn));
+}
+
+// 16-point DFT in registers as 4 x 4: v[n2 + 4 n1] -> v[k1 + 4 k2].
+template <typename C, bool INV> struct Dft<C, 16, INV> {
+  __device__ __forceinline__ static void run(C* v) {
+    C a[16];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      C x0 = v[n2], x1 = v[n2 + 4], x2 = v[n2 + 8], x3 = v[n2 + 12];
+      dft4<C, INV>(x0, x1, x2, x3);
+      a[4 * n2 + 0] = x0;
+      a[4 * n2 + 1] = mulw16<C, INV>(x1, n2);
+      a[4 * n2 + 2] = mulw16<C, INV>(x2, 2 * n2);
+      a[4 * n2 + 3] = mulw16<C, INV>(x3, 3 * n2);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      C y0 = a[k1], y1 = a[4 + k1], y2 = a[8 + k1], y3 = a[12 + k1];
+      dft4<C, INV>(y0, y1, y2, y3);
+      v[k1] = y0;
+      v[k1 + 4] = y1;
+      v[k1 + 8] = y2;
+      v[k1 + 12] = y3;
+    }
+  }
+};
+
+// 16-point DFT of inputs v[0..7] (v[8..15] = 0): X[2m] = DFT8(v)[m],
+// X[2m+1] = DFT8(v_n w16^n)[m].
+template <typename C, bool INV> struct DftHalf<C, 16, INV> {
+  __device__ __forceinline__ static void run(C* v) {
+    C e[8], o[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      e[n] = v[n];
+      o[n] = mulw16<C, INV>(v[n], n);
+    }
+    Dft<C, 8, INV>::run(e);
+    Dft<C, 8, INV>::run(o);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      v[2 * m] = e[m];
+      v[2 * m + 1] = o[m];
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Register-resident transform of length N = 16 N2 (N2 = 4, 8, 16) by a group of N2 lanes,
+// as two DFT steps (the "four-step" factorisation N = 16 x N2): lane j holds the 16
+// elements j + N2 k, transforms them over k (16 points), multiplies by w_N^{j k1},
+// exchanges through shared memory so that lane j' holds rows k1 = j' (16/N2) + r, and
+// transforms over j (N2 points): output k1 + 16 k2. `ex` is the group's exchange scratch
+// (16 rows of pitch EP); the caller synchronises the group around its use.
+// ---------------------------------------------------------------------------
+template <int N>
+__host__ __device__ constexpr int reg_fft_n2() { return N / 16; }
+
+// step 1 on v (in place): 16-point DFT over k, then twiddles w_N^{+- j k1}; HALF: v[8..15] = 0
+template <typename C, int N, bool INV, bool HALF>
+__device__ __forceinline__ void reg_fft_step1(C (&v)[16], int j, const C* tw) {
+  if constexpr (HALF) {
+    DftHalf<C, 16, INV>::run(v);
+  } else {
+    Dft<C, 16, INV>::run(v);
+  }
+#pragma unroll
+  for (int k1 = 1; k1 < 16; ++k1) {
+    C w = tw[j * k1];
+    if (INV) w = cconj(w);
+    v[k1] = cmul(v[k1], w);
+  }
+}
+
+// step 2: rows k1 of the exchange (written as ex[k1 * EP + j] by step 1's lanes) to outputs:
+// out[r][k2] = X[(j R1 + r) + 16 k2], R1 = 16 / N2.
+template <typename C, int N, bool INV, int EP>
+__device__ __forceinline__ void reg_fft_step2(const C* ex, int j, C (&out)[16]) {
+  constexpr int N2 = reg_fft_n2<N>(), R1 = 16 / N2;
+#pragma unroll
+  for (int r = 0; r < R1; ++r) {
+    C row[N2];
+#pragma unroll
+    for (int i = 0; i < N2; ++i) row[i] = ex[(j * R1 + r) * EP + i];
+    Dft<C, N2, INV>::run(row);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) out[r * N2 + k2] = row[k2];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Stockham stages. Butterfly b of a radix-R stage (after stages whose radices multiply
 // to NS) reads elements b + r N/R, twiddles them by exp(-2 pi i r (b mod NS)/(NS R)),

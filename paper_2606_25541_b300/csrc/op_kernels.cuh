@@ -555,6 +555,13 @@ __device__ __forceinline__ void dyadic_apply(C* c0, C* c1, C* c2, typename RealO
 template <int NF> __host__ __device__ constexpr int phase_entries() { return 8 + (NF + 15) / 16; }
 
 // grid (nx / tx, ny, nrhs); dynamic shared memory: 3 tx (NF + 1) columns + tables.
+// FP32 columns of length 64, 128 and 256 use the register-resident transform (groups of
+// NF/16 lanes, one shared-memory exchange per transform, input read straight from HBM);
+// the CTA then has 24 groups: 8 x-modes x 3 components.
+template <typename C, int NF> __host__ __device__ constexpr bool zcol_reg() {
+  return sizeof(C) == 8 && (NF == 64 || NF == 128 || NF == 256);
+}
+
 template <typename C, int NF, int NT>
 __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
   using R = typename RealOf<C>::T;
@@ -620,26 +627,62 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
       cqy[t] = (R)qy64;
     }
   }
-  // The forward transform reads only planes 0 .. NF/2-1 (its input vanishes above, as
-  // ns + 1 <= NF/2): zero plane 0 and planes ns+1 .. NF/2-1, copy planes 1 .. ns.
   constexpr int HF = NF / 2;
-  const int nz = HF - ns;
-  for (int i = threadIdx.x; i < 3 * tx * nz; i += NT) {
-    const int cc = i / nz, zz = i % nz;
-    col[cc * P + fpad(zz == 0 ? 0 : ns + zz)] = mk((R)0, (R)0);
-  }
   // thread -> (column t0, planes p0, p0 + pstep, ...): no divisions inside the copy loops
   const int t0 = threadIdx.x % tx, p0 = threadIdx.x / tx, pstep = NT / tx;
   const size_t pstride = (size_t)ny * nx;
   C* gcol = a.work + (size_t)lr * 3 * ns * pstride + (size_t)y * nx + x0 + t0;
+  constexpr bool REG = zcol_reg<C, NF>();
+  constexpr int N2 = NF / 16, R1 = N2 > 0 ? 16 / N2 : 1;
+  constexpr int EP = 16 * (N2 + 1) <= P ? N2 + 1 : N2;  // exchange row pitch
+  const int rf = threadIdx.x / (N2 > 0 ? N2 : 1), rj = threadIdx.x % (N2 > 0 ? N2 : 1);
+  const bool rvalid = REG && rf < 3 * tx;
+  C* rex = col + (rvalid ? rf : 0) * P;  // the group's column: exchange scratch, then spectrum
+  if constexpr (REG) {
+    // planes j + N2 k (k < 8, the nonzero half: ns + 1 <= NF/2) straight from HBM
+    __syncthreads();  // twiddles
+    C v[16];
+    if (rvalid) {
+      const int cc = rf / tx, t = rf % tx;
+      const C* src = a.work + (size_t)lr * 3 * ns * pstride + (size_t)cc * ns * pstride + (size_t)y * nx + x0 + t;
 #pragma unroll
-  for (int cc = 0; cc < 3; ++cc) {
+      for (int k = 0; k < 8; ++k) {
+        const int n = rj + N2 * k;
+        v[k] = (n >= 1 && n <= ns) ? src[(size_t)(n - 1) * pstride] : mk((R)0, (R)0);
+      }
+#pragma unroll
+      for (int k = 8; k < 16; ++k) v[k] = mk((R)0, (R)0);
+      reg_fft_step1<C, NF, false, true>(v, rj, tw);
+#pragma unroll
+      for (int k1 = 0; k1 < 16; ++k1) rex[k1 * EP + rj] = v[k1];
+    }
+    __syncwarp();
+    C o[16];
+    if (rvalid) reg_fft_step2<C, NF, false, EP>(rex, rj, o);
+    __syncwarp();
+    if (rvalid) {
+#pragma unroll
+      for (int r = 0; r < R1; ++r)
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) rex[fpad(rj * R1 + r + 16 * k2)] = o[r * N2 + k2];
+    }
+  } else {
+    // The forward transform reads only planes 0 .. NF/2-1 (its input vanishes above, as
+    // ns + 1 <= NF/2): zero plane 0 and planes ns+1 .. NF/2-1, copy planes 1 .. ns.
+    const int nz = HF - ns;
+    for (int i = threadIdx.x; i < 3 * tx * nz; i += NT) {
+      const int cc = i / nz, zz = i % nz;
+      col[cc * P + fpad(zz == 0 ? 0 : ns + zz)] = mk((R)0, (R)0);
+    }
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
 #pragma unroll 4
-    for (int pl = p0; pl < ns; pl += pstep)
-      col[(cc * tx + t0) * P + fpad(pl + 1)] = gcol[((size_t)cc * ns + pl) * pstride];
+      for (int pl = p0; pl < ns; pl += pstep)
+        col[(cc * tx + t0) * P + fpad(pl + 1)] = gcol[((size_t)cc * ns + pl) * pstride];
+    }
+    __syncthreads();
+    cta_fft<C, NF, false, false, 1, true>(col, 3 * tx, P, tw);
   }
-  __syncthreads();
-  cta_fft<C, NF, false, false, 1, true>(col, 3 * tx, P, tw);
   __syncthreads();
 
   // constants in the working precision (no FP64 arithmetic in the FP32 kernel)
@@ -670,7 +713,34 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
                  col + (2 * tx + t) * P + fpad(HF), cqx[t], cqy[t], kzs[HF], S, Es, cinv);
   }
   __syncthreads();
-  cta_fft<C, NF, true>(col, 3 * tx, P, tw);
+  if constexpr (REG) {
+    C v[16];
+    if (rvalid) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = rex[fpad(rj + N2 * k)];
+    }
+    __syncwarp();
+    if (rvalid) {
+      reg_fft_step1<C, NF, true, false>(v, rj, tw);
+#pragma unroll
+      for (int k1 = 0; k1 < 16; ++k1) rex[k1 * EP + rj] = v[k1];
+    }
+    __syncwarp();
+    C o[16];
+    if (rvalid) reg_fft_step2<C, NF, true, EP>(rex, rj, o);
+    __syncwarp();
+    if (rvalid) {  // planes 0 .. NF/2 are the ones used below
+#pragma unroll
+      for (int r = 0; r < R1; ++r)
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+          const int n = rj * R1 + r + 16 * k2;
+          if (n <= HF) rex[fpad(n)] = o[r * N2 + k2];
+        }
+    }
+  } else {
+    cta_fft<C, NF, true>(col, 3 * tx, P, tw);
+  }
   __syncthreads();
 
   // normalised spectra of G*(V u) on plane 0 and plane ns+1

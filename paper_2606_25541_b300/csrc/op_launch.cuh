@@ -181,7 +181,7 @@ int launch_cols(const OpCall<C>& a) {
 
 template <typename C, int NF>
 int launch_zcol(const OpCall<C>& a) {
-  constexpr int NT = Tune<C>::ZCOL_NT;
+  constexpr int NT = zcol_reg<C, NF>() ? 24 * (NF / 16) : Tune<C>::ZCOL_NT;
   static_assert(8 + (NF + 15) / 16 == phase_entries<NF>(), "phase table size");
   const int tx = zcol_tile<C>(a.nx, NF);
   const size_t smem = zcol_smem_bytes<C>(NF, tx);

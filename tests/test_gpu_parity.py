@@ -89,7 +89,8 @@ def test_rhs_matches_oracle(psfd):
 # one operator application (the Krylov hot path)
 # ---------------------------------------------------------------------------
 APPLY_CASES = [
-    # (nx, ny, nslab, nz_min): fused planes, split planes, radix 3/5, ragged column tiles
+    # (nx, ny, nslab, nz_min): fused planes, split planes, radix 3/5, ragged column tiles,
+    # z transforms in registers
     (8, 8, 4, 0),
     (16, 8, 5, 0),
     (32, 32, 7, 32),
@@ -97,6 +98,10 @@ APPLY_CASES = [
     (4, 160, 2, 0),
     (64, 64, 6, 0),
     (128, 128, 9, 0),
+    # z lengths of the register-resident FP32 z transform (nf = 64, 128, 256)
+    (16, 16, 12, 64),
+    (32, 16, 20, 128),
+    (16, 32, 9, 256),
 ]
 
 
