@@ -443,9 +443,23 @@ def oracle_solve_seconds(prob, i: int, rtol: float) -> float:
         return time.perf_counter() - t0
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (from /proc/cpuinfo) and its logical core count."""
+    name = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    name = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return f"{name}, {os.cpu_count()} logical cores on the host"
+
+
 def cpu_baseline(prob, rtol: float):
     t = oracle_solve_seconds(prob, 5, rtol)
-    return {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle", "host": cpu_model(),
             "sample": f"one of the 18 illuminations (theta {prob.theta_deg[5]:g}, phi {prob.phi_deg[5]:g}, "
                       f"pol {int(prob.pol[5])}) solved by the FP64 oracle (numpy FFT + GMRES to relative "
                       f"residual {rtol:g}, orders included), single thread: {t:.1f} s"}
@@ -467,7 +481,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "reference_step": "one illumination per step, oracle GMRES"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": cpu_model(),
                          "sample": f"{args.steps} single-illumination oracle solves (GMRES to {rtol:g}), "
                                    f"one thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

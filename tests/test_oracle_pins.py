@@ -294,6 +294,32 @@ def test_mirror_symmetric_layout_at_normal_incidence_gives_mirrored_orders():
     assert err < 1e-15
 
 
+@pytest.mark.parametrize("pol", [0, 1])
+def test_rotated_layout_and_illumination_give_rotated_orders(pol):
+    """Rotating the layout by 90 deg about z together with phi -> phi + 90 deg maps order
+    (m, n) to (-n, m) and rotates its amplitude vector, (Ax, Ay, Az) -> (-Ay, Ax, Az). Odd
+    square grid (no Nyquist bin), dx = dy: exact to the solver tolerance."""
+    n = 9
+    rng = np.random.default_rng(7)
+    mask = rng.random((n, n)) < 0.45
+    eps = layouts.extrude(mask, 3)
+    # eps_rot[y', x'] = eps[y, x] with (x', y') = (-y, x)
+    eps_rot = np.ascontiguousarray(eps[:, (-np.arange(n)) % n, :].transpose(0, 2, 1))
+    assert np.allclose(eps_rot[:, 2, (-5) % n], eps[:, 5, 2])
+    st = layouts.ru_mosi_stack(3)
+    p0 = _problem(eps, st, 6.0, 20.0, pol, 2.5, 2.0, nf=8)
+    p1 = _problem(eps_rot, st, 6.0, 110.0, pol, 2.5, 2.0, nf=8)
+    o0, _, _ = oracle.solve(p0, 0, rtol=1e-14)
+    o1, _, _ = oracle.solve(p1, 0, rtol=1e-14)
+    a0 = {(m, k): a for m, k, a in zip(o0["m"], o0["n"], o0["amp"])}
+    a1 = {(m, k): a for m, k, a in zip(o1["m"], o1["n"], o1["amp"])}
+    assert len(a0) == len(a1) > 4
+    rot = np.array([[0, -1, 0], [1, 0, 0], [0, 0, 1]])
+    scale = max(np.max(np.abs(a)) for a in a0.values())
+    err = max(np.max(np.abs(a1[(-k, m)] - rot @ a)) for (m, k), a in a0.items())
+    assert err < 1e-11 * scale
+
+
 def test_rayleigh_anomaly_is_reported():
     eps = np.ones((2, 9, 9), complex)
     p = _problem(eps, layouts.ru_mosi_stack(1), 0.0, 0.0, 0, 13.5 / 9 * 2, 2.0)
