@@ -87,19 +87,43 @@ __global__ void __launch_bounds__(VEC_NT) k_bicg_xr(int n, int nblk, int rhs0, c
   if (!act[g]) return;
   if (ctac && threadIdx.x == 0) atomicAdd(ctac, 1u);
   const size_t off = (size_t)lr * n;
-  const int chunk = (n + nblk - 1) / nblk;
-  const int lo = blk * chunk, hi = min(n, lo + chunk);
   const C al = from_c64<C>(sc[g].alpha), om = from_c64<C>(sc[g].omega);
   typename Acc<C>::T d0 = mk((R)0, (R)0), d2 = d0;
-  for (int i = lo + threadIdx.x; i < hi; i += VEC_NT) {
-    const size_t k = off + i;
-    const C si = s[k], pk = pn[k];
-    if (pn != p) p[k] = pk;
-    x[k] = cadd(x[k], cadd(cmul(al, pk), cmul(om, si)));
-    const C ri = csub(si, cmul(om, t[k]));
-    r[k] = ri;
-    d0 = cadd(d0, cmulc(r0[k], ri));
-    d2.x += ri.x * ri.x + ri.y * ri.y;
+  auto elem = [&](C si, C pk, C xk, C tk, C zk, C& xo, C& ro) {
+    xo = cadd(xk, cadd(cmul(al, pk), cmul(om, si)));
+    ro = csub(si, cmul(om, tk));
+    d0 = cadd(d0, cmulc(zk, ro));
+    d2.x += ro.x * ro.x + ro.y * ro.y;
+  };
+  if constexpr (sizeof(C) == 8) {
+    // FP32: two elements per 16-byte access (n is even, so every chunk starts 16-byte aligned)
+    const int chunk = (((n + nblk - 1) / nblk) + 1) & ~1;
+    const int lo = blk * chunk, hi = min(n, lo + chunk);
+    auto ld = [](const C* q) { return *reinterpret_cast<const float4*>(q); };
+    auto lo2 = [](float4 v) { return make_float2(v.x, v.y); };
+    auto hi2 = [](float4 v) { return make_float2(v.z, v.w); };
+    for (int i = lo + 2 * (int)threadIdx.x; i < hi; i += 2 * VEC_NT) {
+      const size_t k = off + i;
+      const float4 S = ld(s + k), Pn = ld(pn + k), X = ld(x + k), T = ld(t + k), Z = ld(r0 + k);
+      if (pn != p) *reinterpret_cast<float4*>(p + k) = Pn;
+      C x0, x1, r0v, r1v;
+      elem(lo2(S), lo2(Pn), lo2(X), lo2(T), lo2(Z), x0, r0v);
+      elem(hi2(S), hi2(Pn), hi2(X), hi2(T), hi2(Z), x1, r1v);
+      *reinterpret_cast<float4*>(x + k) = make_float4(x0.x, x0.y, x1.x, x1.y);
+      *reinterpret_cast<float4*>(r + k) = make_float4(r0v.x, r0v.y, r1v.x, r1v.y);
+    }
+  } else {
+    const int chunk = (n + nblk - 1) / nblk;
+    const int lo = blk * chunk, hi = min(n, lo + chunk);
+    for (int i = lo + threadIdx.x; i < hi; i += VEC_NT) {
+      const size_t k = off + i;
+      const C si = s[k], pk = pn[k];
+      if (pn != p) p[k] = pk;
+      C xo, ro;
+      elem(si, pk, x[k], t[k], r0[k], xo, ro);
+      x[k] = xo;
+      r[k] = ro;
+    }
   }
   vec_block_dots<C>(d0, d2, DOT_R0_OUT | DOT_OUT_OUT, partials + ((size_t)g * NDOT) * maxblk + blk, maxblk);
 }
