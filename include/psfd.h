@@ -178,6 +178,15 @@ int psfd_apply(psfd_ctx* ctx, int precision, int rhs0, int n_rhs, const void* u,
 int psfd_get_solution(psfd_ctx* ctx, int rhs, double* dst, int where);
 int psfd_get_rhs(psfd_ctx* ctx, int rhs, double* dst, int where);
 
+/* Warm start: the next psfd_solve starts illumination rhs from x ([3][nslab][ny][nx] complex
+ * double, host or device as `where` says) instead of zero -- a solution from a nearby
+ * problem, or this problem's own solution at a looser tolerance, so that a solve can be
+ * continued to a tighter one. The solve first forms the FP64 residual b - A x; when that is
+ * already below tol it takes no Krylov iteration. Call after psfd_set_illumination (which
+ * discards guesses); x is copied before the call returns. Errors: PSFD_E_ARG (rhs out of
+ * range, null x, bad where). */
+int psfd_set_initial_guess(psfd_ctx* ctx, int rhs, const double* x, int where);
+
 /* Per-mode tables of illumination rhs, each [ny][nx] complex double on the host:
  * beta (z wavenumber, Im >= 0) and the stack reflection coefficients r_s, r_p. */
 int psfd_get_mode_tables(psfd_ctx* ctx, int rhs, double* beta, double* r_s, double* r_p);
@@ -231,7 +240,11 @@ int psfd_server_status(psfd_server* s, long long ticket, int* state, int* status
 /* Orders of illumination rhs of a finished request (layout as psfd_diffraction_orders). */
 int psfd_server_orders(psfd_server* s, long long ticket, int rhs, int capacity, int* n_orders, int* mn,
                        double* amp, double* sp, double* eff);
-/* Forget a finished request. */
+/* Forget a finished request, or cancel a queued one; PSFD_E_STATE for a running request
+ * (it keeps its slots until it finishes). A request whose bucket alone exceeds the HBM
+ * budget finishes at admission with status PSFD_E_BUDGET; one whose bucket cannot be
+ * allocated while no other request runs finishes with PSFD_E_NOMEM (with requests running,
+ * it waits for their memory). */
 int psfd_server_release(psfd_server* s, long long ticket);
 /* Device bytes held by the buckets and their number. */
 int psfd_server_memory(psfd_server* s, size_t* used, int* n_contexts);

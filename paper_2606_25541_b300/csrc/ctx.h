@@ -62,6 +62,7 @@ struct psfd_ctx {
   std::vector<int> pol, clip;
   // engine state per rhs slot
   std::vector<int> phase, outer, iters, status;
+  std::vector<int> guess;  // 1: x64 holds an initial guess for the slot's next solve
   int enq_hi = 0;  // slots covered by the work enqueued by engine_enqueue
   std::vector<double> relres;
   int* h_act = nullptr;      // pinned

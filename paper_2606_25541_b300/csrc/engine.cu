@@ -1,10 +1,11 @@
 // engine.cu -- the solve engine: every illumination ("rhs slot") of a context moves
 // through its own phases, and one tick advances all of them with shared launches.
 //
-//   PH_NEW    right-hand side just built: ||b|| is taken, x64 = 0, r64 = b
+//   PH_NEW    right-hand side just built: ||b|| is taken, x64 = 0, r64 = b (with an initial
+//             guess x64 is kept and the slot goes to PH_RESID)
 //   PH_START  a refinement sweep starts: rs = r64 / ||r64|| in the working precision (FP32
 //             for PSFD_FP32_REFINED, FP64 for PSFD_FP64) and a Krylov solve of A xc = rs
-//             (GMRES by default, or BiCGStab) is initialised
+//             (BiCGStab by default, or GMRES) is initialised
 //   PH_INNER  Krylov iterations (check_every per tick; the device flag of a slot drops when
 //             its residual estimate reaches the sweep's tolerance, its GMRES cycle is full,
 //             or it breaks down); then x64 += ||r64|| xc
@@ -201,9 +202,11 @@ int engine_enqueue(psfd_ctx* ctx, const psfd_solve_opts& o, bool* pending) {
                    o.tol * o.tol, ctx->sc64, ctx->act64, st));
     for (int g = 0; g < R; ++g) {
       if (!sel[g]) continue;
-      CK(cudaMemsetAsync(ctx->x64 + (size_t)g * U, 0, sizeof(double2) * U, st));
-      CK(cudaMemcpyAsync(ctx->r64 + (size_t)g * U, ctx->b64 + (size_t)g * U, sizeof(double2) * U,
-                         cudaMemcpyDeviceToDevice, st));
+      if (!ctx->guess[g]) {  // with an initial guess, x64 holds it and r64 comes from PH_RESID
+        CK(cudaMemsetAsync(ctx->x64 + (size_t)g * U, 0, sizeof(double2) * U, st));
+        CK(cudaMemcpyAsync(ctx->r64 + (size_t)g * U, ctx->b64 + (size_t)g * U, sizeof(double2) * U,
+                           cudaMemcpyDeviceToDevice, st));
+      }
       CK(cudaMemsetAsync(ctx->side64 + (size_t)g * 6 * ctx->plan.plane, 0, sizeof(double2) * 6 * ctx->plan.plane,
                          st));
     }
@@ -245,11 +248,15 @@ int engine_complete(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
           ctx->iters[g] = 0;
           ctx->status[g] = PSFD_OK;
           if (!(s64.bnorm2 > 0.0)) {  // zero right-hand side: x = 0 is exact
+            if (ctx->guess[g]) CK(cudaMemsetAsync(ctx->x64 + (size_t)g * U, 0, sizeof(double2) * U, st));
             ctx->relres[g] = 0.0;
             to_done[g] = 1;
+          } else if (ctx->guess[g]) {  // warm start: its FP64 residual decides what comes next
+            ctx->phase[g] = PH_RESID;
           } else {
             to_start[g] = 1;
           }
+          ctx->guess[g] = 0;
           break;
         case PH_RESID: {
           const double rel = std::sqrt(s64.rnorm2 / s64.bnorm2);

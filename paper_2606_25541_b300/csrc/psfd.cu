@@ -219,6 +219,7 @@ int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs
   ctx->pol.assign(R, 0);
   ctx->clip.assign(R, 0);
   ctx->phase.assign(R, PH_FREE);
+  ctx->guess.assign(R, 0);
   ctx->outer.assign(R, 0);
   ctx->iters.assign(R, 0);
   ctx->status.assign(R, PSFD_OK);
@@ -362,6 +363,7 @@ int ctx_set_rhs(psfd_ctx* ctx, int g0, int n, const double* theta_deg, const dou
                 st));
   for (int i = 0; i < n; ++i) {
     ctx->phase[g0 + i] = PH_NEW;
+    ctx->guess[g0 + i] = 0;
     ctx->outer[g0 + i] = 0;
     ctx->iters[g0 + i] = 0;
     ctx->status[g0 + i] = PSFD_OK;
@@ -640,6 +642,18 @@ int psfd_get_solution(psfd_ctx* ctx, int rhs, double* dst, int where) {
   if (!ctx || !dst || rhs < 0 || rhs >= ctx->n_rhs || (where != PSFD_HOST && where != PSFD_DEVICE)) return PSFD_E_ARG;
   if (ctx->phase[rhs] != PH_DONE) return ctx->fail(PSFD_E_STATE, "get_solution before solve");
   return copy_vec(ctx, ctx->x64 + (size_t)rhs * ctx->plan.U, dst, where);
+}
+
+int psfd_set_initial_guess(psfd_ctx* ctx, int rhs, const double* x, int where) {
+  if (!ctx || !x || (where != PSFD_HOST && where != PSFD_DEVICE)) return PSFD_E_ARG;
+  if (!ctx->have_illum || rhs < 0 || rhs >= ctx->n_rhs) return ctx->fail(PSFD_E_ARG, "rhs out of range");
+  const size_t bytes = sizeof(double2) * ctx->plan.U;
+  CK(cudaMemcpyAsync(ctx->x64 + (size_t)rhs * ctx->plan.U, x, bytes,
+                     where == PSFD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->guess[rhs] = 1;
+  ctx->phase[rhs] = PH_NEW;
+  return PSFD_OK;
 }
 
 int psfd_get_rhs(psfd_ctx* ctx, int rhs, double* dst, int where) {

@@ -179,7 +179,24 @@ int admit(psfd_server* s, Request* r, bool* admitted) {
     for (auto& bp : s->buckets) have_shape = have_shape || same_grid(bp->grid, r->grid);
     if (have_shape && (int)r->th.size() <= s->slots) return PSFD_OK;  // wait for slots of that bucket
     int rc = PSFD_OK;
-    b = make_bucket(s, r->grid, std::max(s->slots, (int)r->th.size()), &rc);
+    const int cap = std::max(s->slots, (int)r->th.size());
+    const Plan plan = make_plan(r->grid, s->precision, cap, cap);
+    if (s->budget && plan.bytes + pool_extra_bytes(plan, s->precision, cap, s->opts) > s->budget) {
+      r->state = 2;  // can never fit: rejected
+      r->status = PSFD_E_BUDGET;
+      *admitted = true;
+      return PSFD_OK;
+    }
+    b = make_bucket(s, r->grid, cap, &rc);
+    if (!b && rc == PSFD_E_NOMEM) {
+      bool running = false;
+      for (auto& bp : s->buckets) running = running || bp->running > 0;
+      if (running) return PSFD_OK;  // device memory may free up when running requests finish
+      r->state = 2;                 // nothing to wait for: the request fails, the server goes on
+      r->status = PSFD_E_NOMEM;
+      *admitted = true;
+      return PSFD_OK;
+    }
     if (!b) return rc == PSFD_E_BUDGET ? PSFD_OK : rc;  // wait for memory
     if (!find_slots(b, (int)r->th.size(), &clip, &g0)) return PSFD_E_ARG;
   }
@@ -417,7 +434,8 @@ int psfd_server_orders(psfd_server* s, long long ticket, int rhs, int capacity, 
 int psfd_server_release(psfd_server* s, long long ticket) {
   if (!s) return PSFD_E_ARG;
   auto it = s->reqs.find(ticket);
-  if (it == s->reqs.end() || it->second->state != 2) return PSFD_E_STATE;
+  if (it == s->reqs.end() || it->second->state == 1) return PSFD_E_STATE;
+  if (it->second->state == 0) s->queue.erase(std::remove(s->queue.begin(), s->queue.end(), ticket), s->queue.end());
   s->reqs.erase(it);
   return PSFD_OK;
 }

@@ -78,6 +78,7 @@ _SIGS = {
     "psfd_apply": (_I, [_P, _I, _I, _I, _P, _P]),
     "psfd_get_solution": (_I, [_P, _I, _P, _I]),
     "psfd_get_rhs": (_I, [_P, _I, _P, _I]),
+    "psfd_set_initial_guess": (_I, [_P, _I, _P, _I]),
     "psfd_get_mode_tables": (_I, [_P, _I, _D, _D, _D]),
     "psfd_test_fft": (_I, [_I, _I, _I, _I, _P]),
     "psfd_apply_fp32_static": (_I, [ctypes.POINTER(Grid), _I, _D, _D, _D, ctypes.c_double, ctypes.c_double, _P,
@@ -318,6 +319,17 @@ class Solver:
         out = np.zeros(self._field_shape(), np.complex128)
         self._check(self.lib.psfd_get_solution(self.ctx, int(rhs), out.ctypes.data_as(ctypes.c_void_p), HOST))
         return out
+
+    def set_initial_guess(self, rhs, x):
+        """Warm start of illumination rhs: x is a complex128 numpy array or CUDA tensor of the
+        field shape; the next solve starts from it."""
+        if hasattr(x, "is_cuda") and x.is_cuda:
+            self._check(self.lib.psfd_set_initial_guess(self.ctx, int(rhs), ctypes.c_void_p(x.data_ptr()), DEVICE))
+        else:
+            a = np.ascontiguousarray(x, dtype=np.complex128)
+            if a.shape != self._field_shape():
+                raise ValueError(f"initial guess of shape {a.shape}, expected {self._field_shape()}")
+            self._check(self.lib.psfd_set_initial_guess(self.ctx, int(rhs), a.ctypes.data_as(ctypes.c_void_p), HOST))
 
     def get_rhs(self, rhs: int = 0) -> np.ndarray:
         out = np.zeros(self._field_shape(), np.complex128)

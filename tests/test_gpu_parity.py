@@ -290,3 +290,31 @@ def test_apply_1024_clip_matches_oracle_on_sampled_modes(psfd, fp64):
         ref = oracle.scattered_spectrum_mode(prob, 0, u0, m, n)
         got = spec[:, :, n % prob.ny, m % prob.nx].cpu().numpy()
         assert np.linalg.norm(got - ref) <= (1e-12 if fp64 else 3e-5) * np.linalg.norm(ref), (m, n)
+
+
+def test_warm_start_continues_a_solve(psfd, contact_hole_reference):
+    """psfd_set_initial_guess: a solve started from this problem's FP64 solution takes no
+    Krylov iteration; one started from a loose FP32-refined solution reaches the tight
+    tolerance with fewer iterations than from zero and the same orders."""
+    prob, ref, xref = contact_hole_reference
+    s = _solver(psfd, prob, psfd.FP64)
+    s.set_initial_guess(0, xref)
+    rep = s.solve(tol=1e-10, max_iter=400)
+    assert rep["iterations"] == 0 and rep["relres"] <= 1e-10
+    assert _orders_err(s.diffraction_orders(0), ref) < 1e-9
+    s.close()
+
+    loose = _solver(psfd, prob, psfd.FP32_REFINED)
+    loose.solve(tol=1e-4, inner_tol=1e-4, max_iter=200)
+    x0 = loose.get_solution(0)
+    loose.close()
+    cold = _solver(psfd, prob, psfd.FP32_REFINED)
+    rep_cold = cold.solve(tol=1e-9, inner_tol=1e-4, max_iter=200, max_outer=10)
+    cold.close()
+    warm = _solver(psfd, prob, psfd.FP32_REFINED)
+    warm.set_initial_guess(0, torch.tensor(x0, device="cuda"))
+    rep_warm = warm.solve(tol=1e-9, inner_tol=1e-4, max_iter=200, max_outer=10)
+    assert rep_warm["relres"] <= 1e-9
+    assert rep_warm["iterations"] < rep_cold["iterations"]
+    assert _orders_err(warm.diffraction_orders(0), ref) < 1e-6
+    warm.close()

@@ -114,3 +114,33 @@ def test_budget_admits_one_bucket_at_a_time(psfd):
     ref = _solve_alone(psfd, clips[2], psfd.FP32_REFINED)
     np.testing.assert_array_equal(srv.orders(tc, 1)["amp"], ref[1]["amp"])
     srv.close()
+
+
+def test_request_over_the_budget_is_rejected_and_queued_one_cancelled(psfd):
+    """A request whose bucket alone exceeds the HBM budget finishes at admission with
+    PSFD_E_BUDGET (it would otherwise wait forever); a queued request can be cancelled; the
+    others are served as usual."""
+    clips = _clips()
+    probe = psfd.Server(psfd.FP32_REFINED, slots_per_context=2, tol=1e-9)
+    probe.submit(clips[2])
+    probe.progress()
+    small_bucket, _ = probe.memory()
+    probe.close()
+    srv = psfd.Server(psfd.FP32_REFINED, hbm_budget=int(small_bucket * 1.05), slots_per_context=2, tol=1e-9)
+    tc = srv.submit(clips[2])   # 8 x 8 grid, 2 illuminations: fills its bucket
+    ta = srv.submit(clips[0])   # 16 x 16 grid: its bucket alone is over the budget
+    tb = srv.submit(clips[2])   # same grid as tc: waits for its slots, then is cancelled
+    srv.progress()
+    assert srv.status(ta) == (2, psfd.E_BUDGET)
+    assert srv.status(tc)[0] == 1 and srv.status(tb)[0] == 0
+    srv.release(tb)
+    with pytest.raises(psfd.PsfdError):
+        srv.status(tb)
+    with pytest.raises(psfd.PsfdError) as e:
+        srv.release(tc)  # running
+    assert e.value.status == psfd.E_STATE
+    srv.run_until_done()
+    assert srv.status(tc) == (2, psfd.OK)
+    ref = _solve_alone(psfd, clips[2], psfd.FP32_REFINED)
+    np.testing.assert_array_equal(srv.orders(tc, 0)["amp"], ref[0]["amp"])
+    srv.close()
