@@ -187,6 +187,14 @@ int psfd_get_rhs(psfd_ctx* ctx, int rhs, double* dst, int where);
  * range, null x, bad where). */
 int psfd_set_initial_guess(psfd_ctx* ctx, int rhs, const double* x, int where);
 
+/* Convergence curve of illumination rhs in the latest solve (the residual-vs-iteration record
+ * the paper plots, Sec. 4): entry k is (iteration[k] Krylov iterations so far, kind[k],
+ * relres[k]); kind 1 = the FP64 relative residual ||b - A x|| / ||b|| (the start of the solve
+ * and the end of every sweep), kind 0 = the Krylov estimate after a batch of check_every
+ * iterations (BiCGStab only: its recursive residual times the sweep's starting residual).
+ * Copies min(capacity, *n) entries; *n = the number recorded (at most 100000). */
+int psfd_residual_history(psfd_ctx* ctx, int rhs, int capacity, int* n, int* iteration, int* kind, double* relres);
+
 /* Per-mode tables of illumination rhs, each [ny][nx] complex double on the host:
  * beta (z wavenumber, Im >= 0) and the stack reflection coefficients r_s, r_p. */
 int psfd_get_mode_tables(psfd_ctx* ctx, int rhs, double* beta, double* r_s, double* r_p);

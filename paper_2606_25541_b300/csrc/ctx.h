@@ -63,6 +63,15 @@ struct psfd_ctx {
   // engine state per rhs slot
   std::vector<int> phase, outer, iters, status;
   std::vector<int> guess;  // 1: x64 holds an initial guess for the slot's next solve
+  // Residual history per slot (the convergence curve of the latest solve): kind 1 = the FP64
+  // residual ||b - A x|| / ||b||, kind 0 = the Krylov estimate of a sweep (BiCGStab's recursive
+  // residual scaled by the sweep's starting residual); iteration = Krylov iterations so far.
+  struct HistEntry {
+    int iteration, kind;
+    double relres;
+  };
+  std::vector<std::vector<HistEntry>> hist;
+  std::vector<double> sweep_rel;  // FP64 relative residual at the start of the current sweep
   int enq_hi = 0;  // slots covered by the work enqueued by engine_enqueue
   std::vector<double> relres;
   int* h_act = nullptr;      // pinned

@@ -239,6 +239,10 @@ int engine_complete(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
     CK(cudaStreamSynchronize(st));
     std::vector<int> to_update(R, 0), to_start(R, 0), to_done(R, 0);
     const double tol2 = o.tol * o.tol;
+    auto record = [&](int g, int it, int kind, double rel) {
+      auto& h = ctx->hist[g];
+      if (h.size() < 100000) h.push_back({it, kind, rel});
+    };
     bool any_update = false, any_start = false, any_done = false;
     for (int g = 0; g < R; ++g) {
       const KScal& s64 = ctx->h_sc64[g];
@@ -247,6 +251,9 @@ int engine_complete(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
           ctx->outer[g] = 0;
           ctx->iters[g] = 0;
           ctx->status[g] = PSFD_OK;
+          ctx->hist[g].clear();
+          ctx->sweep_rel[g] = 1.0;
+          if (!ctx->guess[g]) record(g, 0, 1, s64.bnorm2 > 0.0 ? 1.0 : 0.0);  // x = 0: r = b
           if (!(s64.bnorm2 > 0.0)) {  // zero right-hand side: x = 0 is exact
             if (ctx->guess[g]) CK(cudaMemsetAsync(ctx->x64 + (size_t)g * U, 0, sizeof(double2) * U, st));
             ctx->relres[g] = 0.0;
@@ -261,6 +268,8 @@ int engine_complete(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
         case PH_RESID: {
           const double rel = std::sqrt(s64.rnorm2 / s64.bnorm2);
           ctx->relres[g] = rel;
+          ctx->sweep_rel[g] = rel;
+          record(g, ctx->iters[g], 1, rel);
           if (s64.rnorm2 <= tol2 * s64.bnorm2) {
             ctx->status[g] = PSFD_OK;
             to_done[g] = 1;
@@ -272,12 +281,16 @@ int engine_complete(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
           }
           break;
         }
-        case PH_INNER:
+        case PH_INNER: {
+          const KScal& si = ctx->h_sc[g];
+          if (o.krylov != PSFD_GMRES && si.bnorm2 > 0.0 && si.iters > 0)
+            record(g, ctx->iters[g] + si.iters, 0, std::sqrt(si.rnorm2 / si.bnorm2) * ctx->sweep_rel[g]);
           if (!ctx->h_act[g]) {  // sweep ended (converged, cycle full or breakdown): correct x64
-            ctx->iters[g] += ctx->h_sc[g].iters;
+            ctx->iters[g] += si.iters;
             to_update[g] = 1;
           }
           break;
+        }
         default:
           break;
       }

@@ -220,6 +220,8 @@ int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs
   ctx->clip.assign(R, 0);
   ctx->phase.assign(R, PH_FREE);
   ctx->guess.assign(R, 0);
+  ctx->hist.assign(R, {});
+  ctx->sweep_rel.assign(R, 1.0);
   ctx->outer.assign(R, 0);
   ctx->iters.assign(R, 0);
   ctx->status.assign(R, PSFD_OK);
@@ -653,6 +655,20 @@ int psfd_set_initial_guess(psfd_ctx* ctx, int rhs, const double* x, int where) {
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->guess[rhs] = 1;
   ctx->phase[rhs] = PH_NEW;
+  return PSFD_OK;
+}
+
+int psfd_residual_history(psfd_ctx* ctx, int rhs, int capacity, int* n, int* iteration, int* kind, double* relres) {
+  if (!ctx || !n || rhs < 0 || rhs >= ctx->max_rhs || capacity < 0) return PSFD_E_ARG;
+  const auto& h = ctx->hist[rhs];
+  *n = (int)h.size();
+  const int m = std::min(capacity, (int)h.size());
+  if (m > 0 && (!iteration || !kind || !relres)) return PSFD_E_ARG;
+  for (int k = 0; k < m; ++k) {
+    iteration[k] = h[k].iteration;
+    kind[k] = h[k].kind;
+    relres[k] = h[k].relres;
+  }
   return PSFD_OK;
 }
 

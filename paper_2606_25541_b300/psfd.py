@@ -79,6 +79,7 @@ _SIGS = {
     "psfd_get_solution": (_I, [_P, _I, _P, _I]),
     "psfd_get_rhs": (_I, [_P, _I, _P, _I]),
     "psfd_set_initial_guess": (_I, [_P, _I, _P, _I]),
+    "psfd_residual_history": (_I, [_P, _I, _I, _IP, _IP, _IP, _D]),
     "psfd_get_mode_tables": (_I, [_P, _I, _D, _D, _D]),
     "psfd_test_fft": (_I, [_I, _I, _I, _I, _P]),
     "psfd_apply_fp32_static": (_I, [ctypes.POINTER(Grid), _I, _D, _D, _D, ctypes.c_double, ctypes.c_double, _P,
@@ -330,6 +331,20 @@ class Solver:
             if a.shape != self._field_shape():
                 raise ValueError(f"initial guess of shape {a.shape}, expected {self._field_shape()}")
             self._check(self.lib.psfd_set_initial_guess(self.ctx, int(rhs), a.ctypes.data_as(ctypes.c_void_p), HOST))
+
+    def residual_history(self, rhs: int = 0):
+        """Convergence curve of the latest solve: iteration, kind (1 = FP64 residual, 0 = Krylov
+        estimate) and relative residual per recorded point."""
+        n = ctypes.c_int(0)
+        self._check(self.lib.psfd_residual_history(self.ctx, int(rhs), 0, ctypes.byref(n), None, None, None))
+        cap = n.value
+        it = np.zeros(max(cap, 1), np.int32)
+        kind = np.zeros(max(cap, 1), np.int32)
+        rel = np.zeros(max(cap, 1), np.float64)
+        self._check(self.lib.psfd_residual_history(self.ctx, int(rhs), cap, ctypes.byref(n), it.ctypes.data_as(_IP),
+                                                   kind.ctypes.data_as(_IP), _dptr(rel)))
+        k = min(cap, n.value)
+        return {"iteration": it[:k].copy(), "kind": kind[:k].copy(), "relres": rel[:k].copy()}
 
     def get_rhs(self, rhs: int = 0) -> np.ndarray:
         out = np.zeros(self._field_shape(), np.complex128)

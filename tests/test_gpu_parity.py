@@ -318,3 +318,22 @@ def test_warm_start_continues_a_solve(psfd, contact_hole_reference):
     assert rep_warm["iterations"] < rep_cold["iterations"]
     assert _orders_err(warm.diffraction_orders(0), ref) < 1e-6
     warm.close()
+
+
+def test_residual_history_records_the_refined_solve(psfd, contact_hole_reference):
+    """psfd_residual_history: the FP64 residual starts at 1 (x = 0), falls at every sweep and
+    ends at the reported relres; the BiCGStab estimates in between reach the inner tolerance
+    of each sweep; iteration counts never decrease."""
+    prob, _, _ = contact_hole_reference
+    s = _solver(psfd, prob, psfd.FP32_REFINED)
+    rep = s.solve(tol=1e-8, inner_tol=1e-4, max_iter=200, max_outer=10)
+    h = s.residual_history(0)
+    kind, rel, it = h["kind"], h["relres"], h["iteration"]
+    assert kind[0] == 1 and rel[0] == 1.0
+    fp64 = rel[kind == 1]
+    assert len(fp64) == rep["outer"] + 1
+    assert np.all(np.diff(fp64) < 0) and fp64[-1] == rep["relres"]
+    assert np.all(np.diff(it) >= 0) and it[-1] == rep["iterations"]
+    est = rel[kind == 0]
+    assert len(est) >= 2 and est.min() <= 1e-4 * 1.01
+    s.close()
