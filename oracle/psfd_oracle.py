@@ -46,7 +46,7 @@ __all__ = [
     "green_scalar", "green_dyadic", "RhsContext", "setup_rhs", "apply_operator",
     "apply_operator_dft", "rhs_vector", "gmres", "dense_operator", "diffraction_orders",
     "transmitted_orders", "solve", "solve_all", "AnomalyError", "full_domain_problem",
-    "orders_at_old_reference", "scattered_spectrum_mode",
+    "orders_at_old_reference", "scattered_spectrum_mode", "reflected_field", "solve_fixed_point",
 ]
 
 
@@ -456,6 +456,74 @@ def solve(prob, i: int = 0, rtol: float = 1e-13, maxiter: int = 500, direct: boo
     _, E0, Etop = apply_operator(ctx, x, return_side=True)
     orders = diffraction_orders(ctx, E0, Etop)
     return orders, x, {"iterations": its, "relres": res, "ctx": ctx, "E0": E0, "Etop": Etop}
+
+
+# ---------------------------------------------------------------------------
+# the outer fixed-point iteration of Eq. (8)
+# ---------------------------------------------------------------------------
+def reflected_field(ctx: RhsContext, D: np.ndarray) -> np.ndarray:
+    """R[E] on the absorber planes, Eq. (9), for a downgoing field given by its normalised
+    xy Fourier coefficients D (shape (3, ny, nx)) at z_top:
+    FFT_xy^-1[T_R D] exp(i beta (z_p - z_top)), z_p = (p - 1/2) dz, p = 1..nslab."""
+    zc = (np.arange(1, ctx.nslab + 1) - 0.5) * ctx.dz
+    up = np.exp(1j * ctx.beta[None] * zc[:, None, None])          # (nslab, ny, nx)
+    TD = np.einsum("abyx,byx->ayx", ctx.TR, D)
+    return np.fft.ifft2(TD[:, None] * up[None], axes=(2, 3)) * (ctx.nx * ctx.ny)
+
+
+def solve_fixed_point(prob, i: int = 0, rtol: float = 1e-10, max_outer: int = 50,
+                      inner_rtol: float = 1e-13, maxiter: int = 500):
+    """The background-field method as the paper runs it (Sec. 3, Eqs. (8)-(9)): an outer
+    fixed-point loop in which the stack reflection is built from the mask field of the
+    previous outer step, and each outer step solves a free-space Lippmann-Schwinger problem.
+
+    Outer step k (E_mask^(0) = 0):
+      b_k = E_inc + R[E_inc + E_mask^(k-1)]      on the absorber planes, with R of Eq. (9)
+      u_k - G*(V u_k) = b_k                      (free space: no R in the operator), GMRES
+      E_mask^(k) = G*(V u_k); its downgoing part at z_top comes from plane 0, moved up by
+      exp(-i beta dz/2)
+    and the loop stops when the reflected field changes by at most rtol between steps:
+    ||R[E_mask^(k)] - R[E_mask^(k-1)]|| <= rtol ||b_1|| (b_1 = E_inc + R[E_inc], the driving
+    field of the folded system; the paper leaves the norm and the tolerance open).
+    u_k is the total field on the absorber planes, the unknown of the folded solve, which
+    this loop converges to (Sec. 3: its fixed point is A u = b_1 with A = I - (I + R) G*V).
+
+    Returns (orders, u, info) like solve(); info["changes"] lists the relative change per
+    outer step, info["outer"] the steps taken, info["converged"] whether rtol was met.
+    """
+    ctx = setup_rhs(prob, i)                       # T_R for R and the orders
+    free = setup_rhs(prob, i, reflection=False)    # the free-space operator u - G*(V u)
+    n = ctx.nslab
+    zc = (np.arange(1, n + 1) - 0.5) * ctx.dz
+    E_inc = ctx.e_inc[:, None, None, None] * np.exp(-1j * ctx.beta00 * zc)[None, :, None, None] \
+        * np.ones((1, 1, ctx.ny, ctx.nx))
+    D_inc = np.zeros((3, ctx.ny, ctx.nx), np.complex128)
+    D_inc[:, 0, 0] = ctx.e_inc                     # E_inc at z_top, normalised coefficients
+    R_inc = reflected_field(ctx, D_inc)
+    b1 = E_inc + R_inc
+    b1n = np.linalg.norm(b1)
+    R_mask = np.zeros_like(b1)                     # R[E_mask^(0)] = 0
+    changes, inner = [], 0
+    u = np.zeros_like(b1)
+    converged = False
+    k = 0
+    for k in range(1, max_outer + 1):
+        b_k = E_inc + R_inc + R_mask
+        u, its, _ = gmres(lambda v: apply_operator(free, v), b_k, rtol=inner_rtol, maxiter=maxiter)
+        inner += its
+        _, E0, _ = apply_operator(free, u, return_side=True)
+        D_mask = E0 * np.exp(-0.5j * ctx.beta * ctx.dz)[None]
+        R_new = reflected_field(ctx, D_mask)
+        change = float(np.linalg.norm(R_new - R_mask) / b1n)
+        changes.append(change)
+        R_mask = R_new
+        if change <= rtol:
+            converged = True
+            break
+    _, E0, Etop = apply_operator(free, u, return_side=True)
+    orders = diffraction_orders(ctx, E0, Etop)
+    return orders, u, {"outer": k, "inner_iterations": inner, "changes": changes,
+                       "converged": converged, "ctx": ctx, "E0": E0, "Etop": Etop}
 
 
 # ---------------------------------------------------------------------------

@@ -367,3 +367,57 @@ def test_single_mode_restriction_equals_the_full_operator():
         got = oracle.scattered_spectrum_mode(p, 0, u, m, n)
         ref = W[:, :, n % 8, m % 16]
         assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------------------
+# the outer fixed-point iteration of Eq. (8)
+# ---------------------------------------------------------------------------
+def _fixed_point_clip(stack, pol=1):
+    return layouts.small_clip(nx=4, ny=4, nslab=3, seed=7, theta=(6.0,), phi=(20.0,), pol=(pol,),
+                              stack=stack)
+
+
+@pytest.mark.parametrize("n_bilayers,pol", [(3, 1), (40, 0)])
+def test_fixed_point_converges_to_the_folded_dense_solution(n_bilayers, pol):
+    """At the fixed point of Eq. (8) E_mask stops changing, so R[E_inc + E_mask] is
+    consistent with the solution and the loop lands on the folded system A u = b, here
+    solved by dense LU; the orders agree as well."""
+    p = _fixed_point_clip(layouts.ru_mosi_stack(n_bilayers), pol)
+    o_fp, u_fp, info = oracle.solve_fixed_point(p, 0, rtol=1e-12)
+    o_lu, u_lu, _ = oracle.solve(p, 0, direct=True)
+    assert info["converged"] and 3 <= info["outer"] <= 30
+    assert np.max(np.abs(u_fp - u_lu)) < 1e-10 * np.max(np.abs(u_lu))
+    assert np.max(np.abs(o_fp["amp"] - o_lu["amp"])) < 1e-10 * np.max(np.abs(o_lu["amp"]))
+    ch = info["changes"]
+    assert all(b < a for a, b in zip(ch, ch[1:])), ch  # a contraction on this clip
+
+
+def test_fixed_point_iterates_follow_the_operator_splitting():
+    """Outer step k solves M u_k = b + (M - A) u_(k-1), u_0 = 0, with M the free-space
+    operator (dense, from the reflection-free operator) and A the folded one (dense): the
+    reflection of the previous mask field built from plane 0, T_R and exp(i beta z) must
+    equal (M - A) u_(k-1) on the absorber planes, and the reported change is its step."""
+    p = _fixed_point_clip(layouts.ru_mosi_stack(5))
+    ctx, free = oracle.setup_rhs(p, 0), oracle.setup_rhs(p, 0, reflection=False)
+    A = oracle.dense_operator(ctx)
+    M = oracle.dense_operator(free, lambda v: oracle.apply_operator(free, v))
+    b = oracle.rhs_vector(ctx).reshape(-1)
+    u_prev = np.zeros_like(b)
+    for k in (1, 2, 3):
+        u_k = np.linalg.solve(M, b + (M - A) @ u_prev)
+        _, u, info = oracle.solve_fixed_point(p, 0, rtol=0.0, max_outer=k, inner_rtol=1e-15)
+        assert info["outer"] == k and not info["converged"]
+        assert np.max(np.abs(u.reshape(-1) - u_k)) < 1e-12 * np.max(np.abs(u_k)), k
+        step = np.linalg.norm((M - A) @ (u_k - u_prev)) / np.linalg.norm(b)
+        assert abs(info["changes"][-1] - step) < 1e-9 * step, (k, info["changes"], step)
+        u_prev = u_k
+
+
+def test_fixed_point_without_stack_is_a_single_free_space_solve():
+    """No stack and a vacuum substrate: T_R = 0, R vanishes, the first outer step already
+    has a zero change and its field is the plain free-space solution."""
+    p = _fixed_point_clip(layouts.empty_stack())
+    o_fp, u_fp, info = oracle.solve_fixed_point(p, 0, rtol=1e-12)
+    o_lu, u_lu, _ = oracle.solve(p, 0, direct=True)
+    assert info["outer"] == 1 and info["changes"] == [0.0]
+    assert np.max(np.abs(u_fp - u_lu)) < 1e-11 * np.max(np.abs(u_lu))
