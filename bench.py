@@ -67,6 +67,9 @@ def parse_args(argv=None):
     ap.add_argument("--bilayers", type=int, default=40, help="Mo/Si bilayers of the --crosscheck stack")
     ap.add_argument("--large", action="store_true",
                     help="1024 x 1024 x 60 curvilinear clip, 8 illuminations in memory-bounded batches")
+    ap.add_argument("--fixed-point", action="store_true",
+                    help="the outer fixed-point loop of Eq. (8) against the folded solve, per stack size")
+    ap.add_argument("--fp-bilayers", type=str, default="0,10,40", help="Mo/Si bilayers for --fixed-point")
     ap.add_argument("--serve", type=int, default=24,
                     help="requests in the serving-loop sample (0 = skip); --serve-only prints only that")
     ap.add_argument("--serve-only", action="store_true")
@@ -338,6 +341,47 @@ def run_crosscheck(args):
         idx = [key[(m, n)] for m, n in zip(a["m"], a["n"])]
         diffs.append(float(np.linalg.norm(a["eff"] - b["eff"][idx]) / np.linalg.norm(b["eff"])))
     out["efficiency_rel_diff"] = diffs
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_fixed_point(args):
+    """The paper's outer fixed-point loop (Eq. (8): free-space solves with R rebuilt from the
+    previous step's mask field) against the folded operator, on the 128 x 128 x 60 line/space
+    clip with its 18 illuminations, FP32 with FP64 refinement, both to the same folded FP64
+    residual (--tol), for Ru + n x Mo/Si stacks (--fp-bilayers; 0 = the Ru cap on Si alone).
+    Reported per stack: seconds, Krylov iterations, outer steps of the loop, and the relative
+    difference of the reflected orders between the two (normwise over all illuminations)."""
+    import dataclasses
+    import torch
+    from paper_2606_25541_b300 import psfd
+    base = layouts.line_space_clip(seed=2)
+    stream = torch.cuda.current_stream()
+    kw = dict(tol=args.tol, inner_tol=args.inner_tol, max_iter=400, max_outer=12, raise_on_error=False)
+    out = {"mode": "fixed_point_vs_folded", "workload": WORKLOAD, "tol": args.tol, "stacks": []}
+    for nb in (int(v) for v in args.fp_bilayers.split(",")):
+        n_l, d_l, n_s = layouts.ru_mosi_stack(nb)
+        prob = dataclasses.replace(base, n_layers=n_l, d_layers=d_l, n_sub=n_s)
+        row = {"bilayers": nb}
+        orders = {}
+        for name in ("folded", "fixed_point"):
+            s = psfd.Solver.from_problem(prob, psfd.FP32_REFINED, stream=stream)
+            s.solve(**kw)  # warm-up: tables, pool and the first-call paths
+            s.set_illumination(prob.theta_deg, prob.phi_deg, prob.pol)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = s.solve(**kw) if name == "folded" else s.solve_fixed_point(max_steps=200, **kw)
+            torch.cuda.synchronize()
+            row[name] = {"seconds": time.perf_counter() - t0, "iterations": rep["iterations"],
+                         "outer": rep["outer"], "relres": rep["relres"], "status": psfd.strerror(rep["status"])}
+            if name == "fixed_point":
+                row[name]["outer_steps_per_rhs"] = [int(np.sum(s.residual_history(i)["kind"] == 2))
+                                                    for i in range(prob.n_rhs)]
+            orders[name] = orders_all(s, prob.n_rhs)
+            s.close()
+        row["orders_rel_diff"] = orders_rel_err(orders["fixed_point"], orders["folded"])
+        out["stacks"].append(row)
+        print(json.dumps(row), flush=True)
     print(json.dumps(out), flush=True)
     return 0
 
@@ -711,6 +755,8 @@ def main(argv=None):
         return run_large(args)
     if args.crosscheck:
         return run_crosscheck(args)
+    if args.fixed_point:
+        return run_fixed_point(args)
     if args.serve_only:
         sizes = tuple(int(s) for s in args.serve_sizes.split(","))
         print(json.dumps({"mode": "serving", **run_serving(args.serve, sizes, args.tol, args.inner_tol)}), flush=True)

@@ -153,6 +153,27 @@ int psfd_set_illumination(psfd_ctx* ctx, int n_rhs, const double* theta_deg,
  * right-hand side missed the tolerance (the solution is still stored). */
 int psfd_solve(psfd_ctx* ctx, const psfd_solve_opts* opts, psfd_report* report);
 
+/* The paper's outer fixed-point iteration (Sec. 3, Eqs. (8)-(9)) in place of the folded
+ * operator: outer step k solves the free-space problem u_k - G*(V u_k) = b_k with
+ * b_k = E_inc + R[E_inc + E_mask^(k-1)], E_mask^(0) = 0, so R is rebuilt from the mask
+ * field of the previous step. Each step runs the same engine as psfd_solve (the same
+ * Krylov method, precision and opts) with R left out of the operator, warm-started from the
+ * previous step and solved to step_tol ||b_k|| (0 = tol / 10). Between steps the folded
+ * FP64 residual ||b - A u_k|| / ||b|| (b = E_inc + R[E_inc]) is formed: it is the change of
+ * the reflected field over the step plus the step's own residual, and an illumination stops
+ * once it is <= opts->tol; at the fixed point u solves A u = b, so solution, orders and
+ * residual mean what they mean after psfd_solve. max_steps <= 0 means 50. report->outer is
+ * the number of outer steps, report->iterations the Krylov iterations over all of them,
+ * report->relres the folded residual. The residual history records kind 2 = the folded
+ * residual after each outer step (kinds 0 and 1 refer to the step's own system).
+ * Memory: one more FP64 vector per illumination slot, allocated on the first call under
+ * the context's budget (PSFD_E_BUDGET / PSFD_E_NOMEM otherwise).
+ * Errors: PSFD_E_STATE before potential/illumination, PSFD_E_ARG (step_tol outside [0, 1)),
+ * PSFD_E_NOT_CONVERGED if an illumination is still above tol after max_steps (or one of its
+ * steps missed step_tol), PSFD_E_BREAKDOWN on a non-finite residual. */
+int psfd_solve_fixed_point(psfd_ctx* ctx, const psfd_solve_opts* opts, int max_steps, double step_tol,
+                           psfd_report* report);
+
 /* Number of propagating reflected orders (|q_mn| < k_bg) of illumination rhs. */
 int psfd_num_orders(psfd_ctx* ctx, int rhs, int* n_orders);
 
@@ -191,7 +212,8 @@ int psfd_set_initial_guess(psfd_ctx* ctx, int rhs, const double* x, int where);
  * the paper plots, Sec. 4): entry k is (iteration[k] Krylov iterations so far, kind[k],
  * relres[k]); kind 1 = the FP64 relative residual ||b - A x|| / ||b|| (the start of the solve
  * and the end of every sweep), kind 0 = the Krylov estimate after a batch of check_every
- * iterations (BiCGStab only: its recursive residual times the sweep's starting residual).
+ * iterations (BiCGStab only: its recursive residual times the sweep's starting residual),
+ * kind 2 = the folded FP64 residual after an outer step of psfd_solve_fixed_point.
  * Copies min(capacity, *n) entries; *n = the number recorded (at most 100000). */
 int psfd_residual_history(psfd_ctx* ctx, int rhs, int capacity, int* n, int* iteration, int* kind, double* relres);
 

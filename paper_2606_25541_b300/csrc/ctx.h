@@ -73,6 +73,9 @@ struct psfd_ctx {
   std::vector<std::vector<HistEntry>> hist;
   std::vector<double> sweep_rel;  // FP64 relative residual at the start of the current sweep
   int enq_hi = 0;  // slots covered by the work enqueued by engine_enqueue
+  // Outer fixed-point iteration of Eq. (8) (engine_fixed_point): while set, every operator
+  // application leaves R out, so the engine solves the free-space problem of one outer step.
+  int no_reflect = 0;
   std::vector<double> relres;
   int* h_act = nullptr;      // pinned
   int* h_act64 = nullptr;    // pinned
@@ -110,6 +113,7 @@ struct psfd_ctx {
   int* d_mask[4] = {nullptr, nullptr, nullptr, nullptr};  // per-phase selections
   int *d_nord = nullptr, *d_mn = nullptr;
   double* d_ordout = nullptr;
+  double2* fp_b0 = nullptr;  // [max_rhs][U]: b = E_inc + R[E_inc] during a fixed-point solve (lazy)
 
   int fail(int code, const std::string& what) {
     err = what;
@@ -188,6 +192,8 @@ int engine_tick(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active);
 // The two halves of a tick: enqueue the work (no host wait), then wait and transition.
 int engine_enqueue(psfd_ctx* ctx, const psfd_solve_opts& o, bool* pending);
 int engine_complete(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active);
+// The paper's outer fixed-point loop (Eqs. (8)-(9)) over rhs slots 0 .. n_rhs-1.
+int engine_fixed_point(psfd_ctx* ctx, const psfd_solve_opts& o, int max_steps, double step_tol);
 psfd_solve_opts solve_defaults(const psfd_solve_opts* opts);
 
 // Copy the orders of the finished slots to the host cache (once per batch of finishes).

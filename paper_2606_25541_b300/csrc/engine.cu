@@ -336,4 +336,145 @@ int engine_tick(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
   return engine_complete(ctx, o, n_active);
 }
 
+// ---------------------------------------------------------------------------------------
+// The paper's outer fixed-point iteration (Sec. 3, Eqs. (8)-(9)), as an alternative to the
+// folded operator. Outer step k solves the free-space problem
+//     u_k - G*(V u_k) = b_k,   b_k = E_inc + R[E_inc + E_mask^(k-1)],   E_mask^(0) = 0,
+// with the engine above (context flag no_reflect: K2 adds no reflection). With A the folded
+// operator and M = I - G*V the free-space one, R[E_mask^(k-1)] on the absorber planes is
+// (M - A) u_(k-1), so the next right-hand side is formed from two FP64 applications:
+//     r = b_1 - A u_k  (the folded residual),   b_(k+1) = M u_k + r.
+// r is also the stop test: b_1 - A u_k = (b_k - M u_k) + (R[E_mask^(k)] - R[E_mask^(k-1)]), the
+// step's own residual plus the change of the reflected field, and the loop ends for a slot
+// once ||r|| <= tol ||b_1||. Each step is solved to step_tol ||b_k|| from the previous
+// step's field (warm start), so that the change of the reflected field dominates r.
+// Slots run their outer steps together; a slot that has converged stops taking part.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+int run_engine(psfd_ctx* ctx, const psfd_solve_opts& o) {
+  for (;;) {
+    int active = 0;
+    RC(engine_tick(ctx, o, &active));
+    if (!active) return PSFD_OK;
+  }
+}
+
+}  // namespace
+
+int engine_fixed_point(psfd_ctx* ctx, const psfd_solve_opts& o, int max_steps, double step_tol) {
+  const int R = ctx->n_rhs;
+  const size_t U = ctx->plan.U;
+  cudaStream_t st = ctx->stream;
+  if (R <= 0) return PSFD_OK;
+  if (!ctx->fp_b0) RC(ctx->dalloc(&ctx->fp_b0, (size_t)ctx->max_rhs * U));
+  CK(cudaMemcpyAsync(ctx->fp_b0, ctx->b64, sizeof(double2) * U * R, cudaMemcpyDeviceToDevice, st));
+  psfd_solve_opts os = o;
+  os.tol = step_tol;
+  std::vector<int> open(R, 1), steps(R, 0), total_iters(R, 0), status(R, PSFD_OK);
+  std::vector<double> rel(R, 1.0);
+  std::vector<std::vector<psfd_ctx::HistEntry>> hist(R);
+  auto absorb_step = [&](int g) {  // bookkeeping after the engine solved one outer step
+    for (const auto& h : ctx->hist[g])
+      if (hist[g].size() < 100000) hist[g].push_back({total_iters[g] + h.iteration, h.kind, h.relres});
+    total_iters[g] += ctx->iters[g];
+    steps[g] += 1;
+    if (ctx->status[g] != PSFD_OK) {
+      status[g] = ctx->status[g];
+      open[g] = 0;
+    }
+  };
+  int rc = PSFD_OK;
+  ctx->no_reflect = 1;
+  // step 1: b_1 (from x = 0, or from the caller's initial guess)
+  for (int g = 0; g < R; ++g) ctx->phase[g] = PH_NEW;
+  rc = run_engine(ctx, os);
+  for (int g = 0; rc == PSFD_OK && g < R; ++g) absorb_step(g);
+  while (rc == PSFD_OK) {
+    // r = b_1 - A u_k on the open slots (side spectra for the orders come with it)
+    ctx->no_reflect = 0;
+    if ((rc = upload_mask(ctx, 1, open)) != PSFD_OK) break;
+    const int* mask = ctx->d_mask[1];
+    if ((rc = launch_norm((int)U, std::max(1, std::min(ctx->plan.maxblk, (int)((U + 8191) / 8192))), 0, R, mask,
+                          ctx->fp_b0, ctx->partials, ctx->plan.maxblk, 0, 0.0, ctx->sc64, ctx->act64, st)) != PSFD_OK)
+      break;
+    OpCall<double2> a = base_call64(ctx, 0, R);
+    a.active = mask;
+    a.u = ctx->x64;
+    a.out = ctx->r64;
+    a.b = ctx->fp_b0;
+    a.epi = EPI_RESID;
+    a.work = ctx->work64;
+    a.dot_mask = DOT_OUT_OUT;
+    a.side = ctx->side64;
+    const int nb = op_apply<double2>(a);
+    if (nb < 0) {
+      rc = nb;
+      break;
+    }
+    if ((rc = launch_norm((int)U, nb, 0, R, mask, nullptr, ctx->partials, ctx->plan.maxblk, 1, 0.0, ctx->sc64,
+                          ctx->act64, st)) != PSFD_OK)
+      break;
+    CK(cudaMemcpyAsync(ctx->h_sc64, ctx->sc64, sizeof(KScal) * R, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int n_open = 0;
+    for (int g = 0; g < R; ++g) {
+      if (!open[g]) continue;
+      const KScal& s = ctx->h_sc64[g];
+      rel[g] = std::sqrt(s.rnorm2 / s.bnorm2);
+      if (hist[g].size() < 100000) hist[g].push_back({total_iters[g], 2, rel[g]});
+      if (rel[g] <= o.tol) {
+        open[g] = 0;
+      } else if (!std::isfinite(rel[g])) {
+        status[g] = PSFD_E_BREAKDOWN;
+        open[g] = 0;
+      } else if (steps[g] >= max_steps) {
+        status[g] = PSFD_E_NOT_CONVERGED;
+        open[g] = 0;
+      }
+      n_open += open[g];
+    }
+    if (!n_open) break;
+    // b_(k+1) = M u_k + r for the slots that go on, then solve it from u_k
+    ctx->no_reflect = 1;
+    if ((rc = upload_mask(ctx, 1, open)) != PSFD_OK) break;
+    OpCall<double2> m = base_call64(ctx, 0, R);
+    m.active = ctx->d_mask[1];
+    m.u = ctx->x64;
+    m.out = ctx->b64;
+    m.epi = EPI_AU;
+    m.work = ctx->work64;
+    const int nbm = op_apply<double2>(m);
+    if (nbm < 0) {
+      rc = nbm;
+      break;
+    }
+    if ((rc = launch_vec_add((int)U, 0, R, ctx->d_mask[1], ctx->b64, ctx->r64, st)) != PSFD_OK) break;
+    for (int g = 0; g < R; ++g) {
+      if (!open[g]) continue;
+      ctx->guess[g] = 1;
+      ctx->phase[g] = PH_NEW;
+    }
+    if ((rc = run_engine(ctx, os)) != PSFD_OK) break;
+    for (int g = 0; g < R; ++g)
+      if (open[g]) absorb_step(g);
+  }
+  ctx->no_reflect = 0;
+  if (rc != PSFD_OK) return rc;
+  // the folded right-hand side back in place, and the orders of the last outer step
+  CK(cudaMemcpyAsync(ctx->b64, ctx->fp_b0, sizeof(double2) * U * R, cudaMemcpyDeviceToDevice, st));
+  std::vector<int> all(R, 1);
+  RC(upload_mask(ctx, 0, all));
+  RC(compute_orders(ctx, ctx->d_mask[0], R));
+  for (int g = 0; g < R; ++g) {
+    ctx->phase[g] = PH_DONE;
+    ctx->relres[g] = rel[g];
+    ctx->iters[g] = total_iters[g];
+    ctx->outer[g] = steps[g];
+    ctx->status[g] = status[g];
+    ctx->hist[g] = hist[g];
+  }
+  return PSFD_OK;
+}
+
 }  // namespace psfd

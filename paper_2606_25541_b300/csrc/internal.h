@@ -91,6 +91,7 @@ struct OpCall {
   const float* ktab32;     // [3][nf]: |kz_l| hi, |kz_l| lo, signed kz_l (FP32)
   const double* ktab64;    // [nf]: signed kz_l (FP64)
   const int* active;  // per global rhs, or null = all active
+  int no_reflect;     // 1: leave R out, i.e. the free-space operator u - G*(V u)
   // input stage: J = V * in, in = u | r + beta (u - omega v) | r - alpha v
   int in_mode;
   const C* u;

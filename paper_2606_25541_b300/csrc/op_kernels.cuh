@@ -812,7 +812,8 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
     ptab[i] = r;
   }
   __syncthreads();
-  for (int pl = p0; pl < ns; pl += pstep) {
+  const int pl_end = a.no_reflect ? 0 : ns;  // the free-space operator adds no reflection
+  for (int pl = p0; pl < pl_end; pl += pstep) {
     const C ph = cmul(ptab[t0 * PE + (pl & 7)], ptab[t0 * PE + 8 + (pl >> 3)]);  // exp(i beta pl dz)
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {

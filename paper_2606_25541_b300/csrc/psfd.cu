@@ -413,6 +413,7 @@ static OpCall<C> base_call(psfd_ctx* ctx, int rhs0, int nrhs, const C* V) {
   a.stream = ctx->stream;
   a.in_mode = IN_PLAIN;
   a.epi = EPI_AU;
+  a.no_reflect = ctx->no_reflect;
   return a;
 }
 template OpCall<float2> base_call<float2>(psfd_ctx*, int, int, const float2*);
@@ -573,19 +574,8 @@ int psfd_apply(psfd_ctx* ctx, int precision, int rhs0, int n_rhs, const void* u,
   return PSFD_OK;
 }
 
-int psfd_solve(psfd_ctx* ctx, const psfd_solve_opts* opts, psfd_report* report) {
-  if (!ctx) return PSFD_E_ARG;
-  if (!ctx->have_illum || !ctx->have_potential) return ctx->fail(PSFD_E_STATE, "solve before set_potential/illumination");
-  const auto t0 = std::chrono::steady_clock::now();
-  const psfd_solve_opts o = solve_defaults(opts);
-  RC(ensure_pool(ctx, o));
-  for (int i = 0; i < ctx->n_rhs; ++i)
-    if (ctx->phase[i] == PH_DONE) ctx->phase[i] = PH_NEW;  // re-solve from scratch
-  for (;;) {
-    int active = 0;
-    RC(engine_tick(ctx, o, &active));
-    if (!active) break;
-  }
+// Worst status, iteration count and residual over the single-clip slots, into report.
+static int report_slots(psfd_ctx* ctx, std::chrono::steady_clock::time_point t0, psfd_report* report) {
   int status = PSFD_OK, iters = 0, outer = 0;
   double relres = 0.0;
   for (int i = 0; i < ctx->n_rhs; ++i) {
@@ -603,6 +593,37 @@ int psfd_solve(psfd_ctx* ctx, const psfd_solve_opts* opts, psfd_report* report) 
   }
   if (status != PSFD_OK) ctx->err = psfd_strerror(status);
   return status;
+}
+
+int psfd_solve(psfd_ctx* ctx, const psfd_solve_opts* opts, psfd_report* report) {
+  if (!ctx) return PSFD_E_ARG;
+  if (!ctx->have_illum || !ctx->have_potential) return ctx->fail(PSFD_E_STATE, "solve before set_potential/illumination");
+  const auto t0 = std::chrono::steady_clock::now();
+  const psfd_solve_opts o = solve_defaults(opts);
+  RC(ensure_pool(ctx, o));
+  for (int i = 0; i < ctx->n_rhs; ++i)
+    if (ctx->phase[i] == PH_DONE) ctx->phase[i] = PH_NEW;  // re-solve from scratch
+  for (;;) {
+    int active = 0;
+    RC(engine_tick(ctx, o, &active));
+    if (!active) break;
+  }
+  return report_slots(ctx, t0, report);
+}
+
+int psfd_solve_fixed_point(psfd_ctx* ctx, const psfd_solve_opts* opts, int max_steps, double step_tol,
+                           psfd_report* report) {
+  if (!ctx) return PSFD_E_ARG;
+  if (!ctx->have_illum || !ctx->have_potential)
+    return ctx->fail(PSFD_E_STATE, "solve_fixed_point before set_potential/illumination");
+  if (!(step_tol >= 0.0) || step_tol >= 1.0) return ctx->fail(PSFD_E_ARG, "step_tol must lie in [0, 1)");
+  const auto t0 = std::chrono::steady_clock::now();
+  const psfd_solve_opts o = solve_defaults(opts);
+  if (max_steps <= 0) max_steps = 50;
+  if (step_tol == 0.0) step_tol = 0.1 * o.tol;
+  RC(ensure_pool(ctx, o));
+  RC(engine_fixed_point(ctx, o, max_steps, step_tol));
+  return report_slots(ctx, t0, report);
 }
 
 int psfd_num_orders(psfd_ctx* ctx, int rhs, int* n_orders) {

@@ -453,6 +453,20 @@ __global__ void k_ref_update(int n, int rhs0, const int* act, const KScal* sc, d
     x64[off + i] = cadd(x64[off + i], cscale(as_c64(xc[off + i]), s));
 }
 
+__global__ void k_vec_add(int n, int rhs0, const int* mask, double2* a, const double2* b) {
+  const int lr = blockIdx.y, g = rhs0 + lr;
+  if (mask && !mask[g]) return;
+  const size_t off = (size_t)lr * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    a[off + i] = cadd(a[off + i], b[off + i]);
+}
+
+int launch_vec_add(int n, int rhs0, int nrhs, const int* mask, double2* a, const double2* b, cudaStream_t st) {
+  const int bx = (n + 256 * 8 - 1) / (256 * 8);
+  k_vec_add<<<dim3(bx, nrhs), 256, 0, st>>>(n, rhs0, mask, a, b);
+  return launched();
+}
+
 template <typename C>
 int launch_ref_scale(int n, int rhs0, int nrhs, const int* act, const KScal* sc, const double2* r64, C* rs,
                      cudaStream_t st) {

@@ -72,6 +72,8 @@ int launch_ref_scale(int n, int rhs0, int nrhs, const int* act, const KScal* sc,
 template <typename C>
 int launch_ref_update(int n, int rhs0, int nrhs, const int* act, const KScal* sc, double2* x64, const C* xc,
                       cudaStream_t st);
+// a += b on the right-hand sides in mask (vectors [rhs][n], rhs0 the first one launched)
+int launch_vec_add(int n, int rhs0, int nrhs, const int* mask, double2* a, const double2* b, cudaStream_t st);
 int launch_test_fft(int n, int count, bool inv, bool fp64, void* data, const double2* tw);
 
 }  // namespace psfd

@@ -73,6 +73,7 @@ _SIGS = {
     "psfd_set_potential": (_I, [_P, _P, _I]),
     "psfd_set_illumination": (_I, [_P, _I, _D, _D, _IP]),
     "psfd_solve": (_I, [_P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Report)]),
+    "psfd_solve_fixed_point": (_I, [_P, ctypes.POINTER(SolveOpts), _I, ctypes.c_double, ctypes.POINTER(Report)]),
     "psfd_num_orders": (_I, [_P, _I, _IP]),
     "psfd_diffraction_orders": (_I, [_P, _I, _I, _IP, _IP, _D, _D, _D]),
     "psfd_apply": (_I, [_P, _I, _I, _I, _P, _P]),
@@ -282,6 +283,22 @@ class Solver:
             self._check(st)
         return rep
 
+    def solve_fixed_point(self, tol=1e-10, max_steps=50, step_tol=0.0, max_iter=500, max_outer=12, inner_tol=1e-4,
+                          check_every=4, raise_on_error=True, krylov=BICGSTAB, restart=0):
+        """The outer fixed-point iteration of Eq. (8): free-space solves with R rebuilt from the
+        previous step's mask field, until the folded residual is below tol. "outer" in the
+        report counts the outer steps, "iterations" the Krylov iterations over all of them."""
+        o = SolveOpts(float(tol), int(max_iter), int(max_outer), float(inner_tol), int(check_every), int(krylov),
+                      int(restart))
+        r = Report()
+        st = self.lib.psfd_solve_fixed_point(self.ctx, ctypes.byref(o), int(max_steps), float(step_tol),
+                                             ctypes.byref(r))
+        rep = {"iterations": r.iterations, "outer": r.outer, "relres": r.relres, "seconds": r.seconds,
+               "status": st}
+        if raise_on_error and st != OK:
+            self._check(st)
+        return rep
+
     def num_orders(self, rhs: int) -> int:
         n = ctypes.c_int(0)
         self._check(self.lib.psfd_num_orders(self.ctx, int(rhs), ctypes.byref(n)))
@@ -334,7 +351,8 @@ class Solver:
 
     def residual_history(self, rhs: int = 0):
         """Convergence curve of the latest solve: iteration, kind (1 = FP64 residual, 0 = Krylov
-        estimate) and relative residual per recorded point."""
+        estimate, 2 = folded residual after an outer fixed-point step) and relative residual per
+        recorded point."""
         n = ctypes.c_int(0)
         self._check(self.lib.psfd_residual_history(self.ctx, int(rhs), 0, ctypes.byref(n), None, None, None))
         cap = n.value

@@ -337,3 +337,64 @@ def test_residual_history_records_the_refined_solve(psfd, contact_hole_reference
     est = rel[kind == 0]
     assert len(est) >= 2 and est.min() <= 1e-4 * 1.01
     s.close()
+
+
+# ---------------------------------------------------------------------------
+# outer fixed-point iteration of Eq. (8) (psfd_solve_fixed_point)
+# ---------------------------------------------------------------------------
+def _fixed_point_clip():
+    return layouts.small_clip(nx=16, ny=16, nslab=6, dx=4.0, dz=2.0, seed=11, stack=layouts.ru_mosi_stack(40),
+                              theta=(6.0, 9.0), phi=(0.0, 30.0), pol=(0, 1))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fixed_point_steps_match_the_oracle_iterates(psfd, precision):
+    """Three outer steps, each solved tightly: the field after step 3 and the folded residual
+    after every step (the change of the reflected field) equal the oracle's paper-literal
+    loop, which builds R[E_mask] from plane 0, T_R and exp(i beta z) rather than from the
+    two operator applications the CUDA path uses."""
+    prob = _fixed_point_clip()
+    fp64 = precision == psfd.FP64
+    s = _solver(psfd, prob, precision)
+    rep = s.solve_fixed_point(tol=1e-14, max_steps=3, step_tol=1e-13 if fp64 else 1e-11, max_iter=400,
+                              max_outer=20, raise_on_error=False)
+    assert rep["status"] == psfd.E_NOT_CONVERGED and rep["outer"] == 3
+    for i in range(prob.n_rhs):
+        _, u_ref, info = oracle.solve_fixed_point(prob, i, rtol=0.0, max_outer=3, inner_rtol=1e-14)
+        assert _rel(s.get_solution(i), u_ref) < (1e-10 if fp64 else 1e-8), i
+        h = s.residual_history(i)
+        fold = h["relres"][h["kind"] == 2]
+        assert len(fold) == 3
+        assert np.all(np.abs(fold - np.array(info["changes"])) < 1e-9 * np.array(info["changes"])
+                      + (1e-11 if fp64 else 1e-9)), \
+            (fold, info["changes"])
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fixed_point_converges_to_the_folded_solution(psfd, precision):
+    """Run to a folded residual of 1e-8: the outer step count matches the oracle loop (same
+    stop rule) within one, and solution and orders are those of the folded solve. Afterwards
+    the context's operator has R in it again."""
+    prob = _fixed_point_clip()
+    s = _solver(psfd, prob, precision)
+    rep = s.solve_fixed_point(tol=1e-8, max_steps=80, max_iter=400, max_outer=20)
+    assert rep["relres"] <= 1e-8
+    for i in range(prob.n_rhs):
+        o_fp, _, info = oracle.solve_fixed_point(prob, i, rtol=1e-8, max_outer=80, inner_rtol=1e-11)
+        o_ref, x_ref, _ = oracle.solve(prob, i, rtol=1e-12)
+        h = s.residual_history(i)
+        steps = int(np.sum(h["kind"] == 2))
+        assert info["converged"] and abs(steps - info["outer"]) <= 1, (steps, info["outer"])
+        assert _rel(s.get_solution(i), x_ref) < 1e-6, i
+        assert _orders_err(s.diffraction_orders(i), o_ref) < 1e-6, i
+    assert rep["outer"] >= 10  # a slow contraction on this clip: many outer steps
+    u = layouts.random_field((prob.n_rhs, 3, prob.nslab, prob.ny, prob.nx), seed=4)
+    dt = torch.complex128 if precision == psfd.FP64 else torch.complex64
+    ud = torch.tensor(u, dtype=dt, device="cuda")
+    out = torch.empty_like(ud)
+    s.apply(ud, out)
+    u_used = u if precision == psfd.FP64 else u.astype(np.complex64).astype(np.complex128)
+    ref = oracle.apply_operator(oracle.setup_rhs(prob, 1), u_used[1])
+    assert _rel(out.cpu().numpy()[1], ref) < (1e-12 if precision == psfd.FP64 else 3e-5)
+    s.close()
