@@ -555,11 +555,12 @@ __device__ __forceinline__ void dyadic_apply(C* c0, C* c1, C* c2, typename RealO
 template <int NF> __host__ __device__ constexpr int phase_entries() { return 8 + (NF + 15) / 16; }
 
 // grid (nx / tx, ny, nrhs); dynamic shared memory: 3 tx (NF + 1) columns + tables.
-// FP32 columns of length 64, 128 and 256 use the register-resident transform (groups of
-// NF/16 lanes, one shared-memory exchange per transform, input read straight from HBM);
-// the CTA then has 24 groups: 8 x-modes x 3 components.
+// Columns of length 64, 128 and 256 use the register-resident transform in both precisions
+// (groups of NF/16 lanes, one shared-memory exchange per transform, input read straight
+// from HBM); the CTA then has 24 groups: 8 x-modes x 3 components. In FP64 the 16 x NF/16
+// factorisation also needs fewer FP64 operations than the shared-memory radix 8-8-2 plan.
 template <typename C, int NF> __host__ __device__ constexpr bool zcol_reg() {
-  return sizeof(C) == 8 && (NF == 64 || NF == 128 || NF == 256);
+  return NF == 64 || NF == 128 || NF == 256;
 }
 
 template <typename C, int NF, int NT>

@@ -22,6 +22,7 @@ template <> struct Tune<float2> {
   static constexpr int ZCOL_TILE = 8;             // x-modes per z-column CTA (4 warps: 7 CTAs per SM)
   static constexpr int ZCOL_NT = 128;
   static constexpr size_t ZCOL_SMEM = 80 * 1024;  // z-column tile bound
+  static constexpr size_t ZCOL_SMEM_REG = 80 * 1024;  // the same for the register z transform
 };
 template <> struct Tune<double2> {
   static constexpr int FUSED_MAX = 64;
@@ -32,6 +33,9 @@ template <> struct Tune<double2> {
   static constexpr int ZCOL_TILE = 8;
   static constexpr int ZCOL_NT = 256;
   static constexpr size_t ZCOL_SMEM = 80 * 1024;
+  // register z transform (lengths 64, 128, 256): eight x-modes per CTA even at length 256,
+  // one CTA per SM there (FP64-pipe bound, so twelve warps keep the pipe busy)
+  static constexpr size_t ZCOL_SMEM_REG = 120 * 1024;
 };
 
 template <typename C>
@@ -163,7 +167,9 @@ inline size_t zcol_smem_bytes(int nf, int tx) {
 template <typename C>
 inline int zcol_tile(int nx, int nf) {
   int tx = nx < Tune<C>::ZCOL_TILE ? nx : Tune<C>::ZCOL_TILE;
-  while (tx > 1 && zcol_smem_bytes<C>(nf, tx) > Tune<C>::ZCOL_SMEM) tx >>= 1;
+  const bool reg = nf == 64 || nf == 128 || nf == 256;  // zcol_reg
+  const size_t bound = reg ? Tune<C>::ZCOL_SMEM_REG : Tune<C>::ZCOL_SMEM;
+  while (tx > 1 && zcol_smem_bytes<C>(nf, tx) > bound) tx >>= 1;
   return tx;
 }
 
