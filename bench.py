@@ -67,6 +67,8 @@ def parse_args(argv=None):
     ap.add_argument("--bilayers", type=int, default=40, help="Mo/Si bilayers of the --crosscheck stack")
     ap.add_argument("--large", action="store_true",
                     help="1024 x 1024 x 60 curvilinear clip, 8 illuminations in memory-bounded batches")
+    ap.add_argument("--small", action="store_true",
+                    help="the 32 x 32 x 30 contact-hole clip (one illumination): ms per solve, CUDA graphs on/off")
     ap.add_argument("--fixed-point", action="store_true",
                     help="the outer fixed-point loop of Eq. (8) against the folded solve, per stack size")
     ap.add_argument("--fp-bilayers", type=str, default="0,10,40", help="Mo/Si bilayers for --fixed-point")
@@ -341,6 +343,41 @@ def run_crosscheck(args):
         idx = [key[(m, n)] for m, n in zip(a["m"], a["n"])]
         diffs.append(float(np.linalg.norm(a["eff"] - b["eff"][idx]) / np.linalg.norm(b["eff"])))
     out["efficiency_rel_diff"] = diffs
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_small(args):
+    """The contact-hole clip (32 x 32 x 30 at 2 nm, nf = 64, one s-polarised plane wave at 6 deg)
+    solved to relative residual 1e-10 in FP64 and in FP32 with FP64 refinement, with the
+    Krylov step replayed as a CUDA graph and with its kernels launched one by one. A clip this
+    small is L2-resident: launch overhead, not HBM, decides its speed. Wall time per solve
+    (set_illumination + solve, host synchronised), mean over --steps solves after --warmup."""
+    import torch
+    from paper_2606_25541_b300 import psfd
+    prob = layouts.contact_hole_clip()
+    out = {"mode": "small_clip", "workload": "contact_hole_32x32x30_nf64_1rhs", "tol": 1e-10}
+    steps = max(args.steps, 20)
+    for name, prec in (("fp64", psfd.FP64), ("fp32_refined", psfd.FP32_REFINED)):
+        for graphs in (True, False):
+            s = psfd.Solver.from_problem(prob, prec)
+            s.set_graphs(graphs)
+            kw = dict(tol=1e-10, inner_tol=1e-4, max_iter=400, max_outer=12)
+            for _ in range(max(args.warmup, 3)):
+                s.set_illumination(prob.theta_deg, prob.phi_deg, prob.pol)
+                s.solve(**kw)
+            torch.cuda.synchronize()
+            n0 = psfd.launch_count()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                s.set_illumination(prob.theta_deg, prob.phi_deg, prob.pol)
+                rep = s.solve(**kw)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / steps
+            out[f"{name}_{'graphs' if graphs else 'launches'}"] = {
+                "ms_per_solve": dt * 1e3, "solves_per_s": 1.0 / dt, "iterations": rep["iterations"],
+                "relres": rep["relres"], "kernels_per_solve": (psfd.launch_count() - n0) / steps}
+            s.close()
     print(json.dumps(out), flush=True)
     return 0
 
@@ -757,6 +794,8 @@ def main(argv=None):
         return run_crosscheck(args)
     if args.fixed_point:
         return run_fixed_point(args)
+    if args.small:
+        return run_small(args)
     if args.serve_only:
         sizes = tuple(int(s) for s in args.serve_sizes.split(","))
         print(json.dumps({"mode": "serving", **run_serving(args.serve, sizes, args.tol, args.inner_tol)}), flush=True)

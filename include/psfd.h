@@ -127,6 +127,15 @@ int psfd_destroy(psfd_ctx* ctx);
 /* Rebind the context to another stream. */
 int psfd_set_stream(psfd_ctx* ctx, void* stream);
 
+/* CUDA graphs for the Krylov loop (on by default; no counterpart in the paper, which states
+ * no execution model). Each engine tick runs check_every Krylov iterations of the active
+ * illuminations; that launch sequence depends only on the batch width, the method and the
+ * options, so it is captured once per configuration (on a private stream of the context)
+ * and replayed as one graph launch on the context's stream. Results are bitwise the same
+ * either way. enable = 0 waits for the context's stream and frees the captured graphs.
+ * Profiling (psfd_profile_enable) bypasses the graphs. */
+int psfd_set_graphs(psfd_ctx* ctx, int enable);
+
 /* Planar stack below z_top (Sec. 2, Fig. 1): n_layers layers listed top to bottom with
  * complex refractive index n_complex[2*j], n_complex[2*j+1] and thickness thickness_nm[j],
  * on a substrate of index n_sub[0] + i n_sub[1]. eps = n^2. n_layers may be 0. */

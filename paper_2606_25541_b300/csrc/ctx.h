@@ -115,6 +115,27 @@ struct psfd_ctx {
   double* d_ordout = nullptr;
   double2* fp_b0 = nullptr;  // [max_rhs][U]: b = E_inc + R[E_inc] during a fixed-point solve (lazy)
 
+  // CUDA graphs of the Krylov step (engine.cu): one per launch configuration, replayed on
+  // `stream`; captured on the private stream cap_stream.
+  struct GraphEntry {
+    long long key[8];
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    int kernels;                  // kernel launches the graph holds (launch accounting)
+    unsigned long long last_use;  // for evicting the least recently used entry
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;
+  bool use_graphs = true;
+  unsigned long long graph_clock = 0;
+  void drop_graphs() {
+    for (auto& e : graphs) {
+      cudaGraphExecDestroy(e.exec);
+      cudaGraphDestroy(e.graph);
+    }
+    graphs.clear();
+  }
+
   int fail(int code, const std::string& what) {
     err = what;
     return code;
@@ -149,6 +170,8 @@ struct psfd_ctx {
       }
   }
   ~psfd_ctx() {
+    drop_graphs();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto& q : allocs) cudaFree(q.first);
     for (void* q : {(void*)h_act, (void*)h_act64, (void*)h_sc, (void*)h_sc64, (void*)h_mask})
       if (q) cudaFreeHost(q);

@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <vector>
 
@@ -128,6 +129,72 @@ int krylov_finish(psfd_ctx* ctx, const psfd_solve_opts& o, int hi, const int* ma
   return PSFD_OK;
 }
 
+// check_every Krylov iterations of the slots whose device flag is up. The launch sequence
+// depends only on the configuration in the key below (the per-slot state -- scalars, flags,
+// vectors -- lives on the device), so it is captured once into a CUDA graph and replayed:
+// one launch per tick instead of about ten per iteration. Profiling runs bypass the graphs
+// (their events are recorded per launch). The capture happens on the context's private
+// stream in relaxed mode; nothing runs during it, and the first replay follows at once.
+int inner_step(psfd_ctx* ctx, const psfd_solve_opts& o, int hi, bool f32) {
+  auto direct = [&]() { return f32 ? krylov_iterate<float2>(ctx, o, hi) : krylov_iterate<double2>(ctx, o, hi); };
+  if (!ctx->use_graphs || prof_on()) return direct();
+  long long tol_bits;
+  const double tol = f32 ? o.inner_tol : 0.5 * o.tol;
+  std::memcpy(&tol_bits, &tol, sizeof(tol_bits));
+  const long long key[8] = {hi,
+                            (long long)f32,
+                            o.krylov,
+                            o.krylov == PSFD_BICGSTAB ? 0 : o.restart,
+                            o.check_every,
+                            ((long long)o.max_iter << 1) | ctx->no_reflect,
+                            tol_bits,
+                            (long long)(f32 ? (uintptr_t)ctx->pool32 : (uintptr_t)ctx->pool64)};
+  psfd_ctx::GraphEntry* hit = nullptr;
+  for (auto& e : ctx->graphs)
+    if (std::memcmp(e.key, key, sizeof(key)) == 0) hit = &e;
+  if (!hit) {
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    constexpr size_t kMaxGraphs = 32;
+    if (ctx->graphs.size() >= kMaxGraphs) {  // evict the least recently used
+      auto old = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                  [](const auto& a, const auto& b) { return a.last_use < b.last_use; });
+      cudaGraphExecDestroy(old->exec);
+      cudaGraphDestroy(old->graph);
+      ctx->graphs.erase(old);
+    }
+    psfd_ctx::GraphEntry e{};
+    std::memcpy(e.key, key, sizeof(key));
+    cudaStream_t user = ctx->stream;
+    const unsigned long long n0 = launch_total();
+    CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
+    ctx->stream = ctx->cap_stream;
+    const int rc = direct();
+    ctx->stream = user;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (rc != PSFD_OK || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      if (rc != PSFD_OK) return rc;
+      return ctx->cuda_fail(ce, "cudaStreamEndCapture");
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&e.exec, g, 0);
+    if (ie != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return ctx->cuda_fail(ie, "cudaGraphInstantiate");
+    }
+    e.graph = g;
+    e.kernels = (int)(launch_total() - n0);  // counted during the capture, run by the first replay
+    ctx->graphs.push_back(e);
+    hit = &ctx->graphs.back();
+  } else {
+    count_launch(hit->kernels);
+  }
+  hit->last_use = ++ctx->graph_clock;
+  CK(cudaGraphLaunch(hit->exec, ctx->stream));
+  return PSFD_OK;
+}
+
 // r64 = b - A x64 with the side spectra, then ||r64||^2 into sc64 / act64, for the slots in mask.
 int fp64_residual(psfd_ctx* ctx, const int* mask, double tol, int hi) {
   OpCall<double2> a = base_call64(ctx, 0, hi);
@@ -218,8 +285,7 @@ int engine_enqueue(psfd_ctx* ctx, const psfd_solve_opts& o, bool* pending) {
     *pending = true;
   }
   if (select(PH_INNER)) {
-    if (f32) RC(krylov_iterate<float2>(ctx, o, R));
-    else RC(krylov_iterate<double2>(ctx, o, R));
+    RC(inner_step(ctx, o, R, f32));
     *pending = true;
   }
   if (*pending) {  // read-back of the per-slot scalars, waited for in engine_complete

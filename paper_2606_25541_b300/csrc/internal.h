@@ -128,6 +128,7 @@ enum ProfClass {
   PK_FWD32 = 0, PK_Z32, PK_INV32, PK_FWD64, PK_Z64, PK_INV64, PK_VEC32, PK_VEC64, PK_SCALAR, PK_SETUP, PK_N
 };
 void count_launch(int n = 1);
+unsigned long long launch_total();  // kernels launched by the library so far
 bool prof_on();
 // Opens a profiled launch of class cls on stream st; returns a device counter that the
 // launch's CTAs increment when they do work (null when profiling is off).

@@ -55,6 +55,7 @@ cudaEvent_t take_event() {
 }  // namespace
 
 void count_launch(int n) { g_launches += (unsigned long long)n; }
+unsigned long long launch_total() { return g_launches.load(); }
 bool prof_on() { return g_prof; }
 unsigned* prof_begin(int cls, cudaStream_t st) {
   if (!g_prof || !g_counters || g_next_counter >= kMaxCounters) return nullptr;
@@ -441,6 +442,7 @@ int ensure_pool(psfd_ctx* ctx, const psfd_solve_opts& o) {
   const int need = pool_need(o);
   if (need <= ctx->pool_vecs) return PSFD_OK;
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return ctx->cuda_fail(cudaGetLastError(), "pool resize");
+  ctx->drop_graphs();  // they hold the old pool's addresses
   const size_t n = (size_t)ctx->max_rhs * ctx->plan.U * need;
   if (ctx->precision == PSFD_FP64) {
     ctx->dfree(ctx->pool64);
@@ -505,6 +507,16 @@ int psfd_destroy(psfd_ctx* ctx) {
 int psfd_set_stream(psfd_ctx* ctx, void* stream) {
   if (!ctx) return PSFD_E_ARG;
   ctx->stream = (cudaStream_t)stream;
+  return PSFD_OK;
+}
+
+int psfd_set_graphs(psfd_ctx* ctx, int enable) {
+  if (!ctx) return PSFD_E_ARG;
+  if (!enable) {
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return ctx->cuda_fail(cudaGetLastError(), "set_graphs");
+    ctx->drop_graphs();
+  }
+  ctx->use_graphs = enable != 0;
   return PSFD_OK;
 }
 

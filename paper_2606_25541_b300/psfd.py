@@ -72,6 +72,7 @@ _SIGS = {
     "psfd_set_stack": (_I, [_P, _I, _D, _D, _D]),
     "psfd_set_potential": (_I, [_P, _P, _I]),
     "psfd_set_illumination": (_I, [_P, _I, _D, _D, _IP]),
+    "psfd_set_graphs": (_I, [_P, _I]),
     "psfd_solve": (_I, [_P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Report)]),
     "psfd_solve_fixed_point": (_I, [_P, ctypes.POINTER(SolveOpts), _I, ctypes.c_double, ctypes.POINTER(Report)]),
     "psfd_num_orders": (_I, [_P, _I, _IP]),
@@ -262,6 +263,10 @@ class Solver:
             e = _c128(eps)
             self._keep_eps = e
             self._check(self.lib.psfd_set_potential(self.ctx, e.ctypes.data_as(ctypes.c_void_p), HOST))
+
+    def set_graphs(self, enable: bool):
+        """Replay the Krylov step as a CUDA graph (default) or launch its kernels one by one."""
+        self._check(self.lib.psfd_set_graphs(self.ctx, int(bool(enable))))
 
     def set_illumination(self, theta_deg, phi_deg, pol):
         th = np.ascontiguousarray(theta_deg, dtype=np.float64).reshape(-1)
