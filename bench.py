@@ -40,6 +40,12 @@ METRIC = "solves/s at 1e-6 order error, FP32+refine vs FP64; p50/p99 latency; HB
 UNIT = "solves/s"
 WORKLOAD = "line_space_128x128x60_nf128_18rhs"
 FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 vector rate, nominal
+# The headline metric is quoted at 1e-6 order error. Solving to an FP64 relative residual of
+# 3e-7, with FP32 sweeps asked for 2e-7, keeps the largest per-illumination order error against
+# a tight (1e-11) FP64 solve near 3e-7 on the line/space batch, a factor ~3 inside the target;
+# every run measures and reports that error. The other modes default to 1e-8 / 1e-4.
+HEADLINE_TOL, HEADLINE_INNER_TOL = 3e-7, 2e-7
+DEFAULT_TOL, DEFAULT_INNER_TOL = 1e-8, 1e-4
 
 
 def parse_args(argv=None):
@@ -48,8 +54,10 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--tol", type=float, default=None,
+                    help="FP64 relative residual target (default 3e-7 for the headline, serving and reference "
+                         "arms; 1e-8 for the other modes)")
+    ap.add_argument("--inner-tol", type=float, default=None, help="FP32 sweep tolerance (default 2e-7 / 1e-4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--profile-only", action="store_true", help="one profiled step, for ncu launch lists")
@@ -551,7 +559,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     prob = layouts.line_space_clip(seed=2)
-    rtol = args.tol * 10.0
+    rtol = args.tol
     for w in range(args.warmup):
         oracle_solve_seconds(prob, w % prob.n_rhs, rtol)
     times = [oracle_solve_seconds(prob, (args.warmup + k) % prob.n_rhs, rtol) for k in range(args.steps)]
@@ -617,6 +625,16 @@ def run_ours(args):
     for _ in range(args.warmup):
         rep = step(solver)
     torch.cuda.synchronize()
+
+    # reference orders for the order error the metric is quoted at: FP64 solve to 1e-11 (untimed)
+    sref = psfd.Solver.from_problem(prob, psfd.FP64, stream=stream)
+    sref.solve(tol=1e-11, max_iter=800)
+    orders_ref = orders_all(sref, n_rhs)
+    sref.close()
+
+    def order_error(orders):
+        return {"normwise": orders_rel_err(orders, orders_ref),
+                "max_per_illumination": max(orders_rel_err([a], [b]) for a, b in zip(orders, orders_ref))}
 
     # ---- timed region: device-resident inputs ----
     clocks = ClockSampler(torch.cuda.current_device())
@@ -687,10 +705,32 @@ def run_ours(args):
         torch.cuda.synchronize()
         t64 = reduce_max(e0.elapsed_time(e1), world, dev)
         orders64 = orders_all(s64, n_rhs)
-        fp64 = {"value": n_rhs * world / (t64 * 1e-3), "unit": UNIT, "ms_per_step": t64,
+        fp64 = {"value": n_rhs * world / (t64 * 1e-3), "unit": UNIT, "ms_per_step": t64, "tol": args.tol,
                 "iterations": rep64["iterations"], "relres": rep64["relres"],
+                "order_error_vs_fp64_1e-11": order_error(orders64),
                 "order_rel_err_fp32_refined_vs_fp64": orders_rel_err(orders32, orders64)}
         s64.close()
+
+    # ---- the same FP32 + refinement step solved 30x tighter (FP64 residual 1e-8) ----
+    tight_kw = dict(solve_kw, tol=DEFAULT_TOL, inner_tol=DEFAULT_INNER_TOL)
+
+    def step_tight(s):
+        s.set_potential(eps_dev)
+        s.set_illumination(th, ph, po)
+        return s.solve(**tight_kw)
+
+    step_tight(solver)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        rep_t = step_tight(solver)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_tight = reduce_max(e0.elapsed_time(e1), world, dev)
+    tight = {"value": n_rhs * args.steps * world / (t_tight * 1e-3), "unit": UNIT, "tol": DEFAULT_TOL,
+             "inner_tol": DEFAULT_INNER_TOL, "iterations": rep_t["iterations"], "outer": rep_t["outer"],
+             "relres": rep_t["relres"], "order_error_vs_fp64_1e-11": order_error(orders_all(solver, n_rhs))}
 
     serving = None
     if args.serve > 0 and world == 1:
@@ -699,7 +739,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(prob, rtol=args.tol * 10.0)
+        cpu = cpu_baseline(prob, rtol=args.tol)
 
     if rank != 0:
         return 0
@@ -738,6 +778,7 @@ def run_ours(args):
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "what": "per-step (18-illumination batch) device time"},
         "iterations": reps[-1]["iterations"], "outer": reps[-1]["outer"], "relres": reps[-1]["relres"],
+        "order_error_vs_fp64_1e-11": order_error(orders32),
         "roofline": roofline, "kernels": kernels,
         "cpu_baseline": cpu,
         "e2e": {"value": n_rhs * args.steps * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -745,6 +786,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "fp64_plain": fp64,
+        "fp32_refined_at_tol_1e-8": tight,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)
@@ -782,6 +824,11 @@ def solver_bytes(prob) -> float:
 
 def main(argv=None):
     args = parse_args(argv)
+    headline = not (args.apply or args.sweep or args.large or args.crosscheck or args.fixed_point or args.small)
+    if args.tol is None:
+        args.tol = HEADLINE_TOL if headline else DEFAULT_TOL
+    if args.inner_tol is None:
+        args.inner_tol = HEADLINE_INNER_TOL if headline else DEFAULT_INNER_TOL
     if args.impl == "reference":
         return run_reference(args)
     if args.apply:

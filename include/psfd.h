@@ -72,7 +72,10 @@ typedef struct {
   double tol;       /* target relative residual ||b - A x|| / ||b|| in FP64 [1e-10] */
   int max_iter;     /* Krylov iteration cap per solve or per refinement sweep [500] */
   int max_outer;    /* refinement sweep cap for PSFD_FP32_REFINED [12] */
-  double inner_tol; /* relative tolerance of each FP32 inner solve [1e-4] */
+  double inner_tol; /* tightest relative tolerance of an FP32 inner solve [1e-4]: a sweep
+                       starting from FP64 residual rho (relative) is solved to
+                       min(1/2, max(inner_tol, tol / (4 rho))), i.e. only as far as the
+                       target still needs */
   int check_every;  /* iterations between host reads of the device convergence flags [4] */
   int krylov;       /* PSFD_BICGSTAB [default] or PSFD_GMRES */
   int restart;      /* GMRES basis size per sweep [PSFD_KRYLOV_MAX] (<= PSFD_KRYLOV_MAX) */

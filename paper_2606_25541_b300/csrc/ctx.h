@@ -110,6 +110,8 @@ struct psfd_ctx {
   double2* partials = nullptr;
   psfd::KScal *sc = nullptr, *sc64 = nullptr;
   int *act = nullptr, *act64 = nullptr;
+  double* d_tol = nullptr;  // [max_rhs]: relative tolerance of each slot's current sweep
+  std::vector<double> h_tol;
   int* d_mask[4] = {nullptr, nullptr, nullptr, nullptr};  // per-phase selections
   int *d_nord = nullptr, *d_mn = nullptr;
   double* d_ordout = nullptr;

@@ -45,6 +45,8 @@ psfd_solve_opts solve_defaults(const psfd_solve_opts* opts) {
 
 namespace {
 
+constexpr double kSweepSafety = 0.25;
+
 int upload_mask(psfd_ctx* ctx, int which, const std::vector<int>& sel) {
   // pageable source: the copy is staged before the call returns, so `sel` may be reused
   CK(cudaMemcpyAsync(ctx->d_mask[which], sel.data(), sizeof(int) * sel.size(), cudaMemcpyHostToDevice, ctx->stream));
@@ -83,6 +85,7 @@ KrylovCall<C> krylov_common(psfd_ctx* ctx, const psfd_solve_opts& o, OpCall<C> o
   k.act = ctx->act;
   k.h_act = ctx->h_act;
   k.tol = tol;
+  k.tol_slot = ctx->precision == PSFD_FP32_REFINED ? ctx->d_tol : nullptr;
   k.max_iter = o.max_iter;
   k.check_every = o.check_every;
   return k;
@@ -373,6 +376,18 @@ int engine_complete(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
         if (to_update[g]) ctx->phase[g] = PH_RESID;
     }
     if (any_start) {
+      if (f32) {
+        // A sweep only has to take the FP64 residual from sweep_rel down to tol: its
+        // tolerance is tol / sweep_rel with a safety factor, but never tighter than
+        // inner_tol (what an FP32 solve reliably reaches) nor looser than one half.
+        ctx->h_tol.resize(R);
+        for (int g = 0; g < R; ++g) {
+          if (!to_start[g]) continue;
+          const double want = kSweepSafety * o.tol / std::max(ctx->sweep_rel[g], 1e-300);
+          ctx->h_tol[g] = std::min(0.5, std::max(o.inner_tol, want));
+        }
+        CK(cudaMemcpyAsync(ctx->d_tol, ctx->h_tol.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+      }
       RC(upload_mask(ctx, 3, to_start));
       if (f32) RC(krylov_start<float2>(ctx, o, R, ctx->d_mask[3]));
       else RC(krylov_start<double2>(ctx, o, R, ctx->d_mask[3]));

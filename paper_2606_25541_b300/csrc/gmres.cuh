@@ -41,8 +41,8 @@ __global__ void __launch_bounds__(VEC_NT) k_gm_norm(int n, int nblk, const int* 
 
 // beta = ||b||: a new cycle (j = 0, g = beta e_1) for the rhs in mask.
 static __global__ void __launch_bounds__(VEC_NT) k_gm_begin(int nblk, const int* mask, const double2* gpart,
-                                                             int gblk, int m, double tol, GmState* st, KScal* sc,
-                                                             int* act) {
+                                                             int gblk, int m, double tol, const double* tol_slot,
+                                                             GmState* st, KScal* sc, int* act) {
   __shared__ double2 sh[33];
   const int g = blockIdx.x;
   if (mask && !mask[g]) return;
@@ -54,7 +54,7 @@ static __global__ void __launch_bounds__(VEC_NT) k_gm_begin(int nblk, const int*
     S.m = m;
     S.status = PSFD_OK;
     S.beta = beta;
-    S.tol = tol;
+    S.tol = tol_slot ? tol_slot[g] : tol;
     S.inv_h = beta > 0.0 ? 1.0 / beta : 0.0;
     S.resid = 1.0;
     for (int i = 0; i <= KMAX; ++i) S.g[i] = make_double2(0.0, 0.0);
@@ -230,7 +230,7 @@ int gmres_start_impl(const KrylovCall<C>& k, const int* mask) {
   const int R = k.op.nrhs;  // rhs 0 .. R-1 (the engine always starts at 0)
   k_gm_norm<C><<<dim3(k.gblk, R), VEC_NT, 0, st>>>(k.n, k.gblk, mask, k.b, k.gpart, k.gblk);
   PSFD_CHECK_LAUNCH();
-  k_gm_begin<<<R, VEC_NT, 0, st>>>(k.gblk, mask, k.gpart, k.gblk, k.m, k.tol, k.gm, k.sc, k.act);
+  k_gm_begin<<<R, VEC_NT, 0, st>>>(k.gblk, mask, k.gpart, k.gblk, k.m, k.tol, k.tol_slot, k.gm, k.sc, k.act);
   PSFD_CHECK_LAUNCH();
   const int bx = (k.n + 256 * 8 - 1) / (256 * 8);
   k_gm_scale<C><<<dim3(bx, R), 256, 0, st>>>(k.n, mask, k.act, k.gm, k.b, k.basis, k.bstride, k.z);

@@ -47,6 +47,7 @@ struct KScal {
   double bnorm2;  // ||b||^2 of the system being solved
   double rnorm2;  // ||r||^2 of the recursively updated residual
   double scale;   // defect-correction scale ||r64|| of this sweep
+  double tol2;    // stop when rnorm2 <= tol2 bnorm2 (set when the solve starts)
   int iters;
   int active;  // 1 while iterating
   int status;  // PSFD_OK / PSFD_E_BREAKDOWN / PSFD_E_NOT_CONVERGED
@@ -154,6 +155,7 @@ struct KrylovCall {
   const int* act_in;   // initial activity (device) or null
   int* h_act;          // pinned host mirror of act (>= rhs0 + nrhs entries)
   double tol;
+  const double* tol_slot;  // per global rhs tolerance of this solve (device), or null = tol
   int max_iter;
   int check_every;
   // GMRES: basis vector i of global rhs g at basis + i * bstride + g * n; z = newest basis

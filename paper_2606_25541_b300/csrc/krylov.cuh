@@ -135,7 +135,8 @@ __device__ __forceinline__ const double2* slot_ptr(const double2* partials, int 
 // ||b||^2 -> scalars and activity (b != 0) for the right-hand sides in mask (null = all);
 // the others keep their state.
 static __global__ void __launch_bounds__(VEC_NT) k_scal_init(int rhs0, int nblk, const double2* partials, int maxblk,
-                                                       const int* mask, KScal* sc, int* act) {
+                                                       const int* mask, double tol, const double* tol_slot,
+                                                       KScal* sc, int* act) {
   __shared__ double2 sh[33];
   const int g = rhs0 + blockIdx.x;
   if (mask && !mask[g]) return;
@@ -149,6 +150,8 @@ static __global__ void __launch_bounds__(VEC_NT) k_scal_init(int rhs0, int nblk,
     s.omega = make_double2(1.0, 0.0);
     s.beta = make_double2(0.0, 0.0);
     s.scale = sc[g].scale;
+    const double t = tol_slot ? tol_slot[g] : tol;
+    s.tol2 = t * t;
     s.iters = 0;
     s.status = PSFD_OK;
     s.active = bb.x > 0.0;
@@ -195,7 +198,7 @@ static __global__ void __launch_bounds__(VEC_NT) k_scal_omega(int rhs0, int nblk
 
 // rho_new = <r0, r>, convergence test on ||r||, beta = (rho_new / rho)(alpha / omega).
 static __global__ void __launch_bounds__(VEC_NT) k_scal_rho(int rhs0, int nblk, const double2* partials, int maxblk,
-                                                      double tol2, int max_iter, KScal* sc, int* act) {
+                                                      int max_iter, KScal* sc, int* act) {
   __shared__ double2 sh[33];
   const int g = rhs0 + blockIdx.x;
   if (!act[g]) return;
@@ -208,7 +211,7 @@ static __global__ void __launch_bounds__(VEC_NT) k_scal_rho(int rhs0, int nblk, 
     if (!isfinite(rr.x)) {
       s.status = PSFD_E_BREAKDOWN;
       s.active = 0;
-    } else if (rr.x <= tol2 * s.bnorm2) {
+    } else if (rr.x <= s.tol2 * s.bnorm2) {
       s.active = 0;
     } else if (s.iters >= max_iter) {
       s.status = PSFD_E_NOT_CONVERGED;

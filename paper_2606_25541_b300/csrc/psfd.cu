@@ -100,7 +100,7 @@ Plan make_plan(const psfd_grid& g, int precision, int max_rhs, int max_clips) {
   b += R * p.U * kvec * (2 + kPoolBicg);                     // rs, xc, BiCGStab pool
   b += R * NDOT * (size_t)p.maxblk * 16;                     // partial sums
   b += R * (sizeof(GmState) + (size_t)(KMAX + 1) * p.maxblk * 16);  // GMRES state and partials
-  b += R * (2 * sizeof(KScal) + 6 * sizeof(int));            // scalars, flags, masks
+  b += R * (2 * sizeof(KScal) + 6 * sizeof(int) + sizeof(double));  // scalars, flags, masks, sweep tolerances
   b += R * (size_t)p.max_orders * (2 * sizeof(int) + 12 * sizeof(double)) + R * sizeof(int);
   p.bytes = b;
   return p;
@@ -196,6 +196,7 @@ int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs
   A(&ctx->sc64, R);
   A(&ctx->act, R);
   A(&ctx->act64, R);
+  A(&ctx->d_tol, R);
   for (int i = 0; i < 4; ++i) A(&ctx->d_mask[i], R);
   A(&ctx->d_nord, R);
   A(&ctx->d_mn, R * (size_t)P.max_orders * 2);

@@ -28,7 +28,8 @@ int bicg_start_impl(const KrylovCall<C>& k, const int* mask) {
   k_bicg_init<C><<<dim3(nblk, base.nrhs), VEC_NT, 0, st>>>(k.n, nblk, base.rhs0, mask, k.b, k.x, k.r, k.r0, k.p,
                                                             k.v, base.partials, base.maxblk);
   PSFD_CHECK_LAUNCH();
-  k_scal_init<<<base.nrhs, VEC_NT, 0, st>>>(base.rhs0, nblk, base.partials, base.maxblk, mask, k.sc, k.act);
+  k_scal_init<<<base.nrhs, VEC_NT, 0, st>>>(base.rhs0, nblk, base.partials, base.maxblk, mask, k.tol, k.tol_slot,
+                                            k.sc, k.act);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
@@ -64,7 +65,6 @@ int bicg_iterate_impl(const KrylovCall<C>& k, int iters) {
   ts.out = k.t;
   ts.dot_mask = DOT_OUT_U | DOT_OUT_OUT;
 
-  const double tol2 = k.tol * k.tol;
   for (int it = 0; it < iters; ++it) {
     int nb = op_apply_impl<C>(pv);
     if (nb < 0) return nb;
@@ -82,7 +82,7 @@ int bicg_iterate_impl(const KrylovCall<C>& k, int iters) {
     // reads x, p, s, t, r0; writes x, r (and p when the update went to pn)
     const double nvec = pv.ustore == k.p ? 7.0 : 8.0;
     prof_end(vcls, st, nvec * nrhs * (double)k.n * sizeof(C), 24.0 * nrhs * (double)k.n, (double)nblk * nrhs);
-    k_scal_rho<<<nrhs, VEC_NT, 0, st>>>(rhs0, nblk, base.partials, base.maxblk, tol2, k.max_iter, k.sc, k.act);
+    k_scal_rho<<<nrhs, VEC_NT, 0, st>>>(rhs0, nblk, base.partials, base.maxblk, k.max_iter, k.sc, k.act);
     PSFD_CHECK_LAUNCH();
   }
   return PSFD_OK;
