@@ -553,6 +553,21 @@ __device__ __forceinline__ void dyadic_apply(C* c0, C* c1, C* c2, typename RealO
 // steps) and 8 j' for j' < NF/16 (coarse steps); the phase of plane pl is the
 // product of entries pl % 8 and 8 + pl / 8 (pl < nslab <= nf/2 - 1).
 template <int NF> __host__ __device__ constexpr int phase_entries() { return 8 + (NF + 15) / 16; }
+// Row pitch of the phase table: odd, so that the columns of a CTA read their rows from
+// different banks.
+template <int NF> __host__ __device__ constexpr int phase_pitch() { return phase_entries<NF>() | 1; }
+
+// Column pitch of K2's shared tile (in elements). Odd in general, so that the columns of a
+// CTA are read at a common z from different banks. For the FP32 register transform with
+// groups of n2 = nf/16 < 16 lanes it is n2 modulo 16 instead: 16/n2 groups share a 16-lane
+// memory phase there, and offsets of n2 elements between their columns keep the exchange
+// stores and the contiguous loads and stores of the transforms free of bank conflicts.
+__host__ __device__ constexpr int zcol_pitch(int nf, bool f32reg) {
+  return (f32reg && nf / 16 < 16) ? fft_phys(nf) + ((nf / 16 - fft_phys(nf) % 16) % 16 + 16) % 16
+                                  : (fft_phys(nf) | 1);
+}
+static_assert(zcol_pitch(128, true) == 152 && zcol_pitch(64, true) == 84 && zcol_pitch(256, true) == 289,
+              "register-transform pitches");
 
 // grid (nx / tx, ny, nrhs); dynamic shared memory: 3 tx (NF + 1) columns + tables.
 // Columns of length 64, 128 and 256 use the register-resident transform in both precisions
@@ -567,7 +582,9 @@ template <typename C, int NF, int NT>
 __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
   using R = typename RealOf<C>::T;
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int P = fft_phys(NF) | 1;  // column pitch; element z of a column at fpad(z)
+  constexpr bool F32 = sizeof(C) == sizeof(float2);
+  constexpr bool REG = zcol_reg<C, NF>();
+  constexpr int P = zcol_pitch(NF, F32 && REG);  // column pitch; element z of a column at fpad(z)
   C* col = reinterpret_cast<C*>(smem);
   C* tw = col + 3 * tx * P;
   R* kh = reinterpret_cast<R*>(tw + NF);
@@ -580,14 +597,13 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
   C* ce8 = ce1 + tx;                          // exp(i beta 8 dz)
   C* R0 = ce8 + tx;                           // 3 tx: T_R E(plane 0)
   C* ptab = R0 + 3 * tx;                      // tx phase_entries<NF>(): exp(i beta dz j)
-  R* cqx = reinterpret_cast<R*>(ptab + tx * phase_entries<NF>());
+  R* cqx = reinterpret_cast<R*>(ptab + tx * phase_pitch<NF>());
   R* cqy = cqx + tx;
 
   const int x0 = blockIdx.x * tx, y = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
   const int nx = a.nx, ny = a.ny, ns = a.nslab;
-  constexpr bool F32 = sizeof(C) == sizeof(float2);
   const int slot = a.rhsp[g].slot;
   const size_t mbase = ((size_t)slot * ny + y) * nx + x0;
 
@@ -633,7 +649,6 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
   const int t0 = threadIdx.x % tx, p0 = threadIdx.x / tx, pstep = NT / tx;
   const size_t pstride = (size_t)ny * nx;
   C* gcol = a.work + (size_t)lr * 3 * ns * pstride + (size_t)y * nx + x0 + t0;
-  constexpr bool REG = zcol_reg<C, NF>();
   constexpr int N2 = NF / 16, R1 = N2 > 0 ? 16 / N2 : 1;
   constexpr int EP = 16 * (N2 + 1) <= P ? N2 + 1 : N2;  // exchange row pitch
   const int rf = threadIdx.x / (N2 > 0 ? N2 : 1), rj = threadIdx.x % (N2 > 0 ? N2 : 1);
@@ -799,7 +814,7 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
   }
   // phase table: powers of exp(i beta dz) (fine, j < 8) and of exp(i beta 8 dz) (coarse),
   // both evaluated in FP64; every entry by binary powering in its own thread
-  constexpr int PE = phase_entries<NF>();
+  constexpr int PE = phase_entries<NF>(), PP = phase_pitch<NF>();
   for (int i = threadIdx.x; i < tx * PE; i += NT) {
     const int t = i / PE, j = i % PE;
     C w = j < 8 ? ce1[t] : ce8[t];
@@ -810,12 +825,12 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
       e >>= 1;
       if (e) w = cmul(w, w);
     }
-    ptab[i] = r;
+    ptab[t * PP + j] = r;
   }
   __syncthreads();
   const int pl_end = a.no_reflect ? 0 : ns;  // the free-space operator adds no reflection
   for (int pl = p0; pl < pl_end; pl += pstep) {
-    const C ph = cmul(ptab[t0 * PE + (pl & 7)], ptab[t0 * PE + 8 + (pl >> 3)]);  // exp(i beta pl dz)
+    const C ph = cmul(ptab[t0 * PP + (pl & 7)], ptab[t0 * PP + 8 + (pl >> 3)]);  // exp(i beta pl dz)
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
       C* e = col + (cc * tx + t0) * P + fpad(pl + 1);

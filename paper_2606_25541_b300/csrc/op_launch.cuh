@@ -160,8 +160,9 @@ inline int cols_tile(int nx, int ny) {
 template <typename C>
 inline size_t zcol_smem_bytes(int nf, int tx) {
   using R = typename RealOf<C>::T;
-  const int pe = 8 + (nf + 15) / 16;  // phase_entries
-  return (size_t)(3 * tx * (fft_phys(nf) | 1) + nf) * sizeof(C) + 3 * (size_t)nf * sizeof(R) +
+  const int pe = (8 + (nf + 15) / 16) | 1;  // phase_pitch
+  const bool f32reg = sizeof(C) == sizeof(float2) && (nf == 64 || nf == 128 || nf == 256);  // zcol_reg
+  return (size_t)(3 * tx * zcol_pitch(nf, f32reg) + nf) * sizeof(C) + 3 * (size_t)nf * sizeof(R) +
          (size_t)(8 + pe) * tx * sizeof(C) + 2 * (size_t)tx * sizeof(R) + 16;
 }
 template <typename C>
@@ -188,7 +189,7 @@ int launch_cols(const OpCall<C>& a) {
 template <typename C, int NF>
 int launch_zcol(const OpCall<C>& a) {
   constexpr int NT = zcol_reg<C, NF>() ? 24 * (NF / 16) : Tune<C>::ZCOL_NT;
-  static_assert(8 + (NF + 15) / 16 == phase_entries<NF>(), "phase table size");
+  static_assert(((8 + (NF + 15) / 16) | 1) == phase_pitch<NF>(), "phase table size");
   const int tx = zcol_tile<C>(a.nx, NF);
   const size_t smem = zcol_smem_bytes<C>(NF, tx);
   auto k = k_zcol<C, NF, NT>;
