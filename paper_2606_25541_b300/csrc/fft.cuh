@@ -294,7 +294,8 @@ __device__ __forceinline__ void reg_fft_step1(C (&v)[16], int j, const C* tw) {
 }
 
 // step 2: rows k1 of the exchange (written as ex[k1 * EP + j] by step 1's lanes) to outputs:
-// out[r][k2] = X[(j R1 + r) + 16 k2], R1 = 16 / N2.
+// out[r][k2] = X[(j + N2 r) + 16 k2] (lane j takes rows j, j + N2, ...: at a common r the
+// lanes of a group read rows EP apart, which spreads them over the banks).
 template <typename C, int N, bool INV, int EP>
 __device__ __forceinline__ void reg_fft_step2(const C* ex, int j, C (&out)[16]) {
   constexpr int N2 = reg_fft_n2<N>(), R1 = 16 / N2;
@@ -302,7 +303,7 @@ __device__ __forceinline__ void reg_fft_step2(const C* ex, int j, C (&out)[16]) 
   for (int r = 0; r < R1; ++r) {
     C row[N2];
 #pragma unroll
-    for (int i = 0; i < N2; ++i) row[i] = ex[(j * R1 + r) * EP + i];
+    for (int i = 0; i < N2; ++i) row[i] = ex[(j + N2 * r) * EP + i];
     Dft<C, N2, INV>::run(row);
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) out[r * N2 + k2] = row[k2];

@@ -680,7 +680,7 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
 #pragma unroll
       for (int r = 0; r < R1; ++r)
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) rex[fpad(rj * R1 + r + 16 * k2)] = o[r * N2 + k2];
+        for (int k2 = 0; k2 < N2; ++k2) rex[fpad(rj + N2 * r + 16 * k2)] = o[r * N2 + k2];
     }
   } else {
     // The forward transform reads only planes 0 .. NF/2-1 (its input vanishes above, as
@@ -729,6 +729,10 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
                  col + (2 * tx + t) * P + fpad(HF), cqx[t], cqy[t], kzs[HF], S, Es, cinv);
   }
   __syncthreads();
+  // FP32 register transform: the output leaves from the registers (below); in FP64 the
+  // longer live range of o[] cost more than the shared-memory round trip saves
+  constexpr bool REG_OUT = REG && F32;
+  C o[16];  // register transform: this lane's inverse outputs, planes rj + N2 r + 16 k2
   if constexpr (REG) {
     C v[16];
     if (rvalid) {
@@ -742,16 +746,15 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
       for (int k1 = 0; k1 < 16; ++k1) rex[k1 * EP + rj] = v[k1];
     }
     __syncwarp();
-    C o[16];
     if (rvalid) reg_fft_step2<C, NF, true, EP>(rex, rj, o);
     __syncwarp();
-    if (rvalid) {  // planes 0 .. NF/2 are the ones used below
+    if (rvalid) {  // to shared memory: planes 0 and ns + 1 (R0, side spectra), or all used ones
 #pragma unroll
       for (int r = 0; r < R1; ++r)
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
-          const int n = rj * R1 + r + 16 * k2;
-          if (n <= HF) rex[fpad(n)] = o[r * N2 + k2];
+          const int n = rj + N2 * r + 16 * k2;
+          if (REG_OUT ? (n == 0 || n == ns + 1) : n <= HF) rex[fpad(n)] = o[r * N2 + k2];
         }
     }
   } else {
@@ -828,21 +831,44 @@ __global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
     ptab[t * PP + j] = r;
   }
   __syncthreads();
-  const int pl_end = a.no_reflect ? 0 : ns;  // the free-space operator adds no reflection
-  for (int pl = p0; pl < pl_end; pl += pstep) {
-    const C ph = cmul(ptab[t0 * PP + (pl & 7)], ptab[t0 * PP + 8 + (pl >> 3)]);  // exp(i beta pl dz)
+  const bool reflect = !a.no_reflect;  // the free-space operator adds no reflection
+  if constexpr (REG_OUT) {
+    // straight from the registers: plane pl = n - 1 gets R0 exp(i beta pl dz); a warp's four
+    // columns are consecutive x-modes, so each plane is written as one 32- (64-) byte run
+    if (rvalid) {
+      const int cc = rf / tx, t = rf % tx;
+      const C r0 = R0[cc * tx + t];
+      C* dst = a.work + ((size_t)lr * 3 + cc) * ns * pstride + (size_t)y * nx + x0 + t;
+#pragma unroll
+      for (int r = 0; r < R1; ++r)
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+          const int n = rj + N2 * r + 16 * k2;
+          if (n >= 1 && n <= ns) {
+            const int pl = n - 1;
+            C val = o[r * N2 + k2];
+            if (reflect) val = cadd(val, cmul(r0, cmul(ptab[t * PP + (pl & 7)], ptab[t * PP + 8 + (pl >> 3)])));
+            dst[(size_t)pl * pstride] = val;
+          }
+        }
+    }
+  } else {
+    const int pl_end = reflect ? ns : 0;
+    for (int pl = p0; pl < pl_end; pl += pstep) {
+      const C ph = cmul(ptab[t0 * PP + (pl & 7)], ptab[t0 * PP + 8 + (pl >> 3)]);  // exp(i beta pl dz)
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        C* e = col + (cc * tx + t0) * P + fpad(pl + 1);
+        *e = cadd(*e, cmul(R0[cc * tx + t0], ph));
+      }
+    }
+    __syncthreads();
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
-      C* e = col + (cc * tx + t0) * P + fpad(pl + 1);
-      *e = cadd(*e, cmul(R0[cc * tx + t0], ph));
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int cc = 0; cc < 3; ++cc) {
 #pragma unroll 4
-    for (int pl = p0; pl < ns; pl += pstep)
-      gcol[((size_t)cc * ns + pl) * pstride] = col[(cc * tx + t0) * P + fpad(pl + 1)];
+      for (int pl = p0; pl < ns; pl += pstep)
+        gcol[((size_t)cc * ns + pl) * pstride] = col[(cc * tx + t0) * P + fpad(pl + 1)];
+    }
   }
 }
 
