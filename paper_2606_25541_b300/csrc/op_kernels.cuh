@@ -577,9 +577,14 @@ static_assert(zcol_pitch(128, true) == 152 && zcol_pitch(64, true) == 84 && zcol
 template <typename C, int NF> __host__ __device__ constexpr bool zcol_reg() {
   return NF == 64 || NF == 128 || NF == 256;
 }
+// CTAs per SM the FP32 register-transform kernel is compiled for (it is issue-bound: more
+// resident warps hide the shared-memory and barrier waits); 1 = no register cap.
+template <typename C, int NF> __host__ __device__ constexpr int zcol_min_blocks() {
+  return (sizeof(C) == 8 && NF == 128) ? 5 : 1;
+}
 
 template <typename C, int NF, int NT>
-__global__ void __launch_bounds__(NT) k_zcol(OpCall<C> a, int tx) {
+__global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF>()) k_zcol(OpCall<C> a, int tx) {
   using R = typename RealOf<C>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr bool F32 = sizeof(C) == sizeof(float2);

@@ -194,6 +194,10 @@ int launch_zcol(const OpCall<C>& a) {
   const size_t smem = zcol_smem_bytes<C>(NF, tx);
   auto k = k_zcol<C, NF, NT>;
   if (set_smem(k, smem)) return PSFD_E_CUDA;
+  if constexpr (zcol_min_blocks<C, NF>() > 1) {  // shared memory for all the CTAs the registers allow
+    if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+      return PSFD_E_CUDA;
+  }
   k<<<dim3(a.nx / tx, a.ny, a.nrhs), NT, smem, a.stream>>>(a, tx);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
