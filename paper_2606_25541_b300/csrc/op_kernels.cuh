@@ -303,16 +303,30 @@ __global__ void __launch_bounds__(NT) k_plane_inv(OpCall<C> a, const C* uin) {
 //   y[2m + h] = sum_{k<H} [(Y_k + (-1)^h Y_{k+H}) w^{-k h}] exp(+2 pi i k m / H)
 // and applies the epilogue to the output rows of parity h.
 // ---------------------------------------------------------------------------
-template <int NX, int NY> __host__ __device__ constexpr int half_tile_elems() {
-  return fft_phys(NY / 2) * plane_pitch<NX>();
+// Row pitch of a half-plane tile. The y transforms (length NY/2, element stride PITCH) run in
+// groups of G lanes, 16/G of them side by side in a 16-lane memory phase at consecutive
+// columns; for 8-byte elements PITCH = 16/G (mod 16) interleaves their elements over the
+// banks (an odd pitch would put two columns' elements on neighbouring banks).
+template <typename C, int NX, int NY> __host__ __device__ constexpr int half_pitch() {
+  constexpr int G = fft_group_lanes<C>(NY / 2), base = fft_phys(NX);
+  if constexpr (sizeof(C) == 8 && G < 16) {
+    constexpr int m = 16 / G;
+    return base + ((m - base % 16) % 16 + 16) % 16;
+  } else {
+    return base | 1;
+  }
+}
+static_assert(half_pitch<float2, 128, 128>() == 146, "half-plane pitch");
+template <typename C, int NX, int NY> __host__ __device__ constexpr int half_tile_elems() {
+  return fft_phys(NY / 2) * half_pitch<C, NX, NY>();
 }
 
 template <typename C, int NX, int NY, int IN, int NT>
 __global__ void __launch_bounds__(NT, 2) k_half_fwd(OpCall<C> a) {
-  constexpr int H = NY / 2, PITCH = plane_pitch<NX>();
+  constexpr int H = NY / 2, PITCH = half_pitch<C, NX, NY>();
   extern __shared__ __align__(16) unsigned char smem[];
   C* tile = reinterpret_cast<C*>(smem);
-  C* twx = tile + half_tile_elems<NX, NY>();
+  C* twx = tile + half_tile_elems<C, NX, NY>();
   C* twy = twx + NX;  // exp(-2 pi i r / NY), r < H
   C* twh = twy + H;   // exp(-2 pi i t / H), t < H
   const int p = blockIdx.x >> 1, h = blockIdx.x & 1, c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
@@ -363,10 +377,10 @@ __global__ void __launch_bounds__(NT, 2) k_half_fwd(OpCall<C> a) {
 
 template <typename C, int NX, int NY, int EPI, int NT>
 __global__ void __launch_bounds__(NT, 2) k_half_inv(OpCall<C> a, const C* uin) {
-  constexpr int H = NY / 2, PITCH = plane_pitch<NX>();
+  constexpr int H = NY / 2, PITCH = half_pitch<C, NX, NY>();
   extern __shared__ __align__(16) unsigned char smem[];
   C* tile = reinterpret_cast<C*>(smem);
-  C* twx = tile + half_tile_elems<NX, NY>();
+  C* twx = tile + half_tile_elems<C, NX, NY>();
   C* twy = twx + NX;
   C* twh = twy + H;
   double2* scratch = align16<double2>(twh + H);

@@ -101,7 +101,7 @@ int launch_plane_inv(const OpCall<C>& a, const C* uin) {
 template <typename C, int N, int IN>
 int launch_half_fwd(const OpCall<C>& a) {
   constexpr int NT = 512;
-  const size_t smem = (size_t)(half_tile_elems<N, N>() + 2 * N) * sizeof(C);
+  const size_t smem = (size_t)(half_tile_elems<C, N, N>() + 2 * N) * sizeof(C);
   auto k = k_half_fwd<C, N, N, IN, NT>;
   if (set_smem(k, smem)) return PSFD_E_CUDA;
   k<<<dim3(2 * a.nslab, 3, a.nrhs), NT, smem, a.stream>>>(a);
@@ -112,7 +112,7 @@ int launch_half_fwd(const OpCall<C>& a) {
 template <typename C, int N, int EPI>
 int launch_half_inv(const OpCall<C>& a, const C* uin) {
   constexpr int NT = 512;
-  const size_t smem = (size_t)(half_tile_elems<N, N>() + 2 * N) * sizeof(C) + 16 + NDOT * 32 * sizeof(double2);
+  const size_t smem = (size_t)(half_tile_elems<C, N, N>() + 2 * N) * sizeof(C) + 16 + NDOT * 32 * sizeof(double2);
   auto k = k_half_inv<C, N, N, EPI, NT>;
   if (set_smem(k, smem)) return PSFD_E_CUDA;
   k<<<dim3(2 * a.nslab, 3, a.nrhs), NT, smem, a.stream>>>(a, uin);
