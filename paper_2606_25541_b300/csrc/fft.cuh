@@ -42,6 +42,11 @@ __host__ __device__ constexpr int fft_plan_stages(int n) {
 // conflict free. A transform of length n occupies fft_phys(n) slots.
 __host__ __device__ constexpr int fft_phys(int n) { return n + (n >> 3); }
 __host__ __device__ __forceinline__ int fpad(int i) { return i + (i >> 3); }
+// The same with one spare slot after every RUN elements (RUN = 8 is the layout above). With
+// RUN = 16 a 16-lane memory phase reading 16 consecutive elements stays inside one run and
+// hits 16 different banks, while stores with a stride of eight elements still spread.
+template <int RUN> __host__ __device__ constexpr int fft_physr(int n) { return n + n / RUN; }
+template <int RUN> __host__ __device__ __forceinline__ int fpadr(int i) { return i + i / RUN; }
 
 // Lanes per transform: N/8 rounded down to a power of two, clamped to [1, 32] up to
 // N = 512. Longer transforms span several warps (64 lanes, or 128 in FP64) so that a lane
@@ -314,12 +319,12 @@ __device__ __forceinline__ void reg_fft_step2(const C* ex, int j, C (&out)[16]) 
 // Stockham stages. Butterfly b of a radix-R stage (after stages whose radices multiply
 // to NS) reads elements b + r N/R, twiddles them by exp(-2 pi i r (b mod NS)/(NS R)),
 // and writes element r of its DFT to (b / NS) NS R + (b mod NS) + r NS.
-// Element i sits at fpad(i) * ES. Whenever the R elements of a butterfly stay inside one
-// run of eight (or are spaced by a multiple of eight) their padded offsets differ by
+// Element i sits at fpadr<RUN>(i) * ES. Whenever the R elements of a butterfly stay inside
+// one run (or are spaced by a multiple of the run) their padded offsets differ by
 // compile-time constants, so only the first address of a butterfly is computed.
 // HALF_IN: the input is zero on [N/2, N) and only its lower half is read.
 // ---------------------------------------------------------------------------
-template <typename C, int N, int G, bool INV, int S, int NS, int ES, bool HALF_IN>
+template <typename C, int N, int G, bool INV, int S, int NS, int ES, bool HALF_IN, int RUN = 8>
 __device__ __forceinline__ void fft_stages(C* a, int g, const C* tw, bool valid, int bar) {
   if constexpr (S < fft_plan_stages(N)) {
     constexpr int R = fft_plan_radix(N, S);
@@ -333,13 +338,13 @@ __device__ __forceinline__ void fft_stages(C* a, int g, const C* tw, bool valid,
     for (int k = 0; k < K; ++k) {
       const int b = g + k * G;
       if (valid && (NB % G == 0 || b < NB)) {
-        if constexpr (NB % 8 == 0) {
-          const C* src = a + fpad(b) * ES;
+        if constexpr (NB % RUN == 0) {
+          const C* src = a + fpadr<RUN>(b) * ES;
 #pragma unroll
-          for (int r = 0; r < RL; ++r) v[k][r] = src[r * fft_phys(NB) * ES];
+          for (int r = 0; r < RL; ++r) v[k][r] = src[r * fft_physr<RUN>(NB) * ES];
         } else {
 #pragma unroll
-          for (int r = 0; r < RL; ++r) v[k][r] = a[fpad(b + r * NB) * ES];
+          for (int r = 0; r < RL; ++r) v[k][r] = a[fpadr<RUN>(b + r * NB) * ES];
         }
         if constexpr (NS > 1) {
           const int jt = (b % NS) * TWS;
@@ -364,39 +369,40 @@ __device__ __forceinline__ void fft_stages(C* a, int g, const C* tw, bool valid,
       if (valid && (NB % G == 0 || b < NB)) {
         const int jj = b % NS;
         const int base = (b / NS) * NS * R + jj;
-        if constexpr (NS % 8 == 0) {
-          C* dst = a + fpad(base) * ES;
+        if constexpr (NS % RUN == 0) {
+          C* dst = a + fpadr<RUN>(base) * ES;
 #pragma unroll
-          for (int r = 0; r < R; ++r) dst[r * fft_phys(NS) * ES] = v[k][r];
-        } else if constexpr (NS == 1 && 8 % R == 0) {
-          C* dst = a + fpad(base) * ES;
+          for (int r = 0; r < R; ++r) dst[r * fft_physr<RUN>(NS) * ES] = v[k][r];
+        } else if constexpr (NS == 1 && RUN % R == 0) {
+          C* dst = a + fpadr<RUN>(base) * ES;
 #pragma unroll
           for (int r = 0; r < R; ++r) dst[r * ES] = v[k][r];
         } else {
 #pragma unroll
-          for (int r = 0; r < R; ++r) a[fpad(base + r * NS) * ES] = v[k][r];
+          for (int r = 0; r < R; ++r) a[fpadr<RUN>(base + r * NS) * ES] = v[k][r];
         }
       }
     }
     group_sync<G>(bar);
-    fft_stages<C, N, G, INV, S + 1, NS * R, ES, HALF_IN>(a, g, tw, valid, bar);
+    fft_stages<C, N, G, INV, S + 1, NS * R, ES, HALF_IN, RUN>(a, g, tw, valid, bar);
   }
 }
 
 // One length-N transform per group of G lanes. Every lane of the warp must call this
 // (lanes of groups without work pass valid = false) because stages end in __syncwarp.
-template <typename C, int N, bool INV, int ES = 1, bool HALF_IN = false>
+template <typename C, int N, bool INV, int ES = 1, bool HALF_IN = false, int RUN = 8>
 __device__ __forceinline__ void group_fft(C* a, int g, const C* tw, bool valid, int bar = 0) {
   constexpr int G = fft_group_lanes<C>(N);
-  fft_stages<C, N, G, INV, 0, 1, ES, HALF_IN>(a, g, tw, valid, bar);
+  fft_stages<C, N, G, INV, 0, 1, ES, HALF_IN, RUN>(a, g, tw, valid, bar);
 }
 
 // Batched transforms by a whole CTA: `count` transforms, transform f starting at
-// a + f' * fs with f' = fpad(f) if PADF (transforms along the second axis of a padded
-// 2-D tile) else f, element i at fpad(i) * ES. Groups of G <= 32 lanes share a warp
+// a + f' * fs with f' = fpadr<FRUN>(f) if PADF (transforms along the second axis of a padded
+// 2-D tile) else f, element i at fpadr<RUN>(i) * ES. Groups of G <= 32 lanes share a warp
 // (32/G transforms per warp at a time); larger groups are G consecutive threads with
 // named barrier 1 + (thread / G), so the CTA size must be a multiple of G and below 16 G.
-template <typename C, int N, bool INV, bool PADF = false, int ES = 1, bool HALF_IN = false>
+template <typename C, int N, bool INV, bool PADF = false, int ES = 1, bool HALF_IN = false, int RUN = 8,
+          int FRUN = 8>
 __device__ __forceinline__ void cta_fft(C* a, int count, int fs, const C* tw) {
   constexpr int G = fft_group_lanes<C>(N);
   int gid, ngroups, bar = 0;
@@ -413,8 +419,8 @@ __device__ __forceinline__ void cta_fft(C* a, int count, int fs, const C* tw) {
   for (int it = 0; it < rounds; ++it) {
     const int f = gid + it * ngroups;
     const bool valid = f < count;
-    const int fo = valid ? (PADF ? fpad(f) : f) : 0;
-    group_fft<C, N, INV, ES, HALF_IN>(a + fo * fs, g, tw, valid, bar);
+    const int fo = valid ? (PADF ? fpadr<FRUN>(f) : f) : 0;
+    group_fft<C, N, INV, ES, HALF_IN, RUN>(a + fo * fs, g, tw, valid, bar);
   }
 }
 

@@ -307,8 +307,12 @@ __global__ void __launch_bounds__(NT) k_plane_inv(OpCall<C> a, const C* uin) {
 // groups of G lanes, 16/G of them side by side in a 16-lane memory phase at consecutive
 // columns; for 8-byte elements PITCH = 16/G (mod 16) interleaves their elements over the
 // banks (an odd pitch would put two columns' elements on neighbouring banks).
+// Half-plane tiles pad every 16 elements along x (the x transforms read 16 consecutive
+// elements per 16-lane phase) and every 8 along y.
+constexpr int kHalfXRun = 16;
+
 template <typename C, int NX, int NY> __host__ __device__ constexpr int half_pitch() {
-  constexpr int G = fft_group_lanes<C>(NY / 2), base = fft_phys(NX);
+  constexpr int G = fft_group_lanes<C>(NY / 2), base = fft_physr<kHalfXRun>(NX);
   if constexpr (sizeof(C) == 8 && G < 16) {
     constexpr int m = 16 / G;
     return base + ((m - base % 16) % 16 + 16) % 16;
@@ -361,17 +365,17 @@ __global__ void __launch_bounds__(NT, 2) k_half_fwd(OpCall<C> a) {
       const C u0 = combine_in<C, IN>(in0[j], s), u1 = combine_in<C, IN>(in1[j], s);
       if constexpr (IN != IN_PLAIN) a.ustore[plane + i + (h ? TOT : 0)] = h ? u1 : u0;  // owner's half
       const C v0 = cmul(va[j], u0), v1 = cmul(vb[j], u1);
-      tile[fpad(r) * PITCH + fpad(i % NX)] = h ? cmul(csub(v0, v1), twy[r]) : cadd(v0, v1);
+      tile[fpad(r) * PITCH + fpadr<kHalfXRun>(i % NX)] = h ? cmul(csub(v0, v1), twy[r]) : cadd(v0, v1);
     }
   }
   __syncthreads();
-  cta_fft<C, NX, false, true, 1>(tile, H, PITCH, twx);
+  cta_fft<C, NX, false, true, 1, false, kHalfXRun, 8>(tile, H, PITCH, twx);
   __syncthreads();
-  cta_fft<C, H, false, true, PITCH>(tile, NX, 1, twh);
+  cta_fft<C, H, false, true, PITCH, false, 8, kHalfXRun>(tile, NX, 1, twh);
   __syncthreads();
   for (int i = threadIdx.x; i < H * NX; i += NT) {
     const int m = i / NX, x = i % NX;
-    a.work[plane + (size_t)(2 * m + h) * NX + x] = tile[fpad(m) * PITCH + fpad(x)];
+    a.work[plane + (size_t)(2 * m + h) * NX + x] = tile[fpad(m) * PITCH + fpadr<kHalfXRun>(x)];
   }
 }
 
@@ -405,13 +409,13 @@ __global__ void __launch_bounds__(NT, 2) k_half_inv(OpCall<C> a, const C* uin) {
 #pragma unroll
     for (int j = 0; j < BL; ++j) {
       const int i = i0 + j * NT, k = i / NX;
-      tile[fpad(k) * PITCH + fpad(i % NX)] = h ? cmul(csub(y0[j], y1[j]), cconj(twy[k])) : cadd(y0[j], y1[j]);
+      tile[fpad(k) * PITCH + fpadr<kHalfXRun>(i % NX)] = h ? cmul(csub(y0[j], y1[j]), cconj(twy[k])) : cadd(y0[j], y1[j]);
     }
   }
   __syncthreads();
-  cta_fft<C, H, true, true, PITCH>(tile, NX, 1, twh);
+  cta_fft<C, H, true, true, PITCH, false, 8, kHalfXRun>(tile, NX, 1, twh);
   __syncthreads();
-  cta_fft<C, NX, true, true, 1>(tile, H, PITCH, twx);
+  cta_fft<C, NX, true, true, 1, false, kHalfXRun, 8>(tile, H, PITCH, twx);
   __syncthreads();
   Dots<C> dt;
   zero_dots(dt);
@@ -428,7 +432,7 @@ __global__ void __launch_bounds__(NT, 2) k_half_inv(OpCall<C> a, const C* uin) {
 #pragma unroll
     for (int j = 0; j < BT; ++j) {
       const int i = i0 + j * NT, m = i / NX, x = i % NX;
-      store_epi<C, EPI>(a, plane + (size_t)(2 * m + h) * NX + x, e[j], tile[fpad(m) * PITCH + fpad(x)], dt);
+      store_epi<C, EPI>(a, plane + (size_t)(2 * m + h) * NX + x, e[j], tile[fpad(m) * PITCH + fpadr<kHalfXRun>(x)], dt);
     }
   }
   if (a.dot_mask) {
