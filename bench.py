@@ -75,6 +75,10 @@ def parse_args(argv=None):
     ap.add_argument("--bilayers", type=int, default=40, help="Mo/Si bilayers of the --crosscheck stack")
     ap.add_argument("--large", action="store_true",
                     help="1024 x 1024 x 60 curvilinear clip, 8 illuminations in memory-bounded batches")
+    ap.add_argument("--layers", type=str, default=None,
+                    help="layer-count study: comma-separated Mo/Si bilayer counts (decomposition, outer fixed "
+                         "point and stack meshed into the domain on the 256 x 256 crop)")
+    ap.add_argument("--mesh-max", type=int, default=10, help="largest bilayer count --layers meshes into the domain")
     ap.add_argument("--small", action="store_true",
                     help="the 32 x 32 x 30 contact-hole clip (one illumination): ms per solve, CUDA graphs on/off")
     ap.add_argument("--fixed-point", action="store_true",
@@ -351,6 +355,60 @@ def run_crosscheck(args):
         idx = [key[(m, n)] for m, n in zip(a["m"], a["n"])]
         diffs.append(float(np.linalg.norm(a["eff"] - b["eff"][idx]) / np.linalg.norm(b["eff"])))
     out["efficiency_rel_diff"] = diffs
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_layers(args):
+    """Cost against the number of stack layers (the paper's comparison of the background-field
+    method with a full-domain PSFD, Sec. 4): for Ru + n x (Mo/Si), the 256 x 256 crop of the
+    1024 x 1024 curvilinear clip (60 planes at 1 nm, 6 deg s and p) solved three ways in FP32
+    with FP64 refinement to --tol: the decomposition with R folded into the operator, the
+    paper's outer fixed point of Eq. (8), and the stack meshed into the domain (thickness-
+    weighted permittivity per 1 nm cell, substrate-only reflection; up to --mesh-max bilayers).
+    Reported per n: seconds, Krylov iterations, outer steps, status, and the relative
+    difference of the reflected efficiencies of the meshed solve against the decomposition."""
+    import dataclasses
+    import torch
+    from paper_2606_25541_b300 import psfd
+    big = layouts.curvilinear_clip()
+    crop = dataclasses.replace(big, nx=256, ny=256, eps=np.ascontiguousarray(big.eps[:, :256, :256]),
+                               name="curvilinear_crop_256x256x60")
+    crop = crop.with_illumination([6.0, 6.0], [0.0, 0.0], [0, 1])
+    stream = torch.cuda.current_stream()
+    kw = dict(tol=args.tol, inner_tol=args.inner_tol, max_iter=1000, max_outer=12, raise_on_error=False)
+    out = {"mode": "layer_count_study", "workload": "curvilinear_crop_256x256x60_2rhs", "tol": args.tol, "rows": []}
+
+    def timed(prob, fixed_point=False):
+        s = psfd.Solver.from_problem(prob, psfd.FP32_REFINED, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = s.solve_fixed_point(max_steps=300, **kw) if fixed_point else s.solve(**kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        eff = [s.diffraction_orders(i) for i in range(prob.n_rhs)]
+        s.close()
+        return {"seconds": dt, "iterations": rep["iterations"], "outer": rep["outer"], "relres": rep["relres"],
+                "status": psfd.strerror(rep["status"])}, eff
+
+    for nb in (int(v) for v in args.layers.split(",")):
+        n_l, d_l, n_s = layouts.ru_mosi_stack(nb)
+        prob = dataclasses.replace(crop, n_layers=n_l, d_layers=d_l, n_sub=n_s)
+        row = {"bilayers": nb, "layers": len(n_l)}
+        row["decomposition"], eff_dec = timed(prob)
+        row["fixed_point"], _ = timed(prob, fixed_point=True)
+        if nb <= args.mesh_max:
+            full, depth = layouts.stack_in_domain(prob)
+            row["stack_in_domain"], eff_full = timed(full)
+            row["stack_in_domain"].update({"planes": full.nslab, "nf": full.nf, "depth_nm": depth})
+            diffs = []
+            for a, b in zip(eff_full, eff_dec):
+                key = {(m, n): k for k, (m, n) in enumerate(zip(b["m"], b["n"]))}
+                idx = [key[(m, n)] for m, n in zip(a["m"], a["n"])]
+                diffs.append(float(np.linalg.norm(a["eff"] - b["eff"][idx]) / np.linalg.norm(b["eff"])))
+            row["efficiency_rel_diff"] = diffs
+        out["rows"].append(row)
+        print(json.dumps(row), flush=True)
     print(json.dumps(out), flush=True)
     return 0
 
@@ -824,7 +882,8 @@ def solver_bytes(prob) -> float:
 
 def main(argv=None):
     args = parse_args(argv)
-    headline = not (args.apply or args.sweep or args.large or args.crosscheck or args.fixed_point or args.small)
+    headline = not (args.apply or args.sweep or args.large or args.crosscheck or args.fixed_point or args.small
+                    or args.layers)
     if args.tol is None:
         args.tol = HEADLINE_TOL if headline else DEFAULT_TOL
     if args.inner_tol is None:
@@ -843,6 +902,8 @@ def main(argv=None):
         return run_fixed_point(args)
     if args.small:
         return run_small(args)
+    if args.layers:
+        return run_layers(args)
     if args.serve_only:
         sizes = tuple(int(s) for s in args.serve_sizes.split(","))
         print(json.dumps({"mode": "serving", **run_serving(args.serve, sizes, args.tol, args.inner_tol)}), flush=True)
