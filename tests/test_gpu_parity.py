@@ -398,3 +398,26 @@ def test_fixed_point_converges_to_the_folded_solution(psfd, precision):
     ref = oracle.apply_operator(oracle.setup_rhs(prob, 1), u_used[1])
     assert _rel(out.cpu().numpy()[1], ref) < (1e-12 if precision == psfd.FP64 else 3e-5)
     s.close()
+
+
+def test_sweeps_are_solved_only_as_far_as_the_target_needs(psfd, contact_hole_reference):
+    """psfd_solve_opts.inner_tol: a sweep starting from FP64 residual rho is solved to
+    max(inner_tol, tol / (4 rho)). At the metric's 1e-6 order error one FP32 sweep to 2e-7
+    meets tol = 3e-7; a second sweep, when needed, asks only for what is left (its Krylov
+    estimates stop near tol / 4, not at inner_tol times its starting residual)."""
+    prob, ref, _ = contact_hole_reference
+    s = _solver(psfd, prob, psfd.FP32_REFINED)
+    rep = s.solve(tol=3e-7, inner_tol=2e-7, max_iter=300, max_outer=10)
+    assert rep["outer"] == 1 and rep["relres"] <= 3e-7
+    assert _orders_err(s.diffraction_orders(0), ref) < 1e-6
+    rep = s.solve(tol=1e-9, inner_tol=1e-6, max_iter=300, max_outer=10)
+    assert rep["relres"] <= 1e-9
+    h = s.residual_history(0)
+    kind, rel = h["kind"], h["relres"]
+    fp64 = rel[kind == 1]
+    assert len(fp64) == rep["outer"] + 1 and rep["outer"] >= 2
+    # the last sweep started from fp64[-2]; its estimates stop within a factor ~4 below tol
+    last = np.nonzero(kind == 1)[0][-2]
+    est = rel[last + 1:][kind[last + 1:] == 0]
+    assert len(est) >= 1 and est.min() >= 1e-9 / 200, (fp64, est)  # inner_tol * rho would be ~1e-12
+    s.close()
