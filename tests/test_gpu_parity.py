@@ -102,6 +102,10 @@ APPLY_CASES = [
     (16, 16, 12, 64),
     (32, 16, 20, 128),
     (16, 32, 9, 256),
+    # fewer x-modes than a register-transform CTA holds (idle groups); the thickest slab
+    # nf = 128 allows (plane ns + 1 = nf/2 - 1)
+    (4, 32, 20, 128),
+    (8, 8, 62, 128),
 ]
 
 
