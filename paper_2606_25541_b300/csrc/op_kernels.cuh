@@ -444,16 +444,19 @@ __global__ void __launch_bounds__(NT, 2) k_half_inv(OpCall<C> a, const C* uin) {
 // ---------------------------------------------------------------------------
 // split path: row pass and column pass (planes larger than shared memory)
 // ---------------------------------------------------------------------------
-// blockIdx.x = plane * (ny / rb) + row block; each CTA transforms rb rows of length NX.
+// Each CTA transforms rb rows of length NX (k_rows_inv: blockIdx.x = plane * (ny / rb) + row
+// block; k_rows_fwd orders its grid for V's reuse in L2, below).
 template <typename C, int NX, int IN, int NT>
 __global__ void __launch_bounds__(NT) k_rows_fwd(OpCall<C> a, int rb) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int RP = fft_phys(NX);  // row pitch of the tile
   C* tile = reinterpret_cast<C*>(smem);
   C* tw = tile + rb * RP;
-  const int nrb = a.ny / rb;
-  const int p = blockIdx.x / nrb, y0 = (blockIdx.x % nrb) * rb;
-  const int c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
+  // blockIdx.x = rhs * 3 + component, blockIdx.y = row block, blockIdx.z = plane: the CTAs
+  // that read the same rows of V run next to each other, so V (hundreds of MB on large
+  // grids, beyond L2) comes from DRAM once per launch rather than once per rhs and component
+  const int p = blockIdx.z, y0 = blockIdx.y * rb;
+  const int c = blockIdx.x % 3, lr = blockIdx.x / 3, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
   for (int i = threadIdx.x; i < NX; i += NT) tw[i] = from_c64<C>(a.twx[i]);
@@ -595,10 +598,11 @@ static_assert(zcol_pitch(128, true) == 152 && zcol_pitch(64, true) == 84 && zcol
 template <typename C, int NF> __host__ __device__ constexpr bool zcol_reg() {
   return NF == 64 || NF == 128 || NF == 256;
 }
-// CTAs per SM the FP32 register-transform kernel is compiled for (it is issue-bound: more
-// resident warps hide the shared-memory and barrier waits); 1 = no register cap.
+// CTAs per SM the FP32 kernel is compiled for at the z lengths of the measured workloads
+// (128: register transform, 160: shared-memory transform); it is issue- or latency-bound, and
+// more resident warps hide the shared-memory and barrier waits. 1 = no register cap.
 template <typename C, int NF> __host__ __device__ constexpr int zcol_min_blocks() {
-  return (sizeof(C) == 8 && NF == 128) ? 5 : 1;
+  return (sizeof(C) == 8 && (NF == 128 || NF == 160)) ? 5 : 1;
 }
 
 template <typename C, int NF, int NT>

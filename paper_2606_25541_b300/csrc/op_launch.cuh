@@ -127,7 +127,7 @@ int launch_rows_fwd(const OpCall<C>& a) {
   const size_t smem = (size_t)(rb * fft_phys(NX) + NX) * sizeof(C);
   auto k = k_rows_fwd<C, NX, IN, NT>;
   if (set_smem(k, smem)) return PSFD_E_CUDA;
-  k<<<dim3(a.nslab * (a.ny / rb), 3, a.nrhs), NT, smem, a.stream>>>(a, rb);
+  k<<<dim3(3 * a.nrhs, a.ny / rb, a.nslab), NT, smem, a.stream>>>(a, rb);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }

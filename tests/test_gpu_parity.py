@@ -106,6 +106,8 @@ APPLY_CASES = [
     # nf = 128 allows (plane ns + 1 = nf/2 - 1)
     (4, 32, 20, 128),
     (8, 8, 62, 128),
+    # nf = 160 (shared-memory z transform, radix 8-4-5)
+    (16, 8, 30, 160),
 ]
 
 
