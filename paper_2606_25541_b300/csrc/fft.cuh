@@ -164,6 +164,27 @@ template <typename C, bool INV> struct Dft<C, 5, INV> {
   }
 };
 
+// 10-point DFT as two 5-point DFTs of the even and odd inputs combined with w_10^k.
+template <typename C, bool INV> struct Dft<C, 10, INV> {
+  __device__ __forceinline__ static void run(C* v) {
+    using R = typename RealOf<C>::T;
+    C e[5] = {v[0], v[2], v[4], v[6], v[8]};
+    C o[5] = {v[1], v[3], v[5], v[7], v[9]};
+    Dft<C, 5, INV>::run(e);
+    Dft<C, 5, INV>::run(o);
+    const R c36 = (R)0.80901699437494742410, s36 = (R)0.58778525229247312917;
+    const R c72 = (R)0.30901699437494742410, s72 = (R)0.95105651629515357212;
+    const R sg = INV ? (R)1 : (R)-1;  // w_10^k = exp(-+ 2 pi i k / 10)
+    const C w[5] = {mk((R)1, (R)0), mk(c36, sg * s36), mk(c72, sg * s72), mk(-c72, sg * s72), mk(-c36, sg * s36)};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const C t = k ? cmul(o[k], w[k]) : o[k];
+      v[k] = cadd(e[k], t);
+      v[k + 5] = csub(e[k], t);
+    }
+  }
+};
+
 // Radix-R DFT of inputs whose upper half is zero (v[r] = 0 for r >= R/2; only v[0..R/2)
 // are read), as the first stage of a transform whose input is zero on [N/2, N).
 template <typename C, int R, bool INV> struct DftHalf;

@@ -444,10 +444,19 @@ __global__ void __launch_bounds__(NT, 2) k_half_inv(OpCall<C> a, const C* uin) {
 // ---------------------------------------------------------------------------
 // split path: row pass and column pass (planes larger than shared memory)
 // ---------------------------------------------------------------------------
+// CTAs per SM the split-plane kernels (rows, columns; planes above 128^2 in FP32, FP64
+// planes above 64^2) are compiled for. In FP32 they are latency-bound: an 80-register cap
+// makes three 256-thread CTAs resident instead of two. It spills a little at 512 and 1024
+// points and still pays there (1024^2: K1 and K3 25-28 % faster); FP64 is FP64-pipe bound
+// and keeps its registers.
+template <typename C, int N> __host__ __device__ constexpr int split_min_blocks() {
+  return sizeof(C) == 8 ? 3 : 1;
+}
+
 // Each CTA transforms rb rows of length NX (k_rows_inv: blockIdx.x = plane * (ny / rb) + row
 // block; k_rows_fwd orders its grid for V's reuse in L2, below).
 template <typename C, int NX, int IN, int NT>
-__global__ void __launch_bounds__(NT) k_rows_fwd(OpCall<C> a, int rb) {
+__global__ void __launch_bounds__(NT, split_min_blocks<C, NX>()) k_rows_fwd(OpCall<C> a, int rb) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int RP = fft_phys(NX);  // row pitch of the tile
   C* tile = reinterpret_cast<C*>(smem);
@@ -471,7 +480,7 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(OpCall<C> a, int rb) {
 }
 
 template <typename C, int NX, int EPI, int NT>
-__global__ void __launch_bounds__(NT) k_rows_inv(OpCall<C> a, const C* uin, int rb) {
+__global__ void __launch_bounds__(NT, split_min_blocks<C, NX>()) k_rows_inv(OpCall<C> a, const C* uin, int rb) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int RP = fft_phys(NX);
   C* tile = reinterpret_cast<C*>(smem);
@@ -500,7 +509,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(OpCall<C> a, const C* uin, int 
 // In-place transforms along y of tx consecutive columns of one plane.
 // blockIdx.x = plane * (nx / tx) + column block.
 template <typename C, int NY, bool INV, int NT>
-__global__ void __launch_bounds__(NT) k_cols(OpCall<C> a, int tx) {
+__global__ void __launch_bounds__(NT, split_min_blocks<C, NY>()) k_cols(OpCall<C> a, int tx) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int PITCH = fft_phys(NY) | 1;  // odd column pitch: the transposing copies spread over the banks
   C* tile = reinterpret_cast<C*>(smem);
@@ -598,11 +607,16 @@ static_assert(zcol_pitch(128, true) == 152 && zcol_pitch(64, true) == 84 && zcol
 template <typename C, int NF> __host__ __device__ constexpr bool zcol_reg() {
   return NF == 64 || NF == 128 || NF == 256;
 }
+// FP32 columns of length 160 use a register transform as 16 x 10: a group of 16 lanes per
+// column, lanes j < 10 doing 16-point DFTs of the elements j + 10k, then each lane one
+// 10-point DFT of an exchange row; the spectrum and the output go through shared memory.
+template <typename C, int NF> __host__ __device__ constexpr bool zcol_r10() { return sizeof(C) == 8 && NF == 160; }
 // CTAs per SM the FP32 kernel is compiled for at the z lengths of the measured workloads
-// (128: register transform, 160: shared-memory transform); it is issue- or latency-bound, and
-// more resident warps hide the shared-memory and barrier waits. 1 = no register cap.
+// (128: register transform with 192 threads, 160: the 16 x 10 transform with 384 threads); it
+// is issue- or latency-bound, and more resident warps hide the shared-memory and barrier
+// waits (neither cap spills). 1 = no register cap.
 template <typename C, int NF> __host__ __device__ constexpr int zcol_min_blocks() {
-  return (sizeof(C) == 8 && (NF == 128 || NF == 160)) ? 5 : 1;
+  return (sizeof(C) == 8 && NF == 128) ? 5 : (zcol_r10<C, NF>() ? 3 : 1);
 }
 
 template <typename C, int NF, int NT>
@@ -611,6 +625,7 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF>()) k_zcol(OpCall<C>
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr bool F32 = sizeof(C) == sizeof(float2);
   constexpr bool REG = zcol_reg<C, NF>();
+  constexpr bool R10 = zcol_r10<C, NF>();
   constexpr int P = zcol_pitch(NF, F32 && REG);  // column pitch; element z of a column at fpad(z)
   C* col = reinterpret_cast<C*>(smem);
   C* tw = col + 3 * tx * P;
@@ -709,6 +724,39 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF>()) k_zcol(OpCall<C>
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) rex[fpad(rj + N2 * r + 16 * k2)] = o[r * N2 + k2];
     }
+  } else if constexpr (R10) {
+    __syncthreads();  // twiddles
+    const int gf = threadIdx.x >> 4, gj = threadIdx.x & 15;
+    const bool gok = gf < 3 * tx;
+    C* gx = col + (gok ? gf : 0) * P;  // the group's column: exchange (16 rows of 11), then spectrum
+    if (gok && gj < 10) {
+      // planes j + 10 k (k < 8: the nonzero half, ns + 1 <= NF/2) straight from HBM
+      const int cc = gf / tx, t = gf % tx;
+      const C* src = a.work + (size_t)lr * 3 * ns * pstride + (size_t)cc * ns * pstride + (size_t)y * nx + x0 + t;
+      C v[16];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int n = gj + 10 * k;
+        v[k] = (n >= 1 && n <= ns) ? src[(size_t)(n - 1) * pstride] : mk((R)0, (R)0);
+      }
+#pragma unroll
+      for (int k = 8; k < 16; ++k) v[k] = mk((R)0, (R)0);
+      DftHalf<C, 16, false>::run(v);
+#pragma unroll
+      for (int k1 = 0; k1 < 16; ++k1) gx[k1 * 11 + gj] = k1 ? cmul(v[k1], tw[gj * k1]) : v[k1];
+    }
+    __syncwarp();
+    C w10[10];
+    if (gok) {  // lane j: row k1 = j, outputs k1 + 16 k2
+#pragma unroll
+      for (int i = 0; i < 10; ++i) w10[i] = gx[gj * 11 + i];
+      Dft<C, 10, false>::run(w10);
+    }
+    __syncwarp();
+    if (gok) {
+#pragma unroll
+      for (int k2 = 0; k2 < 10; ++k2) gx[fpad(gj + 16 * k2)] = w10[k2];
+    }
   } else {
     // The forward transform reads only planes 0 .. NF/2-1 (its input vanishes above, as
     // ns + 1 <= NF/2): zero plane 0 and planes ns+1 .. NF/2-1, copy planes 1 .. ns.
@@ -783,6 +831,36 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF>()) k_zcol(OpCall<C>
           const int n = rj + N2 * r + 16 * k2;
           if (REG_OUT ? (n == 0 || n == ns + 1) : n <= HF) rex[fpad(n)] = o[r * N2 + k2];
         }
+    }
+  } else if constexpr (R10) {
+    const int gf = threadIdx.x >> 4, gj = threadIdx.x & 15;
+    const bool gok = gf < 3 * tx;
+    C* gx = col + (gok ? gf : 0) * P;
+    C v[16];
+    if (gok && gj < 10) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = gx[fpad(gj + 10 * k)];
+      Dft<C, 16, true>::run(v);
+    }
+    __syncwarp();
+    if (gok && gj < 10) {
+#pragma unroll
+      for (int k1 = 0; k1 < 16; ++k1) gx[k1 * 11 + gj] = k1 ? cmul(v[k1], cconj(tw[gj * k1])) : v[k1];
+    }
+    __syncwarp();
+    C w10[10];
+    if (gok) {
+#pragma unroll
+      for (int i = 0; i < 10; ++i) w10[i] = gx[gj * 11 + i];
+      Dft<C, 10, true>::run(w10);
+    }
+    __syncwarp();
+    if (gok) {  // planes 0 .. NF/2 are the ones used below
+#pragma unroll
+      for (int k2 = 0; k2 < 10; ++k2) {
+        const int n = gj + 16 * k2;
+        if (n <= HF) gx[fpad(n)] = w10[k2];
+      }
     }
   } else {
     cta_fft<C, NF, true>(col, 3 * tx, P, tw);

@@ -67,11 +67,14 @@ inline int blocks_per_rhs_t(int nx, int ny, int nslab) {
   } while (0)
 
 template <typename K>
-inline int set_smem(K kernel, size_t bytes) {
+inline int set_smem(K kernel, size_t bytes, bool max_carveout = false) {
   if (bytes > 48 * 1024) {
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
       return PSFD_E_CUDA;
   }
+  // kernels compiled for several CTAs per SM: shared memory for all of them
+  if (max_carveout && cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+    return PSFD_E_CUDA;
   return PSFD_OK;
 }
 
@@ -126,7 +129,7 @@ int launch_rows_fwd(const OpCall<C>& a) {
   const int rb = row_block(NX, a.ny, Tune<C>::ROW_ELEMS);
   const size_t smem = (size_t)(rb * fft_phys(NX) + NX) * sizeof(C);
   auto k = k_rows_fwd<C, NX, IN, NT>;
-  if (set_smem(k, smem)) return PSFD_E_CUDA;
+  if (set_smem(k, smem, split_min_blocks<C, NX>() > 1)) return PSFD_E_CUDA;
   k<<<dim3(3 * a.nrhs, a.ny / rb, a.nslab), NT, smem, a.stream>>>(a, rb);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
@@ -138,7 +141,7 @@ int launch_rows_inv(const OpCall<C>& a, const C* uin) {
   const int rb = row_block(NX, a.ny, Tune<C>::ROW_ELEMS);
   const size_t smem = (size_t)(rb * fft_phys(NX) + NX) * sizeof(C) + 16 + NDOT * 32 * sizeof(double2);
   auto k = k_rows_inv<C, NX, EPI, NT>;
-  if (set_smem(k, smem)) return PSFD_E_CUDA;
+  if (set_smem(k, smem, split_min_blocks<C, NX>() > 1)) return PSFD_E_CUDA;
   k<<<dim3(a.nslab * (a.ny / rb), 3, a.nrhs), NT, smem, a.stream>>>(a, uin, rb);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
@@ -180,7 +183,7 @@ int launch_cols(const OpCall<C>& a) {
   const int tx = cols_tile<C>(a.nx, NY);
   const size_t smem = cols_smem_bytes<C>(NY, tx);
   auto k = k_cols<C, NY, INV, NT>;
-  if (set_smem(k, smem)) return PSFD_E_CUDA;
+  if (set_smem(k, smem, split_min_blocks<C, NY>() > 1)) return PSFD_E_CUDA;
   k<<<dim3(a.nslab * (a.nx / tx), 3, a.nrhs), NT, smem, a.stream>>>(a, tx);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
@@ -188,16 +191,12 @@ int launch_cols(const OpCall<C>& a) {
 
 template <typename C, int NF>
 int launch_zcol(const OpCall<C>& a) {
-  constexpr int NT = zcol_reg<C, NF>() ? 24 * (NF / 16) : Tune<C>::ZCOL_NT;
+  constexpr int NT = zcol_reg<C, NF>() ? 24 * (NF / 16) : (zcol_r10<C, NF>() ? 384 : Tune<C>::ZCOL_NT);
   static_assert(((8 + (NF + 15) / 16) | 1) == phase_pitch<NF>(), "phase table size");
   const int tx = zcol_tile<C>(a.nx, NF);
   const size_t smem = zcol_smem_bytes<C>(NF, tx);
   auto k = k_zcol<C, NF, NT>;
-  if (set_smem(k, smem)) return PSFD_E_CUDA;
-  if constexpr (zcol_min_blocks<C, NF>() > 1) {  // shared memory for all the CTAs the registers allow
-    if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
-      return PSFD_E_CUDA;
-  }
+  if (set_smem(k, smem, zcol_min_blocks<C, NF>() > 1)) return PSFD_E_CUDA;
   k<<<dim3(a.nx / tx, a.ny, a.nrhs), NT, smem, a.stream>>>(a, tx);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
