@@ -447,10 +447,12 @@ __global__ void __launch_bounds__(NT, 2) k_half_inv(OpCall<C> a, const C* uin) {
 // CTAs per SM the split-plane kernels (rows, columns; planes above 128^2 in FP32, FP64
 // planes above 64^2) are compiled for. In FP32 they are latency-bound: an 80-register cap
 // makes three 256-thread CTAs resident instead of two. It spills a little at 512 and 1024
-// points and still pays there (1024^2: K1 and K3 25-28 % faster); FP64 is FP64-pipe bound
-// and keeps its registers.
+// points and still pays there (1024^2: K1 and K3 25-28 % faster). FP64 is FP64-pipe bound:
+// up to 256 points a cap of 128 registers keeps two CTAs per SM without spills (an explicit
+// minimum of one let the compiler take 130-136 registers, one CTA per SM and a 30 % slower
+// FP64 residual); longer FP64 transforms would spill under that cap and keep one CTA.
 template <typename C, int N> __host__ __device__ constexpr int split_min_blocks() {
-  return sizeof(C) == 8 ? 3 : 1;
+  return sizeof(C) == 8 ? 3 : (N <= 256 ? 2 : 1);
 }
 
 // Each CTA transforms rb rows of length NX (k_rows_inv: blockIdx.x = plane * (ny / rb) + row
