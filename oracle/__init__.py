@@ -6,3 +6,4 @@ has its own transforms (numpy's FFT used as a library primitive), its own stack
 recursion, Green's function, Krylov solver and extraction, all in complex128.
 """
 from .psfd_oracle import *  # noqa: F401,F403
+from .isolated_oracle import *  # noqa: F401,F403
