@@ -130,6 +130,25 @@ int psfd_destroy(psfd_ctx* ctx);
 /* Rebind the context to another stream. */
 int psfd_set_stream(psfd_ctx* ctx, void* stream);
 
+/* Green's function of the operator. PSFD_GREEN_PERIODIC (default): the clip is periodic in x
+ * and y (diffraction orders), the kernel is exact per transverse mode and windowed in z only.
+ * PSFD_GREEN_SPHERICAL: an isolated clip (Sec. 3, Eqs. (13)-(17)): the dyadic Green's function
+ * truncated to |r| < R, F[G_R](k) = A(|k|) I + B(|k|) khat khat^T, evaluated at
+ * k = (q_x, q_y, kz_l), with no stack reflection (free space around the clip). The caller pads
+ * the clip transversally in the grid (eps = eps_bg in the border) so that every period exceeds
+ * the scatterer's extent plus R, and R exceeds the scatterer's diameter; z is padded
+ * internally to nf, which must satisfy nf dz >= nslab dz + R. Unknowns remain Bloch envelopes
+ * (the field times exp(-i q_inc . r)), the right-hand side the incident envelope.
+ * Must precede psfd_set_illumination (it discards the current illuminations). The kernel is
+ * tabulated per illumination: (nf/2 + 1) nx ny entries of 32 B (FP64) + 16 B (FP32) per
+ * illumination slot, allocated here under the context's budget. The diffraction-order calls
+ * keep their periodic meaning and are not defined for this kind.
+ * Errors: PSFD_E_ARG (unknown kind, R <= 0, R above a transverse period, nf too short),
+ * PSFD_E_BUDGET / PSFD_E_NOMEM. */
+#define PSFD_GREEN_PERIODIC 0
+#define PSFD_GREEN_SPHERICAL 1
+int psfd_set_green(psfd_ctx* ctx, int kind, double R);
+
 /* CUDA graphs for the Krylov loop (on by default; no counterpart in the paper, which states
  * no execution model). Each engine tick runs check_every Krylov iterations of the active
  * illuminations; that launch sequence depends only on the batch width, the method and the

@@ -110,13 +110,24 @@ class IsolatedProblem:
     theta: float = 0.0
     phi: float = 0.0
     pol: int = 0
+    # Bloch envelopes: the unknown is the field times exp(-i q_inc . r_perp), so the kernel is
+    # taken at k + q_inc and E_inc becomes e exp(-i beta z) (the same linear convolution, on a
+    # k-grid shifted by q_inc)
+    bloch: bool = False
+
+
+def _q_inc(p: IsolatedProblem):
+    kb = 2 * math.pi / p.wavelength * math.sqrt(p.eps_bg)
+    th, ph = math.radians(p.theta), math.radians(p.phi)
+    return kb * math.sin(th) * math.cos(ph), kb * math.sin(th) * math.sin(ph)
 
 
 def isolated_kernel(p: IsolatedProblem) -> np.ndarray:
-    """F[G_R] at the grid wavenumbers, array (3, 3, nz, ny, nx)."""
+    """F[G_R] at the grid wavenumbers (shifted by q_inc for Bloch envelopes), (3, 3, nz, ny, nx)."""
     kb = 2 * math.pi / p.wavelength * math.sqrt(p.eps_bg)
-    kx = 2 * math.pi * np.fft.fftfreq(p.nx, p.dx)
-    ky = 2 * math.pi * np.fft.fftfreq(p.ny, p.dy)
+    qix, qiy = _q_inc(p) if p.bloch else (0.0, 0.0)
+    kx = qix + 2 * math.pi * np.fft.fftfreq(p.nx, p.dx)
+    ky = qiy + 2 * math.pi * np.fft.fftfreq(p.ny, p.dy)
     kz = 2 * math.pi * np.fft.fftfreq(p.nz, p.dz)
     KZ, KY, KX = np.meshgrid(kz, ky, kx, indexing="ij")
     kk = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)
@@ -143,7 +154,10 @@ def isolated_rhs(p: IsolatedProblem) -> np.ndarray:
     y = np.arange(p.ny) * p.dy
     x = np.arange(p.nx) * p.dx
     Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
-    phase = np.exp(1j * (qx * X + qy * Y - beta[0, 0] * Z))
+    if p.bloch:
+        phase = np.exp(-1j * beta[0, 0] * Z)
+    else:
+        phase = np.exp(1j * (qx * X + qy * Y - beta[0, 0] * Z))
     return e[:, None, None, None] * phase[None]
 
 

@@ -116,6 +116,12 @@ struct psfd_ctx {
   int *d_nord = nullptr, *d_mn = nullptr;
   double* d_ordout = nullptr;
   double2* fp_b0 = nullptr;  // [max_rhs][U]: b = E_inc + R[E_inc] during a fixed-point solve (lazy)
+  // isolated clip (psfd_set_green): spherically windowed kernel of radius green_R, tabulated
+  // per illumination slot when the illuminations are set; no stack reflection
+  int green = 0;
+  double green_R = 0.0;
+  double2* sph64 = nullptr;
+  float4* sph32 = nullptr;
 
   // CUDA graphs of the Krylov step (engine.cu): one per launch configuration, replayed on
   // `stream`; captured on the private stream cap_stream.

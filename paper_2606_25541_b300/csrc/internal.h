@@ -93,6 +93,10 @@ struct OpCall {
   const double* ktab64;    // [nf]: signed kz_l (FP64)
   const int* active;  // per global rhs, or null = all active
   int no_reflect;     // 1: leave R out, i.e. the free-space operator u - G*(V u)
+  // isolated clip: per (slot, l <= nf/2, mode) the spherically windowed kernel's (A, B/|k|^2)
+  // (FP32 float4 / FP64 pair of double2); null = the periodic z-windowed kernel
+  const float4* sph32;
+  const double2* sph64;
   // input stage: J = V * in, in = u | r + beta (u - omega v) | r - alpha v
   int in_mode;
   const C* u;

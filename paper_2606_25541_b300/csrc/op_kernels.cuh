@@ -581,6 +581,18 @@ __device__ __forceinline__ void dyadic_apply(C* c0, C* c1, C* c2, typename RealO
   *c2 = csub(cmul(S, csub(J2, cscale(ckJ, kz))), cmul(Es, J2));
 }
 
+// W = A J + (B/|k|^2) k (k.J) for k = (qx, qy, kz): the spherically windowed kernel of an
+// isolated clip (Eqs. (15)-(17)), in place.
+template <typename C>
+__device__ __forceinline__ void dyadic_sph(C* c0, C* c1, C* c2, typename RealOf<C>::T qx, typename RealOf<C>::T qy,
+                                           typename RealOf<C>::T kz, C A, C Bt) {
+  const C J0 = *c0, J1 = *c1, J2 = *c2;
+  const C t = cmul(Bt, cadd(cadd(cscale(J0, qx), cscale(J1, qy)), cscale(J2, kz)));
+  *c0 = cadd(cmul(A, J0), cscale(t, qx));
+  *c1 = cadd(cmul(A, J1), cscale(t, qy));
+  *c2 = cadd(cmul(A, J2), cscale(t, kz));
+}
+
 // Entries of the per-column reflection phase table exp(i beta dz j): j < 8 (fine
 // steps) and 8 j' for j' < NF/16 (coarse steps); the phase of plane pl is the
 // product of entries pl % 8 and 8 + pl / 8 (pl < nslab <= nf/2 - 1).
@@ -783,8 +795,31 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF>()) k_zcol(OpCall<C>
   const R kbr = (R)a.kb;
   const R cinv = (R)1 / (kbr * kbr);
   const R scale = (R)1 / ((R)NF * (R)nx * (R)ny);
+  const bool sph = F32 ? a.sph32 != nullptr : a.sph64 != nullptr;
+  if (sph) {
+    // isolated clip: tabulated A, B/|k|^2 of |k|, shared by l and nf - l
+    for (int i = threadIdx.x; i < tx * (HF + 1); i += NT) {
+      const int t = i / (HF + 1), l = i % (HF + 1);
+      const size_t o = (((size_t)slot * (HF + 1) + l) * ny + y) * nx + x0 + t;
+      C A, Bt;
+      if constexpr (F32) {
+        const float4 v = a.sph32[o];
+        A = mk(v.x, v.y);
+        Bt = mk(v.z, v.w);
+      } else {
+        A = from_c64<C>(a.sph64[2 * o]);
+        Bt = from_c64<C>(a.sph64[2 * o + 1]);
+      }
+      C* c0 = col + (0 * tx + t) * P;
+      C* c1 = col + (1 * tx + t) * P;
+      C* c2 = col + (2 * tx + t) * P;
+      dyadic_sph(c0 + fpad(l), c1 + fpad(l), c2 + fpad(l), cqx[t], cqy[t], kzs[l], A, Bt);
+      if (l > 0 && l < HF)
+        dyadic_sph(c0 + fpad(NF - l), c1 + fpad(NF - l), c2 + fpad(NF - l), cqx[t], cqy[t], kzs[NF - l], A, Bt);
+    }
+  }
   // pairs (l, nf - l) share S and E; l = 0 stands alone, l = nf/2 follows below
-  for (int i = threadIdx.x; i < tx * HF; i += NT) {
+  for (int i = threadIdx.x; i < (sph ? 0 : tx * HF); i += NT) {
     const int t = i / HF, l = i % HF;
     C E = cebl[t];
     if (l & 1) E = cneg(E);
@@ -797,7 +832,7 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF>()) k_zcol(OpCall<C>
     dyadic_apply(c0 + fpad(l), c1 + fpad(l), c2 + fpad(l), qx, qy, kzs[l], S, Es, cinv);
     if (l) dyadic_apply(c0 + fpad(NF - l), c1 + fpad(NF - l), c2 + fpad(NF - l), qx, qy, kzs[NF - l], S, Es, cinv);
   }
-  for (int t = threadIdx.x; t < tx; t += NT) {
+  for (int t = threadIdx.x; t < (sph ? 0 : tx); t += NT) {
     C E = cebl[t];
     if (HF & 1) E = cneg(E);
     C S, Es;

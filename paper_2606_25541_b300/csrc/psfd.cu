@@ -363,6 +363,22 @@ int ctx_set_rhs(psfd_ctx* ctx, int g0, int n, const double* theta_deg, const dou
   m.modes32 = ctx->modes32;
   m.anomaly = ctx->anomaly;
   RC(launch_modes(m, n, st));
+  if (ctx->green == PSFD_GREEN_SPHERICAL) {
+    SphArgs sa;
+    sa.slot0 = g0;
+    sa.nx = g.nx;
+    sa.ny = g.ny;
+    sa.nf = g.nf;
+    sa.dx = g.dx;
+    sa.dy = g.dy;
+    sa.dz = g.dz;
+    sa.kb = ctx->kb;
+    sa.R = ctx->green_R;
+    sa.slot_par = ctx->slot_par;
+    sa.t64 = ctx->sph64;
+    sa.t32 = ctx->sph32;
+    RC(launch_sph_table(sa, n, st));
+  }
   RC(launch_rhs(g0, n, ctx->rhsp, ctx->modes, g.nx, g.ny, g.nslab, g.dz, ctx->kb, ctx->b64 + (size_t)g0 * ctx->plan.U,
                 st));
   for (int i = 0; i < n; ++i) {
@@ -415,7 +431,11 @@ static OpCall<C> base_call(psfd_ctx* ctx, int rhs0, int nrhs, const C* V) {
   a.stream = ctx->stream;
   a.in_mode = IN_PLAIN;
   a.epi = EPI_AU;
-  a.no_reflect = ctx->no_reflect;
+  a.no_reflect = ctx->no_reflect || ctx->green == PSFD_GREEN_SPHERICAL;
+  if (ctx->green == PSFD_GREEN_SPHERICAL) {
+    a.sph64 = ctx->sph64;
+    a.sph32 = ctx->sph32;
+  }
   return a;
 }
 template OpCall<float2> base_call<float2>(psfd_ctx*, int, int, const float2*);
@@ -508,6 +528,28 @@ int psfd_destroy(psfd_ctx* ctx) {
 int psfd_set_stream(psfd_ctx* ctx, void* stream) {
   if (!ctx) return PSFD_E_ARG;
   ctx->stream = (cudaStream_t)stream;
+  return PSFD_OK;
+}
+
+int psfd_set_green(psfd_ctx* ctx, int kind, double R) {
+  if (!ctx) return PSFD_E_ARG;
+  if (kind == PSFD_GREEN_PERIODIC) {
+    ctx->green = kind;
+    ctx->have_illum = false;
+    return PSFD_OK;
+  }
+  if (kind != PSFD_GREEN_SPHERICAL) return ctx->fail(PSFD_E_ARG, "unknown Green's function kind");
+  const psfd_grid& g = ctx->g;
+  if (!(R > 0.0) || R > g.nx * g.dx || R > g.ny * g.dy || g.nslab * g.dz + R > g.nf * g.dz)
+    return ctx->fail(PSFD_E_ARG, "window radius must be positive, within the transverse periods, and nf dz >= nslab dz + R");
+  if (!ctx->sph64) {
+    const size_t n = (size_t)ctx->max_rhs * (g.nf / 2 + 1) * ctx->plan.plane;
+    RC(ctx->dalloc(&ctx->sph64, 2 * n));
+    if (ctx->precision == PSFD_FP32_REFINED) RC(ctx->dalloc(&ctx->sph32, n));
+  }
+  ctx->green = kind;
+  ctx->green_R = R;
+  ctx->have_illum = false;  // the tables are built with the illuminations
   return PSFD_OK;
 }
 

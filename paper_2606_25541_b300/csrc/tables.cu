@@ -252,6 +252,70 @@ __global__ void k_modes(ModesArgs a) {
   }
 }
 
+// (e^z - 1)/z for z = i a (a real): sin(a)/a + i 2 sin^2(a/2)/a, by its Taylor series near 0.
+__device__ __forceinline__ double2 phi1_imag(double a) {
+  if (fabs(a) < 1e-3) {
+    const double a2 = a * a;
+    return make_double2(1.0 - a2 / 6.0 + a2 * a2 / 120.0, a / 2.0 - a * a2 / 24.0 + a * a2 * a2 / 720.0);
+  }
+  const double s = sin(0.5 * a);
+  return make_double2(sin(a) / a, 2.0 * s * s / a);
+}
+
+// One thread per (mode, l): A(|k|) and B(|k|)/|k|^2 of the windowed dyadic kernel.
+//   F[g_R](k) = (1/k) int_0^R exp(i kb r) sin(k r) dr: (E - 1)/(kb^2 - k^2) with
+//   E = exp(i kb R)(cos kR - i (kb/k) sin kR), or, near k = kb, R (phi1(i(kb+k)R) -
+//   phi1(i(kb-k)R)) / (2ik); at k = 0, (exp(i kb R)(1 - i kb R) - 1)/kb^2.
+//   h(k) = 4 pi R^2 g'(R) j1(kR)/(kb^2 kR) = exp(i kb R)(i kb R - 1) j1(kR)/(kR kb^2),
+//   A = F[g_R] + h, B = -F[g_R] - 3h - 1/kb^2 (k > 0); B khat khat^T vanishes at k = 0.
+__global__ void k_sph_table(SphArgs a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, sl = blockIdx.z;
+  const int HF = a.nf / 2;
+  if (x >= a.nx) return;
+  const int slot = a.slot0 + sl;
+  const double two_pi = 6.283185307179586476925286766559;
+  const double qx = a.slot_par[4 * slot] + two_pi * fft_freq(x, a.nx) / (a.nx * a.dx);
+  const double qy = a.slot_par[4 * slot + 1] + two_pi * fft_freq(y, a.ny) / (a.ny * a.dy);
+  const double kb = a.kb, R = a.R, kb2 = kb * kb;
+  const double2 ekR = make_double2(cos(kb * R), sin(kb * R));
+  const double scale = 1.0 / ((double)a.nf * a.nx * a.ny);
+  for (int l = 0; l <= HF; ++l) {
+    const double kz = two_pi * l / (a.nf * a.dz);
+    const double k2 = qx * qx + qy * qy + kz * kz, k = sqrt(k2);
+    double2 f;
+    if (k < 1e-12 * kb) {
+      f = cscale(csub(cmul(ekR, make_double2(1.0, -kb * R)), make_double2(1.0, 0.0)), 1.0 / kb2);
+    } else if (fabs(k - kb) * R < 0.5) {
+      const double2 d = csub(phi1_imag((kb + k) * R), phi1_imag((kb - k) * R));
+      f = make_double2(R * d.y / (2.0 * k), -R * d.x / (2.0 * k));  // R d / (2 i k)
+    } else {
+      const double2 E = cmul(ekR, make_double2(cos(k * R), -(kb / k) * sin(k * R)));
+      f = cscale(csub(E, make_double2(1.0, 0.0)), 1.0 / (kb2 - k2));
+    }
+    const double x1 = k * R;
+    const double j1x = x1 < 1e-2 ? 1.0 / 3.0 - x1 * x1 / 30.0 + x1 * x1 * x1 * x1 / 840.0
+                                 : (sin(x1) - x1 * cos(x1)) / (x1 * x1 * x1);
+    const double2 h = cscale(cmul(ekR, make_double2(-1.0, kb * R)), j1x / kb2);
+    const double2 A = cadd(f, h);
+    double2 Bt = make_double2(0.0, 0.0);
+    if (k >= 1e-12 * kb) {
+      const double2 B = csub(csub(cneg(f), cscale(h, 3.0)), make_double2(1.0 / kb2, 0.0));
+      Bt = cscale(B, 1.0 / k2);
+    }
+    const size_t o = (((size_t)slot * (HF + 1) + l) * a.ny + y) * a.nx + x;
+    a.t64[2 * o] = cscale(A, scale);
+    a.t64[2 * o + 1] = cscale(Bt, scale);
+    if (a.t32)
+      a.t32[o] = make_float4((float)(A.x * scale), (float)(A.y * scale), (float)(Bt.x * scale), (float)(Bt.y * scale));
+  }
+}
+
+int launch_sph_table(const SphArgs& a, int n_slots, cudaStream_t st) {
+  dim3 grid((a.nx + 127) / 128, a.ny, n_slots);
+  k_sph_table<<<grid, 128, 0, st>>>(a);
+  return launched();
+}
+
 int launch_modes(const ModesArgs& a, int n_slots, cudaStream_t st) {
   dim3 grid((a.nx + 127) / 128, a.ny, n_slots);
   k_modes<<<grid, 128, 0, st>>>(a);

@@ -45,6 +45,17 @@ struct ModesArgs {
   int* anomaly;
 };
 
+// Spherically windowed dyadic Green's function of an isolated clip (Sec. 3, Eqs. (13)-(17)):
+// F[G_R](k) = A(|k|) I + B(|k|) khat khat^T at k = (q_x, q_y, kz_l) for l = 0 .. nf/2, stored
+// per slot, l, mode as (A, B/|k|^2) times 1/(nf nx ny) (the inverse FFT normalisation).
+struct SphArgs {
+  int slot0, nx, ny, nf;
+  double dx, dy, dz, kb, R;
+  const double* slot_par;  // [slot][4]: q_inc x, q_inc y, ...
+  double2* t64;            // [slot][nf/2 + 1][ny][nx][2]
+  float4* t32;             // [slot][nf/2 + 1][ny][nx]
+};
+
 struct OrdersArgs {
   int nx, ny, nslab;
   double dx, dy, dz, kb;
@@ -64,6 +75,7 @@ int launch_modes(const ModesArgs& a, int n_slots, cudaStream_t st);
 int launch_rhs(int rhs0, int nrhs, RhsParam* rp, const ModeEntry* modes, int nx, int ny, int nslab, double dz,
                double kb, double2* b, cudaStream_t st);
 int launch_orders(const OrdersArgs& a, int nrhs, cudaStream_t st);
+int launch_sph_table(const SphArgs& a, int n_slots, cudaStream_t st);
 int launch_norm(int n, int nblk, int rhs0, int nrhs, const int* mask, const double2* v, double2* partials,
                 int maxblk, int mode, double tol2, KScal* sc, int* act, cudaStream_t st);
 template <typename C>

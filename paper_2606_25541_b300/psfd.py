@@ -28,6 +28,7 @@ class Grid(ctypes.Structure):
 
 
 BICGSTAB, GMRES = 0, 1
+GREEN_PERIODIC, GREEN_SPHERICAL = 0, 1
 
 
 class SolveOpts(ctypes.Structure):
@@ -73,6 +74,7 @@ _SIGS = {
     "psfd_set_potential": (_I, [_P, _P, _I]),
     "psfd_set_illumination": (_I, [_P, _I, _D, _D, _IP]),
     "psfd_set_graphs": (_I, [_P, _I]),
+    "psfd_set_green": (_I, [_P, _I, ctypes.c_double]),
     "psfd_solve": (_I, [_P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Report)]),
     "psfd_solve_fixed_point": (_I, [_P, ctypes.POINTER(SolveOpts), _I, ctypes.c_double, ctypes.POINTER(Report)]),
     "psfd_num_orders": (_I, [_P, _I, _IP]),
@@ -263,6 +265,11 @@ class Solver:
             e = _c128(eps)
             self._keep_eps = e
             self._check(self.lib.psfd_set_potential(self.ctx, e.ctypes.data_as(ctypes.c_void_p), HOST))
+
+    def set_green(self, kind: int, R: float = 0.0):
+        """GREEN_PERIODIC (default) or GREEN_SPHERICAL with window radius R (isolated clip);
+        call before set_illumination."""
+        self._check(self.lib.psfd_set_green(self.ctx, int(kind), float(R)))
 
     def set_graphs(self, enable: bool):
         """Replay the Krylov step as a CUDA graph (default) or launch its kernels one by one."""
