@@ -79,6 +79,8 @@ def parse_args(argv=None):
                     help="layer-count study: comma-separated Mo/Si bilayer counts (decomposition, outer fixed "
                          "point and stack meshed into the domain on the 256 x 256 crop)")
     ap.add_argument("--mesh-max", type=int, default=10, help="largest bilayer count --layers meshes into the domain")
+    ap.add_argument("--isolated", action="store_true",
+                    help="an isolated clip with the spherically windowed kernel (block absorber, padded box)")
     ap.add_argument("--small", action="store_true",
                     help="the 32 x 32 x 30 contact-hole clip (one illumination): ms per solve, CUDA graphs on/off")
     ap.add_argument("--fixed-point", action="store_true",
@@ -409,6 +411,60 @@ def run_layers(args):
             row["efficiency_rel_diff"] = diffs
         out["rows"].append(row)
         print(json.dumps(row), flush=True)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_isolated(args):
+    """An isolated clip (the paper's spherically windowed dyadic kernel, Sec. 3, Eqs. (13)-(18)):
+    a 40 x 40 nm absorber block, 60 nm thick (n = 0.94 + 0.04i, 2 nm cells), in a 256 x 256 nm
+    transverse period (128 x 128 cells, vacuum around the block) with a z column of 256 nm
+    (nf = 128); R = 83 nm exceeds the block's diameter, and period and column exceed its extent
+    plus R. Two illuminations (6 deg s, 0 deg p), FP32 with FP64 refinement to --tol, no stack.
+    Reported: solves/s over --steps solves of the pair and operator applications/s."""
+    import torch
+    from paper_2606_25541_b300 import psfd
+    n, d, nslab, nf = 128, 2.0, 30, 128
+    R = 1.001 * d * math.sqrt(20 ** 2 + 20 ** 2 + 30 ** 2)
+    eps = np.ones((nslab, n, n), np.complex128)
+    eps[:, 54:74, 54:74] = (0.94 + 0.04j) ** 2
+    g = psfd.make_grid(n, n, nslab, nf, d, d, d, 13.5)
+    stream = torch.cuda.current_stream()
+    s = psfd.Solver(g, psfd.FP32_REFINED, 2, stream=stream)
+    s.set_stack(np.zeros(0, np.complex128), np.zeros(0), 1.0)
+    s.set_green(psfd.GREEN_SPHERICAL, R)
+    s.set_potential(eps)
+    kw = dict(tol=args.tol, inner_tol=args.inner_tol, max_iter=400, max_outer=12)
+
+    def step():
+        s.set_illumination([6.0, 0.0], [0.0, 0.0], [0, 1])
+        return s.solve(**kw)
+
+    for _ in range(max(args.warmup, 1)):
+        rep = step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        rep = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    u = torch.tensor(layouts.random_field((2, 3, nslab, n, n), seed=1), dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(u)
+    s.apply(u, y)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(20):
+        s.apply(u, y)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    out = {"mode": "isolated_clip", "workload": "block_40x40x60nm_in_256x256x256nm_2rhs", "R_nm": R,
+           "tol": args.tol, "solves_per_s": 2e3 / ms, "ms_per_pair": ms, "iterations": rep["iterations"],
+           "outer": rep["outer"], "relres": rep["relres"],
+           "fp32_applications_per_s": 20e3 / a0.elapsed_time(a1)}
+    s.close()
     print(json.dumps(out), flush=True)
     return 0
 
@@ -883,7 +939,7 @@ def solver_bytes(prob) -> float:
 def main(argv=None):
     args = parse_args(argv)
     headline = not (args.apply or args.sweep or args.large or args.crosscheck or args.fixed_point or args.small
-                    or args.layers)
+                    or args.layers or args.isolated)
     if args.tol is None:
         args.tol = HEADLINE_TOL if headline else DEFAULT_TOL
     if args.inner_tol is None:
@@ -904,6 +960,8 @@ def main(argv=None):
         return run_small(args)
     if args.layers:
         return run_layers(args)
+    if args.isolated:
+        return run_isolated(args)
     if args.serve_only:
         sizes = tuple(int(s) for s in args.serve_sizes.split(","))
         print(json.dumps({"mode": "serving", **run_serving(args.serve, sizes, args.tol, args.inner_tol)}), flush=True)
