@@ -7,3 +7,4 @@ recursion, Green's function, Krylov solver and extraction, all in complex128.
 """
 from .psfd_oracle import *  # noqa: F401,F403
 from .isolated_oracle import *  # noqa: F401,F403
+from .differential_oracle import *  # noqa: F401,F403
