@@ -81,6 +81,9 @@ def parse_args(argv=None):
     ap.add_argument("--mesh-max", type=int, default=10, help="largest bilayer count --layers meshes into the domain")
     ap.add_argument("--isolated", action="store_true",
                     help="an isolated clip with the spherically windowed kernel (block absorber, padded box)")
+    ap.add_argument("--differential", action="store_true",
+                    help="FP64 applications/s of the differential PSFD operator (PML column) and of the "
+                         "Lippmann-Schwinger operator on the same 64 x 64 x 30 clip")
     ap.add_argument("--small", action="store_true",
                     help="the 32 x 32 x 30 contact-hole clip (one illumination): ms per solve, CUDA graphs on/off")
     ap.add_argument("--fixed-point", action="store_true",
@@ -466,6 +469,67 @@ def run_isolated(args):
            "fp32_applications_per_s": 20e3 / a0.elapsed_time(a1)}
     s.close()
     print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_differential(args):
+    """Per-application cost of the two formulations of Sec. 3 on one seeded 64 x 64 x 30 clip at
+    2 nm (one illumination, 6 deg): the differential PSFD operator on its z column (30 nm PML,
+    34 nm vacuum spacer above and below the clip: 128 planes) and the Lippmann-Schwinger operator
+    on the clip's own planes (nf = 64, no stack), both in FP64. Reported: applications/s of each,
+    their ratio, and the differential apply's effective HBM rate (E and eps read, out written
+    once: 112 bytes per cell), so that the preconditioner study's operator counts convert to
+    time."""
+    import torch
+    from paper_2606_25541_b300 import psfd
+    n, d, nslab, nf, npml, nz = 64, 2.0, 30, 64, 15, 128
+    prob = layouts.small_clip(nx=n, ny=n, nslab=nslab, dx=d, dz=d, seed=7, stack=layouts.empty_stack(),
+                              theta=(6.0,), pol=(0,))
+    eps_col = np.ones((nz, n, n), np.complex128)
+    z0 = (nz - nslab) // 2
+    eps_col[z0:z0 + nslab] = prob.eps
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream()
+    reps = max(args.steps, 1) * 10
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    eps_d = torch.from_numpy(eps_col).to(dev)
+    E = torch.from_numpy(layouts.random_field((3, nz, n, n), seed=2)).to(dev)
+    out, work = torch.empty_like(E), torch.empty_like(E)
+    sp = stream.cuda_stream
+
+    def diff_apply():
+        st = psfd.apply_differential(n, nz, npml, d, d, 13.5, 1.0, 6.0, 0.0, eps_d, E, out, work, stream=sp)
+        if st != 0:
+            raise RuntimeError(psfd.strerror(st))
+
+    ms_diff = timed(diff_apply)
+    g = psfd.make_grid(n, n, nslab, nf, d, d, d, 13.5)
+    s = psfd.Solver(g, psfd.FP64, 1, stream=stream)
+    s.set_stack(np.zeros(0, np.complex128), np.zeros(0), 1.0)
+    s.set_potential(prob.eps)
+    s.set_illumination([6.0], [0.0], [0])
+    u = torch.from_numpy(layouts.random_field((1, 3, nslab, n, n), seed=3)).to(dev)
+    y = torch.empty_like(u)
+    ms_ls = timed(lambda: s.apply(u, y, precision=psfd.FP64))
+    s.close()
+    cells = nz * n * n
+    print(json.dumps({"mode": "differential_vs_ls_apply", "workload": "clip_64x64x30_2nm_column_128_planes",
+                      "dtype": "c128", "differential_ms": ms_diff, "differential_applications_per_s": 1e3 / ms_diff,
+                      "differential_gbs_112B_per_cell": 112.0 * cells / (ms_diff * 1e6),
+                      "ls_ms": ms_ls, "ls_applications_per_s": 1e3 / ms_ls,
+                      "ratio_ls_over_differential_ms": ms_ls / ms_diff, "reps": reps}), flush=True)
     return 0
 
 
@@ -939,7 +1003,7 @@ def solver_bytes(prob) -> float:
 def main(argv=None):
     args = parse_args(argv)
     headline = not (args.apply or args.sweep or args.large or args.crosscheck or args.fixed_point or args.small
-                    or args.layers or args.isolated)
+                    or args.layers or args.isolated or args.differential)
     if args.tol is None:
         args.tol = HEADLINE_TOL if headline else DEFAULT_TOL
     if args.inner_tol is None:
@@ -962,6 +1026,8 @@ def main(argv=None):
         return run_layers(args)
     if args.isolated:
         return run_isolated(args)
+    if args.differential:
+        return run_differential(args)
     if args.serve_only:
         sizes = tuple(int(s) for s in args.serve_sizes.split(","))
         print(json.dumps({"mode": "serving", **run_serving(args.serve, sizes, args.tol, args.inner_tol)}), flush=True)

@@ -358,6 +358,30 @@ int psfd_apply_fp32_static(const psfd_grid* grid, int n_layers, const double* n_
                            const double* thickness_nm, const double* n_sub, double theta_deg,
                            double phi_deg, const void* eps, const void* u, void* out, void* stream);
 
+/* ---------------------------------------------------------------------------------
+ * The conventional differential PSFD operator (Sec. 3, Eqs. (4)-(7)), the formulation the
+ * paper measures its Lippmann-Schwinger form against:
+ *   out = curl curl E - k0^2 eps E
+ * on Bloch envelopes of a periodic clip whose z column (free space, PML at both ends) holds
+ * the absorber. Derivatives are spectral (Eq. (6)): along x and y exact per transverse mode
+ * (d/dx -> i q_x, q = q_inc + 2 pi m / P), along z by an FFT over the column divided by the
+ * stretch s(z) = 1 + i sigma(z) (Eq. (7)). The paper gives no PML profile; this one is
+ * sigma(z) = sigma_max (depth / L)^3 over n_pml planes at each end, sigma_max =
+ * -4 ln(1e-8) / (2 kb L), L = n_pml dz, plane k at z = (k + 1/2) dz. Complex FP64 throughout.
+ *   n                 transverse points, nx = ny = n in {8, 16, 32, 64}; dx = dy
+ *   nz                planes of the column in {32, 64, 128}; 0 <= 2 n_pml < nz
+ *   wavelength, eps_bg, theta_deg, phi_deg   as in psfd_grid / psfd_set_illumination
+ *   eps               device, complex double [nz][n][n]
+ *   E, out            device, complex double [3][nz][n][n]; must not alias
+ *   work              device, complex double [3][nz][n][n], caller-owned scratch
+ *   stream            cudaStream_t (NULL = legacy default stream)
+ * Three launches (FFT_xy; per-mode curls with the z derivatives; inverse FFT_xy with the
+ * k0^2 eps term), no allocation, no synchronisation. Returns PSFD_OK, PSFD_E_ARG
+ * (unsupported size, null pointer, non-positive spacing) or PSFD_E_CUDA. */
+int psfd_apply_differential(int n, int nz, int n_pml, double dx, double dz, double wavelength, double eps_bg,
+                            double theta_deg, double phi_deg, const double* eps, const double* E, double* out,
+                            double* work, void* stream);
+
 /* Test hook for the device FFT: `count` contiguous transforms of length n, in place, on
  * device data (complex double if fp64 else complex float). inverse = 1 applies the
  * unnormalised inverse. Runs on the legacy default stream and synchronises. */

@@ -88,6 +88,8 @@ _SIGS = {
     "psfd_test_fft": (_I, [_I, _I, _I, _I, _P]),
     "psfd_apply_fp32_static": (_I, [ctypes.POINTER(Grid), _I, _D, _D, _D, ctypes.c_double, ctypes.c_double, _P,
                                     _P, _P, _P]),
+    "psfd_apply_differential": (_I, [_I, _I, _I, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, _P, _P, _P, _P]),
     "psfd_server_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _I, ctypes.POINTER(SolveOpts)]),
     "psfd_server_destroy": (_I, [_P]),
     "psfd_server_submit": (_I, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)]),
@@ -116,6 +118,18 @@ def apply_fp32_static(grid: Grid, n_layers, thickness, n_sub, theta_deg, phi_deg
                                          _dptr(ns), float(theta_deg), float(phi_deg),
                                          ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(u.data_ptr()),
                                          ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
+
+
+def apply_differential(n, nz, n_pml, dx, dz, wavelength, eps_bg, theta_deg, phi_deg, eps, E, out, work,
+                       stream=None):
+    """out = curl curl E - k0^2 eps E (the differential PSFD operator, PML in z) on the GPU.
+    eps: complex128 CUDA tensor (nz, n, n); E, out, work: complex128 CUDA tensors
+    (3, nz, n, n), work being scratch. Returns the status code."""
+    return load().psfd_apply_differential(int(n), int(nz), int(n_pml), float(dx), float(dz), float(wavelength),
+                                          float(eps_bg), float(theta_deg), float(phi_deg),
+                                          ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(E.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(work.data_ptr()),
+                                          _stream_ptr(stream))
 
 
 def launch_count() -> int:
