@@ -51,6 +51,7 @@ extern "C" {
 
 #define PSFD_FP64 0         /* every step in complex FP64 */
 #define PSFD_FP32_REFINED 1 /* complex FP32 Krylov inside FP64 defect correction */
+#define PSFD_FP64_DF 2      /* psfd_apply only: FP64 data, z pass in double-float (see below) */
 
 #define PSFD_HOST 0   /* pointer argument is host memory */
 #define PSFD_DEVICE 1 /* pointer argument is device memory of the context's GPU */
@@ -158,6 +159,20 @@ int psfd_set_green(psfd_ctx* ctx, int kind, double R);
  * Profiling (psfd_profile_enable) bypasses the graphs. */
 int psfd_set_graphs(psfd_ctx* ctx, int enable);
 
+/* Arithmetic of the FP64 residual r = b - A x that certifies a PSFD_FP32_REFINED solve
+ * (no counterpart in the paper; the defect correction is not one of its steps).
+ *   PSFD_RESID_FP64    every step in FP64;
+ *   PSFD_RESID_DFLOAT  (default) the z pass's transforms and dyadic products in double-float
+ *                      (a pair of FP32 numbers, about 48 significant bits, ~1e-14 normwise)
+ *                      on nf = 64 or 128 with the periodic kernel, FP64 elsewhere. B300 runs
+ *                      FP32 about sixty times faster than FP64, and the refinement needs the
+ *                      residual only to well below its tolerance.
+ * Vectors, the xy passes, the Green's scalars and the reflection stay FP64 either way.
+ * Contexts of precision PSFD_FP64 ignore the setting. Errors: PSFD_E_ARG (unknown kind). */
+#define PSFD_RESID_FP64 0
+#define PSFD_RESID_DFLOAT 1
+int psfd_set_residual_arith(psfd_ctx* ctx, int kind);
+
 /* Planar stack below z_top (Sec. 2, Fig. 1): n_layers layers listed top to bottom with
  * complex refractive index n_complex[2*j], n_complex[2*j+1] and thickness thickness_nm[j],
  * on a substrate of index n_sub[0] + i n_sub[1]. eps = n^2. n_layers may be 0. */
@@ -221,7 +236,9 @@ int psfd_diffraction_orders(psfd_ctx* ctx, int rhs, int capacity, int* n_orders,
 
 /* One operator application out = A u for right-hand sides rhs0 .. rhs0+n_rhs-1 with the
  * current potential and illumination tables (the Krylov hot path, Eq. (18) with Eq. (9)).
- * precision selects complex FP64 (double pairs) or complex FP32 (float pairs) data.
+ * precision selects complex FP64 (double pairs) or complex FP32 (float pairs) data;
+ * PSFD_FP64_DF applies the operator as a refined solve's residual does under
+ * PSFD_RESID_DFLOAT (FP64 data, the z pass in double-float where supported).
  * u and out are device arrays [n_rhs][3][nslab][ny][nx]; they must not alias. */
 int psfd_apply(psfd_ctx* ctx, int precision, int rhs0, int n_rhs, const void* u, void* out);
 

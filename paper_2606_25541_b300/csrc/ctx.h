@@ -135,6 +135,7 @@ struct psfd_ctx {
   std::vector<GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;
   bool use_graphs = true;
+  int resid_arith = PSFD_RESID_DFLOAT;  // arithmetic of the refined solve's FP64 residual
   unsigned long long graph_clock = 0;
   void drop_graphs() {
     for (auto& e : graphs) {

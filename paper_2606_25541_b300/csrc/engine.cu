@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "dfloat_ops.h"
 
 namespace psfd {
 
@@ -198,6 +199,11 @@ int inner_step(psfd_ctx* ctx, const psfd_solve_opts& o, int hi, bool f32) {
   return PSFD_OK;
 }
 
+// Whether the refined solve's FP64 residual runs its z pass in double-float.
+static bool resid_df(const psfd_ctx* ctx) {
+  return ctx->precision == PSFD_FP32_REFINED && ctx->resid_arith == PSFD_RESID_DFLOAT;
+}
+
 // r64 = b - A x64 with the side spectra, then ||r64||^2 into sc64 / act64, for the slots in mask.
 int fp64_residual(psfd_ctx* ctx, const int* mask, double tol, int hi) {
   OpCall<double2> a = base_call64(ctx, 0, hi);
@@ -209,7 +215,7 @@ int fp64_residual(psfd_ctx* ctx, const int* mask, double tol, int hi) {
   a.work = ctx->work64;
   a.dot_mask = DOT_OUT_OUT;
   a.side = ctx->side64;
-  const int nb = op_apply<double2>(a);
+  const int nb = resid_df(ctx) ? op_apply_df(a) : op_apply<double2>(a);
   RC(nb);
   RC(launch_norm((int)ctx->plan.U, nb, 0, hi, mask, nullptr, ctx->partials, ctx->plan.maxblk, 1, tol * tol,
                  ctx->sc64, ctx->act64, ctx->stream));
@@ -488,7 +494,7 @@ int engine_fixed_point(psfd_ctx* ctx, const psfd_solve_opts& o, int max_steps, d
     a.work = ctx->work64;
     a.dot_mask = DOT_OUT_OUT;
     a.side = ctx->side64;
-    const int nb = op_apply<double2>(a);
+    const int nb = resid_df(ctx) ? op_apply_df(a) : op_apply<double2>(a);
     if (nb < 0) {
       rc = nb;
       break;

@@ -1,4 +1,5 @@
 // op_f64.cu -- complex FP64 instantiation of the operator and the Krylov solvers.
+#include "dfloat_ops.h"
 #include "gmres.cuh"
 #include "solver.cuh"
 
@@ -18,6 +19,44 @@ template <> int gmres_iterate<double2>(const KrylovCall<double2>& k, int iters) 
 }
 template <> int gmres_finish<double2>(const KrylovCall<double2>& k, const int* mask) {
   return gmres_finish_impl<double2>(k, mask);
+}
+
+// The FP64 operator with the z pass in double-float (zcol_df.cu) where that kernel handles
+// the call: K1 and K3 as in op_apply<double2>, the profile class of each pass unchanged.
+int op_apply_df(const OpCall<double2>& a0) {
+  if (!zcol_df_supported(a0)) return op_apply_impl<double2>(a0);
+  const bool prof = prof_on();
+  OpCall<double2> a = a0;
+  PassCost cost;
+  double cx = 0, cz = 0;
+  if (prof) {
+    cost = pass_cost(a);
+    pass_ctas(a, &cx, &cz);
+  }
+  int rc;
+  a.ctac = prof ? prof_begin(PK_FWD64, a.stream) : nullptr;
+  switch (a.in_mode) {
+    case IN_PLAIN: rc = dispatch_fwd<double2, IN_PLAIN>(a); break;
+    case IN_PUPDATE: rc = dispatch_fwd<double2, IN_PUPDATE>(a); break;
+    case IN_SUPDATE: rc = dispatch_fwd<double2, IN_SUPDATE>(a); break;
+    default: return PSFD_E_ARG;
+  }
+  if (rc) return rc;
+  if (prof) prof_end(PK_FWD64, a.stream, cost.bytes[0], cost.flops[0], cx);
+  a.ctac = prof ? prof_begin(PK_Z64, a.stream) : nullptr;
+  if ((rc = launch_zcol_df(a))) return rc;
+  if (prof) prof_end(PK_Z64, a.stream, cost.bytes[1], cost.flops[1], (double)a.ny * a.nrhs * (a.nx < 8 ? 1 : a.nx / 8));
+  if (a.epi == EPI_NONE) return blocks_per_rhs_t<double2>(a.nx, a.ny, a.nslab);
+  const double2* uin = a.in_mode == IN_PLAIN ? a.u : a.ustore;
+  a.ctac = prof ? prof_begin(PK_INV64, a.stream) : nullptr;
+  switch (a.epi) {
+    case EPI_AU: rc = dispatch_inv<double2, EPI_AU>(a, uin); break;
+    case EPI_RESID: rc = dispatch_inv<double2, EPI_RESID>(a, uin); break;
+    default: return PSFD_E_ARG;
+  }
+  if (rc) return rc;
+  if (prof) prof_end(PK_INV64, a.stream, cost.bytes[2], cost.flops[2], cx);
+  return blocks_per_rhs_t<double2>(a.nx, a.ny, a.nslab);
 }
 
 int op_blocks_per_rhs(int nx, int ny, int nslab, bool fp64) {

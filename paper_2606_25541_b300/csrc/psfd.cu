@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "dfloat_ops.h"
 
 using namespace psfd;
 
@@ -507,7 +508,8 @@ int psfd_supported_length(int n) { return fft_length_supported(n) ? 1 : 0; }
 
 int psfd_workspace_bytes(const psfd_grid* grid, int precision, int max_rhs, size_t* bytes) {
   std::string why;
-  if (!bytes || !grid_ok(grid, why) || max_rhs < 1) return PSFD_E_ARG;
+  if (!bytes || !grid_ok(grid, why) || max_rhs < 1 || (precision != PSFD_FP64 && precision != PSFD_FP32_REFINED))
+    return PSFD_E_ARG;
   *bytes = make_plan(*grid, precision, max_rhs, 1).bytes;
   return PSFD_OK;
 }
@@ -563,6 +565,13 @@ int psfd_set_graphs(psfd_ctx* ctx, int enable) {
   return PSFD_OK;
 }
 
+int psfd_set_residual_arith(psfd_ctx* ctx, int kind) {
+  if (!ctx) return PSFD_E_ARG;
+  if (kind != PSFD_RESID_FP64 && kind != PSFD_RESID_DFLOAT) return ctx->fail(PSFD_E_ARG, "unknown residual arithmetic");
+  ctx->resid_arith = kind;
+  return PSFD_OK;
+}
+
 int psfd_set_stack(psfd_ctx* ctx, int n_layers, const double* n_complex, const double* thickness_nm,
                    const double* n_sub) {
   if (!ctx) return PSFD_E_ARG;
@@ -611,12 +620,12 @@ int psfd_apply(psfd_ctx* ctx, int precision, int rhs0, int n_rhs, const void* u,
   if (!ctx->have_illum || !ctx->have_potential) return ctx->fail(PSFD_E_STATE, "apply before set_potential/illumination");
   if (!u || !out || rhs0 < 0 || n_rhs < 1 || rhs0 + n_rhs > ctx->n_rhs)
     return ctx->fail(PSFD_E_ARG, "invalid apply arguments");
-  if (precision == PSFD_FP64) {
+  if (precision == PSFD_FP64 || precision == PSFD_FP64_DF) {
     OpCall<double2> a = base_call64(ctx, rhs0, n_rhs);
     a.u = (const double2*)u;
     a.out = (double2*)out;
     a.work = ctx->work64;
-    RC(op_apply<double2>(a));
+    RC(precision == PSFD_FP64 ? op_apply<double2>(a) : op_apply_df(a));
   } else if (precision == PSFD_FP32_REFINED) {
     OpCall<float2> a = base_call32(ctx, rhs0, n_rhs);
     a.u = (const float2*)u;

@@ -18,6 +18,8 @@ OK = 0
 E_ARG, E_NOMEM, E_BUDGET, E_CUDA, E_NOT_CONVERGED, E_BREAKDOWN, E_ANOMALY, E_TIMEOUT, E_STATE = \
     -1, -2, -3, -4, -5, -6, -7, -8, -9
 FP64, FP32_REFINED = 0, 1
+FP64_DF = 2  # apply only: FP64 data, z pass in double-float
+RESID_FP64, RESID_DFLOAT = 0, 1
 HOST, DEVICE = 0, 1
 
 
@@ -74,6 +76,7 @@ _SIGS = {
     "psfd_set_potential": (_I, [_P, _P, _I]),
     "psfd_set_illumination": (_I, [_P, _I, _D, _D, _IP]),
     "psfd_set_graphs": (_I, [_P, _I]),
+    "psfd_set_residual_arith": (_I, [_P, _I]),
     "psfd_set_green": (_I, [_P, _I, ctypes.c_double]),
     "psfd_solve": (_I, [_P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Report)]),
     "psfd_solve_fixed_point": (_I, [_P, ctypes.POINTER(SolveOpts), _I, ctypes.c_double, ctypes.POINTER(Report)]),
@@ -288,6 +291,11 @@ class Solver:
     def set_graphs(self, enable: bool):
         """Replay the Krylov step as a CUDA graph (default) or launch its kernels one by one."""
         self._check(self.lib.psfd_set_graphs(self.ctx, int(bool(enable))))
+
+    def set_residual_arith(self, kind: int):
+        """RESID_DFLOAT (default): the refined solve's FP64 residual runs its z pass in
+        double-float; RESID_FP64: all in FP64."""
+        self._check(self.lib.psfd_set_residual_arith(self.ctx, int(kind)))
 
     def set_illumination(self, theta_deg, phi_deg, pol):
         th = np.ascontiguousarray(theta_deg, dtype=np.float64).reshape(-1)
