@@ -37,8 +37,13 @@ size_t df_smem_bytes(int tx) {
   return (c16 + c16col) * 16 + c8 * 8 + 16;
 }
 
+// CTAs per SM the kernel is compiled for: at nf = 128 three (96 registers, a few bytes of
+// spill) measured faster than two at 168 registers (the pass is issue- and latency-bound,
+// so resident warps count more than the spill); 1 = no register cap.
+template <int NF> __host__ __device__ constexpr int df_min_blocks() { return NF == 128 ? 3 : 1; }
+
 template <int NF, int NT>
-__global__ void __launch_bounds__(NT) k_zcol_df(OpCall<double2> a, int tx) {
+__global__ void __launch_bounds__(NT, df_min_blocks<NF>()) k_zcol_df(OpCall<double2> a, int tx) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int P = df_pitch<NF>();
   constexpr int PE = phase_entries<NF>(), PP = phase_pitch<NF>();
