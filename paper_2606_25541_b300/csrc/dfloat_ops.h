@@ -10,8 +10,13 @@ namespace psfd {
 bool zcol_df_supported(const OpCall<double2>& a);
 // K2 of an FP64 operator call with the z transforms and dyadic products in double-float.
 int launch_zcol_df(const OpCall<double2>& a);
-// op_apply<double2> with launch_zcol_df as its z pass where supported (the refined solve's
-// residual); returns the partial-sum blocks per RHS or a negative status, like op_apply.
+// Whether launch_cols_df handles the column pass of this call's split planes (ny 128 or 256,
+// nx a multiple of 8); the pass transforms in place along y (inverse = 1: unnormalised inverse).
+bool cols_df_supported(const OpCall<double2>& a);
+int launch_cols_df(const OpCall<double2>& a, bool inverse);
+// op_apply<double2> with launch_zcol_df as its z pass and launch_cols_df as the column passes
+// of split planes where supported (the refined solve's residual); returns the partial-sum
+// blocks per RHS or a negative status, like op_apply.
 int op_apply_df(const OpCall<double2>& a);
 
 }  // namespace psfd

@@ -21,10 +21,37 @@ template <> int gmres_finish<double2>(const KrylovCall<double2>& k, const int* m
   return gmres_finish_impl<double2>(k, mask);
 }
 
-// The FP64 operator with the z pass in double-float (zcol_df.cu) where that kernel handles
-// the call: K1 and K3 as in op_apply<double2>, the profile class of each pass unchanged.
+// Row passes of FP64 split planes, for op_apply_df.
+template <int IN>
+static int rows_fwd64(const OpCall<double2>& a) {
+  switch (a.nx) {
+#define X(n) \
+  case n:    \
+    return launch_rows_fwd<double2, n, IN>(a);
+    PSFD_FOR_EACH_LENGTH(X)
+#undef X
+  }
+  return PSFD_E_ARG;
+}
+template <int EPI>
+static int rows_inv64(const OpCall<double2>& a, const double2* uin) {
+  switch (a.nx) {
+#define X(n) \
+  case n:    \
+    return launch_rows_inv<double2, n, EPI>(a, uin);
+    PSFD_FOR_EACH_LENGTH(X)
+#undef X
+  }
+  return PSFD_E_ARG;
+}
+
+// The FP64 operator with the double-float passes where their kernels handle the call: the z
+// pass (zcol_df.cu) and the column passes of split planes (cols_df.cu); the row passes, fused
+// planes and the epilogue as in op_apply<double2>, the profile class of each pass unchanged.
 int op_apply_df(const OpCall<double2>& a0) {
-  if (!zcol_df_supported(a0)) return op_apply_impl<double2>(a0);
+  const bool zdf = zcol_df_supported(a0);
+  const bool ydf = !use_fused<double2>(a0.nx, a0.ny) && cols_df_supported(a0);
+  if (!zdf && !ydf) return op_apply_impl<double2>(a0);
   const bool prof = prof_on();
   OpCall<double2> a = a0;
   PassCost cost;
@@ -36,22 +63,24 @@ int op_apply_df(const OpCall<double2>& a0) {
   int rc;
   a.ctac = prof ? prof_begin(PK_FWD64, a.stream) : nullptr;
   switch (a.in_mode) {
-    case IN_PLAIN: rc = dispatch_fwd<double2, IN_PLAIN>(a); break;
-    case IN_PUPDATE: rc = dispatch_fwd<double2, IN_PUPDATE>(a); break;
-    case IN_SUPDATE: rc = dispatch_fwd<double2, IN_SUPDATE>(a); break;
+    case IN_PLAIN: rc = ydf ? rows_fwd64<IN_PLAIN>(a) : dispatch_fwd<double2, IN_PLAIN>(a); break;
+    case IN_PUPDATE: rc = ydf ? rows_fwd64<IN_PUPDATE>(a) : dispatch_fwd<double2, IN_PUPDATE>(a); break;
+    case IN_SUPDATE: rc = ydf ? rows_fwd64<IN_SUPDATE>(a) : dispatch_fwd<double2, IN_SUPDATE>(a); break;
     default: return PSFD_E_ARG;
   }
   if (rc) return rc;
+  if (ydf && (rc = launch_cols_df(a, false))) return rc;
   if (prof) prof_end(PK_FWD64, a.stream, cost.bytes[0], cost.flops[0], cx);
   a.ctac = prof ? prof_begin(PK_Z64, a.stream) : nullptr;
-  if ((rc = launch_zcol_df(a))) return rc;
-  if (prof) prof_end(PK_Z64, a.stream, cost.bytes[1], cost.flops[1], (double)a.ny * a.nrhs * (a.nx < 8 ? 1 : a.nx / 8));
+  if ((rc = zdf ? launch_zcol_df(a) : dispatch_z<double2>(a))) return rc;
+  if (prof) prof_end(PK_Z64, a.stream, cost.bytes[1], cost.flops[1], cz);
   if (a.epi == EPI_NONE) return blocks_per_rhs_t<double2>(a.nx, a.ny, a.nslab);
   const double2* uin = a.in_mode == IN_PLAIN ? a.u : a.ustore;
   a.ctac = prof ? prof_begin(PK_INV64, a.stream) : nullptr;
+  if (ydf && (rc = launch_cols_df(a, true))) return rc;
   switch (a.epi) {
-    case EPI_AU: rc = dispatch_inv<double2, EPI_AU>(a, uin); break;
-    case EPI_RESID: rc = dispatch_inv<double2, EPI_RESID>(a, uin); break;
+    case EPI_AU: rc = ydf ? rows_inv64<EPI_AU>(a, uin) : dispatch_inv<double2, EPI_AU>(a, uin); break;
+    case EPI_RESID: rc = ydf ? rows_inv64<EPI_RESID>(a, uin) : dispatch_inv<double2, EPI_RESID>(a, uin); break;
     default: return PSFD_E_ARG;
   }
   if (rc) return rc;

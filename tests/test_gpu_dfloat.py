@@ -1,4 +1,4 @@
-"""The FP64 residual with its z pass in double-float (PSFD_RESID_DFLOAT, psfd_apply with
+"""The FP64 residual with its z pass (and the column passes of split planes) in double-float (PSFD_RESID_DFLOAT, psfd_apply with
 PSFD_FP64_DF) against the FP64 oracle and the all-FP64 path.
 
 Double-float carries about 48 significant bits; the sloppy sum and the FMA product each err
@@ -31,14 +31,16 @@ def psfd():
 
 
 # (nx, ny, nslab, nz_min): nf = 64 and 128 run the double-float z pass (full tiles, fewer
-# x-modes than a tile, the thickest slab nf = 128 allows, split FP64 planes at 128 x 128);
-# nf = 32, 160 and 256 fall back to the FP64 pass
+# x-modes than a tile, the thickest slab nf = 128 allows); split FP64 planes with ny = 128 or
+# 256 run the double-float column passes (128 x 128 both, 256 x 256 at a short nf the column
+# passes alone); the other cases keep every FP64 pass
 DF_CASES = [
     (16, 16, 12, 64),
     (32, 16, 20, 128),
     (4, 32, 20, 128),
     (8, 8, 62, 128),
     (128, 128, 9, 128),
+    (256, 256, 4, 0),
     (8, 8, 4, 0),
     (16, 8, 30, 160),
     (16, 32, 9, 256),
@@ -68,8 +70,9 @@ def test_double_float_apply_matches_oracle(psfd, nx, ny, nslab, nz):
         ref = oracle.apply_operator(oracle.setup_rhs(prob, i), u[i])
         assert _rel(got[i], ref) < 1e-12, i
         assert _rel(u[i] - got[i], u[i] - ref) < 1e-12, i
-    if nf in (64, 128):
-        # the double-float pass ran: close to the FP64 one, but not bit for bit
+    fused = nx == ny and nx <= 64
+    if nf in (64, 128) or (not fused and ny in (128, 256) and nx % 8 == 0):
+        # a double-float pass ran: close to the FP64 one, but not bit for bit
         assert _rel(u - got, u - f64) < 1e-12
         assert not np.array_equal(got, f64)
     else:
