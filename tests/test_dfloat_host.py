@@ -1,0 +1,48 @@
+"""The double-float primitives of the CUDA path's FP64 residual (csrc/dfloat.cuh) on the host:
+the header is compiled with g++ (no floating-point contraction, as the device code forbids it
+through round-to-nearest intrinsics) and checked against long double on a million seeded
+operand pairs, a quarter of them near cancellation.
+
+Bounds (u = 2^-48, the format's precision): TwoSum and the FMA TwoProduct exact; conversion
+from FP64 within u |x|; the sloppy sum within 4 u (|a| + |b|); the product within 6 u |a b|;
+every result normalised (|lo| <= 2^-24 |hi|); a double literal folded at compile time within u."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2606_25541_b300", "csrc")
+CUDA_INC = "/usr/local/cuda/include"
+U = 2.0 ** -48
+
+
+@pytest.fixture(scope="module")
+def results(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
+        pytest.skip("g++ or the CUDA headers are missing")
+    exe = str(tmp_path_factory.mktemp("dfloat") / "dfloat_check")
+    subprocess.run([gxx, "-O2", "-std=c++17", "-ffp-contract=off", f"-I{CSRC}", f"-I{CUDA_INC}",
+                    os.path.join(HERE, "dfloat_check.cpp"), "-o", exe], check=True, capture_output=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    return {k: float(v) for k, v in (line.split() for line in out.strip().splitlines())}
+
+
+def test_error_free_transformations_are_exact(results):
+    assert results["two_sum_inexact"] == 0
+    assert results["two_prod_inexact"] == 0
+
+
+def test_double_float_error_bounds(results):
+    assert results["conv"] <= U
+    assert results["add"] <= 4 * U
+    assert results["mul"] <= 6 * U
+    assert results["constant"] <= U
+    # and the format is really about 48 bits, not FP32 with extra steps
+    assert results["add"] > 0 and results["mul"] < 2.0 ** -40
+
+
+def test_results_are_normalised(results):
+    assert results["unnormalised"] == 0
