@@ -162,12 +162,14 @@ int psfd_set_graphs(psfd_ctx* ctx, int enable);
 /* Arithmetic of the FP64 residual r = b - A x that certifies a PSFD_FP32_REFINED solve
  * (no counterpart in the paper; the defect correction is not one of its steps).
  *   PSFD_RESID_FP64    every step in FP64;
- *   PSFD_RESID_DFLOAT  (default) the z pass's transforms and dyadic products in double-float
- *                      (a pair of FP32 numbers, about 48 significant bits, ~1e-14 normwise)
- *                      on nf = 64 or 128 with the periodic kernel, FP64 elsewhere. B300 runs
- *                      FP32 about sixty times faster than FP64, and the refinement needs the
- *                      residual only to well below its tolerance.
- * Vectors, the xy passes, the Green's scalars and the reflection stay FP64 either way.
+ *   PSFD_RESID_DFLOAT  (default) in double-float (a pair of FP32 numbers, about 48
+ *                      significant bits, ~1e-14 normwise): the z pass's transforms and dyadic
+ *                      products on nf = 64 or 128 with the periodic kernel, and the y
+ *                      transforms of planes too large for one CTA (ny = 128 or 256, nx a
+ *                      multiple of 8); FP64 elsewhere. B300 runs FP32 about sixty times
+ *                      faster than FP64, and the refinement needs the residual only to well
+ *                      below its tolerance.
+ * Vectors, the x passes, the Green's scalars and the reflection stay FP64 either way.
  * Contexts of precision PSFD_FP64 ignore the setting. Errors: PSFD_E_ARG (unknown kind). */
 #define PSFD_RESID_FP64 0
 #define PSFD_RESID_DFLOAT 1

@@ -293,8 +293,9 @@ class Solver:
         self._check(self.lib.psfd_set_graphs(self.ctx, int(bool(enable))))
 
     def set_residual_arith(self, kind: int):
-        """RESID_DFLOAT (default): the refined solve's FP64 residual runs its z pass in
-        double-float; RESID_FP64: all in FP64."""
+        """RESID_DFLOAT (default): the refined solve's FP64 residual runs its z transforms and
+        dyadic products (and the y transforms of split planes) in double-float; RESID_FP64: all
+        in FP64."""
         self._check(self.lib.psfd_set_residual_arith(self.ctx, int(kind)))
 
     def set_illumination(self, theta_deg, phi_deg, pol):
