@@ -64,7 +64,9 @@ def parse_args(argv=None):
     ap.add_argument("--apply", action="store_true",
                     help="operator applications/s only (psfd_apply), for kernel captures")
     ap.add_argument("--rhs", type=int, default=18, help="illuminations used by --apply")
-    ap.add_argument("--precision", choices=["fp32", "fp64", "both"], default="both", help="--apply precision")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "fp64df", "both", "all"], default="both",
+                    help="--apply precision (fp64df: FP64 data with the residual's double-float passes; "
+                         "both = fp32 + fp64, all = the three)")
     ap.add_argument("--krylov", choices=["bicgstab", "gmres"], default="bicgstab",
                     help="inner Krylov method of the refined solve")
     ap.add_argument("--restart", type=int, default=0, help="GMRES basis size per sweep (0 = maximum)")
@@ -196,21 +198,22 @@ def run_apply(args):
     prob = prob.with_illumination(prob.theta_deg[sel], prob.phi_deg[sel], prob.pol[sel])
     stream = torch.cuda.current_stream()
     out = {"mode": "apply", "workload": WORKLOAD.replace("18rhs", f"{args.rhs}rhs")}
-    precs = ["fp32", "fp64"] if args.precision == "both" else [args.precision]
+    precs = {"both": ["fp32", "fp64"], "all": ["fp32", "fp64", "fp64df"]}.get(args.precision, [args.precision])
     for name in precs:
-        prec = psfd.FP32_REFINED if name == "fp32" else psfd.FP64
+        prec = psfd.FP64 if name == "fp64" else psfd.FP32_REFINED
+        apply_prec = {"fp32": psfd.FP32_REFINED, "fp64": psfd.FP64, "fp64df": psfd.FP64_DF}[name]
         s = psfd.Solver.from_problem(prob, prec, stream=stream)
         dt = torch.complex64 if name == "fp32" else torch.complex128
         u = torch.tensor(layouts.random_field((args.rhs, 3, prob.nslab, prob.ny, prob.nx), seed=1), dtype=dt,
                          device="cuda")
         y = torch.empty_like(u)
         for _ in range(args.warmup):
-            s.apply(u, y)
+            s.apply(u, y, precision=apply_prec)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            s.apply(u, y)
+            s.apply(u, y, precision=apply_prec)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / max(args.steps, 1)
