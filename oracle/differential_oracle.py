@@ -3,7 +3,7 @@ problem and of the preconditioner comparison it is measured with (Sec. 3, Eqs. (
 and the preconditioner table).
 
 Test infrastructure only: imported by ``tests/`` (and nothing on the product path). It shares
-no code with the CUDA path; numpy's FFT serves as a library primitive.
+no code with the CUDA path; its transforms are the oracle's own (``oracle/fft.py``).
 
 Problem: a periodic clip in free space (no stack), scattered-field form of Eq. (3),
     curl curl E_s - k0^2 eps E_s = k0^2 (eps - eps_bg) E_inc,
@@ -27,6 +27,7 @@ import math
 
 import numpy as np
 
+from . import fft as offt
 from .psfd_oracle import triad, upper_sqrt
 
 __all__ = ["DiffProblem", "diff_problem_from_clip", "apply_differential", "differential_rhs",
@@ -67,9 +68,9 @@ def _geometry(p: DiffProblem):
     kb = k0 * math.sqrt(p.eps_bg)
     th, ph = math.radians(p.theta), math.radians(p.phi)
     qix, qiy = kb * math.sin(th) * math.cos(ph), kb * math.sin(th) * math.sin(ph)
-    qx = qix + 2 * math.pi * np.fft.fftfreq(p.nx, p.dx)
-    qy = qiy + 2 * math.pi * np.fft.fftfreq(p.ny, p.dy)
-    kz = 2 * math.pi * np.fft.fftfreq(p.nz, p.dz)
+    qx = qix + 2 * math.pi * offt.fftfreq(p.nx, p.dx)
+    qy = qiy + 2 * math.pi * offt.fftfreq(p.ny, p.dy)
+    kz = 2 * math.pi * offt.fftfreq(p.nz, p.dz)
     # PML stretch, cubic profile over n_pml planes at both ends
     Lp = p.n_pml * p.dz
     smax = -4.0 * math.log(1e-8) / (2.0 * kb * Lp) if p.n_pml > 0 else 0.0
@@ -83,10 +84,10 @@ def _d(f, axis, p, g):
     """Spectral derivative of f (nz, ny, nx) along x (axis 2), y (1) or z (0, stretched)."""
     k0, kb, qix, qiy, qx, qy, kz, s = g
     if axis == 2:
-        return np.fft.ifft(1j * qx[None, None, :] * np.fft.fft(f, axis=2), axis=2)
+        return offt.ifft(1j * qx[None, None, :] * offt.fft(f, axis=2), axis=2)
     if axis == 1:
-        return np.fft.ifft(1j * qy[None, :, None] * np.fft.fft(f, axis=1), axis=1)
-    return np.fft.ifft(1j * kz[:, None, None] * np.fft.fft(f, axis=0), axis=0) / s[:, None, None]
+        return offt.ifft(1j * qy[None, :, None] * offt.fft(f, axis=1), axis=1)
+    return offt.ifft(1j * kz[:, None, None] * offt.fft(f, axis=0), axis=0) / s[:, None, None]
 
 
 def _curl(E, p, g):
@@ -121,7 +122,7 @@ def spectral_damping(p: DiffProblem, r: np.ndarray, g=None) -> np.ndarray:
     kb, qx, qy, kz = g[1], g[4], g[5], g[6]
     k2 = qx[None, None, :] ** 2 + qy[None, :, None] ** 2 + kz[:, None, None] ** 2
     D = np.minimum(1.0, kb * kb / np.maximum(k2, 1e-300))
-    return np.fft.ifftn(D[None] * np.fft.fftn(r, axes=(1, 2, 3)), axes=(1, 2, 3))
+    return offt.ifftn(D[None] * offt.fftn(r, axes=(1, 2, 3)), axes=(1, 2, 3))
 
 
 def gmres_restarted(apply, b: np.ndarray, rtol: float = 1e-8, restart: int = 60, maxiter: int = 20000):

@@ -2,7 +2,7 @@
 with the paper's spherically windowed dyadic Green's function (Sec. 3, Eqs. (13)-(18)).
 
 Test infrastructure only: imported by ``tests/`` (and nothing on the product path). It
-shares no code with the CUDA path. numpy's FFT serves as a library primitive.
+shares no code with the CUDA path; its transforms are the oracle's own (``oracle/fft.py``).
 
 The problem: a scatterer of permittivity eps on a box grid, free space eps_bg around it, a
 plane wave E_inc. With V = k0^2 (eps - eps_bg) and the total field u,
@@ -28,6 +28,7 @@ import math
 
 import numpy as np
 
+from . import fft as offt
 from .psfd_oracle import gmres, triad, upper_sqrt
 
 __all__ = ["windowed_scalar_spectrum", "windowed_dyadic_coefficients", "dyadic_green_realspace",
@@ -126,9 +127,9 @@ def isolated_kernel(p: IsolatedProblem) -> np.ndarray:
     """F[G_R] at the grid wavenumbers (shifted by q_inc for Bloch envelopes), (3, 3, nz, ny, nx)."""
     kb = 2 * math.pi / p.wavelength * math.sqrt(p.eps_bg)
     qix, qiy = _q_inc(p) if p.bloch else (0.0, 0.0)
-    kx = qix + 2 * math.pi * np.fft.fftfreq(p.nx, p.dx)
-    ky = qiy + 2 * math.pi * np.fft.fftfreq(p.ny, p.dy)
-    kz = 2 * math.pi * np.fft.fftfreq(p.nz, p.dz)
+    kx = qix + 2 * math.pi * offt.fftfreq(p.nx, p.dx)
+    ky = qiy + 2 * math.pi * offt.fftfreq(p.ny, p.dy)
+    kz = 2 * math.pi * offt.fftfreq(p.nz, p.dz)
     KZ, KY, KX = np.meshgrid(kz, ky, kx, indexing="ij")
     kk = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)
     A, B = windowed_dyadic_coefficients(kk, kb, p.R)
@@ -167,9 +168,9 @@ def apply_isolated(p: IsolatedProblem, u: np.ndarray, G: np.ndarray | None = Non
         G = isolated_kernel(p)
     k0 = 2 * math.pi / p.wavelength
     V = k0 * k0 * (np.asarray(p.eps, np.complex128) - p.eps_bg)
-    J = np.fft.fftn(V[None] * u, axes=(1, 2, 3))
+    J = offt.fftn(V[None] * u, axes=(1, 2, 3))
     W = np.einsum("ab...,b...->a...", G, J)
-    return u - np.fft.ifftn(W, axes=(1, 2, 3))
+    return u - offt.ifftn(W, axes=(1, 2, 3))
 
 
 def solve_isolated(p: IsolatedProblem, rtol: float = 1e-12, maxiter: int = 400, direct: bool = False):

@@ -3,8 +3,9 @@
 Test infrastructure only: imported by ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py``; nothing on the product path may call it.
 
-Everything is complex128, written for reading rather than speed. numpy's FFT and
-dense linear algebra serve as library primitives; there is no blocking, fusion or
+Everything is complex128, written for reading rather than speed. The discrete Fourier
+transforms are the oracle's own (``oracle/fft.py``, pinned against the direct sums) and dense
+linear algebra serves as a library primitive; there is no blocking, fusion or
 reordering beyond the steps below. Paper references are to arXiv 2606.25541
 (Lee, Gillijns, Kim: "Pseudo-spectral frequency-domain method with background field
 decomposition and Green's function preconditioner ..."), by section and equation.
@@ -41,6 +42,8 @@ import math
 
 import numpy as np
 
+from . import fft as offt
+
 __all__ = [
     "upper_sqrt", "fft_integers", "parratt_reflection", "tmm_reflection", "triad",
     "green_scalar", "green_dyadic", "RhsContext", "setup_rhs", "apply_operator",
@@ -66,7 +69,7 @@ def upper_sqrt(z):
 
 def fft_integers(n: int) -> np.ndarray:
     """Signed integer frequency of each FFT bin (numpy order; the Nyquist bin is negative)."""
-    return np.rint(np.fft.fftfreq(n) * n).astype(np.int64)
+    return np.rint(offt.fftfreq(n) * n).astype(np.int64)
 
 
 # ---------------------------------------------------------------------------
@@ -290,7 +293,7 @@ def _reflect_and_invert(ctx: RhsContext, Wt: np.ndarray):
     steps = np.arange(n, dtype=np.float64)[:, None, None]
     phase = np.exp(1j * ctx.beta[None] * ctx.dz * steps)
     W_slab = Wt[:, 1:n + 1] + R0[:, None] * phase[None]
-    return np.fft.ifft2(W_slab, axes=(2, 3))
+    return offt.ifft2(W_slab, axes=(2, 3))
 
 
 def apply_operator(ctx: RhsContext, u: np.ndarray, return_side: bool = False):
@@ -306,9 +309,9 @@ def apply_operator(ctx: RhsContext, u: np.ndarray, return_side: bool = False):
     n = ctx.nslab
     J = np.zeros((3, ctx.nf, ctx.ny, ctx.nx), dtype=np.complex128)
     J[:, 1:n + 1] = ctx.V[None] * u
-    Jh = np.fft.fftn(J, axes=(1, 2, 3))
+    Jh = offt.fftn(J, axes=(1, 2, 3))
     Wh = np.einsum("ablyx,blyx->alyx", ctx.G, Jh)
-    Wt = np.fft.ifft(Wh, axis=1)
+    Wt = offt.ifft(Wh, axis=1)
     w = _reflect_and_invert(ctx, Wt)
     Au = u - w
     if return_side:
@@ -468,7 +471,7 @@ def reflected_field(ctx: RhsContext, D: np.ndarray) -> np.ndarray:
     zc = (np.arange(1, ctx.nslab + 1) - 0.5) * ctx.dz
     up = np.exp(1j * ctx.beta[None] * zc[:, None, None])          # (nslab, ny, nx)
     TD = np.einsum("abyx,byx->ayx", ctx.TR, D)
-    return np.fft.ifft2(TD[:, None] * up[None], axes=(2, 3)) * (ctx.nx * ctx.ny)
+    return offt.ifft2(TD[:, None] * up[None], axes=(2, 3)) * (ctx.nx * ctx.ny)
 
 
 def solve_fixed_point(prob, i: int = 0, rtol: float = 1e-10, max_outer: int = 50,
@@ -593,7 +596,7 @@ def scattered_spectrum_mode(prob, i: int, u: np.ndarray, m: int, n: int) -> np.n
     for p in range(prob.nslab):
         J[:, p + 1] = np.einsum("cyx,yx->c", V[p][None] * u[:, p], phase)
     G = green_dyadic(qx, qy, beta, prob.nf, prob.dz, kb)[:, :, :, 0, 0]  # (3, 3, nf)
-    Wt = np.fft.ifft(np.einsum("abl,bl->al", G, np.fft.fft(J, axis=1)), axis=1)
+    Wt = offt.ifft(np.einsum("abl,bl->al", G, offt.fft(J, axis=1)), axis=1)
     R0 = TR[:, :, 0, 0] @ Wt[:, 0]
     steps = np.arange(prob.nslab, dtype=np.float64)
     return Wt[:, 1:prob.nslab + 1] + R0[:, None] * np.exp(1j * beta[0, 0] * prob.dz * steps)[None]
