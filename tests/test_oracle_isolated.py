@@ -145,3 +145,79 @@ def test_no_scatterer_leaves_the_incident_field():
     assert np.array_equal(iso.apply_isolated(p, b), b)
     u, info = iso.solve_isolated(p)
     assert info["iterations"] <= 1 and np.max(np.abs(u - b)) < 1e-15 * np.max(np.abs(b))
+
+
+# ---------------------------------------------------------------------------
+# Bloch envelopes (the form the CUDA path solves): u_B = u exp(-i q_inc . r_perp), the kernel
+# taken at k + q_inc and E_inc = e exp(-i beta z). On a grid where q_inc is a grid frequency
+# (q_inc = 2 pi m / (n dx)) the envelope problem is the plain problem with its spectrum moved
+# by m bins, which fixes the sign of the shift in the kernel and of the envelope phase.
+# ---------------------------------------------------------------------------
+_NB, _DB = 40, 1.0
+_THB = math.degrees(math.asin(LAM / (_NB * _DB)))  # sin(theta) = lambda / (n dx): one bin
+
+
+def _grid_wave_problem(phi, bloch, R=12.0, pol=1):
+    """A weak scatterer whose permittivity is a raised cosine over the box, (1 - cos)/2 along
+    each axis: its spectrum occupies bins -1, 0, 1 only, so each order of multiple scattering
+    widens the field's transverse spectrum by one bin, and the Nyquist bins (20 bins away from
+    the incident one) are reached only at order ~20, suppressed far below rounding."""
+    n, d = _NB, _DB
+    t = (1.0 - np.cos(2 * math.pi * np.arange(n) / n)) / 2
+    h = t[:, None, None] * t[None, :, None] * t[None, None, :]
+    eps = 1.0 + (-0.03 + 0.02j) * h
+    return iso.IsolatedProblem(nx=n, ny=n, nz=n, dx=d, dy=d, dz=d, wavelength=LAM, eps_bg=1.0, eps=eps, R=R,
+                               theta=_THB, phi=phi, pol=pol, bloch=bloch)
+
+
+def _bin_shift(phi):
+    return {0.0: (1, 0), 90.0: (0, 1), 180.0: (-1, 0)}[phi]
+
+
+@pytest.mark.parametrize("phi", [0.0, 90.0, 180.0])
+def test_bloch_kernel_is_the_plain_kernel_one_bin_over(phi):
+    """isolated_kernel(bloch=True) at bin j equals the plain kernel at bin j + m (m the incident
+    wavevector in bins), wherever j + m does not wrap past the Nyquist bin. A shift of the wrong
+    sign would match bin j - m instead."""
+    sx, sy = _bin_shift(phi)
+    Gb = iso.isolated_kernel(_grid_wave_problem(phi, True))
+    Gp = iso.isolated_kernel(_grid_wave_problem(phi, False))
+    n = _NB
+    f = np.where(np.arange(n) < n // 2, np.arange(n), np.arange(n) - n)
+    okx = (f + sx >= -(n // 2)) & (f + sx < n // 2)
+    oky = (f + sy >= -(n // 2)) & (f + sy < n // 2)
+    shifted = np.roll(np.roll(Gp, -sx, axis=4), -sy, axis=3)
+    sel = (slice(None), slice(None), slice(None), oky, slice(None))
+    a = Gb[sel][..., okx]
+    b = shifted[sel][..., okx]
+    assert np.max(np.abs(a - b)) < 1e-12 * np.max(np.abs(b))
+    wrong = np.roll(np.roll(Gp, sx, axis=4), sy, axis=3)[sel][..., okx]
+    assert np.max(np.abs(a - wrong)) > 1e-3 * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("phi", [0.0, 90.0])
+def test_bloch_rhs_is_the_plain_rhs_times_the_envelope(phi):
+    pb, pp = _grid_wave_problem(phi, True), _grid_wave_problem(phi, False)
+    n, d = _NB, _DB
+    qx, qy = iso._q_inc(pp)
+    x = np.arange(n) * d
+    env = np.exp(1j * (qx * x[None, None, :] + qy * x[None, :, None]))
+    assert np.max(np.abs(iso.isolated_rhs(pb) * env[None] - iso.isolated_rhs(pp))) < 1e-13
+
+
+@pytest.mark.parametrize("phi", [0.0, 90.0])
+def test_bloch_solution_times_the_envelope_is_the_plain_solution(phi):
+    """With no field spectrum left at the Nyquist bins (the band-limited scatterer above), the
+    envelope problem and the plain one are the same problem, so u_B exp(i q_inc . r) = u to
+    the solver tolerance. A sign error in the kernel's shift or in the envelope phase changes
+    the scattered field at order one."""
+    pb, pp = _grid_wave_problem(phi, True), _grid_wave_problem(phi, False)
+    ub, _ = iso.solve_isolated(pb, rtol=1e-13)
+    up, _ = iso.solve_isolated(pp, rtol=1e-13)
+    n, d = _NB, _DB
+    qx, qy = iso._q_inc(pp)
+    x = np.arange(n) * d
+    env = np.exp(1j * (qx * x[None, None, :] + qy * x[None, :, None]))
+    scat = up - iso.isolated_rhs(pp)
+    assert np.max(np.abs(scat)) > 1e-3 * np.max(np.abs(up))  # the scatterer does scatter
+    assert np.max(np.abs(ub * env[None] - up)) < 1e-10 * np.max(np.abs(scat))
