@@ -63,7 +63,7 @@ def parse_args(argv=None):
     ap.add_argument("--profile-only", action="store_true", help="one profiled step, for ncu launch lists")
     ap.add_argument("--apply", action="store_true",
                     help="operator applications/s only (psfd_apply), for kernel captures")
-    ap.add_argument("--rhs", type=int, default=18, help="illuminations used by --apply")
+    ap.add_argument("--rhs", type=int, default=18, help="illuminations used by --apply and --profile-only")
     ap.add_argument("--precision", choices=["fp32", "fp64", "fp64df", "both", "all"], default="both",
                     help="--apply precision (fp64df: FP64 data with the residual's double-float passes; "
                          "both = fp32 + fp64, all = the three)")
@@ -86,6 +86,8 @@ def parse_args(argv=None):
     ap.add_argument("--differential", action="store_true",
                     help="FP64 applications/s of the differential PSFD operator (PML column) and of the "
                          "Lippmann-Schwinger operator on the same 64 x 64 x 30 clip")
+    ap.add_argument("--autotune", action="store_true",
+                    help="autotuner table: built-in vs tuned tile shapes per workload grid")
     ap.add_argument("--small", action="store_true",
                     help="the 32 x 32 x 30 contact-hole clip (one illumination): ms per solve, CUDA graphs on/off")
     ap.add_argument("--fixed-point", action="store_true",
@@ -536,6 +538,37 @@ def run_differential(args):
     return 0
 
 
+def run_autotune(args):
+    """The autotuner on the workload sizes: per grid and precision, one operator application
+    with the built-in tile shapes against the tuned ones (psfd_autotune, forced)."""
+    import torch
+    from paper_2606_25541_b300 import psfd
+    torch.cuda.set_device(0)
+    serving = layouts.serving_requests(40, sizes=(64, 128, 256, 384, 512))
+    by_size = {}
+    for r in serving:
+        by_size.setdefault((r.nx, r.ny, r.nslab, r.nf), r)
+    cases = [("line_space_128x128x60_nf128_18rhs", layouts.line_space_clip(), (psfd.FP32_REFINED, psfd.FP64)),
+             ("manhattan_256x256x60_nf128_2rhs", layouts.manhattan_clip(), (psfd.FP32_REFINED, psfd.FP64))]
+    for key in sorted(by_size, key=lambda k: k[0] * k[1])[:: max(1, len(by_size) // 4)]:
+        r = by_size[key]
+        cases.append((f"serving_{key[0]}x{key[1]}x{key[2]}_nf{key[3]}_{r.n_rhs}rhs", r, (psfd.FP32_REFINED,)))
+    big = layouts.curvilinear_clip()
+    big = big.with_illumination(big.theta_deg[:2], big.phi_deg[:2], big.pol[:2])
+    cases.append(("curvilinear_1024x1024x60_nf160_2rhs", big, (psfd.FP32_REFINED,)))
+    rows = []
+    for name, prob, precisions in cases:
+        for prec in precisions:
+            s = psfd.Solver.from_problem(prob, prec)
+            rep = s.autotune(force=True)
+            s.close()
+            rows.append({"workload": name, "precision": "fp32" if prec == psfd.FP32_REFINED else "fp64", **rep,
+                         "speedup": rep["default_ms"] / rep["tuned_ms"]})
+            torch.cuda.empty_cache()
+    print(json.dumps({"mode": "autotune", "rows": rows}), flush=True)
+    return 0
+
+
 def run_small(args):
     """The contact-hole clip (32 x 32 x 30 at 2 nm, nf = 64, one s-polarised plane wave at 6 deg)
     solved to relative residual 1e-10 in FP64 and in FP32 with FP64 refinement, with the
@@ -697,20 +730,21 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # CPU oracle sample (the baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_solve_seconds(prob, i: int, rtol: float) -> float:
-    """Wall time of one oracle solve of illumination i: set-up, GMRES, orders."""
-    import contextlib
+ORACLE_TIGHT = 1e-11      # the oracle solve the GPU orders are checked against
+ORACLE_BYTES_PER_PROC = 3e9
 
+
+def oracle_apply_seconds(prob, i: int, reps: int = 1) -> float:
+    """Mean wall time of one oracle operator application (illumination i) on one thread."""
     import oracle
-    try:  # numpy's FFT and einsum are single threaded; pin BLAS (GMRES least squares) too
-        from threadpoolctl import threadpool_limits
-        limit = threadpool_limits(1)
-    except ImportError:
-        limit = contextlib.nullcontext()
-    with limit:
+    from oracle.parallel import _one_thread
+    with _one_thread():
+        ctx = oracle.setup_rhs(prob, i)
+        u = oracle.rhs_vector(ctx)
         t0 = time.perf_counter()
-        oracle.solve(prob, i, rtol=rtol, maxiter=400)
-        return time.perf_counter() - t0
+        for _ in range(reps):
+            oracle.apply_operator(ctx, u)
+        return (time.perf_counter() - t0) / reps
 
 
 def cpu_model() -> str:
@@ -727,33 +761,82 @@ def cpu_model() -> str:
     return f"{name}, {os.cpu_count()} logical cores on the host"
 
 
-def cpu_baseline(prob, rtol: float):
-    t = oracle_solve_seconds(prob, 5, rtol)
-    return {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle", "host": cpu_model(),
-            "sample": f"one of the 18 illuminations (theta {prob.theta_deg[5]:g}, phi {prob.phi_deg[5]:g}, "
-                      f"pol {int(prob.pol[5])}) solved by the FP64 oracle (numpy FFT + GMRES to relative "
-                      f"residual {rtol:g}, orders included), single thread: {t:.1f} s"}
+def orders_vs(got: dict, ref: dict) -> float:
+    """Relative 2-norm difference of the order amplitudes of one illumination, matched by (m, n)."""
+    key = {(int(m), int(n)): k for k, (m, n) in enumerate(zip(ref["m"], ref["n"]))}
+    idx = [key[(int(m), int(n))] for m, n in zip(got["m"], got["n"])]
+    assert len(idx) == len(ref["m"])
+    return float(np.linalg.norm(got["amp"] - ref["amp"][idx]) / np.linalg.norm(ref["amp"]))
+
+
+def cpu_baseline(prob, rtol: float, gpu_orders: list):
+    """The oracle timed on the host: one illumination on one core (the baseline value), the same
+    per operator application, and the batch on all usable cores; plus the GPU orders of that
+    illumination checked against the oracle solved to 1e-11."""
+    from oracle.parallel import apply_many, solve_timed, usable_processes
+    i = 5
+    r = solve_timed(prob, i, ORACLE_TIGHT, marks=(rtol,))
+    t_tol = r["at"][rtol]["seconds"]
+    n_app = r["at"][rtol]["iterations"] + 1  # GMRES applications + the one for the orders
+    t_app = oracle_apply_seconds(prob, i)
+    # all cores: concurrent applications (bounded), scaled to solves by the single-core ratio of
+    # a solve's time to its applications' time (which carries GMRES's orthogonalisation)
+    procs = usable_processes(prob.n_rhs, ORACLE_BYTES_PER_PROC)
+    reps = 2
+    per, wall = apply_many(prob, range(procs), reps, procs)
+    app_rate = procs * reps / max(per)
+    overhead = t_tol / (n_app * t_app)
+    return {
+        "value": 1.0 / t_tol, "unit": UNIT, "cores": 1, "kind": "oracle", "host": cpu_model(),
+        "sample": f"illumination {i} of 18 (theta {prob.theta_deg[i]:g}, phi {prob.phi_deg[i]:g}, pol "
+                  f"{int(prob.pol[i])}) solved by the FP64 oracle (its own FFT, GMRES) on one thread: "
+                  f"{t_tol:.1f} s to relative residual {rtol:g} ({r['at'][rtol]['iterations']} iterations, "
+                  f"orders included), timed within one solve to {ORACLE_TIGHT:g} ({r['iterations']} "
+                  f"iterations, {r['seconds']:.1f} s)",
+        "per_application": {"value": 1.0 / t_app, "unit": "operator applications/s", "cores": 1,
+                            "seconds": t_app},
+        "all_cores": {"value": app_rate / (n_app * overhead), "unit": UNIT, "cores": procs,
+                      "per_application": {"value": app_rate, "unit": "operator applications/s"},
+                      "sample": f"{reps} oracle operator applications of each of illuminations 0-{procs - 1} at "
+                                f"once, one single-threaded process each (spawn pool; slowest {max(per):.1f} s, "
+                                f"{wall:.1f} s wall with start-up); solves/s = applications/s / ({n_app} "
+                                f"applications per solve x {overhead:.2f}, the single-core ratio of solve time "
+                                f"to application time)"},
+        "order_error_vs_oracle_1e-11": {"illumination": i,
+                                        "rel_err": orders_vs(gpu_orders[i], r["orders"])},
+    }
 
 
 def run_reference(args):
+    """The reference arm: the oracle on the host. One step is a bounded sample: one oracle
+    operator application (one thread) on the next illumination; solves/s follow from the
+    applications one oracle solve needs (GMRES iterations + 1 for the orders, measured by a full
+    solve before the warm-up). GMRES's orthogonalisation is left out of the steps, so the value
+    is an upper bound of the oracle's solves/s."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    from oracle.parallel import solve_timed
     prob = layouts.line_space_clip(seed=2)
     rtol = args.tol
+    full = solve_timed(prob, 5, rtol)
+    n_app = full["iterations"] + 1
     for w in range(args.warmup):
-        oracle_solve_seconds(prob, w % prob.n_rhs, rtol)
-    times = [oracle_solve_seconds(prob, (args.warmup + k) % prob.n_rhs, rtol) for k in range(args.steps)]
-    total = sum(times)
-    value = args.steps / total
+        oracle_apply_seconds(prob, w % prob.n_rhs)
+    times = [oracle_apply_seconds(prob, (args.warmup + k) % prob.n_rhs) for k in range(args.steps)]
+    t_app = sum(times) / len(times)
+    value = 1.0 / (n_app * t_app)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_app,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "reference_step": "one illumination per step, oracle GMRES"},
+        "config": {"workload": WORKLOAD, "reference_step": "one oracle operator application (one illumination, "
+                                                           "one thread); solves/s = 1 / (applications per "
+                                                           "solve x seconds per application)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": cpu_model(),
-                         "sample": f"{args.steps} single-illumination oracle solves (GMRES to {rtol:g}), "
-                                   f"one thread"},
+                         "sample": f"{args.steps} oracle operator applications on one thread, "
+                                   f"{t_app:.2f} s each; one oracle solve to {rtol:g} takes {n_app} "
+                                   f"applications (illumination 5: {full['seconds']:.1f} s in full)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -785,6 +868,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     prob = layouts.line_space_clip(seed=2 + rank)
+    if args.profile_only and args.rhs < prob.n_rhs:  # a smaller batch for full ncu captures
+        k = args.rhs
+        prob = prob.with_illumination(prob.theta_deg[:k], prob.phi_deg[:k], prob.pol[:k])
     n_rhs = prob.n_rhs
     solve_kw = dict(tol=args.tol, inner_tol=args.inner_tol, max_iter=400, max_outer=12, check_every=4,
                     krylov=psfd.GMRES if args.krylov == "gmres" else psfd.BICGSTAB, restart=args.restart)
@@ -920,7 +1006,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(prob, rtol=args.tol)
+        cpu = cpu_baseline(prob, args.tol, orders32)
 
     if rank != 0:
         return 0
@@ -960,6 +1046,7 @@ def run_ours(args):
                        "what": "per-step (18-illumination batch) device time"},
         "iterations": reps[-1]["iterations"], "outer": reps[-1]["outer"], "relres": reps[-1]["relres"],
         "order_error_vs_fp64_1e-11": order_error(orders32),
+        "order_error_vs_oracle_1e-11": cpu["order_error_vs_oracle_1e-11"] if cpu else None,
         "roofline": roofline, "kernels": kernels,
         "cpu_baseline": cpu,
         "e2e": {"value": n_rhs * args.steps * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -1006,7 +1093,7 @@ def solver_bytes(prob) -> float:
 def main(argv=None):
     args = parse_args(argv)
     headline = not (args.apply or args.sweep or args.large or args.crosscheck or args.fixed_point or args.small
-                    or args.layers or args.isolated or args.differential)
+                    or args.layers or args.isolated or args.differential or args.autotune)
     if args.tol is None:
         args.tol = HEADLINE_TOL if headline else DEFAULT_TOL
     if args.inner_tol is None:
@@ -1025,6 +1112,8 @@ def main(argv=None):
         return run_fixed_point(args)
     if args.small:
         return run_small(args)
+    if args.autotune:
+        return run_autotune(args)
     if args.layers:
         return run_layers(args)
     if args.isolated:

@@ -446,8 +446,9 @@ def transmitted_orders(ctx: RhsContext, E0: np.ndarray):
 
 
 def solve(prob, i: int = 0, rtol: float = 1e-13, maxiter: int = 500, direct: bool = False,
-          reflection: bool = True):
-    """Solve one illumination; returns (orders, solution u, info dict)."""
+          reflection: bool = True, history=None):
+    """Solve one illumination; returns (orders, solution u, info dict). `history`, if given,
+    receives GMRES's relative residual after every iteration."""
     ctx = setup_rhs(prob, i, reflection=reflection)
     b = rhs_vector(ctx)
     if direct:
@@ -455,7 +456,7 @@ def solve(prob, i: int = 0, rtol: float = 1e-13, maxiter: int = 500, direct: boo
         x = np.linalg.solve(A, b.reshape(-1)).reshape(b.shape)
         its, res = 0, float(np.linalg.norm(A @ x.reshape(-1) - b.reshape(-1)) / np.linalg.norm(b))
     else:
-        x, its, res = gmres(lambda v: apply_operator(ctx, v), b, rtol=rtol, maxiter=maxiter)
+        x, its, res = gmres(lambda v: apply_operator(ctx, v), b, rtol=rtol, maxiter=maxiter, history=history)
     _, E0, Etop = apply_operator(ctx, x, return_side=True)
     orders = diffraction_orders(ctx, E0, Etop)
     return orders, x, {"iterations": its, "relres": res, "ctx": ctx, "E0": E0, "Etop": Etop}
