@@ -156,7 +156,17 @@ extern "C" int psfd_apply_fp32_static(const psfd_grid* g, int n_layers, const do
     eps_l[j] = make_double2(a * a - b * b, 2.0 * a * b);
     d_l[j] = thickness_nm[j];
   }
-  if (n_layers > 0) {
+  // A stack of few distinct media, interfaces and layers (the periodic EUV stacks) is carried
+  // by value in the kernel arguments; only one that does not deduplicate goes through the
+  // scratch, copied from the stack arrays above and synchronised before they go out of scope.
+  StackDev stack = {};
+  stack.n_layers = n_layers;
+  stack.reflect = 1;
+  stack.eps = reinterpret_cast<const double2*>(base + o_epsl);
+  stack.d = reinterpret_cast<const double*>(base + o_dl);
+  stack.eps_sub = make_double2(n_sub[0] * n_sub[0] - n_sub[1] * n_sub[1], 2.0 * n_sub[0] * n_sub[1]);
+  stack_dedup(stack, eps_l, d_l, n_layers, make_double2(g->eps_bg, 0.0), stack.eps_sub);
+  if (n_layers > 0 && stack.n_mat == 0) {
     if (cudaMemcpyAsync(base + o_epsl, eps_l, sizeof(double2) * n_layers, cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
         cudaMemcpyAsync(base + o_dl, d_l, sizeof(double) * n_layers, cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -197,12 +207,7 @@ extern "C" int psfd_apply_fp32_static(const psfd_grid* g, int n_layers, const do
   m.dz = g->dz;
   m.kb = kb;
   m.slot_par = sq;
-  m.stack.n_layers = n_layers;
-  m.stack.reflect = 1;
-  m.stack.eps = reinterpret_cast<const double2*>(base + o_epsl);
-  m.stack.d = reinterpret_cast<const double*>(base + o_dl);
-  m.stack.eps_sub = make_double2(n_sub[0] * n_sub[0] - n_sub[1] * n_sub[1], 2.0 * n_sub[0] * n_sub[1]);
-  stack_dedup(m.stack, eps_l, d_l, n_layers, make_double2(g->eps_bg, 0.0), m.stack.eps_sub);
+  m.stack = stack;
   m.modes = modes;
   m.modes32 = reinterpret_cast<ModeF32*>(base + o_m32);
   m.anomaly = reinterpret_cast<int*>(base + o_anom);
