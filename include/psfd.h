@@ -159,6 +159,46 @@ int psfd_set_green(psfd_ctx* ctx, int kind, double R);
  * Profiling (psfd_profile_enable) bypasses the graphs. */
 int psfd_set_graphs(psfd_ctx* ctx, int enable);
 
+/* Device-side sweep loop (on by default; needs graphs on; no counterpart in the paper). While
+ * every busy illumination of the context is inside a Krylov sweep, the ticks of that sweep
+ * run inside one graph launch: a conditional WHILE node repeats the tick's graph, and a
+ * one-block kernel at the end of each tick records every slot's Krylov estimate and clears
+ * the condition once no slot is active (or after max_iter / check_every + 1 ticks, after
+ * which any slot still active goes on in ordinary ticks). The host then waits once per sweep
+ * instead of once per tick. Slots whose sweep ends early wait for the others before their
+ * FP64 residual. Results, iteration counts and the residual history are bitwise those of the
+ * host-driven ticks. Contexts of the serving loop keep host-driven ticks, so that requests
+ * are admitted between ticks. */
+int psfd_set_device_loop(psfd_ctx* ctx, int enable);
+
+/* Autotuner (no counterpart in the paper). Tile shapes of the operator's passes that leave
+ * every element's arithmetic and every reduction order unchanged are chosen at run time:
+ *   zx  x-modes per CTA of the z pass (K2), 1-16; the lane-group z transforms (nf = 64,
+ *       128, 256, and 160 in FP32) take 4, 8 or 16;
+ *   rb  rows per CTA of the forward row pass on planes too large for one CTA;
+ *   cx  columns per CTA of the column passes on such planes.
+ * psfd_autotune times the candidate shapes on the context's own grid, illuminations and
+ * buffers (CUDA events around 3 applications each, one tunable at a time, each from the best
+ * shape so far) in the precision of the context's Krylov loop (FP32 for PSFD_FP32_REFINED,
+ * FP64 for PSFD_FP64), and stores the fastest in a process-wide table keyed by (precision,
+ * nx, ny, nslab, nf) that every context of that grid then uses. A grid already in the table
+ * is not timed again unless force != 0. Results are bitwise the same for every shape. The
+ * call synchronises the context's stream, overwrites two of its Krylov scratch vectors (not
+ * the solution), drops its captured graphs, and needs set_potential and set_illumination
+ * first (PSFD_E_STATE). Contexts that captured graphs before keep the old shapes in them.
+ * report (may be NULL): the built-in and the tuned time of one application in ms (0 when the
+ * table already held the grid), the chosen shapes (0 = built-in) and the shapes timed.
+ * psfd_tune_set stores given shapes for a grid and precision (0 = built-in; PSFD_E_ARG for a
+ * shape the kernels cannot take); psfd_tune_reset empties the table. */
+typedef struct {
+  double default_ms, tuned_ms;
+  int zx, rb, cx;
+  int candidates;
+} psfd_tune_report;
+int psfd_autotune(psfd_ctx* ctx, int force, psfd_tune_report* report);
+int psfd_tune_set(const psfd_grid* grid, int precision, int zx, int rb, int cx);
+int psfd_tune_reset(void);
+
 /* Arithmetic of the FP64 residual r = b - A x that certifies a PSFD_FP32_REFINED solve
  * (no counterpart in the paper; the defect correction is not one of its steps).
  *   PSFD_RESID_FP64    every step in FP64;
@@ -196,8 +236,9 @@ int psfd_set_illumination(psfd_ctx* ctx, int n_rhs, const double* theta_deg,
 
 /* Solve A u = b for every illumination (Krylov: BiCGStab; PSFD_FP32_REFINED runs it in
  * complex FP32 inside FP64 defect correction r = b - A u, u += A^-1 r). opts may be NULL.
- * The Krylov loop stays on the device; the host reads the convergence flags every
- * check_every iterations. report may be NULL. Returns PSFD_E_NOT_CONVERGED if some
+ * The Krylov loop stays on the device; the host reads the convergence flags once per sweep
+ * (psfd_set_device_loop), or every check_every iterations with the loop off. report may be
+ * NULL. Returns PSFD_E_NOT_CONVERGED if some
  * right-hand side missed the tolerance (the solution is still stored). */
 int psfd_solve(psfd_ctx* ctx, const psfd_solve_opts* opts, psfd_report* report);
 
@@ -365,13 +406,15 @@ int psfd_profile_get(int cls, const char** name, unsigned long long* launches, d
  * library holds on every GPU it is loaded on until the process exits. A grid needs
  * about nx*ny*(152 + 32*nslab) + 16 KiB of it (128 x 128 x 60: 34.0 MB); larger grids
  * are rejected with PSFD_E_BUDGET before any device work. The first call on each
- * device looks the array's device address up (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture. All calls share the array
- * and it keeps the previous call's contents: calls that overlap on the GPU (other
- * streams, other host threads) race and must be serialised by the caller. The stack
- * arrays are read before return; the call synchronises the stream once when
- * n_layers > 0. Returns PSFD_OK, PSFD_E_ARG, PSFD_E_BUDGET, PSFD_E_ANOMALY or
- * PSFD_E_CUDA. */
+ * device does a one-time set-up: it looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current, so make the first call on a device
+ * before any stream capture begins. All calls share the array and it keeps the previous
+ * call's contents: calls that overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller. The stack arrays are read before return. A stack
+ * with at most 8 distinct media, 16 distinct interfaces and 8 distinct (medium,
+ * thickness) layers -- the Ru / Mo/Si stacks -- is passed to the kernels by value; any
+ * other stack is copied into the array and the call then synchronises the stream once.
+ * Returns PSFD_OK, PSFD_E_ARG, PSFD_E_BUDGET, PSFD_E_ANOMALY or PSFD_E_CUDA. */
 #define PSFD_STATIC_SCRATCH_BYTES (48u * 1024u * 1024u)
 int psfd_apply_fp32_static(const psfd_grid* grid, int n_layers, const double* n_complex,
                            const double* thickness_nm, const double* n_sub, double theta_deg,

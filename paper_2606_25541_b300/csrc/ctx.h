@@ -28,6 +28,13 @@ constexpr int kPoolBicg = 7;
 Plan make_plan(const psfd_grid& g, int precision, int max_rhs, int max_clips);
 bool grid_ok(const psfd_grid* g, std::string& why);
 
+// Krylov estimate of one slot after one tick of a device-side sweep loop (engine.cu).
+struct LoopHist {
+  int iters, pad;
+  double rnorm2, bnorm2;
+};
+constexpr int kLoopHist = 128;  // ticks recorded per slot and loop
+
 // Life cycle of one illumination in a context (see engine.cu).
 enum Phase { PH_FREE = 0, PH_NEW, PH_START, PH_INNER, PH_RESID, PH_DONE };
 
@@ -135,6 +142,20 @@ struct psfd_ctx {
   std::vector<GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;
   bool use_graphs = true;
+  // Device-side sweep loop (engine.cu): while every busy slot is inside a Krylov sweep, the
+  // ticks repeat inside one graph launch (a WHILE node) until no slot is active, so the host
+  // waits once per sweep instead of once per tick.
+  bool device_loop = true;
+  int* d_loop = nullptr;              // [0]: ticks run by the current loop
+  int* d_prev_act = nullptr;          // [max_rhs]: activity at the start of the current tick
+  psfd::LoopHist* d_lhist = nullptr;  // [max_rhs][kLoopHist]: Krylov estimate after each tick
+  int* d_lhist_n = nullptr;           // [max_rhs]
+  int* h_loop = nullptr;              // pinned mirrors of the three above
+  psfd::LoopHist* h_lhist = nullptr;
+  int* h_lhist_n = nullptr;
+  bool loop_ran = false;              // the enqueued tick was a device-side loop
+  int loop_kernels = 0;               // kernels per tick of that loop
+  int loop_precounted = 0;            // of those, already counted while capturing
   int resid_arith = PSFD_RESID_DFLOAT;  // arithmetic of the refined solve's FP64 residual
   unsigned long long graph_clock = 0;
   void drop_graphs() {
@@ -182,7 +203,8 @@ struct psfd_ctx {
     drop_graphs();
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto& q : allocs) cudaFree(q.first);
-    for (void* q : {(void*)h_act, (void*)h_act64, (void*)h_sc, (void*)h_sc64, (void*)h_mask})
+    for (void* q : {(void*)h_act, (void*)h_act64, (void*)h_sc, (void*)h_sc64, (void*)h_mask, (void*)h_loop,
+                    (void*)h_lhist, (void*)h_lhist_n})
       if (q) cudaFreeHost(q);
   }
 };

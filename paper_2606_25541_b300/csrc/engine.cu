@@ -133,20 +133,56 @@ int krylov_finish(psfd_ctx* ctx, const psfd_solve_opts& o, int hi, const int* ma
   return PSFD_OK;
 }
 
+// End of one tick of a device-side sweep loop: record the Krylov estimate of every slot that
+// was active when the tick began, and keep the loop going while some slot is still active and
+// fewer than `cap` ticks have run (the cap is a backstop: the Krylov kernels drop a slot's
+// flag at max_iter, so the loop ends on its own; a loop stopped by the cap leaves its active
+// slots to the host's next tick).
+__global__ void k_sweep_cond(cudaGraphConditionalHandle cond, int R, const int* act, const KScal* sc,
+                             int* prev_act, int* tick, int cap, LoopHist* hist, int* hist_n) {
+  int any = 0;
+  for (int g = threadIdx.x; g < R; g += blockDim.x) {
+    if (prev_act[g]) {
+      const int n = hist_n[g];
+      if (n < kLoopHist) {
+        LoopHist h;
+        h.iters = sc[g].iters;
+        h.pad = 0;
+        h.rnorm2 = sc[g].rnorm2;
+        h.bnorm2 = sc[g].bnorm2;
+        hist[(size_t)g * kLoopHist + n] = h;
+        hist_n[g] = n + 1;
+      }
+    }
+    const int a = act[g];
+    prev_act[g] = a;
+    any |= a;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    const int t = *tick + 1;
+    *tick = t;
+    cudaGraphSetConditional(cond, (any && t < cap) ? 1u : 0u);
+  }
+}
+
 // check_every Krylov iterations of the slots whose device flag is up. The launch sequence
 // depends only on the configuration in the key below (the per-slot state -- scalars, flags,
 // vectors -- lives on the device), so it is captured once into a CUDA graph and replayed:
 // one launch per tick instead of about ten per iteration. Profiling runs bypass the graphs
 // (their events are recorded per launch). The capture happens on the context's private
 // stream in relaxed mode; nothing runs during it, and the first replay follows at once.
-int inner_step(psfd_ctx* ctx, const psfd_solve_opts& o, int hi, bool f32) {
+// With loop = true the graph is a WHILE node whose body is one tick followed by
+// k_sweep_cond: one launch runs ticks until no slot is active (the whole sweep).
+int inner_step(psfd_ctx* ctx, const psfd_solve_opts& o, int hi, bool f32, bool loop) {
   auto direct = [&]() { return f32 ? krylov_iterate<float2>(ctx, o, hi) : krylov_iterate<double2>(ctx, o, hi); };
   if (!ctx->use_graphs || prof_on()) return direct();
   long long tol_bits;
   const double tol = f32 ? o.inner_tol : 0.5 * o.tol;
   std::memcpy(&tol_bits, &tol, sizeof(tol_bits));
-  const long long key[8] = {hi,
-                            (long long)f32,
+  const int cap = (o.max_iter + o.check_every - 1) / o.check_every + 1;
+  const long long key[8] = {hi | ((long long)cap << 20),
+                            (long long)f32 | ((long long)loop << 1),
                             o.krylov,
                             o.krylov == PSFD_BICGSTAB ? 0 : o.restart,
                             o.check_every,
@@ -156,6 +192,7 @@ int inner_step(psfd_ctx* ctx, const psfd_solve_opts& o, int hi, bool f32) {
   psfd_ctx::GraphEntry* hit = nullptr;
   for (auto& e : ctx->graphs)
     if (std::memcmp(e.key, key, sizeof(key)) == 0) hit = &e;
+  int precounted = 0;
   if (!hit) {
     if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     constexpr size_t kMaxGraphs = 32;
@@ -170,17 +207,57 @@ int inner_step(psfd_ctx* ctx, const psfd_solve_opts& o, int hi, bool f32) {
     std::memcpy(e.key, key, sizeof(key));
     cudaStream_t user = ctx->stream;
     const unsigned long long n0 = launch_total();
-    CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
-    ctx->stream = ctx->cap_stream;
-    const int rc = direct();
-    ctx->stream = user;
     cudaGraph_t g = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
-    if (rc != PSFD_OK || ce != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      cudaGetLastError();
-      if (rc != PSFD_OK) return rc;
-      return ctx->cuda_fail(ce, "cudaStreamEndCapture");
+    if (loop) {
+      // outer graph: one WHILE node (condition 1 at every launch); its body is captured below
+      CK(cudaGraphCreate(&g, 0));
+      cudaGraphConditionalHandle cond;
+      cudaGraphNodeParams np{};
+      np.type = cudaGraphNodeTypeConditional;
+      cudaGraphNode_t node;
+      cudaError_t ge = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+      if (ge == cudaSuccess) {
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        ge = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+      }
+      if (ge == cudaSuccess)
+        ge = cudaStreamBeginCaptureToGraph(ctx->cap_stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed);
+      if (ge != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return ctx->cuda_fail(ge, "device loop graph");
+      }
+      ctx->stream = ctx->cap_stream;
+      int rc = direct();
+      if (rc == PSFD_OK) {
+        k_sweep_cond<<<1, 256, 0, ctx->cap_stream>>>(cond, hi, ctx->act, ctx->sc, ctx->d_prev_act, ctx->d_loop, cap,
+                                                      ctx->d_lhist, ctx->d_lhist_n);
+        count_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = PSFD_E_CUDA;
+      }
+      ctx->stream = user;
+      cudaGraph_t body = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &body);
+      if (rc != PSFD_OK || ce != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        if (rc != PSFD_OK) return rc;
+        return ctx->cuda_fail(ce, "cudaStreamEndCapture (device loop)");
+      }
+    } else {
+      CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
+      ctx->stream = ctx->cap_stream;
+      const int rc = direct();
+      ctx->stream = user;
+      const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
+      if (rc != PSFD_OK || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        if (rc != PSFD_OK) return rc;
+        return ctx->cuda_fail(ce, "cudaStreamEndCapture");
+      }
     }
     const cudaError_t ie = cudaGraphInstantiate(&e.exec, g, 0);
     if (ie != cudaSuccess) {
@@ -191,11 +268,30 @@ int inner_step(psfd_ctx* ctx, const psfd_solve_opts& o, int hi, bool f32) {
     e.kernels = (int)(launch_total() - n0);  // counted during the capture, run by the first replay
     ctx->graphs.push_back(e);
     hit = &ctx->graphs.back();
-  } else {
+    precounted = e.kernels;
+  } else if (!loop) {
     count_launch(hit->kernels);
   }
   hit->last_use = ++ctx->graph_clock;
+  if (loop) {  // a loop's kernel count is known once its ticks are read back (engine_complete)
+    ctx->loop_kernels = hit->kernels;
+    ctx->loop_precounted = precounted;
+  }
   CK(cudaGraphLaunch(hit->exec, ctx->stream));
+  return PSFD_OK;
+}
+
+// Device buffers of the sweep loop (allocated on first use).
+int ensure_loop_buffers(psfd_ctx* ctx) {
+  if (ctx->d_loop) return PSFD_OK;
+  const int n = ctx->max_rhs;
+  RC(ctx->dalloc(&ctx->d_loop, 1));
+  RC(ctx->dalloc(&ctx->d_prev_act, n));
+  RC(ctx->dalloc(&ctx->d_lhist, (size_t)n * kLoopHist));
+  RC(ctx->dalloc(&ctx->d_lhist_n, n));
+  CK(cudaMallocHost(&ctx->h_loop, sizeof(int)));
+  CK(cudaMallocHost(&ctx->h_lhist, sizeof(LoopHist) * (size_t)n * kLoopHist));
+  CK(cudaMallocHost(&ctx->h_lhist_n, sizeof(int) * n));
   return PSFD_OK;
 }
 
@@ -293,8 +389,24 @@ int engine_enqueue(psfd_ctx* ctx, const psfd_solve_opts& o, bool* pending) {
     RC(fp64_residual(ctx, ctx->d_mask[1], o.tol, R));
     *pending = true;
   }
+  ctx->loop_ran = false;
   if (select(PH_INNER)) {
-    RC(inner_step(ctx, o, R, f32));
+    // every busy slot inside a sweep: run the sweep to its end on the device
+    const bool loop = ctx->device_loop && ctx->use_graphs && !prof_on() && !*pending;
+    if (loop) {
+      RC(ensure_loop_buffers(ctx));
+      CK(cudaMemsetAsync(ctx->d_loop, 0, sizeof(int), st));
+      CK(cudaMemsetAsync(ctx->d_lhist_n, 0, sizeof(int) * R, st));
+      CK(cudaMemcpyAsync(ctx->d_prev_act, ctx->act, sizeof(int) * R, cudaMemcpyDeviceToDevice, st));
+    }
+    RC(inner_step(ctx, o, R, f32, loop));
+    if (loop) {
+      CK(cudaMemcpyAsync(ctx->h_loop, ctx->d_loop, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(ctx->h_lhist_n, ctx->d_lhist_n, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(ctx->h_lhist, ctx->d_lhist, sizeof(LoopHist) * (size_t)R * kLoopHist,
+                         cudaMemcpyDeviceToHost, st));
+      ctx->loop_ran = true;
+    }
     *pending = true;
   }
   if (*pending) {  // read-back of the per-slot scalars, waited for in engine_complete
@@ -312,6 +424,8 @@ int engine_complete(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
   cudaStream_t st = ctx->stream;
   if (R > 0) {
     CK(cudaStreamSynchronize(st));
+    if (ctx->loop_ran)  // kernels the loop ran: its ticks times the kernels of one tick
+      count_launch(std::max(0, *ctx->h_loop * ctx->loop_kernels - ctx->loop_precounted));
     std::vector<int> to_update(R, 0), to_start(R, 0), to_done(R, 0);
     const double tol2 = o.tol * o.tol;
     auto record = [&](int g, int it, int kind, double rel) {
@@ -358,8 +472,15 @@ int engine_complete(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
         }
         case PH_INNER: {
           const KScal& si = ctx->h_sc[g];
-          if (o.krylov != PSFD_GMRES && si.bnorm2 > 0.0 && si.iters > 0)
+          if (ctx->loop_ran) {  // the estimates after every tick of the device-side loop
+            for (int k = 0; k < std::min(ctx->h_lhist_n[g], kLoopHist); ++k) {
+              const LoopHist& h = ctx->h_lhist[(size_t)g * kLoopHist + k];
+              if (o.krylov != PSFD_GMRES && h.bnorm2 > 0.0 && h.iters > 0)
+                record(g, ctx->iters[g] + h.iters, 0, std::sqrt(h.rnorm2 / h.bnorm2) * ctx->sweep_rel[g]);
+            }
+          } else if (o.krylov != PSFD_GMRES && si.bnorm2 > 0.0 && si.iters > 0) {
             record(g, ctx->iters[g] + si.iters, 0, std::sqrt(si.rnorm2 / si.bnorm2) * ctx->sweep_rel[g]);
+          }
           if (!ctx->h_act[g]) {  // sweep ended (converged, cycle full or breakdown): correct x64
             ctx->iters[g] += si.iters;
             to_update[g] = 1;
@@ -410,6 +531,7 @@ int engine_complete(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
         if (to_done[g]) ctx->phase[g] = PH_DONE;
     }
     ctx->enq_hi = 0;
+    ctx->loop_ran = false;
   }
   int n = 0;
   for (int g = 0; g < ctx->max_rhs; ++g) n += ctx->phase[g] != PH_FREE && ctx->phase[g] != PH_DONE;

@@ -128,6 +128,20 @@ int op_blocks_per_rhs(int nx, int ny, int nslab, bool fp64);
 // Whether the kernels are built for an FFT length.
 bool fft_length_supported(int n);
 
+// Tile shapes chosen at run time by the autotuner (tune.cu), per grid and precision; a zero
+// field keeps the built-in choice. Only shapes that leave every element's arithmetic and
+// every reduction order unchanged are tunable, so a tuned operator gives bitwise the same
+// results as the built-in one.
+struct RunTune {
+  int zx;  // K2: transverse x-modes per CTA of the z pass
+  int rb;  // K1 on split planes: rows per CTA of the forward row pass
+  int cx;  // split planes: columns per CTA of the column passes (forward and inverse)
+};
+RunTune run_tune(bool fp64, int nx, int ny, int nslab, int nf);
+void set_run_tune(bool fp64, int nx, int ny, int nslab, int nf, RunTune t);
+bool has_run_tune(bool fp64, int nx, int ny, int nslab, int nf);
+void clear_run_tune();
+
 // Kernel-launch accounting and optional per-class CUDA-event timing (psfd.cu).
 enum ProfClass {
   PK_FWD32 = 0, PK_Z32, PK_INV32, PK_FWD64, PK_Z64, PK_INV64, PK_VEC32, PK_VEC64, PK_SCALAR, PK_SETUP, PK_N

@@ -629,12 +629,15 @@ template <typename C, int NF> __host__ __device__ constexpr bool zcol_r10() { re
 // (128: register transform with 192 threads, 160: the 16 x 10 transform with 384 threads); it
 // is issue- or latency-bound, and more resident warps hide the shared-memory and barrier
 // waits (neither cap spills). 1 = no register cap.
-template <typename C, int NF> __host__ __device__ constexpr int zcol_min_blocks() {
-  return (sizeof(C) == 8 && NF == 128) ? 5 : (zcol_r10<C, NF>() ? 3 : 1);
+// Scaled with the CTA size NT (the 8-mode CTA has 192 and 384 threads), so that the register
+// cap stays the same for the 4- and 16-mode CTAs the autotuner may pick.
+template <typename C, int NF, int NT> __host__ __device__ constexpr int zcol_min_blocks() {
+  return (sizeof(C) == 8 && NF == 128) ? (960 / NT > 1 ? 960 / NT : 1)
+                                       : (zcol_r10<C, NF>() ? (1152 / NT > 1 ? 1152 / NT : 1) : 1);
 }
 
 template <typename C, int NF, int NT>
-__global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF>()) k_zcol(OpCall<C> a, int tx) {
+__global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCall<C> a, int tx) {
   using R = typename RealOf<C>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr bool F32 = sizeof(C) == sizeof(float2);

@@ -126,7 +126,7 @@ int launch_half_inv(const OpCall<C>& a, const C* uin) {
 template <typename C, int NX, int IN>
 int launch_rows_fwd(const OpCall<C>& a) {
   constexpr int NT = 256;
-  const int rb = row_block(NX, a.ny, Tune<C>::ROW_ELEMS);
+  const int rb = rows_fwd_rb_of(a);
   const size_t smem = (size_t)(rb * fft_phys(NX) + NX) * sizeof(C);
   auto k = k_rows_fwd<C, NX, IN, NT>;
   if (set_smem(k, smem, split_min_blocks<C, NX>() > 1)) return PSFD_E_CUDA;
@@ -177,10 +177,56 @@ inline int zcol_tile(int nx, int nf) {
   return tx;
 }
 
+// Lanes per column of the z pass: NF/16 for the register transform, 16 for the FP32 16 x 10
+// transform, 0 for the CTA-wide Stockham transform.
+__host__ __device__ constexpr int zcol_lanes_of(bool f32, int nf) {
+  return (nf == 64 || nf == 128 || nf == 256) ? nf / 16 : ((f32 && nf == 160) ? 16 : 0);
+}
+constexpr size_t kMaxSmem = 227 * 1024;
+
+// Run-time shapes (RunTune) must divide the grid, fit shared memory and, for the lane-group
+// transforms, give one of the instantiated CTA sizes (x-modes 4, 8 or 16).
+template <typename C>
+inline bool zcol_tile_ok(int nx, int nf, int tx) {
+  if (tx < 1 || tx > 16 || nx % tx) return false;
+  const int lanes = zcol_lanes_of(sizeof(C) == 8, nf);
+  if (lanes && tx != 4 && tx != 8 && tx != 16) return false;
+  if (!lanes && tx > Tune<C>::ZCOL_NT) return false;
+  return zcol_smem_bytes<C>(nf, tx) <= kMaxSmem;
+}
+template <typename C>
+inline bool rows_fwd_ok(int nx, int ny, int rb) {
+  return rb >= 1 && ny % rb == 0 && (size_t)(rb * fft_phys(nx) + nx) * sizeof(C) <= kMaxSmem;
+}
+template <typename C>
+inline bool cols_tile_ok(int nx, int ny, int tx) {
+  return tx >= 1 && tx <= 256 && 256 % tx == 0 && nx % tx == 0 && cols_smem_bytes<C>(ny, tx) <= kMaxSmem;
+}
+template <typename C>
+inline RunTune tune_of(const OpCall<C>& a) {
+  return run_tune(sizeof(C) == 16, a.nx, a.ny, a.nslab, a.nf);
+}
+// The shapes the launches use: the tuned one when set and valid, else the built-in one.
+template <typename C>
+inline int zcol_tx_of(const OpCall<C>& a) {
+  const int t = tune_of(a).zx;
+  return (t && zcol_tile_ok<C>(a.nx, a.nf, t)) ? t : zcol_tile<C>(a.nx, a.nf);
+}
+template <typename C>
+inline int rows_fwd_rb_of(const OpCall<C>& a) {
+  const int t = tune_of(a).rb;
+  return (t && rows_fwd_ok<C>(a.nx, a.ny, t)) ? t : row_block(a.nx, a.ny, Tune<C>::ROW_ELEMS);
+}
+template <typename C>
+inline int cols_tx_of(const OpCall<C>& a) {
+  const int t = tune_of(a).cx;
+  return (t && cols_tile_ok<C>(a.nx, a.ny, t)) ? t : cols_tile<C>(a.nx, a.ny);
+}
+
 template <typename C, int NY, bool INV>
 int launch_cols(const OpCall<C>& a) {
   constexpr int NT = 256;
-  const int tx = cols_tile<C>(a.nx, NY);
+  const int tx = cols_tx_of(a);
   const size_t smem = cols_smem_bytes<C>(NY, tx);
   auto k = k_cols<C, NY, INV, NT>;
   if (set_smem(k, smem, split_min_blocks<C, NY>() > 1)) return PSFD_E_CUDA;
@@ -189,17 +235,30 @@ int launch_cols(const OpCall<C>& a) {
   return PSFD_OK;
 }
 
-template <typename C, int NF>
-int launch_zcol(const OpCall<C>& a) {
-  constexpr int NT = zcol_reg<C, NF>() ? 24 * (NF / 16) : (zcol_r10<C, NF>() ? 384 : Tune<C>::ZCOL_NT);
+template <typename C, int NF, int NT>
+int launch_zcol_nt(const OpCall<C>& a, int tx) {
   static_assert(((8 + (NF + 15) / 16) | 1) == phase_pitch<NF>(), "phase table size");
-  const int tx = zcol_tile<C>(a.nx, NF);
   const size_t smem = zcol_smem_bytes<C>(NF, tx);
   auto k = k_zcol<C, NF, NT>;
-  if (set_smem(k, smem, zcol_min_blocks<C, NF>() > 1)) return PSFD_E_CUDA;
+  if (set_smem(k, smem, zcol_min_blocks<C, NF, NT>() > 1)) return PSFD_E_CUDA;
   k<<<dim3(a.nx / tx, a.ny, a.nrhs), NT, smem, a.stream>>>(a, tx);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
+}
+
+// The lane-group transforms run 3 tx groups per CTA, one per (component, x-mode): the CTA
+// size follows tx (instantiated for 4, 8 and 16 x-modes; fewer leave groups idle).
+template <typename C, int NF>
+int launch_zcol(const OpCall<C>& a) {
+  constexpr int LN = zcol_lanes_of(sizeof(C) == 8, NF);
+  const int tx = zcol_tx_of(a);
+  if constexpr (LN > 0) {
+    if (tx == 16) return launch_zcol_nt<C, NF, 3 * 16 * LN>(a, tx);
+    if (tx == 8) return launch_zcol_nt<C, NF, 3 * 8 * LN>(a, tx);
+    return launch_zcol_nt<C, NF, 3 * 4 * LN>(a, tx);
+  } else {
+    return launch_zcol_nt<C, NF, Tune<C>::ZCOL_NT>(a, tx);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -324,10 +383,10 @@ void pass_ctas(const OpCall<C>& a, double* xy, double* z) {
   if (use_fused<C>(a.nx, a.ny)) {
     *xy = use_half<C>(a.nx, a.ny) ? 2 * planes : planes;
   } else {
-    const int rb = row_block(a.nx, a.ny, Tune<C>::ROW_ELEMS);
-    *xy = planes * ((double)(a.ny / rb) + (double)(a.nx / cols_tile<C>(a.nx, a.ny)));
+    const int rb = rows_fwd_rb_of(a);
+    *xy = planes * ((double)(a.ny / rb) + (double)(a.nx / cols_tx_of(a)));
   }
-  *z = (double)(a.nx / zcol_tile<C>(a.nx, a.nf)) * a.ny * a.nrhs;
+  *z = (double)(a.nx / zcol_tx_of(a)) * a.ny * a.nrhs;
 }
 
 template <typename C>

@@ -565,6 +565,12 @@ int psfd_set_graphs(psfd_ctx* ctx, int enable) {
   return PSFD_OK;
 }
 
+int psfd_set_device_loop(psfd_ctx* ctx, int enable) {
+  if (!ctx) return PSFD_E_ARG;
+  ctx->device_loop = enable != 0;
+  return PSFD_OK;
+}
+
 int psfd_set_residual_arith(psfd_ctx* ctx, int kind) {
   if (!ctx) return PSFD_E_ARG;
   if (kind != PSFD_RESID_FP64 && kind != PSFD_RESID_DFLOAT) return ctx->fail(PSFD_E_ARG, "unknown residual arithmetic");

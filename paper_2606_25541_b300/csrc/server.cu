@@ -131,6 +131,7 @@ Bucket* make_bucket(psfd_server* s, const psfd_grid& g, int cap, int* rc) {
   }
   b->stream = b->prio[kPrioLevels - 1];
   *rc = ctx_create(&b->ctx, &g, s->precision, cap, cap, 0, b->stream);
+  if (*rc == PSFD_OK) b->ctx->device_loop = false;  // admission happens between ticks
   if (*rc == PSFD_OK) *rc = ensure_pool(b->ctx, s->opts);
   if (*rc != PSFD_OK) {
     if (b->ctx) psfd_destroy(b->ctx);

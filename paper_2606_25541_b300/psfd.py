@@ -52,6 +52,11 @@ class Request(ctypes.Structure):
                 ("pol", ctypes.POINTER(ctypes.c_int))]
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("default_ms", ctypes.c_double), ("tuned_ms", ctypes.c_double), ("zx", ctypes.c_int),
+                ("rb", ctypes.c_int), ("cx", ctypes.c_int), ("candidates", ctypes.c_int)]
+
+
 class PsfdError(RuntimeError):
     def __init__(self, status, msg=""):
         super().__init__(f"psfd status {status}: {msg}")
@@ -76,7 +81,11 @@ _SIGS = {
     "psfd_set_potential": (_I, [_P, _P, _I]),
     "psfd_set_illumination": (_I, [_P, _I, _D, _D, _IP]),
     "psfd_set_graphs": (_I, [_P, _I]),
+    "psfd_set_device_loop": (_I, [_P, _I]),
     "psfd_set_residual_arith": (_I, [_P, _I]),
+    "psfd_autotune": (_I, [_P, _I, ctypes.POINTER(TuneReport)]),
+    "psfd_tune_set": (_I, [ctypes.POINTER(Grid), _I, _I, _I, _I]),
+    "psfd_tune_reset": (_I, []),
     "psfd_set_green": (_I, [_P, _I, ctypes.c_double]),
     "psfd_solve": (_I, [_P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Report)]),
     "psfd_solve_fixed_point": (_I, [_P, ctypes.POINTER(SolveOpts), _I, ctypes.c_double, ctypes.POINTER(Report)]),
@@ -133,6 +142,18 @@ def apply_differential(n, nz, n_pml, dx, dz, wavelength, eps_bg, theta_deg, phi_
                                           ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(E.data_ptr()),
                                           ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(work.data_ptr()),
                                           _stream_ptr(stream))
+
+
+def tune_set(grid: Grid, precision: int, zx: int = 0, rb: int = 0, cx: int = 0):
+    """Store tile shapes for a grid and precision in the autotuner's table (0 = built-in)."""
+    st = load().psfd_tune_set(ctypes.byref(grid), int(precision), int(zx), int(rb), int(cx))
+    if st != OK:
+        raise PsfdError(st, strerror(st))
+
+
+def tune_reset():
+    """Empty the autotuner's table (every grid back to the built-in shapes)."""
+    load().psfd_tune_reset()
 
 
 def launch_count() -> int:
@@ -291,6 +312,19 @@ class Solver:
     def set_graphs(self, enable: bool):
         """Replay the Krylov step as a CUDA graph (default) or launch its kernels one by one."""
         self._check(self.lib.psfd_set_graphs(self.ctx, int(bool(enable))))
+
+    def autotune(self, force: bool = False) -> dict:
+        """Time the candidate tile shapes on this context's grid and keep the fastest
+        (process-wide, per grid and precision); returns the report."""
+        r = TuneReport()
+        self._check(self.lib.psfd_autotune(self.ctx, int(bool(force)), ctypes.byref(r)))
+        return {"default_ms": r.default_ms, "tuned_ms": r.tuned_ms, "zx": r.zx, "rb": r.rb, "cx": r.cx,
+                "candidates": r.candidates}
+
+    def set_device_loop(self, enable: bool):
+        """Run each Krylov sweep as one graph launch that loops on the device (default) or
+        return to the host after every check_every iterations."""
+        self._check(self.lib.psfd_set_device_loop(self.ctx, int(bool(enable))))
 
     def set_residual_arith(self, kind: int):
         """RESID_DFLOAT (default): the refined solve's FP64 residual runs its z transforms and

@@ -56,3 +56,22 @@ def test_host_side_entry_points():
     with pytest.raises(psfd.PsfdError):
         psfd.workspace_bytes(bad, psfd.FP64, 1)
     assert lib.psfd_last_error(None) == b"null context"
+
+
+def test_tune_set_rejects_shapes_the_kernels_cannot_take():
+    from paper_2606_25541_b300 import psfd
+    build_mod.build()
+    psfd.load()
+    g = psfd.make_grid(128, 128, 60, 128, 1.0, 1.0, 1.0, 13.5)
+    for bad in ((3, 0, 0), (2, 0, 0), (32, 0, 0), (0, 0, 0)):
+        if bad == (0, 0, 0):
+            psfd.tune_set(g, psfd.FP32_REFINED, *bad)  # all built-in: accepted
+            continue
+        with pytest.raises(psfd.PsfdError):  # lane-group z transform: 4, 8 or 16 x-modes only
+            psfd.tune_set(g, psfd.FP32_REFINED, *bad)
+    psfd.tune_set(g, psfd.FP32_REFINED, 16, 0, 0)
+    g2 = psfd.make_grid(256, 256, 12, 96, 1.0, 1.0, 1.0, 13.5)
+    psfd.tune_set(g2, psfd.FP64, 2, 4, 8)
+    with pytest.raises(psfd.PsfdError):
+        psfd.tune_set(g2, psfd.FP64, 0, 3, 0)  # rows per CTA must divide ny
+    psfd.tune_reset()

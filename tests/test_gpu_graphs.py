@@ -1,5 +1,6 @@
-"""CUDA-graph replay of the Krylov step (psfd_set_graphs): bitwise the same results and the
-same kernel count as launching the kernels one by one."""
+"""CUDA-graph replay of the Krylov step (psfd_set_graphs) and the device-side sweep loop
+(psfd_set_device_loop): bitwise the same results, iteration counts and residual history, and
+the same kernel count, as launching the kernels one by one."""
 import numpy as np
 import pytest
 
@@ -19,10 +20,11 @@ def psfd():
     return m
 
 
-def _run(psfd, prob, precision, graphs, **kw):
+def _run(psfd, prob, precision, graphs, loop=True, **kw):
     s = psfd.Solver.from_problem(prob, precision)
     s.set_graphs(graphs)
-    reps, sols = [], []
+    s.set_device_loop(loop)
+    reps, sols, hists = [], [], []
     for _ in range(2):  # the second solve replays what the first captured
         s.set_illumination(prob.theta_deg, prob.phi_deg, prob.pol)
         torch.cuda.synchronize()
@@ -31,8 +33,9 @@ def _run(psfd, prob, precision, graphs, **kw):
         torch.cuda.synchronize()
         reps.append((rep["iterations"], rep["outer"], rep["relres"], psfd.launch_count() - n0))
         sols.append([s.get_solution(i) for i in range(prob.n_rhs)])
+        hists.append([s.residual_history(i) for i in range(prob.n_rhs)])
     s.close()
-    return reps, sols
+    return reps, sols, hists
 
 
 @pytest.mark.parametrize("precision,krylov", [(0, 0), (1, 0), (1, 1)])
@@ -41,9 +44,19 @@ def test_graph_replay_is_bitwise_the_same(psfd, precision, krylov):
                               theta=(6.0, 8.0, 4.0), phi=(0.0, 45.0, 90.0), pol=(0, 1, 0))
     kw = dict(tol=1e-10 if precision == 0 else 1e-8, inner_tol=1e-4, max_iter=300, max_outer=10,
               check_every=3, krylov=krylov, restart=8 if krylov else 0)
-    reps_on, sols_on = _run(psfd, prob, precision, True, **kw)
-    reps_off, sols_off = _run(psfd, prob, precision, False, **kw)
-    assert reps_on == reps_off, (reps_on, reps_off)
-    for a, b in zip(sols_on, sols_off):
-        for x, y in zip(a, b):
-            assert np.array_equal(x, y)
+    runs = {name: _run(psfd, prob, precision, graphs, loop, **kw)
+            for name, graphs, loop in (("loop", True, True), ("ticks", True, False), ("plain", False, False))}
+    reps0, sols0, hists0 = runs["plain"]
+    for name in ("loop", "ticks"):
+        reps, sols, hists = runs[name]
+        if name == "ticks":
+            assert reps == reps0, (name, reps, reps0)
+        else:  # the loop also runs one small condition kernel per tick
+            assert [r[:3] for r in reps] == [r[:3] for r in reps0], (name, reps, reps0)
+            assert all(a[3] > b[3] for a, b in zip(reps, reps0)), (reps, reps0)
+        for a, b in zip(sols, sols0):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y), name
+        for a, b in zip(hists, hists0):
+            for x, y in zip(a, b):
+                assert all(np.array_equal(x[k], y[k]) for k in x), name
