@@ -10,8 +10,10 @@
 // spectra, with
 //   - the forward and inverse z transforms (the register four-step transform, 16 x nf/16)
 //     and the dyadic products in double-float (dfloat.cuh: ~48 significant bits);
-//   - the Green's scalars S_l, E_l, the reflection T_R E(plane 0) and the per-column
-//     exponentials in FP64 (a few dozen FP64 operations per column, not per element);
+//   - the Green's scalars S_l, E_l in double-float too (the FP32 reciprocal refined by a
+//     Newton step; the same closed forms and series as the FP64 kernel);
+//   - the reflection T_R E(plane 0) and the per-column exponentials in FP64 (a few dozen
+//     FP64 operations per column, not per element);
 //   - the reflection phase table by binary powering in double-float.
 // Columns of length 64 and 128 on the periodic (z-windowed) kernel; other lengths and the
 // isolated clip's spherical kernel stay on the FP64 k_zcol.
@@ -32,9 +34,58 @@ __host__ __device__ constexpr int df_pitch() { return fft_phys(NF) | 1; }
 template <int NF>
 size_t df_smem_bytes(int tx) {
   const size_t c16 = (size_t)3 * tx * df_pitch<NF>() + NF + 3 * tx + (size_t)tx * phase_pitch<NF>();
-  const size_t c16col = 5 * (size_t)tx;           // beta, exp(i beta L), exp(i beta dz), exp(i beta 8 dz), (qx, qy)
+  // beta, exp(i beta L) (FP64), exp(i beta dz), exp(i beta 8 dz), beta, exp(i beta L) (double-float), (qx, qy)
+  const size_t c16col = 7 * (size_t)tx;
   const size_t c8 = 2 * (size_t)NF;               // kz (dfr) and kz (FP64)
   return (c16 + c16col) * 16 + c8 * 8 + 16;
+}
+
+// 1 / x in double-float: the FP32 reciprocal refined by one Newton step, r (1 + (1 - x r)),
+// relative error about 2^-46.
+__device__ __forceinline__ dfr df_recip(dfr x) {
+  const dfr r(__frcp_rn(x.hi), 0.0f);
+  const dfr e = dfr(1.0f, 0.0f) - x * r;
+  return r + r * e;
+}
+// a / b = conj(b) a / |b|^2 in double-float
+__device__ __forceinline__ dfc df_cdiv(dfc a, dfc b) {
+  const dfr inv = df_recip(b.x * b.x + b.y * b.y);
+  const dfc n = cmulc(b, a);
+  return mk(n.x * inv, n.y * inv);
+}
+// 1/K as the nearest double-float (compile-time constants)
+template <int K> struct DfInv {
+  static constexpr float hi = (float)(1.0 / K);
+  static constexpr float lo = (float)(1.0 / K - (double)(float)(1.0 / K));
+};
+// phi1(w) = 1 + w/2 (1 + w/3 (1 + ...)) by Horner from the K-th term down
+template <int K>
+__device__ __forceinline__ void df_phi1_horner(dfc w, dfc& phi) {
+  const dfc t = cmul(w, phi);
+  const dfr ik(DfInv<K>::hi, DfInv<K>::lo);
+  phi = mk(dfr(1.0f, 0.0f) + t.x * ik, t.y * ik);
+  if constexpr (K > 2) df_phi1_horner<K - 1>(w, phi);
+}
+// The windowed Green's scalars of one mode at |kz| = kap (the same closed forms as the FP64
+// and FP32 kernels, Sec. 3's one-dimensional window): with delta = beta - kap and E =
+// (-1)^l exp(i beta L), S = (E - 1) / (delta (kap + beta)), or i L phi1(i delta L) / (kap + beta)
+// by its Taylor series where |delta L| < 1/2 (15 terms: below 1e-15 there); both scaled by the
+// inverse-transform normalisation, Es = E / kb^2 likewise.
+__device__ __forceinline__ void green_scalars_df(dfr kap, dfc beta, dfc E, dfr L, dfr cinv, dfr scale, dfc& S,
+                                                 dfc& Es) {
+  const dfc d = mk(beta.x - kap, beta.y);
+  const dfc kpb = mk(kap + beta.x, beta.y);
+  const dfc w = mk(-(d.y * L), d.x * L);
+  if (w.x.hi * w.x.hi + w.y.hi * w.y.hi < 0.25f) {
+    dfc phi = mk(dfr(1.0f, 0.0f), dfr(0.0f, 0.0f));
+    df_phi1_horner<15>(w, phi);
+    S = df_cdiv(mk(-(phi.y * L), phi.x * L), kpb);
+  } else {
+    S = df_cdiv(mk(E.x - dfr(1.0f, 0.0f), E.y), cmul(d, kpb));
+  }
+  S = mk(S.x * scale, S.y * scale);
+  const dfr es = cinv * scale;
+  Es = mk(E.x * es, E.y * es);
 }
 
 // CTAs per SM the kernel is compiled for: at nf = 128 three (96 registers, a few bytes of
@@ -42,7 +93,7 @@ size_t df_smem_bytes(int tx) {
 // so resident warps count more than the spill); 1 = no register cap.
 template <int NF> __host__ __device__ constexpr int df_min_blocks() { return NF == 128 ? 3 : 1; }
 
-template <int NF, int NT>
+template <int NF, int NT, bool WDF>
 __global__ void __launch_bounds__(NT, df_min_blocks<NF>()) k_zcol_df(OpCall<double2> a, int tx) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int P = df_pitch<NF>();
@@ -58,7 +109,9 @@ __global__ void __launch_bounds__(NT, df_min_blocks<NF>()) k_zcol_df(OpCall<doub
   double2* cebl = cbeta + tx;   // exp(i beta L)
   dfc* ce1 = reinterpret_cast<dfc*>(cebl + tx);  // exp(i beta dz)
   dfc* ce8 = ce1 + tx;                            // exp(i beta 8 dz)
-  dfr* cq = reinterpret_cast<dfr*>(ce8 + tx);     // 2 tx: qx, qy
+  dfc* cbeta_d = ce8 + tx;                        // beta
+  dfc* cebl_d = cbeta_d + tx;                      // exp(i beta L)
+  dfr* cq = reinterpret_cast<dfr*>(cebl_d + tx);  // 2 tx: qx, qy
   dfr* kzd = cq + 2 * tx;       // signed kz_l
   double* kz64 = reinterpret_cast<double*>(kzd + NF);
 
@@ -79,6 +132,8 @@ __global__ void __launch_bounds__(NT, df_min_blocks<NF>()) k_zcol_df(OpCall<doub
     const ModeEntry me = a.modes[mbase + t];
     cbeta[t] = me.beta;
     cebl[t] = me.ebL;
+    cbeta_d[t] = to_dfc(me.beta);
+    cebl_d[t] = to_dfc(me.ebL);
     ce1[t] = to_dfc(cexp_d(make_double2(-me.beta.y * a.dz, me.beta.x * a.dz)));
     ce8[t] = to_dfc(cexp_d(make_double2(-8.0 * me.beta.y * a.dz, 8.0 * me.beta.x * a.dz)));
     cq[2 * t] = to_dfr(rp.qix + two_pi * (double)fft_freq(x0 + t, nx) / ((double)nx * a.dx));
@@ -95,11 +150,14 @@ __global__ void __launch_bounds__(NT, df_min_blocks<NF>()) k_zcol_df(OpCall<doub
     dfc v[16];
     if (rvalid) {
       const int cc = rf / tx, t = rf % tx;
-      const double2* src = a.work + ((size_t)lr * 3 + cc) * ns * pstride + (size_t)y * nx + x0 + t;
+      const size_t so = ((size_t)lr * 3 + cc) * ns * pstride + (size_t)y * nx + x0 + t;
+      const double2* src = a.work + so;
+      const dfc* srcd = reinterpret_cast<const dfc*>(a.work) + so;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int n = rj + N2 * k;
-        v[k] = (n >= 1 && n <= ns) ? to_dfc(src[(size_t)(n - 1) * pstride]) : zero;
+        if (n >= 1 && n <= ns) v[k] = WDF ? srcd[(size_t)(n - 1) * pstride] : to_dfc(src[(size_t)(n - 1) * pstride]);
+        else v[k] = zero;
       }
 #pragma unroll
       for (int k = 8; k < 16; ++k) v[k] = zero;
@@ -120,18 +178,18 @@ __global__ void __launch_bounds__(NT, df_min_blocks<NF>()) k_zcol_df(OpCall<doub
   }
   __syncthreads();
 
-  // Green's scalars in FP64 (one evaluation serves l and nf - l), products in double-float
-  const double L = 0.5 * (double)NF * a.dz;
-  const double cinv = 1.0 / (a.kb * a.kb);
-  const double scale = 1.0 / ((double)NF * (double)nx * (double)ny);
-  const dfr cinv_d = to_dfr(cinv);
+  // Green's scalars (one evaluation serves l and nf - l) and products in double-float
+  const dfr L_d = to_dfr(0.5 * (double)NF * a.dz);
+  const dfr cinv_d = to_dfr(1.0 / (a.kb * a.kb));
+  const dfr scale_d = to_dfr(1.0 / ((double)NF * (double)nx * (double)ny));
   for (int i = threadIdx.x; i < tx * (HF + 1); i += NT) {
     const int t = i / (HF + 1), l = i % (HF + 1);
-    double2 E = cebl[t];
+    dfc E = cebl_d[t];
     if (l & 1) E = cneg(E);
-    double2 S, Es;
-    green_scalars<double2>(fabs(kz64[l]), 0.0, cbeta[t], make_double2(0.0, 0.0), E, L, cinv, scale, S, Es);
-    const dfc Sd = to_dfc(S), Ed = to_dfc(Es);
+    const dfr kz = kzd[l];
+    const dfr kap = kz.hi < 0.0f ? -kz : kz;
+    dfc Sd, Ed;
+    green_scalars_df(kap, cbeta_d[t], E, L_d, cinv_d, scale_d, Sd, Ed);
     const dfr qx = cq[2 * t], qy = cq[2 * t + 1];
     dfc* c0 = col + (0 * tx + t) * P;
     dfc* c1 = col + (1 * tx + t) * P;
@@ -232,21 +290,26 @@ __global__ void __launch_bounds__(NT, df_min_blocks<NF>()) k_zcol_df(OpCall<doub
     }
     __syncthreads();
   }
-  double2* gcol = a.work + (size_t)lr * 3 * ns * pstride + (size_t)y * nx + x0 + t0;
+  const size_t go = (size_t)lr * 3 * ns * pstride + (size_t)y * nx + x0 + t0;
+  double2* gcol = a.work + go;
+  dfc* gcold = reinterpret_cast<dfc*>(a.work) + go;
 #pragma unroll
   for (int cc = 0; cc < 3; ++cc) {
 #pragma unroll 4
-    for (int pl = p0; pl < ns; pl += pstep)
-      gcol[((size_t)cc * ns + pl) * pstride] = to_d2(col[(cc * tx + t0) * P + fpad(pl + 1)]);
+    for (int pl = p0; pl < ns; pl += pstep) {
+      const dfc v = col[(cc * tx + t0) * P + fpad(pl + 1)];
+      if constexpr (WDF) gcold[((size_t)cc * ns + pl) * pstride] = v;
+      else gcol[((size_t)cc * ns + pl) * pstride] = to_d2(v);
+    }
   }
 }
 
 template <int NF>
-int launch(const OpCall<double2>& a) {
+int launch(const OpCall<double2>& a, bool wdf) {
   constexpr int NT = 24 * (NF / 16);
   int tx = a.nx < kDfTile ? a.nx : kDfTile;
   const size_t smem = df_smem_bytes<NF>(tx);
-  auto k = k_zcol_df<NF, NT>;
+  auto k = wdf ? k_zcol_df<NF, NT, true> : k_zcol_df<NF, NT, false>;
   if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return PSFD_E_CUDA;
   k<<<dim3(a.nx / tx, a.ny, a.nrhs), NT, smem, a.stream>>>(a, tx);
@@ -263,9 +326,9 @@ bool zcol_df_supported(const OpCall<double2>& a) {
   return (a.nf == 64 || a.nf == 128) && a.sph64 == nullptr && tx >= 1 && (tx & (tx - 1)) == 0 && a.nx % tx == 0;
 }
 
-int launch_zcol_df(const OpCall<double2>& a) {
+int launch_zcol_df(const OpCall<double2>& a, bool wdf) {
   if (!zcol_df_supported(a)) return PSFD_E_ARG;
-  return a.nf == 64 ? launch<64>(a) : launch<128>(a);
+  return a.nf == 64 ? launch<64>(a, wdf) : launch<128>(a, wdf);
 }
 
 }  // namespace psfd

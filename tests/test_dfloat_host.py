@@ -6,6 +6,9 @@ operand pairs, a quarter of them near cancellation.
 Bounds (u = 2^-48, the format's precision): TwoSum and the FMA TwoProduct exact; conversion
 from FP64 within u |x|; the sloppy sum within 4 u (|a| + |b|); the product within 6 u |a b|;
 every result normalised (|lo| <= 2^-24 |hi|); a double literal folded at compile time within u.
+The integer-path conversions between FP64 and double-float that the device uses (exponent
+rebias and round-to-nearest-even by integer operations, one exact FP64 addition) give bitwise
+the values of the plain conversions on three million seeded doubles and the rounding edge cases.
 The register four-step transform of the z pass (fft.cuh, 16 x nf/16) is run on the host in
 double-float and in FP64 against a long-double DFT (lengths 64 and 128, forward on the
 half-filled input and inverse): double-float within 2e-14 normwise, FP64 within 1e-15."""
@@ -59,3 +62,10 @@ def test_register_transform_in_double_float(tmp_path_factory):
     r = _run(tmp_path_factory, "dfloat_fft_check")
     assert r["fft_dfloat"] < 2e-14
     assert r["fft_fp64"] < 1e-15
+
+
+def test_integer_path_conversions_are_bitwise_the_plain_ones(tmp_path_factory):
+    r = _run(tmp_path_factory, "dfloat_conv_check")
+    assert r["checked"] > 3e6 and r["int_path"] > 0.5 * r["checked"]
+    assert r["to_dfr_mismatch"] == 0
+    assert r["to_d_mismatch"] == 0
