@@ -356,6 +356,18 @@ int psfd_server_submit(psfd_server* s, const psfd_request* req, long long* ticke
 /* Complete finished engine steps, admit, enqueue the next step of idle buckets, retire;
  * *n_pending = queued + running. */
 int psfd_server_progress(psfd_server* s, int* n_pending);
+/* Fused rounds (no counterpart in the paper; off by default). With ticks_per_round > 0 every
+ * bucket runs on one stream of the server and progress() works in rounds: when the previous
+ * round has finished, every bucket completes, queued requests are admitted, each bucket's
+ * phase work (norms, FP64 residuals, sweep starts, orders) is enqueued, and then ONE graph
+ * launch advances every bucket that is inside a Krylov sweep -- clips of different grids side
+ * by side -- through up to ticks_per_round ticks of check_every iterations each (one
+ * conditional WHILE node per bucket, see psfd_set_device_loop). The graph is captured once per
+ * set of buckets and batch widths and replayed. A request's results are bitwise the same as
+ * with independent buckets. Admission happens between rounds. 0 returns to independent
+ * buckets on priority streams. Call between progress() calls with no round in flight
+ * (PSFD_E_STATE otherwise). */
+int psfd_server_set_rounds(psfd_server* s, int ticks_per_round);
 /* *state: 0 queued, 1 running, 2 done; *status: PSFD_OK or the request's failure. */
 int psfd_server_status(psfd_server* s, long long ticket, int* state, int* status);
 /* Orders of illumination rhs of a finished request (layout as psfd_diffraction_orders). */
@@ -443,6 +455,25 @@ int psfd_apply_fp32_static(const psfd_grid* grid, int n_layers, const double* n_
 int psfd_apply_differential(int n, int nz, int n_pml, double dx, double dz, double wavelength, double eps_bg,
                             double theta_deg, double phi_deg, const double* eps, const double* E, double* out,
                             double* work, void* stream);
+
+/* Measurement of the z pass's forward transform (K2 at nf = 128) on two kinds of units, for
+ * deciding whether the tensor cores pay (no counterpart in the paper):
+ *   method 0  CUDA cores: the register four-step transform of K2 (16 x 8 points, FP32);
+ *   method 1  tensor cores: the transform as dense real DFT products, Re/Im of 128 columns as
+ *             the 256 columns of B, the cos and -sin matrices as A (128 bins x 64 planes),
+ *             every operand split into BF16 hi + lo and three products (hi hi, hi lo, lo hi)
+ *             accumulated in FP32 (tcgen05.mma kind::f16 from shared memory into tensor
+ *             memory; accuracy about 1e-5 normwise against 1e-7 for method 0).
+ *   in   device, complex float [nsets][nslab][ny][nx]: plane p sits at z index p + 1 of a
+ *        column of 128 (zero elsewhere); 1 <= nslab <= 63
+ *   out  device, complex float [nsets][128][ny][nx]: the unnormalised DFT along z
+ * nx must be a multiple of 128 (method 1) or 32 (method 0). Runs on `stream` without
+ * synchronising; the first call on a device builds its tables (and synchronises).
+ * psfd_zdft_status returns the device's error flag of method 1: 0, or 1 / 2 when a bounded
+ * wait for the table copy / the products gave up (the output is then not written).
+ * Returns PSFD_OK, PSFD_E_ARG, PSFD_E_NOMEM or PSFD_E_CUDA. */
+int psfd_zdft_measure(int method, int nx, int ny, int nsets, int nslab, const void* in, void* out, void* stream);
+int psfd_zdft_status(int* flag);
 
 /* Test hook for the device FFT: `count` contiguous transforms of length n, in place, on
  * device data (complex double if fp64 else complex float). inverse = 1 applies the

@@ -244,8 +244,14 @@ int ctx_set_rhs(psfd_ctx* ctx, int g0, int n, const double* theta, const double*
 // Solve engine: one tick advances every slot by one phase step (see engine.cu).
 int engine_tick(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active);
 // The two halves of a tick: enqueue the work (no host wait), then wait and transition.
-int engine_enqueue(psfd_ctx* ctx, const psfd_solve_opts& o, bool* pending);
+// With loop_deferred non-null, a tick in which every busy slot is inside a Krylov sweep is
+// only prepared (*loop_deferred = true): the caller adds the context's loop to a graph
+// (add_sweep_loop), launches it, then calls loop_readback and engine_readback.
+int engine_enqueue(psfd_ctx* ctx, const psfd_solve_opts& o, bool* pending, bool* loop_deferred);
 int engine_complete(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active);
+int engine_readback(psfd_ctx* ctx);
+int add_sweep_loop(psfd_ctx* ctx, const psfd_solve_opts& o, int hi, bool f32, cudaGraph_t g, int cap, int* kernels);
+int loop_readback(psfd_ctx* ctx, int hi);
 // The paper's outer fixed-point loop (Eqs. (8)-(9)) over rhs slots 0 .. n_rhs-1.
 int engine_fixed_point(psfd_ctx* ctx, const psfd_solve_opts& o, int max_steps, double step_tol);
 psfd_solve_opts solve_defaults(const psfd_solve_opts* opts);

@@ -166,6 +166,89 @@ __global__ void k_sweep_cond(cudaGraphConditionalHandle cond, int R, const int* 
   }
 }
 
+// Device buffers of the sweep loop (allocated on first use).
+int ensure_loop_buffers(psfd_ctx* ctx) {
+  if (ctx->d_loop) return PSFD_OK;
+  const int n = ctx->max_rhs;
+  RC(ctx->dalloc(&ctx->d_loop, 1));
+  RC(ctx->dalloc(&ctx->d_prev_act, n));
+  RC(ctx->dalloc(&ctx->d_lhist, (size_t)n * kLoopHist));
+  RC(ctx->dalloc(&ctx->d_lhist_n, n));
+  CK(cudaMallocHost(&ctx->h_loop, sizeof(int)));
+  CK(cudaMallocHost(&ctx->h_lhist, sizeof(LoopHist) * (size_t)n * kLoopHist));
+  CK(cudaMallocHost(&ctx->h_lhist_n, sizeof(int) * n));
+  return PSFD_OK;
+}
+
+}  // namespace
+
+// Adds to graph g one WHILE node (condition 1 at every launch of g, no dependencies) whose body
+// is one tick of the context -- check_every Krylov iterations of its active slots -- followed
+// by k_sweep_cond with the given tick cap; the body is captured on the context's private
+// stream. *kernels: the kernels one tick launches.
+int add_sweep_loop(psfd_ctx* ctx, const psfd_solve_opts& o, int hi, bool f32, cudaGraph_t g, int cap, int* kernels) {
+  RC(ensure_loop_buffers(ctx));
+  if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  cudaGraphConditionalHandle cond;
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  cudaGraphNode_t node;
+  cudaError_t ge = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+  if (ge == cudaSuccess) {
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    ge = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  }
+  if (ge == cudaSuccess)
+    ge = cudaStreamBeginCaptureToGraph(ctx->cap_stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeRelaxed);
+  if (ge != cudaSuccess) return ctx->cuda_fail(ge, "device loop graph");
+  cudaStream_t user = ctx->stream;
+  const unsigned long long n0 = launch_total();
+  ctx->stream = ctx->cap_stream;
+  int rc = f32 ? krylov_iterate<float2>(ctx, o, hi) : krylov_iterate<double2>(ctx, o, hi);
+  if (rc == PSFD_OK) {
+    k_sweep_cond<<<1, 256, 0, ctx->cap_stream>>>(cond, hi, ctx->act, ctx->sc, ctx->d_prev_act, ctx->d_loop, cap,
+                                                  ctx->d_lhist, ctx->d_lhist_n);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = PSFD_E_CUDA;
+  }
+  ctx->stream = user;
+  cudaGraph_t body = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &body);
+  *kernels = (int)(launch_total() - n0);
+  if (rc != PSFD_OK || ce != cudaSuccess) {
+    cudaGetLastError();
+    if (rc != PSFD_OK) return rc;
+    return ctx->cuda_fail(ce, "cudaStreamEndCapture (device loop)");
+  }
+  return PSFD_OK;
+}
+
+// Before a loop launch: tick counter and history cleared, activity at the start recorded.
+int loop_prepare(psfd_ctx* ctx, int hi) {
+  RC(ensure_loop_buffers(ctx));
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(ctx->d_loop, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->d_lhist_n, 0, sizeof(int) * hi, st));
+  CK(cudaMemcpyAsync(ctx->d_prev_act, ctx->act, sizeof(int) * hi, cudaMemcpyDeviceToDevice, st));
+  return PSFD_OK;
+}
+
+// After a loop launch: its ticks and history, then the per-slot scalars, back to the host.
+int loop_readback(psfd_ctx* ctx, int hi) {
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(ctx->h_loop, ctx->d_loop, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ctx->h_lhist_n, ctx->d_lhist_n, sizeof(int) * hi, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ctx->h_lhist, ctx->d_lhist, sizeof(LoopHist) * (size_t)hi * kLoopHist, cudaMemcpyDeviceToHost,
+                     st));
+  ctx->loop_ran = true;
+  return PSFD_OK;
+}
+
+namespace {
+
 // check_every Krylov iterations of the slots whose device flag is up. The launch sequence
 // depends only on the configuration in the key below (the per-slot state -- scalars, flags,
 // vectors -- lives on the device), so it is captured once into a CUDA graph and replayed:
@@ -209,42 +292,12 @@ int inner_step(psfd_ctx* ctx, const psfd_solve_opts& o, int hi, bool f32, bool l
     const unsigned long long n0 = launch_total();
     cudaGraph_t g = nullptr;
     if (loop) {
-      // outer graph: one WHILE node (condition 1 at every launch); its body is captured below
       CK(cudaGraphCreate(&g, 0));
-      cudaGraphConditionalHandle cond;
-      cudaGraphNodeParams np{};
-      np.type = cudaGraphNodeTypeConditional;
-      cudaGraphNode_t node;
-      cudaError_t ge = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
-      if (ge == cudaSuccess) {
-        np.conditional.handle = cond;
-        np.conditional.type = cudaGraphCondTypeWhile;
-        np.conditional.size = 1;
-        ge = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
-      }
-      if (ge == cudaSuccess)
-        ge = cudaStreamBeginCaptureToGraph(ctx->cap_stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeRelaxed);
-      if (ge != cudaSuccess) {
+      int kernels = 0;
+      const int rc = add_sweep_loop(ctx, o, hi, f32, g, cap, &kernels);
+      if (rc != PSFD_OK) {
         cudaGraphDestroy(g);
-        return ctx->cuda_fail(ge, "device loop graph");
-      }
-      ctx->stream = ctx->cap_stream;
-      int rc = direct();
-      if (rc == PSFD_OK) {
-        k_sweep_cond<<<1, 256, 0, ctx->cap_stream>>>(cond, hi, ctx->act, ctx->sc, ctx->d_prev_act, ctx->d_loop, cap,
-                                                      ctx->d_lhist, ctx->d_lhist_n);
-        count_launch();
-        if (cudaGetLastError() != cudaSuccess) rc = PSFD_E_CUDA;
-      }
-      ctx->stream = user;
-      cudaGraph_t body = nullptr;
-      const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &body);
-      if (rc != PSFD_OK || ce != cudaSuccess) {
-        cudaGraphDestroy(g);
-        cudaGetLastError();
-        if (rc != PSFD_OK) return rc;
-        return ctx->cuda_fail(ce, "cudaStreamEndCapture (device loop)");
+        return rc;
       }
     } else {
       CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
@@ -278,20 +331,6 @@ int inner_step(psfd_ctx* ctx, const psfd_solve_opts& o, int hi, bool f32, bool l
     ctx->loop_precounted = precounted;
   }
   CK(cudaGraphLaunch(hit->exec, ctx->stream));
-  return PSFD_OK;
-}
-
-// Device buffers of the sweep loop (allocated on first use).
-int ensure_loop_buffers(psfd_ctx* ctx) {
-  if (ctx->d_loop) return PSFD_OK;
-  const int n = ctx->max_rhs;
-  RC(ctx->dalloc(&ctx->d_loop, 1));
-  RC(ctx->dalloc(&ctx->d_prev_act, n));
-  RC(ctx->dalloc(&ctx->d_lhist, (size_t)n * kLoopHist));
-  RC(ctx->dalloc(&ctx->d_lhist_n, n));
-  CK(cudaMallocHost(&ctx->h_loop, sizeof(int)));
-  CK(cudaMallocHost(&ctx->h_lhist, sizeof(LoopHist) * (size_t)n * kLoopHist));
-  CK(cudaMallocHost(&ctx->h_lhist_n, sizeof(int) * n));
   return PSFD_OK;
 }
 
@@ -350,8 +389,9 @@ static int busy_hi(const psfd_ctx* ctx) {
   return hi;
 }
 
-int engine_enqueue(psfd_ctx* ctx, const psfd_solve_opts& o, bool* pending) {
+int engine_enqueue(psfd_ctx* ctx, const psfd_solve_opts& o, bool* pending, bool* loop_deferred) {
   const int R = busy_hi(ctx);
+  if (loop_deferred) *loop_deferred = false;
   const size_t U = ctx->plan.U;
   const bool f32 = ctx->precision == PSFD_FP32_REFINED;
   cudaStream_t st = ctx->stream;
@@ -392,28 +432,29 @@ int engine_enqueue(psfd_ctx* ctx, const psfd_solve_opts& o, bool* pending) {
   ctx->loop_ran = false;
   if (select(PH_INNER)) {
     // every busy slot inside a sweep: run the sweep to its end on the device
-    const bool loop = ctx->device_loop && ctx->use_graphs && !prof_on() && !*pending;
+    const bool loop = (ctx->device_loop || loop_deferred) && ctx->use_graphs && !prof_on() && !*pending;
+    *pending = true;
     if (loop) {
-      RC(ensure_loop_buffers(ctx));
-      CK(cudaMemsetAsync(ctx->d_loop, 0, sizeof(int), st));
-      CK(cudaMemsetAsync(ctx->d_lhist_n, 0, sizeof(int) * R, st));
-      CK(cudaMemcpyAsync(ctx->d_prev_act, ctx->act, sizeof(int) * R, cudaMemcpyDeviceToDevice, st));
+      RC(loop_prepare(ctx, R));
+      if (loop_deferred) {  // the caller launches the loop (in a graph of several contexts)
+        *loop_deferred = true;
+        return PSFD_OK;
+      }
     }
     RC(inner_step(ctx, o, R, f32, loop));
-    if (loop) {
-      CK(cudaMemcpyAsync(ctx->h_loop, ctx->d_loop, sizeof(int), cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(ctx->h_lhist_n, ctx->d_lhist_n, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(ctx->h_lhist, ctx->d_lhist, sizeof(LoopHist) * (size_t)R * kLoopHist,
-                         cudaMemcpyDeviceToHost, st));
-      ctx->loop_ran = true;
-    }
-    *pending = true;
+    if (loop) RC(loop_readback(ctx, R));
   }
-  if (*pending) {  // read-back of the per-slot scalars, waited for in engine_complete
-    CK(cudaMemcpyAsync(ctx->h_sc64, ctx->sc64, sizeof(KScal) * R, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(KScal) * R, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(ctx->h_act, ctx->act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
-  }
+  if (*pending) RC(engine_readback(ctx));
+  return PSFD_OK;
+}
+
+// Read-back of the per-slot scalars of the enqueued work, waited for in engine_complete.
+int engine_readback(psfd_ctx* ctx) {
+  const int R = ctx->enq_hi;
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(ctx->h_sc64, ctx->sc64, sizeof(KScal) * R, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ctx->h_sc, ctx->sc, sizeof(KScal) * R, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ctx->h_act, ctx->act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
   return PSFD_OK;
 }
 
@@ -541,7 +582,7 @@ int engine_complete(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
 
 int engine_tick(psfd_ctx* ctx, const psfd_solve_opts& o, int* n_active) {
   bool pending = false;
-  RC(engine_enqueue(ctx, o, &pending));
+  RC(engine_enqueue(ctx, o, &pending, nullptr));
   return engine_complete(ctx, o, n_active);
 }
 

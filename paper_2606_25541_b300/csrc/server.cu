@@ -68,6 +68,17 @@ struct Request {
 
 }  // namespace
 
+// A graph that advances several buckets at once: one WHILE node per bucket (engine.cu,
+// add_sweep_loop), keyed by the buckets, their batch widths and buffers.
+struct RoundGraph {
+  std::vector<long long> key;
+  std::vector<int> kernels;  // kernels per tick of each bucket's loop
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool replayed = false;
+  unsigned long long last_use = 0;
+};
+
 struct psfd_server {
   int precision = PSFD_FP32_REFINED;
   size_t budget = 0, used = 0;
@@ -77,11 +88,28 @@ struct psfd_server {
   std::deque<long long> queue;
   std::map<long long, std::unique_ptr<Request>> reqs;
   std::vector<std::unique_ptr<Bucket>> buckets;
+  // fused rounds (psfd_server_set_rounds): every bucket runs on round_stream, and the Krylov
+  // ticks of all buckets inside a sweep run as one graph launch per round
+  int round_ticks = 0;  // 0: buckets advance independently on their own streams
+  cudaStream_t round_stream = nullptr;
+  cudaEvent_t round_done = nullptr;
+  bool round_in_flight = false;
+  std::vector<RoundGraph> rounds;
+  unsigned long long round_clock = 0;
 };
 
 namespace {
 
+void drop_rounds(psfd_server* s) {
+  for (auto& r : s->rounds) {
+    if (r.exec) cudaGraphExecDestroy(r.exec);
+    if (r.graph) cudaGraphDestroy(r.graph);
+  }
+  s->rounds.clear();
+}
+
 void destroy_bucket(psfd_server* s, Bucket* b) {
+  drop_rounds(s);  // round graphs may refer to the bucket's buffers
   if (b->ctx) psfd_destroy(b->ctx);
   for (cudaStream_t st : b->prio)
     if (st) cudaStreamDestroy(st);
@@ -318,7 +346,7 @@ static int progress_pass(psfd_server* s, bool* moved) {
       psfd_set_stream(b->ctx, want);
     }
     bool pending = false;
-    const int rc = engine_enqueue(b->ctx, s->opts, &pending);
+    const int rc = engine_enqueue(b->ctx, s->opts, &pending, nullptr);
     if (rc != PSFD_OK) return rc;
     if (cudaEventRecord(b->tick_done, b->stream) != cudaSuccess) return PSFD_E_CUDA;
     b->in_flight = true;
@@ -326,9 +354,146 @@ static int progress_pass(psfd_server* s, bool* moved) {
   return PSFD_OK;
 }
 
+// The round graph of these buckets (built on first use; the context's loop bodies are captured
+// with their current batch width and buffers, which are part of the key).
+RoundGraph* round_graph(psfd_server* s, const std::vector<Bucket*>& list, int* rc) {
+  const bool f32 = s->precision == PSFD_FP32_REFINED;
+  std::vector<long long> key;
+  for (Bucket* b : list) {
+    psfd_ctx* c = b->ctx;
+    key.push_back((long long)(uintptr_t)c);
+    key.push_back(c->enq_hi);
+    key.push_back((long long)(f32 ? (uintptr_t)c->pool32 : (uintptr_t)c->pool64));
+    key.push_back(c->no_reflect);
+  }
+  for (auto& r : s->rounds)
+    if (r.key == key) {
+      r.last_use = ++s->round_clock;
+      return &r;
+    }
+  constexpr size_t kMaxRounds = 16;
+  if (s->rounds.size() >= kMaxRounds) {
+    auto old = std::min_element(s->rounds.begin(), s->rounds.end(),
+                                [](const RoundGraph& a, const RoundGraph& b) { return a.last_use < b.last_use; });
+    if (old->exec) cudaGraphExecDestroy(old->exec);
+    if (old->graph) cudaGraphDestroy(old->graph);
+    s->rounds.erase(old);
+  }
+  RoundGraph r;
+  r.key = key;
+  if (cudaGraphCreate(&r.graph, 0) != cudaSuccess) {
+    *rc = PSFD_E_CUDA;
+    return nullptr;
+  }
+  for (Bucket* b : list) {
+    int k = 0;
+    *rc = add_sweep_loop(b->ctx, s->opts, b->ctx->enq_hi, f32, r.graph, s->round_ticks, &k);
+    if (*rc != PSFD_OK) {
+      cudaGraphDestroy(r.graph);
+      return nullptr;
+    }
+    r.kernels.push_back(k);
+  }
+  if (cudaGraphInstantiate(&r.exec, r.graph, 0) != cudaSuccess) {
+    cudaGraphDestroy(r.graph);
+    *rc = PSFD_E_CUDA;
+    return nullptr;
+  }
+  r.last_use = ++s->round_clock;
+  s->rounds.push_back(std::move(r));
+  *rc = PSFD_OK;
+  return &s->rounds.back();
+}
+
+// One non-blocking pass of the fused rounds: when the previous round has finished, complete
+// every bucket, admit, enqueue each bucket's phase work (norms, FP64 residuals, sweep starts,
+// orders) on round_stream, and launch one graph whose WHILE nodes run up to round_ticks ticks
+// of every bucket that is inside a Krylov sweep, side by side.
+int progress_round(psfd_server* s, bool* moved) {
+  *moved = false;
+  if (s->round_in_flight) {
+    const cudaError_t q = cudaEventQuery(s->round_done);
+    if (q == cudaErrorNotReady) return PSFD_OK;
+    if (q != cudaSuccess) return PSFD_E_CUDA;
+    s->round_in_flight = false;
+    *moved = true;
+    for (auto& bp : s->buckets) {
+      Bucket* b = bp.get();
+      if (!b->in_flight) continue;
+      b->in_flight = false;
+      int active = 0;
+      int rc = engine_complete(b->ctx, s->opts, &active);
+      if (rc != PSFD_OK) return rc;
+      if ((rc = retire(s, b)) != PSFD_OK) return rc;
+    }
+  }
+  for (auto it = s->queue.begin(); it != s->queue.end();) {
+    Request* r = s->reqs[*it].get();
+    bool admitted = false;
+    const int rc = admit(s, r, &admitted);
+    if (rc != PSFD_OK) return rc;
+    *moved = *moved || admitted;
+    it = admitted ? s->queue.erase(it) : std::next(it);
+  }
+  std::vector<Bucket*> looping;
+  bool any = false;
+  for (auto& bp : s->buckets) {
+    Bucket* b = bp.get();
+    if (b->running == 0) continue;
+    if (b->stream != s->round_stream) {
+      if (cudaEventRecord(b->handoff, b->stream) != cudaSuccess ||
+          cudaStreamWaitEvent(s->round_stream, b->handoff, 0) != cudaSuccess)
+        return PSFD_E_CUDA;
+      b->stream = s->round_stream;
+      psfd_set_stream(b->ctx, s->round_stream);
+    }
+    bool pending = false, deferred = false;
+    const int rc = engine_enqueue(b->ctx, s->opts, &pending, &deferred);
+    if (rc != PSFD_OK) return rc;
+    if (deferred) looping.push_back(b);
+    b->in_flight = pending;
+    any = any || pending;
+  }
+  if (!looping.empty()) {
+    int rc = PSFD_OK;
+    RoundGraph* r = round_graph(s, looping, &rc);
+    if (!r) return rc;
+    for (size_t i = 0; i < looping.size(); ++i) {
+      looping[i]->ctx->loop_kernels = r->kernels[i];
+      looping[i]->ctx->loop_precounted = r->replayed ? 0 : r->kernels[i];
+    }
+    r->replayed = true;
+    if (cudaGraphLaunch(r->exec, s->round_stream) != cudaSuccess) return PSFD_E_CUDA;
+    for (Bucket* b : looping) {
+      if ((rc = loop_readback(b->ctx, b->ctx->enq_hi)) != PSFD_OK) return rc;
+      if ((rc = engine_readback(b->ctx)) != PSFD_OK) return rc;
+    }
+  }
+  if (any) {
+    if (cudaEventRecord(s->round_done, s->round_stream) != cudaSuccess) return PSFD_E_CUDA;
+    s->round_in_flight = true;
+  }
+  return PSFD_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int psfd_server_set_rounds(psfd_server* s, int ticks_per_round) {
+  if (!s || ticks_per_round < 0) return PSFD_E_ARG;
+  // only between rounds, with every bucket idle
+  if (s->round_in_flight) return PSFD_E_STATE;
+  for (auto& bp : s->buckets)
+    if (bp->in_flight) return PSFD_E_STATE;
+  if (ticks_per_round > 0 && !s->round_stream) {
+    if (cudaStreamCreateWithFlags(&s->round_stream, cudaStreamNonBlocking) != cudaSuccess) return PSFD_E_CUDA;
+    if (cudaEventCreateWithFlags(&s->round_done, cudaEventDisableTiming) != cudaSuccess) return PSFD_E_CUDA;
+  }
+  drop_rounds(s);
+  s->round_ticks = ticks_per_round;
+  return PSFD_OK;
+}
 
 int psfd_server_create(psfd_server** out, int precision, size_t hbm_budget, int slots_per_context,
                        const psfd_solve_opts* opts) {
@@ -345,7 +510,11 @@ int psfd_server_create(psfd_server** out, int precision, size_t hbm_budget, int 
 
 int psfd_server_destroy(psfd_server* s) {
   if (!s) return PSFD_OK;
+  if (s->round_stream) cudaStreamSynchronize(s->round_stream);
   while (!s->buckets.empty()) destroy_bucket(s, s->buckets.back().get());
+  drop_rounds(s);
+  if (s->round_done) cudaEventDestroy(s->round_done);
+  if (s->round_stream) cudaStreamDestroy(s->round_stream);
   delete s;
   return PSFD_OK;
 }
@@ -385,9 +554,9 @@ int psfd_server_progress(psfd_server* s, int* n_pending) {
   const auto t0 = std::chrono::steady_clock::now();
   for (;;) {
     bool moved = false;
-    const int rc = progress_pass(s, &moved);
+    const int rc = s->round_ticks > 0 ? progress_round(s, &moved) : progress_pass(s, &moved);
     if (rc != PSFD_OK) return rc;
-    bool any_in_flight = false;
+    bool any_in_flight = s->round_in_flight;
     for (auto& bp : s->buckets) any_in_flight = any_in_flight || bp->in_flight;
     if (moved || !any_in_flight ||
         std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(2000))

@@ -98,6 +98,8 @@ _SIGS = {
     "psfd_residual_history": (_I, [_P, _I, _I, _IP, _IP, _IP, _D]),
     "psfd_get_mode_tables": (_I, [_P, _I, _D, _D, _D]),
     "psfd_test_fft": (_I, [_I, _I, _I, _I, _P]),
+    "psfd_zdft_measure": (_I, [_I, _I, _I, _I, _I, _P, _P, _P]),
+    "psfd_zdft_status": (_I, [_IP]),
     "psfd_apply_fp32_static": (_I, [ctypes.POINTER(Grid), _I, _D, _D, _D, ctypes.c_double, ctypes.c_double, _P,
                                     _P, _P, _P]),
     "psfd_apply_differential": (_I, [_I, _I, _I, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -106,6 +108,7 @@ _SIGS = {
     "psfd_server_destroy": (_I, [_P]),
     "psfd_server_submit": (_I, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)]),
     "psfd_server_progress": (_I, [_P, _IP]),
+    "psfd_server_set_rounds": (_I, [_P, _I]),
     "psfd_server_status": (_I, [_P, ctypes.c_longlong, _IP, _IP]),
     "psfd_server_orders": (_I, [_P, ctypes.c_longlong, _I, _I, _IP, _IP, _D, _D, _D]),
     "psfd_server_release": (_I, [_P, ctypes.c_longlong]),
@@ -142,6 +145,25 @@ def apply_differential(n, nz, n_pml, dx, dz, wavelength, eps_bg, theta_deg, phi_
                                           ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(E.data_ptr()),
                                           ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(work.data_ptr()),
                                           _stream_ptr(stream))
+
+
+def zdft_measure(method: int, x, out, stream=None):
+    """Forward z transform of the z pass, x: complex64 CUDA tensor (nsets, nslab, ny, nx) ->
+    out (nsets, 128, ny, nx); method 0 = CUDA cores, 1 = tensor cores (split BF16)."""
+    ns, nslab, ny, nx = x.shape
+    st = load().psfd_zdft_measure(int(method), int(nx), int(ny), int(ns), int(nslab), ctypes.c_void_p(x.data_ptr()),
+                                  ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
+    if st != OK:
+        raise PsfdError(st, strerror(st))
+    return out
+
+
+def zdft_status() -> int:
+    flag = ctypes.c_int(0)
+    st = load().psfd_zdft_status(ctypes.byref(flag))
+    if st != OK:
+        raise PsfdError(st, strerror(st))
+    return flag.value
 
 
 def tune_set(grid: Grid, precision: int, zx: int = 0, rb: int = 0, cx: int = 0):
@@ -487,6 +509,11 @@ class Server:
             self.close()
         except Exception:
             pass
+
+    def set_rounds(self, ticks_per_round: int):
+        """Fused rounds: one graph launch per round advances every bucket inside a Krylov sweep
+        by up to ticks_per_round ticks (0: buckets advance independently)."""
+        self._check(self.lib.psfd_server_set_rounds(self.h, int(ticks_per_round)))
 
     def submit(self, prob, theta=None, phi=None, pol=None) -> int:
         """Queue one clip (a layouts.Problem); illuminations default to the problem's."""

@@ -45,12 +45,14 @@ def _solve_alone(psfd, prob, precision):
     return out
 
 
-@pytest.mark.parametrize("precision", [1, 0])
-def test_results_are_identical_alone_and_in_the_mix(psfd, precision):
+@pytest.mark.parametrize("precision,rounds", [(1, 0), (0, 0), (1, 3)])
+def test_results_are_identical_alone_and_in_the_mix(psfd, precision, rounds):
+    """rounds > 0: fused rounds, one graph launch advancing both buckets (two grids) per round."""
     clips = _clips()
     alone = [_solve_alone(psfd, p, precision) for p in clips]
 
     srv = psfd.Server(precision, slots_per_context=6, tol=1e-9)
+    srv.set_rounds(rounds)
     t0 = srv.submit(clips[0])
     t1 = srv.submit(clips[1])
     for _ in range(3):
