@@ -61,6 +61,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--profile-only", action="store_true", help="one profiled step, for ncu launch lists")
+    ap.add_argument("--plain-launches", action="store_true",
+                    help="with --profile-only: launch every kernel on its own (no CUDA graphs)")
     ap.add_argument("--apply", action="store_true",
                     help="operator applications/s only (psfd_apply), for kernel captures")
     ap.add_argument("--rhs", type=int, default=18, help="illuminations used by --apply and --profile-only")
@@ -86,6 +88,8 @@ def parse_args(argv=None):
     ap.add_argument("--differential", action="store_true",
                     help="FP64 applications/s of the differential PSFD operator (PML column) and of the "
                          "Lippmann-Schwinger operator on the same 64 x 64 x 30 clip")
+    ap.add_argument("--zdft", action="store_true",
+                    help="z pass forward transform: CUDA-core register FFT vs split-BF16 tensor-core DFT")
     ap.add_argument("--autotune", action="store_true",
                     help="autotuner table: built-in vs tuned tile shapes per workload grid")
     ap.add_argument("--small", action="store_true",
@@ -97,11 +101,13 @@ def parse_args(argv=None):
                     help="requests in the serving-loop sample (0 = skip); --serve-only prints only that")
     ap.add_argument("--serve-only", action="store_true")
     ap.add_argument("--serve-sizes", type=str, default="64,128")
+    ap.add_argument("--serve-rounds", type=int, default=4,
+                    help="ticks per fused serving round (0 = independent buckets only)")
     return ap.parse_args(argv)
 
 
 def run_serving(n_req: int, sizes, tol: float, inner_tol: float, seed: int = 4, slots: int = 18,
-                budget_gb: float = 120.0):
+                budget_gb: float = 120.0, rounds: int = 4, fp64_sample: int = 8):
     """Seeded Poisson stream of mixed-size Manhattan clips through the continuous-batching server.
 
     Every request is first solved alone (its isolated service time); the arrival rate is then set
@@ -109,7 +115,10 @@ def run_serving(n_req: int, sizes, tol: float, inner_tol: float, seed: int = 4, 
     one-at-a-time latency under the same arrivals is the FIFO recursion over the isolated
     service times. Latency = completion - arrival, wall clock. At 0.8 load the stream's
     solves/s is its arrival rate; the capacity is the saturated run (all requests submitted
-    at once). The plain FP64 path is timed one request at a time on the first 8 requests."""
+    at once). The stream and the saturated run are measured with fused rounds (one graph
+    launch per round advances every bucket, `rounds` ticks) and with independent buckets on
+    priority streams. The plain FP64 path is timed one request at a time on the first
+    `fp64_sample` requests."""
     from paper_2606_25541_b300 import psfd
     reqs = layouts.serving_requests(n_req, seed=seed, sizes=sizes)
     kw = dict(hbm_budget=int(budget_gb * 2 ** 30), slots_per_context=slots, tol=tol, inner_tol=inner_tol)
@@ -131,38 +140,47 @@ def run_serving(n_req: int, sizes, tol: float, inner_tol: float, seed: int = 4, 
     for a, s in zip(arrivals, service):
         done = max(a, done) + s
         fifo.append(done - a)
-    srv = psfd.Server(psfd.FP32_REFINED, **kw)
-    pending, lat, i, peak_ctx = {}, [], 0, 0
-    start = time.perf_counter()
-    while i < n_req or pending:
-        now = time.perf_counter() - start
-        while i < n_req and arrivals[i] <= now:
-            pending[srv.submit(reqs[i])] = arrivals[i]
-            i += 1
-        if not pending:
-            time.sleep(max(0.0, arrivals[i] - now))
-            continue
-        srv.progress()
-        peak_ctx = max(peak_ctx, srv.memory()[1])
-        now = time.perf_counter() - start
-        for t in list(pending):
-            state, status = srv.status(t)
-            if state == 2:
-                if status != psfd.OK:
-                    raise RuntimeError(f"request {t} failed: {psfd.strerror(status)}")
-                lat.append(now - pending.pop(t))
-                srv.release(t)
-    makespan = time.perf_counter() - start
-    # capacity: every request submitted at once (the server keeps the device full)
-    t0 = time.perf_counter()
-    tickets = [srv.submit(p) for p in reqs]
-    srv.run_until_done()
-    saturated = time.perf_counter() - t0
-    for t in tickets:
-        srv.release(t)
-    srv.close()
+    def served(ticks):
+        srv = psfd.Server(psfd.FP32_REFINED, **kw)
+        srv.set_rounds(ticks)
+        pending, lat, i, peak_ctx = {}, [], 0, 0
+        start = time.perf_counter()
+        while i < n_req or pending:
+            now = time.perf_counter() - start
+            while i < n_req and arrivals[i] <= now:
+                pending[srv.submit(reqs[i])] = arrivals[i]
+                i += 1
+            if not pending:
+                time.sleep(max(0.0, arrivals[i] - now))
+                continue
+            srv.progress()
+            peak_ctx = max(peak_ctx, srv.memory()[1])
+            now = time.perf_counter() - start
+            for t in list(pending):
+                state, status = srv.status(t)
+                if state == 2:
+                    if status != psfd.OK:
+                        raise RuntimeError(f"request {t} failed: {psfd.strerror(status)}")
+                    lat.append(now - pending.pop(t))
+                    srv.release(t)
+        makespan = time.perf_counter() - start
+        # capacity: every request submitted at once (the server keeps the device full)
+        t0 = time.perf_counter()
+        tickets = [srv.submit(p) for p in reqs]
+        srv.run_until_done()
+        saturated = time.perf_counter() - t0
+        for t in tickets:
+            srv.release(t)
+        srv.close()
+        return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "solves_per_s": n_rhs / makespan, "saturated_solves_per_s": n_rhs / saturated,
+                "peak_contexts": peak_ctx}
+
+    n_rhs = int(sum(p.n_rhs for p in reqs))
+    fused = served(rounds) if rounds > 0 else None
+    independent = served(0)
     # the plain FP64 path one request at a time, on a sample of the stream
-    sample = reqs[:8]
+    sample = reqs[:fp64_sample]
     srv = psfd.Server(psfd.FP64, **kw)
     t = srv.submit(sample[0])
     srv.run_until_done()
@@ -174,18 +192,17 @@ def run_serving(n_req: int, sizes, tol: float, inner_tol: float, seed: int = 4, 
         srv.release(t)
     fp64_s = time.perf_counter() - t0
     srv.close()
-    n_rhs = int(sum(p.n_rhs for p in reqs))
     n_sample = int(sum(p.n_rhs for p in sample))
     return {"requests": n_req, "illuminations": n_rhs, "sizes_nm": list(sizes), "offered_load": 0.8,
-            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-            "solves_per_s": n_rhs / makespan, "saturated_solves_per_s": n_rhs / saturated,
-            "peak_contexts": peak_ctx,
+            "mode": "independent buckets on priority streams",
+            **independent,
+            "fused_rounds": dict(fused, ticks_per_round=rounds) if fused else None,
             "one_at_a_time": {"p50_ms": 1e3 * float(np.percentile(fifo, 50)),
                               "p99_ms": 1e3 * float(np.percentile(fifo, 99)),
                               "solves_per_s": n_rhs / float(np.sum(service))},
             "fp64_one_at_a_time": {"solves_per_s": n_sample / fp64_s,
-                                   "fp32_refined_same_sample": n_sample / float(np.sum(service[:8])),
-                                   "sample": "the first 8 requests of the stream"},
+                                   "fp32_refined_same_sample": n_sample / float(np.sum(service[:fp64_sample])),
+                                   "sample": f"the first {fp64_sample} requests of the stream"},
             "stream": "seeded Poisson arrivals; 1-18 illuminations, 50-70 nm Manhattan absorber, "
                       "z from {64,96,128} nm, slab rounded up to 8 planes"}
 
@@ -569,6 +586,48 @@ def run_autotune(args):
     return 0
 
 
+def run_zdft(args):
+    """The z pass's forward transform on the 256 x 256 x 60 Manhattan clip's columns (3
+    components x 2 illuminations): CUDA-core register transform vs split-BF16 tensor-core DFT
+    products, time per launch (CUDA events, 20 launches after 3), algorithmic HBM rate (60
+    planes read, 128 bins written, 8 B each), tensor-core rate of the products, and the error
+    against an FP64 DFT of a sample of columns."""
+    import torch
+    from paper_2606_25541_b300 import psfd
+    torch.cuda.set_device(0)
+    n, nslab, nsets = 256, 60, 6
+    x = torch.tensor(layouts.random_field((nsets, nslab, n, n), seed=12), dtype=torch.complex64, device="cuda")
+    out = torch.empty((nsets, 128, n, n), dtype=torch.complex64, device="cuda")
+    xs = x[:, :, :8].cpu().numpy().astype(np.complex128)
+    full = np.zeros((nsets, 128, 8, n), np.complex128)
+    full[:, 1:nslab + 1] = xs
+    ref = np.fft.fft(full, axis=1)
+    rows = {}
+    cols = nsets * n * n
+    for method, name in ((0, "cuda_cores_register_fft"), (1, "tensor_cores_split_bf16")):
+        for _ in range(3):
+            psfd.zdft_measure(method, x, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            psfd.zdft_measure(method, x, out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        got = out[:, :, :8].cpu().numpy().astype(np.complex128)
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        bytes_ = cols * (nslab + 128) * 8.0
+        row = {"ms": ms, "algorithmic_GBps": bytes_ / (ms * 1e-3) / 1e9, "rel_err_vs_fp64": err,
+               "status": psfd.zdft_status()}
+        if method == 1:
+            flops = 2 * 3 * 2.0 * 128 * 64 * 2 * cols  # 2 matrices x 3 products x 2 M K N
+            row["tensor_TFLOPs"] = flops / (ms * 1e-3) / 1e12
+        rows[name] = row
+    print(json.dumps({"mode": "zdft", "workload": "manhattan_256x256x60_nf128_6columns_sets", **rows}), flush=True)
+    return 0
+
+
 def run_small(args):
     """The contact-hole clip (32 x 32 x 30 at 2 nm, nf = 64, one s-polarised plane wave at 6 deg)
     solved to relative residual 1e-10 in FP64 and in FP32 with FP64 refinement, with the
@@ -885,6 +944,8 @@ def run_ours(args):
         return s.solve(**solve_kw)
 
     if args.profile_only:
+        if args.plain_launches:  # every kernel its own launch (ncu lists no kernels inside a graph's loop)
+            solver.set_graphs(False)
         step(solver)
         torch.cuda.synchronize()
         return 0
@@ -1002,7 +1063,7 @@ def run_ours(args):
     serving = None
     if args.serve > 0 and world == 1:
         sizes = tuple(int(s) for s in args.serve_sizes.split(","))
-        serving = run_serving(args.serve, sizes, args.tol, args.inner_tol)
+        serving = run_serving(args.serve, sizes, args.tol, args.inner_tol, rounds=args.serve_rounds)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1093,7 +1154,7 @@ def solver_bytes(prob) -> float:
 def main(argv=None):
     args = parse_args(argv)
     headline = not (args.apply or args.sweep or args.large or args.crosscheck or args.fixed_point or args.small
-                    or args.layers or args.isolated or args.differential or args.autotune)
+                    or args.layers or args.isolated or args.differential or args.autotune or args.zdft)
     if args.tol is None:
         args.tol = HEADLINE_TOL if headline else DEFAULT_TOL
     if args.inner_tol is None:
@@ -1114,6 +1175,8 @@ def main(argv=None):
         return run_small(args)
     if args.autotune:
         return run_autotune(args)
+    if args.zdft:
+        return run_zdft(args)
     if args.layers:
         return run_layers(args)
     if args.isolated:
@@ -1122,7 +1185,8 @@ def main(argv=None):
         return run_differential(args)
     if args.serve_only:
         sizes = tuple(int(s) for s in args.serve_sizes.split(","))
-        print(json.dumps({"mode": "serving", **run_serving(args.serve, sizes, args.tol, args.inner_tol)}), flush=True)
+        print(json.dumps({"mode": "serving", **run_serving(args.serve, sizes, args.tol, args.inner_tol,
+                                                           rounds=args.serve_rounds)}), flush=True)
         return 0
     return run_ours(args)
 
