@@ -60,12 +60,15 @@ def parse_args(argv=None):
     ap.add_argument("--inner-tol", type=float, default=None, help="FP32 sweep tolerance (default 2e-7 / 1e-4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in tile shapes")
     ap.add_argument("--profile-only", action="store_true", help="one profiled step, for ncu launch lists")
     ap.add_argument("--plain-launches", action="store_true",
                     help="with --profile-only: launch every kernel on its own (no CUDA graphs)")
     ap.add_argument("--apply", action="store_true",
                     help="operator applications/s only (psfd_apply), for kernel captures")
     ap.add_argument("--rhs", type=int, default=18, help="illuminations used by --apply and --profile-only")
+    ap.add_argument("--pf", type=str, default=None,
+                    help="--apply: comma-separated L2 prefetch distances of the half-plane kernels to time")
     ap.add_argument("--precision", choices=["fp32", "fp64", "fp64df", "both", "all"], default="both",
                     help="--apply precision (fp64df: FP64 data with the residual's double-float passes; "
                          "both = fp32 + fp64, all = the three)")
@@ -88,6 +91,8 @@ def parse_args(argv=None):
     ap.add_argument("--differential", action="store_true",
                     help="FP64 applications/s of the differential PSFD operator (PML column) and of the "
                          "Lippmann-Schwinger operator on the same 64 x 64 x 30 clip")
+    ap.add_argument("--precond-study", action="store_true",
+                    help="Sec. 3's preconditioner comparison on the GPU (differential none / spectral damping, LS)")
     ap.add_argument("--zdft", action="store_true",
                     help="z pass forward transform: CUDA-core register FFT vs split-BF16 tensor-core DFT")
     ap.add_argument("--autotune", action="store_true",
@@ -103,6 +108,9 @@ def parse_args(argv=None):
     ap.add_argument("--serve-sizes", type=str, default="64,128")
     ap.add_argument("--serve-rounds", type=int, default=4,
                     help="ticks per fused serving round (0 = independent buckets only)")
+    ap.add_argument("--serve-slots", type=int, default=18, help="illumination slots per serving context")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0, help="HBM budget of the server")
+    ap.add_argument("--serve-fp64-sample", type=int, default=8, help="requests timed on the plain FP64 path")
     return ap.parse_args(argv)
 
 
@@ -226,18 +234,24 @@ def run_apply(args):
         u = torch.tensor(layouts.random_field((args.rhs, 3, prob.nslab, prob.ny, prob.nx), seed=1), dtype=dt,
                          device="cuda")
         y = torch.empty_like(u)
-        for _ in range(args.warmup):
-            s.apply(u, y, precision=apply_prec)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            s.apply(u, y, precision=apply_prec)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / max(args.steps, 1)
-        out[name] = {"ms_per_application": ms, "applications_per_s": 1e3 / ms,
-                     "rhs_applications_per_s": args.rhs * 1e3 / ms}
+        grid = psfd.make_grid(prob.nx, prob.ny, prob.nslab, prob.nf, prob.dx, prob.dy, prob.dz, prob.wavelength)
+        for pf in ([int(v) for v in args.pf.split(",")] if args.pf else [None]):
+            if pf is not None:  # the half-plane kernels' L2 prefetch distance (0: none)
+                psfd.tune_set(grid, psfd.FP64 if name == "fp64" else psfd.FP32_REFINED, pf=pf)
+            for _ in range(args.warmup):
+                s.apply(u, y, precision=apply_prec)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                s.apply(u, y, precision=apply_prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / max(args.steps, 1)
+            key = name if pf is None else f"{name}_pf{pf}"
+            out[key] = {"ms_per_application": ms, "applications_per_s": 1e3 / ms,
+                        "rhs_applications_per_s": args.rhs * 1e3 / ms}
+        psfd.tune_reset()
         s.close()
     print(json.dumps(out), flush=True)
     return 0
@@ -583,6 +597,62 @@ def run_autotune(args):
                          "speedup": rep["default_ms"] / rep["tuned_ms"]})
             torch.cuda.empty_cache()
     print(json.dumps({"mode": "autotune", "rows": rows}), flush=True)
+    return 0
+
+
+def run_precond_study(args):
+    """The preconditioner comparison of Sec. 3 on the GPU: one seeded Manhattan clip in free
+    space (no stack), 6 deg s, solved to relative residual 1e-8 by GMRES(60) three ways:
+    the differential PSFD with PMLs (psfd_solve_differential) without and with the spectral
+    damping preconditioner, and the Lippmann-Schwinger form (the Green's function as
+    preconditioner; psfd_solve, FP64 GMRES(24), the device's largest cycle). Reports operator
+    applications and wall time, relative to the unpreconditioned solve (the paper's table
+    reports both)."""
+    import torch
+    from paper_2606_25541_b300 import psfd
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    rows = {}
+    for n, dx, dz, nslab, spacer, pml in ((32, 4.0, 2.0, 14, 20.0, 30.0), (64, 2.0, 2.0, 14, 20.0, 30.0)):
+        prob = layouts.small_clip(nx=n, ny=n, nslab=nslab, dx=dx, dz=dz, seed=21, stack=layouts.empty_stack(),
+                                  theta=(6.0,), phi=(0.0,), pol=(0,))
+        # the differential column (input preparation): PML, spacer, slab, spacer, PML, and the
+        # scattered-field source k0^2 (eps - eps_bg) E_inc with E_inc = s exp(-i beta z), s-polarised
+        ns, npml = int(round(spacer / dz)), int(round(pml / dz))
+        nz = 2 * npml + 2 * ns + nslab
+        eps = np.full((nz, n, n), prob.eps_bg, np.complex128)
+        eps[npml + ns:npml + ns + nslab] = prob.eps
+        k0 = 2 * math.pi / prob.wavelength
+        th = math.radians(6.0)
+        beta = k0 * math.cos(th)
+        inc = np.exp(-1j * beta * np.arange(nz) * dz)
+        b = np.zeros((3, nz, n, n), np.complex128)
+        b[1] = k0 * k0 * (eps - prob.eps_bg) * inc[:, None, None]  # s = (-sin 0, cos 0, 0)
+        epsd = torch.from_numpy(eps).to(dev)
+        bd = torch.from_numpy(b).to(dev)
+        row = {"grid": [n, n, nz], "slab_planes": nslab, "dx_nm": dx, "dz_nm": dz}
+        for name, pc in (("none", 0), ("spectral_damping", 1)):
+            x = torch.zeros_like(bd)
+            t0 = time.perf_counter()
+            st, mv, rel = psfd.solve_differential(n, nz, npml, dx, dz, prob.wavelength, prob.eps_bg, 6.0, 0.0, epsd,
+                                                  bd, x, precond=pc, restart=60, max_matvecs=40000, rtol=1e-8)
+            torch.cuda.synchronize()
+            row[name] = {"matvecs": mv, "relres": rel, "seconds": time.perf_counter() - t0, "status": st}
+        s = psfd.Solver.from_problem(prob, psfd.FP64)
+        s.solve(tol=1e-8, max_iter=2000, krylov=psfd.GMRES, restart=24)  # warm-up (graph capture)
+        s.set_illumination(prob.theta_deg, prob.phi_deg, prob.pol)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = s.solve(tol=1e-8, max_iter=2000, krylov=psfd.GMRES, restart=24)
+        torch.cuda.synchronize()
+        row["lippmann_schwinger"] = {"matvecs": rep["iterations"], "relres": rep["relres"],
+                                     "seconds": time.perf_counter() - t0}
+        s.close()
+        t_none = row["none"]["seconds"]
+        for k in ("none", "spectral_damping", "lippmann_schwinger"):
+            row[k]["relative_wall_time"] = row[k]["seconds"] / t_none
+        rows[f"manhattan_{n}x{n}x{nslab}"] = row
+    print(json.dumps({"mode": "precond_study", **rows}), flush=True)
     return 0
 
 
@@ -953,6 +1023,10 @@ def run_ours(args):
     for _ in range(args.warmup):
         rep = step(solver)
     torch.cuda.synchronize()
+    # first use of this grid: time the tile shapes once (bitwise the same results), untimed
+    tuned = None if args.no_autotune else solver.autotune()
+    step(solver)
+    torch.cuda.synchronize()
 
     # reference orders for the order error the metric is quoted at: FP64 solve to 1e-11 (untimed)
     sref = psfd.Solver.from_problem(prob, psfd.FP64, stream=stream)
@@ -1108,7 +1182,7 @@ def run_ours(args):
         "iterations": reps[-1]["iterations"], "outer": reps[-1]["outer"], "relres": reps[-1]["relres"],
         "order_error_vs_fp64_1e-11": order_error(orders32),
         "order_error_vs_oracle_1e-11": cpu["order_error_vs_oracle_1e-11"] if cpu else None,
-        "roofline": roofline, "kernels": kernels,
+        "roofline": roofline, "kernels": kernels, "autotune": tuned,
         "cpu_baseline": cpu,
         "e2e": {"value": n_rhs * args.steps * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
@@ -1154,7 +1228,8 @@ def solver_bytes(prob) -> float:
 def main(argv=None):
     args = parse_args(argv)
     headline = not (args.apply or args.sweep or args.large or args.crosscheck or args.fixed_point or args.small
-                    or args.layers or args.isolated or args.differential or args.autotune or args.zdft)
+                    or args.layers or args.isolated or args.differential or args.autotune or args.zdft
+                    or args.precond_study)
     if args.tol is None:
         args.tol = HEADLINE_TOL if headline else DEFAULT_TOL
     if args.inner_tol is None:
@@ -1177,6 +1252,8 @@ def main(argv=None):
         return run_autotune(args)
     if args.zdft:
         return run_zdft(args)
+    if args.precond_study:
+        return run_precond_study(args)
     if args.layers:
         return run_layers(args)
     if args.isolated:
@@ -1186,7 +1263,9 @@ def main(argv=None):
     if args.serve_only:
         sizes = tuple(int(s) for s in args.serve_sizes.split(","))
         print(json.dumps({"mode": "serving", **run_serving(args.serve, sizes, args.tol, args.inner_tol,
-                                                           rounds=args.serve_rounds)}), flush=True)
+                                                           slots=args.serve_slots, budget_gb=args.serve_budget_gb,
+                                                           rounds=args.serve_rounds,
+                                                           fp64_sample=args.serve_fp64_sample)}), flush=True)
         return 0
     return run_ours(args)
 

@@ -176,7 +176,9 @@ int psfd_set_device_loop(psfd_ctx* ctx, int enable);
  *   zx  x-modes per CTA of the z pass (K2), 1-16; the lane-group z transforms (nf = 64,
  *       128, 256, and 160 in FP32) take 4, 8 or 16;
  *   rb  rows per CTA of the forward row pass on planes too large for one CTA;
- *   cx  columns per CTA of the column passes on such planes.
+ *   cx  columns per CTA of the column passes on such planes;
+ *   pf  on planes split into two half-plane CTAs (FP32 128 x 128): each CTA asks the bulk-copy
+ *       unit to prefetch into L2 the planes of the CTA pf launches later (0: none).
  * psfd_autotune times the candidate shapes on the context's own grid, illuminations and
  * buffers (CUDA events around 3 applications each, one tunable at a time, each from the best
  * shape so far) in the precision of the context's Krylov loop (FP32 for PSFD_FP32_REFINED,
@@ -194,9 +196,10 @@ typedef struct {
   double default_ms, tuned_ms;
   int zx, rb, cx;
   int candidates;
+  int pf;
 } psfd_tune_report;
 int psfd_autotune(psfd_ctx* ctx, int force, psfd_tune_report* report);
-int psfd_tune_set(const psfd_grid* grid, int precision, int zx, int rb, int cx);
+int psfd_tune_set(const psfd_grid* grid, int precision, int zx, int rb, int cx, int pf);
 int psfd_tune_reset(void);
 
 /* Arithmetic of the FP64 residual r = b - A x that certifies a PSFD_FP32_REFINED solve
@@ -455,6 +458,29 @@ int psfd_apply_fp32_static(const psfd_grid* grid, int n_layers, const double* n_
 int psfd_apply_differential(int n, int nz, int n_pml, double dx, double dz, double wavelength, double eps_bg,
                             double theta_deg, double phi_deg, const double* eps, const double* E, double* out,
                             double* work, void* stream);
+
+/* GMRES(restart) solve of the differential system A x = b of psfd_apply_differential (the
+ * paper's comparator, Sec. 3, Eqs. (4)-(7); its preconditioner table), FP64, on the device:
+ *   precond 0  none;
+ *   precond 1  the spectral damping D(k) = min(1, kb^2 / |k|^2) on the column's 3-D Fourier
+ *              grid (k = (q_x, q_y, k_z), q = q_inc + 2 pi m / P), applied on the left: the
+ *              system M A x = M b is solved and its residual is what rtol bounds.
+ * Arnoldi with classical Gram-Schmidt and one reorthogonalisation pass (on the device),
+ * Givens rotations and the triangular solve on the host (one host wait per iteration); the
+ * residual M (b - A x) is recomputed at every restart. Arguments as psfd_apply_differential,
+ * and:
+ *   b, x          device, complex double [3][nz][n][n]; x is overwritten (start: 0)
+ *   work          device scratch of psfd_solve_differential_work(...) complex doubles
+ *   restart       basis size per cycle (1 .. 512); max_matvecs bounds the operator applications
+ *                 of the Arnoldi steps (the restart residuals are not counted)
+ *   matvecs, relres (may be NULL) applications taken, final relative residual
+ * Returns PSFD_OK, PSFD_E_NOT_CONVERGED (x holds the last iterate), PSFD_E_ARG or PSFD_E_CUDA. */
+int psfd_solve_differential(int n, int nz, int n_pml, double dx, double dz, double wavelength, double eps_bg,
+                            double theta_deg, double phi_deg, int precond, const double* eps, const double* b,
+                            double* x, double* work, int restart, int max_matvecs, double rtol, int* matvecs,
+                            double* relres, void* stream);
+/* Complex doubles of work psfd_solve_differential needs: (restart + 4) fields plus the partial sums. */
+size_t psfd_solve_differential_work(int n, int nz, int restart);
 
 /* Measurement of the z pass's forward transform (K2 at nf = 128) on two kinds of units, for
  * deciding whether the tensor cores pay (no counterpart in the paper):

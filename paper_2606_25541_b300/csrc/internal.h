@@ -93,6 +93,7 @@ struct OpCall {
   const double* ktab64;    // [nf]: signed kz_l (FP64)
   const int* active;  // per global rhs, or null = all active
   int no_reflect;     // 1: leave R out, i.e. the free-space operator u - G*(V u)
+  int pf;             // half-plane K1/K3: L2 prefetch of the planes of the CTA pf launches ahead (0: off)
   // isolated clip: per (slot, l <= nf/2, mode) the spherically windowed kernel's (A, B/|k|^2)
   // (FP32 float4 / FP64 pair of double2); null = the periodic z-windowed kernel
   const float4* sph32;
@@ -136,6 +137,7 @@ struct RunTune {
   int zx;  // K2: transverse x-modes per CTA of the z pass
   int rb;  // K1 on split planes: rows per CTA of the forward row pass
   int cx;  // split planes: columns per CTA of the column passes (forward and inverse)
+  int pf;  // half-plane K1/K3: L2 prefetch distance in CTAs (0: no prefetch)
 };
 RunTune run_tune(bool fp64, int nx, int ny, int nslab, int nf);
 void set_run_tune(bool fp64, int nx, int ny, int nslab, int nf, RunTune t);

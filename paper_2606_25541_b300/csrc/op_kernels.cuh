@@ -325,6 +325,40 @@ template <typename C, int NX, int NY> __host__ __device__ constexpr int half_til
   return fft_phys(NY / 2) * half_pitch<C, NX, NY>();
 }
 
+// L2 prefetch of a contiguous range by the bulk-copy unit (no registers, no wait).
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Half-plane K1 and K3 are latency-bound: a CTA's global loads come in one phase and its
+// transforms in another. Thread 0 of each CTA therefore asks the bulk-copy unit to bring into
+// L2 the planes that the CTA a.pf launches later (in linear block order) will read, so that
+// its loads hit L2. Only the even CTA of a plane pair prefetches (both read the whole plane).
+template <typename C, int NX, int NY, int IN, bool INV>
+__device__ __forceinline__ void half_prefetch(const OpCall<C>& a, const C* uin) {
+  const unsigned nbx = gridDim.x, nby = gridDim.y;
+  const unsigned lin = blockIdx.x + nbx * (blockIdx.y + nby * blockIdx.z) + (unsigned)a.pf;
+  if (lin >= nbx * nby * gridDim.z) return;
+  const unsigned bx = lin % nbx, yz = lin / nbx;
+  if (bx & 1u) return;
+  const int p = (int)(bx >> 1), c = (int)(yz % nby), lr = (int)(yz / nby), g = a.rhs0 + lr;
+  if (a.active && !a.active[g]) return;
+  constexpr unsigned bytes = NX * NY * sizeof(C);
+  const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
+  if constexpr (INV) {
+    l2_prefetch(a.work + plane, bytes);
+    l2_prefetch(uin + plane, bytes);
+    if (a.dot_mask & DOT_R0_OUT) l2_prefetch(a.r0 + plane, bytes);
+  } else {
+    l2_prefetch(a.V + ((size_t)a.rhsp[g].clip * a.nslab + p) * (NX * NY), bytes);
+    if constexpr (IN != IN_SUPDATE) l2_prefetch(a.u + plane, bytes);
+    if constexpr (IN != IN_PLAIN) {
+      l2_prefetch(a.r + plane, bytes);
+      l2_prefetch(a.v + plane, bytes);
+    }
+  }
+}
+
 template <typename C, int NX, int NY, int IN, int NT>
 __global__ void __launch_bounds__(NT, 2) k_half_fwd(OpCall<C> a) {
   constexpr int H = NY / 2, PITCH = half_pitch<C, NX, NY>();
@@ -334,6 +368,7 @@ __global__ void __launch_bounds__(NT, 2) k_half_fwd(OpCall<C> a) {
   C* twy = twx + NX;  // exp(-2 pi i r / NY), r < H
   C* twh = twy + H;   // exp(-2 pi i t / H), t < H
   const int p = blockIdx.x >> 1, h = blockIdx.x & 1, c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
+  if (a.pf && threadIdx.x == 0) half_prefetch<C, NX, NY, IN, false>(a, nullptr);
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
   for (int i = threadIdx.x; i < NX; i += NT) twx[i] = from_c64<C>(a.twx[i]);
@@ -389,6 +424,7 @@ __global__ void __launch_bounds__(NT, 2) k_half_inv(OpCall<C> a, const C* uin) {
   C* twh = twy + H;
   double2* scratch = align16<double2>(twh + H);
   const int p = blockIdx.x >> 1, h = blockIdx.x & 1, c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
+  if (a.pf && threadIdx.x == 0) half_prefetch<C, NX, NY, IN_PLAIN, true>(a, uin);
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
   for (int i = threadIdx.x; i < NX; i += NT) twx[i] = from_c64<C>(a.twx[i]);

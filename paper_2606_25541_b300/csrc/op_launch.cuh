@@ -101,23 +101,34 @@ int launch_plane_inv(const OpCall<C>& a, const C* uin) {
   return PSFD_OK;
 }
 
+// L2 prefetch distance of the half-plane kernels: the tuned one, or none.
+template <typename C>
+inline int half_pf_of(const OpCall<C>& a) {
+  const int t = run_tune(sizeof(C) == 16, a.nx, a.ny, a.nslab, a.nf).pf;
+  return t > 0 ? t : 0;
+}
+
 template <typename C, int N, int IN>
-int launch_half_fwd(const OpCall<C>& a) {
+int launch_half_fwd(const OpCall<C>& a0) {
   constexpr int NT = 512;
   const size_t smem = (size_t)(half_tile_elems<C, N, N>() + 2 * N) * sizeof(C);
   auto k = k_half_fwd<C, N, N, IN, NT>;
   if (set_smem(k, smem)) return PSFD_E_CUDA;
+  OpCall<C> a = a0;
+  a.pf = half_pf_of(a0);
   k<<<dim3(2 * a.nslab, 3, a.nrhs), NT, smem, a.stream>>>(a);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;
 }
 
 template <typename C, int N, int EPI>
-int launch_half_inv(const OpCall<C>& a, const C* uin) {
+int launch_half_inv(const OpCall<C>& a0, const C* uin) {
   constexpr int NT = 512;
   const size_t smem = (size_t)(half_tile_elems<C, N, N>() + 2 * N) * sizeof(C) + 16 + NDOT * 32 * sizeof(double2);
   auto k = k_half_inv<C, N, N, EPI, NT>;
   if (set_smem(k, smem)) return PSFD_E_CUDA;
+  OpCall<C> a = a0;
+  a.pf = half_pf_of(a0);
   k<<<dim3(2 * a.nslab, 3, a.nrhs), NT, smem, a.stream>>>(a, uin);
   PSFD_CHECK_LAUNCH();
   return PSFD_OK;

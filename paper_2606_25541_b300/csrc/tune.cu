@@ -20,7 +20,7 @@ std::map<std::tuple<int, int, int, int, int>, RunTune> g_tune;
 RunTune run_tune(bool fp64, int nx, int ny, int nslab, int nf) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tune.find({fp64, nx, ny, nslab, nf});
-  return it == g_tune.end() ? RunTune{0, 0, 0} : it->second;
+  return it == g_tune.end() ? RunTune{0, 0, 0, 0} : it->second;
 }
 
 bool has_run_tune(bool fp64, int nx, int ny, int nslab, int nf) {
@@ -42,9 +42,12 @@ namespace {
 
 // Candidate shapes of each tunable for a grid (the built-in choice among them).
 template <typename C>
-void candidates(const psfd_grid& g, std::vector<int>& zx, std::vector<int>& rb, std::vector<int>& cx) {
+void candidates(const psfd_grid& g, std::vector<int>& zx, std::vector<int>& rb, std::vector<int>& cx,
+                std::vector<int>& pf) {
   for (int t : {1, 2, 4, 8, 16})
     if (zcol_tile_ok<C>(g.nx, g.nf, t)) zx.push_back(t);
+  if (use_half<C>(g.nx, g.ny))  // prefetch distances: a quarter to one wave of resident CTAs
+    for (int d : {37, 74, 111, 148, 296}) pf.push_back(d);
   if (!use_fused<C>(g.nx, g.ny)) {
     for (int r = 1; r <= g.ny; r *= 2)
       if (rows_fwd_ok<C>(g.nx, g.ny, r)) rb.push_back(r);
@@ -74,13 +77,13 @@ template <typename C>
 int autotune_impl(psfd_ctx* ctx, OpCall<C> a, psfd_tune_report* rep) {
   const psfd_grid& g = ctx->g;
   const bool fp64 = sizeof(C) == 16;
-  std::vector<int> zx, rb, cx;
-  candidates<C>(g, zx, rb, cx);
+  std::vector<int> zx, rb, cx, pf;
+  candidates<C>(g, zx, rb, cx, pf);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   constexpr int kReps = 3;
-  RunTune best{0, 0, 0};
+  RunTune best{0, 0, 0, 0};
   double t_best = 0.0, t_default = 0.0;
   int tried = 0, rc = PSFD_OK;
   auto measure = [&](RunTune t, double* ms) {
@@ -91,11 +94,11 @@ int autotune_impl(psfd_ctx* ctx, OpCall<C> a, psfd_tune_report* rep) {
   rc = measure(best, &t_default);
   t_best = t_default;
   // one tunable at a time, each from the best shape found so far
-  for (int which = 0; rc == PSFD_OK && which < 3; ++which) {
-    const std::vector<int>& cand = which == 0 ? zx : (which == 1 ? rb : cx);
+  for (int which = 0; rc == PSFD_OK && which < 4; ++which) {
+    const std::vector<int>& cand = which == 0 ? zx : (which == 1 ? rb : (which == 2 ? cx : pf));
     for (int v : cand) {
       RunTune t = best;
-      (which == 0 ? t.zx : (which == 1 ? t.rb : t.cx)) = v;
+      (which == 0 ? t.zx : (which == 1 ? t.rb : (which == 2 ? t.cx : t.pf))) = v;
       double ms = 0.0;
       if ((rc = measure(t, &ms)) != PSFD_OK) break;
       if (ms < t_best) {
@@ -106,7 +109,7 @@ int autotune_impl(psfd_ctx* ctx, OpCall<C> a, psfd_tune_report* rep) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  set_run_tune(fp64, g.nx, g.ny, g.nslab, g.nf, rc == PSFD_OK ? best : RunTune{0, 0, 0});
+  set_run_tune(fp64, g.nx, g.ny, g.nslab, g.nf, rc == PSFD_OK ? best : RunTune{0, 0, 0, 0});
   if (rc != PSFD_OK) return rc;
   if (rep) {
     rep->default_ms = t_default;
@@ -114,6 +117,7 @@ int autotune_impl(psfd_ctx* ctx, OpCall<C> a, psfd_tune_report* rep) {
     rep->zx = best.zx;
     rep->rb = best.rb;
     rep->cx = best.cx;
+    rep->pf = best.pf;
     rep->candidates = tried;
   }
   return PSFD_OK;
@@ -133,7 +137,7 @@ extern "C" int psfd_autotune(psfd_ctx* ctx, int force, psfd_tune_report* report)
   if (!force && has_run_tune(!f32, g.nx, g.ny, g.nslab, g.nf)) {
     if (report) {
       const RunTune t = run_tune(!f32, g.nx, g.ny, g.nslab, g.nf);
-      *report = psfd_tune_report{0.0, 0.0, t.zx, t.rb, t.cx, 0};
+      *report = psfd_tune_report{0.0, 0.0, t.zx, t.rb, t.cx, 0, t.pf};
     }
     return PSFD_OK;
   }
@@ -162,8 +166,8 @@ extern "C" int psfd_autotune(psfd_ctx* ctx, int force, psfd_tune_report* report)
   return rc;
 }
 
-extern "C" int psfd_tune_set(const psfd_grid* g, int precision, int zx, int rb, int cx) {
-  if (!g || zx < 0 || rb < 0 || cx < 0) return PSFD_E_ARG;
+extern "C" int psfd_tune_set(const psfd_grid* g, int precision, int zx, int rb, int cx, int pf) {
+  if (!g || zx < 0 || rb < 0 || cx < 0 || pf < 0) return PSFD_E_ARG;
   if (precision != PSFD_FP64 && precision != PSFD_FP32_REFINED) return PSFD_E_ARG;
   const bool fp64 = precision == PSFD_FP64;
   const bool ok = fp64 ? ((!zx || zcol_tile_ok<double2>(g->nx, g->nf, zx)) &&
@@ -173,7 +177,7 @@ extern "C" int psfd_tune_set(const psfd_grid* g, int precision, int zx, int rb, 
                           (!rb || rows_fwd_ok<float2>(g->nx, g->ny, rb)) &&
                           (!cx || cols_tile_ok<float2>(g->nx, g->ny, cx)));
   if (!ok) return PSFD_E_ARG;
-  set_run_tune(fp64, g->nx, g->ny, g->nslab, g->nf, RunTune{zx, rb, cx});
+  set_run_tune(fp64, g->nx, g->ny, g->nslab, g->nf, RunTune{zx, rb, cx, pf});
   return PSFD_OK;
 }
 

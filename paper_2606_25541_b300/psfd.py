@@ -54,7 +54,7 @@ class Request(ctypes.Structure):
 
 class TuneReport(ctypes.Structure):
     _fields_ = [("default_ms", ctypes.c_double), ("tuned_ms", ctypes.c_double), ("zx", ctypes.c_int),
-                ("rb", ctypes.c_int), ("cx", ctypes.c_int), ("candidates", ctypes.c_int)]
+                ("rb", ctypes.c_int), ("cx", ctypes.c_int), ("candidates", ctypes.c_int), ("pf", ctypes.c_int)]
 
 
 class PsfdError(RuntimeError):
@@ -84,7 +84,7 @@ _SIGS = {
     "psfd_set_device_loop": (_I, [_P, _I]),
     "psfd_set_residual_arith": (_I, [_P, _I]),
     "psfd_autotune": (_I, [_P, _I, ctypes.POINTER(TuneReport)]),
-    "psfd_tune_set": (_I, [ctypes.POINTER(Grid), _I, _I, _I, _I]),
+    "psfd_tune_set": (_I, [ctypes.POINTER(Grid), _I, _I, _I, _I, _I]),
     "psfd_tune_reset": (_I, []),
     "psfd_set_green": (_I, [_P, _I, ctypes.c_double]),
     "psfd_solve": (_I, [_P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Report)]),
@@ -104,6 +104,10 @@ _SIGS = {
                                     _P, _P, _P]),
     "psfd_apply_differential": (_I, [_I, _I, _I, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, _P, _P, _P, _P]),
+    "psfd_solve_differential": (_I, [_I, _I, _I, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, _I, _P, _P, _P, _P, _I, _I,
+                                     ctypes.c_double, _IP, _D, _P]),
+    "psfd_solve_differential_work": (ctypes.c_size_t, [_I, _I, _I]),
     "psfd_server_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _I, ctypes.POINTER(SolveOpts)]),
     "psfd_server_destroy": (_I, [_P]),
     "psfd_server_submit": (_I, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)]),
@@ -166,9 +170,9 @@ def zdft_status() -> int:
     return flag.value
 
 
-def tune_set(grid: Grid, precision: int, zx: int = 0, rb: int = 0, cx: int = 0):
+def tune_set(grid: Grid, precision: int, zx: int = 0, rb: int = 0, cx: int = 0, pf: int = 0):
     """Store tile shapes for a grid and precision in the autotuner's table (0 = built-in)."""
-    st = load().psfd_tune_set(ctypes.byref(grid), int(precision), int(zx), int(rb), int(cx))
+    st = load().psfd_tune_set(ctypes.byref(grid), int(precision), int(zx), int(rb), int(cx), int(pf))
     if st != OK:
         raise PsfdError(st, strerror(st))
 
@@ -176,6 +180,26 @@ def tune_set(grid: Grid, precision: int, zx: int = 0, rb: int = 0, cx: int = 0):
 def tune_reset():
     """Empty the autotuner's table (every grid back to the built-in shapes)."""
     load().psfd_tune_reset()
+
+
+def solve_differential(n, nz, n_pml, dx, dz, wavelength, eps_bg, theta_deg, phi_deg, eps, b, x, precond=0,
+                       restart=60, max_matvecs=20000, rtol=1e-8, stream=None):
+    """GMRES(restart) on the device for the differential system (psfd_solve_differential):
+    eps, b, x complex128 CUDA tensors; precond 0 = none, 1 = spectral damping. Returns
+    (status, matvecs, relres)."""
+    import torch
+    lib = load()
+    need = int(lib.psfd_solve_differential_work(int(n), int(nz), int(restart)))
+    work = torch.empty(need, dtype=torch.complex128, device=b.device)
+    mv = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = lib.psfd_solve_differential(int(n), int(nz), int(n_pml), float(dx), float(dz), float(wavelength),
+                                     float(eps_bg), float(theta_deg), float(phi_deg), int(precond),
+                                     ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                     ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(work.data_ptr()), int(restart),
+                                     int(max_matvecs), float(rtol), ctypes.byref(mv), ctypes.byref(rel),
+                                     _stream_ptr(stream))
+    return st, mv.value, rel.value
 
 
 def launch_count() -> int:
@@ -341,7 +365,7 @@ class Solver:
         r = TuneReport()
         self._check(self.lib.psfd_autotune(self.ctx, int(bool(force)), ctypes.byref(r)))
         return {"default_ms": r.default_ms, "tuned_ms": r.tuned_ms, "zx": r.zx, "rb": r.rb, "cx": r.cx,
-                "candidates": r.candidates}
+                "pf": r.pf, "candidates": r.candidates}
 
     def set_device_loop(self, enable: bool):
         """Run each Krylov sweep as one graph launch that loops on the device (default) or

@@ -47,6 +47,8 @@ def _shapes(psfd, g, precision):
         out.append((0, rb, 0))
     for cx in (1, 2, 4, 8, 16, 32):
         out.append((0, 0, cx))
+    for pf in (148, 296, 592):
+        out.append((0, 0, 0, pf))
     ok = []
     for t in out:
         try:

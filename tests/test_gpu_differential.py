@@ -108,3 +108,36 @@ def test_differential_apply_rejects_unsupported_sizes(psfd):
     for n, nz, npml, dx, dz in bad:
         st = psfd.apply_differential(n, nz, npml, dx, dz, p.wavelength, 1.0, 6.0, 0.0, eps, e, e.clone(), e.clone())
         assert st == -1, (n, nz, npml, dx, dz, st)
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_differential_gmres_on_the_device_matches_the_oracle(psfd, precond):
+    """GMRES(20) on the device (psfd_solve_differential) against the oracle's GMRES(20) on the
+    same system and preconditioner (Sec. 3's comparison): the solutions agree to the solve
+    tolerance's scale and the device's residual is at most rtol. The operator counts (thousands
+    of restarted steps without a preconditioner) agree within a factor 1.4: the two
+    orthogonalise differently (classical twice on the device, modified on the host), so their
+    rounding, and with it the restart history, differs."""
+    p = _problem(8, 32, 6, 4.0, 2.0, 6.0, 0.0, seed=3)
+    b = dif.differential_rhs(p)
+    g = dif._geometry(p)
+    if precond:
+        x_ref, mv_ref, _ = dif.gmres_restarted(lambda v: dif.spectral_damping(p, dif.apply_differential(p, v, g), g),
+                                               dif.spectral_damping(p, b, g), 1e-10, 20, 20000)
+    else:
+        x_ref, mv_ref, _ = dif.gmres_restarted(lambda v: dif.apply_differential(p, v, g), b, 1e-10, 20, 20000)
+    dev = torch.device("cuda:0")
+    eps = torch.from_numpy(np.ascontiguousarray(p.eps)).to(dev)
+    bd = torch.from_numpy(np.ascontiguousarray(b)).to(dev)
+    x = torch.full_like(bd, float("nan"))
+    st, mv, rel = psfd.solve_differential(p.nx, p.nz, p.n_pml, p.dx, p.dz, p.wavelength, p.eps_bg, p.theta, p.phi,
+                                          eps, bd, x, precond=precond, restart=20, max_matvecs=20000, rtol=1e-10)
+    torch.cuda.synchronize()
+    assert st == 0, psfd.strerror(st)
+    assert rel <= 1e-10
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - x_ref) <= 1e-6 * np.linalg.norm(x_ref)
+    # the device solution solves the system: ||b - A x|| small against ||b|| (unpreconditioned check)
+    r = b - dif.apply_differential(p, xg, g)
+    assert np.linalg.norm(r) <= 1e-6 * np.linalg.norm(b)
+    assert mv_ref / 1.4 <= mv <= 1.4 * mv_ref, (mv, mv_ref)
