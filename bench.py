@@ -61,6 +61,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in tile shapes")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the sampled precision sweep and large clip in the default run")
     ap.add_argument("--profile-only", action="store_true", help="one profiled step, for ncu launch lists")
     ap.add_argument("--plain-launches", action="store_true",
                     help="with --profile-only: launch every kernel on its own (no CUDA graphs)")
@@ -258,20 +260,26 @@ def run_apply(args):
 
 
 def run_sweep(args):
+    print(json.dumps({"mode": "precision_sweep", **precision_sweep(args.tol, args.inner_tol, args.steps,
+                                                                   args.warmup)}), flush=True)
+    return 0
+
+
+def precision_sweep(tol: float, inner_tol: float, steps: int, warmup: int) -> dict:
     """Precision sweep on the 256 x 256 x 60 Manhattan clip (nf = 128, 6 deg s and p): the plain
     FP64 path and the FP32 path with FP64 defect correction, each timed over whole solves of
-    both illuminations, with the order error of every variant against the FP64 solution."""
+    both illuminations, with the order error of every variant against the FP64 solution; the
+    split-BF16 tensor-core row is the z transform stage measured against the CUDA cores."""
     import torch
     from paper_2606_25541_b300 import psfd
     prob = layouts.manhattan_clip(256, seed=3)
     stream = torch.cuda.current_stream()
     eps_dev = torch.from_numpy(prob.eps).cuda()
-    out = {"mode": "precision_sweep", "workload": f"manhattan_256x256x60_nf{prob.nf}_2rhs",
-           "n_rhs": prob.n_rhs, "tol": args.tol}
+    out = {"workload": f"manhattan_256x256x60_nf{prob.nf}_2rhs", "n_rhs": prob.n_rhs, "tol": tol}
     orders = {}
-    for name, prec, kw in (("fp64", psfd.FP64, dict(tol=args.tol, max_iter=600)),
+    for name, prec, kw in (("fp64", psfd.FP64, dict(tol=tol, max_iter=600)),
                            ("fp32_refined", psfd.FP32_REFINED,
-                            dict(tol=args.tol, inner_tol=args.inner_tol, max_iter=400, max_outer=12))):
+                            dict(tol=tol, inner_tol=inner_tol, max_iter=400, max_outer=12))):
         s = psfd.Solver.from_problem(prob, prec, stream=stream)
 
         def step():
@@ -279,16 +287,16 @@ def run_sweep(args):
             s.set_illumination(prob.theta_deg, prob.phi_deg, prob.pol)
             return s.solve(**kw)
 
-        for _ in range(max(args.warmup, 1)):
+        for _ in range(max(warmup, 1)):
             rep = step()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             rep = step()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = e0.elapsed_time(e1) / steps
         orders[name] = [s.diffraction_orders(i) for i in range(prob.n_rhs)]
         out[name] = {"solves_per_s": prob.n_rhs * 1e3 / ms, "ms_per_batch": ms, "iterations": rep["iterations"],
                      "outer": rep["outer"], "relres": rep["relres"]}
@@ -302,18 +310,27 @@ def run_sweep(args):
     out["fp32_refined"]["order_rel_err_vs_fp64"] = max(
         err(a, b) for a, b in zip(orders["fp32_refined"], orders["fp64"]))
     out["fp32_refined"]["speedup_vs_fp64"] = out["fp32_refined"]["solves_per_s"] / out["fp64"]["solves_per_s"]
-    out["bf16x3"] = {"status": "not built", "why": "split-BF16 tensor-core DFT stages are not implemented"}
-    print(json.dumps(out), flush=True)
-    return 0
+    out["bf16x3_tensor_cores"] = {"status": "the z transform stage measured, not used in the solve "
+                                            "(slower and less accurate than the CUDA-core transform)",
+                                  **zdft_rows()}
+    return out
 
 
 def run_large(args):
-    """Large curvilinear clip, 1024 x 1024 x 60 (nf = 160), 4 polar angles x s/p, FP32 with FP64
-    defect correction and the memory-light layout (BiCGStab pool, FP32 spectra inside the FP64
-    ones): the illuminations run in the largest batches whose workspace fits a 180 GB budget."""
+    print(json.dumps({"mode": "large_clip", **large_clip(args.tol, args.inner_tol, args.warmup)}), flush=True)
+    return 0
+
+
+def large_clip(tol: float, inner_tol: float, warmup: int, n_rhs: int | None = None) -> dict:
+    """Large curvilinear clip, 1024 x 1024 x 60 (nf = 160), 4 polar angles x s/p (or the first
+    n_rhs of them), FP32 with FP64 defect correction and the memory-light layout (BiCGStab pool,
+    FP32 spectra inside the FP64 ones): the illuminations run in the largest batches whose
+    workspace fits a 180 GB budget."""
     import torch
     from paper_2606_25541_b300 import psfd
     prob = layouts.curvilinear_clip()
+    if n_rhs:
+        prob = prob.with_illumination(prob.theta_deg[:n_rhs], prob.phi_deg[:n_rhs], prob.pol[:n_rhs])
     budget = 180e9
     g = psfd.make_grid(prob.nx, prob.ny, prob.nslab, prob.nf, prob.dx, prob.dy, prob.dz, prob.wavelength,
                        prob.eps_bg)
@@ -323,7 +340,7 @@ def run_large(args):
                                  set_inputs=False)
     s.set_stack(prob.n_layers, prob.d_layers, prob.n_sub)
     s.set_potential(prob.eps)
-    kw = dict(tol=args.tol, inner_tol=args.inner_tol, max_iter=600, max_outer=12)
+    kw = dict(tol=tol, inner_tol=inner_tol, max_iter=600, max_outer=12)
     groups = [list(range(i, min(i + batch, prob.n_rhs))) for i in range(0, prob.n_rhs, batch)]
 
     def run_all():
@@ -334,7 +351,7 @@ def run_large(args):
             effs += [float(s.diffraction_orders(i)["eff"].sum()) for i in range(len(grp))]
         return reps, effs
 
-    if args.warmup > 0:
+    if warmup > 0:
         run_all()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -343,14 +360,13 @@ def run_large(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    out = {"mode": "large_clip", "workload": f"curvilinear_1024x1024x60_nf{prob.nf}_8rhs", "n_rhs": prob.n_rhs,
+    out = {"workload": f"curvilinear_1024x1024x60_nf{prob.nf}_{prob.n_rhs}rhs", "n_rhs": prob.n_rhs,
            "batch_rhs": batch, "workspace_gb": psfd.workspace_bytes(g, psfd.FP32_REFINED, batch) / 1e9,
            "budget_gb": budget / 1e9, "solves_per_s": prob.n_rhs * 1e3 / ms, "ms_total": ms,
            "iterations": [r["iterations"] for r in reps], "outer": [r["outer"] for r in reps],
            "relres": max(r["relres"] for r in reps), "reflected_efficiency": effs}
     s.close()
-    print(json.dumps(out), flush=True)
-    return 0
+    return out
 
 
 def run_crosscheck(args):
@@ -657,6 +673,12 @@ def run_precond_study(args):
 
 
 def run_zdft(args):
+    print(json.dumps({"mode": "zdft", "workload": "manhattan_256x256x60_nf128_6columns_sets", **zdft_rows()}),
+          flush=True)
+    return 0
+
+
+def zdft_rows() -> dict:
     """The z pass's forward transform on the 256 x 256 x 60 Manhattan clip's columns (3
     components x 2 illuminations): CUDA-core register transform vs split-BF16 tensor-core DFT
     products, time per launch (CUDA events, 20 launches after 3), algorithmic HBM rate (60
@@ -694,8 +716,7 @@ def run_zdft(args):
             flops = 2 * 3 * 2.0 * 128 * 64 * 2 * cols  # 2 matrices x 3 products x 2 M K N
             row["tensor_TFLOPs"] = flops / (ms * 1e-3) / 1e12
         rows[name] = row
-    print(json.dumps({"mode": "zdft", "workload": "manhattan_256x256x60_nf128_6columns_sets", **rows}), flush=True)
-    return 0
+    return rows
 
 
 def run_small(args):
@@ -1134,6 +1155,18 @@ def run_ours(args):
              "inner_tol": DEFAULT_INNER_TOL, "iterations": rep_t["iterations"], "outer": rep_t["outer"],
              "relres": rep_t["relres"], "order_error_vs_fp64_1e-11": order_error(orders_all(solver, n_rhs))}
 
+    # the other workloads, sampled: cfg 3's precision sweep (256^2 Manhattan, both paths and the
+    # tensor-core stage) and cfg 5's large clip (1024^2, 2 of its 8 illuminations), at 1e-8
+    extra = {}
+    if world == 1 and not args.no_extra:
+        solver.close()
+        torch.cuda.empty_cache()
+        extra["precision_sweep_manhattan_256"] = precision_sweep(DEFAULT_TOL, DEFAULT_INNER_TOL, 1, 1)
+        torch.cuda.empty_cache()
+        extra["large_clip_curvilinear_1024_2rhs"] = large_clip(DEFAULT_TOL, DEFAULT_INNER_TOL, 1, n_rhs=2)
+        torch.cuda.empty_cache()
+        solver = None
+
     serving = None
     if args.serve > 0 and world == 1:
         sizes = tuple(int(s) for s in args.serve_sizes.split(","))
@@ -1191,9 +1224,11 @@ def run_ours(args):
         "fp64_plain": fp64,
         "fp32_refined_at_tol_1e-8": tight,
         "serving": serving,
+        **extra,
     }
     print(json.dumps(line), flush=True)
-    solver.close()
+    if solver is not None:
+        solver.close()
     return 0
 
 

@@ -177,8 +177,9 @@ int psfd_set_device_loop(psfd_ctx* ctx, int enable);
  *       128, 256, and 160 in FP32) take 4, 8 or 16;
  *   rb  rows per CTA of the forward row pass on planes too large for one CTA;
  *   cx  columns per CTA of the column passes on such planes;
- *   pf  on planes split into two half-plane CTAs (FP32 128 x 128): each CTA asks the bulk-copy
- *       unit to prefetch into L2 the planes of the CTA pf launches later (0: none).
+ *   pf  on planes split into two half-plane CTAs (FP32 128 x 128): each CTA of the inverse pass
+ *       (and of the forward pass with the plain input stage) asks the bulk-copy unit to
+ *       prefetch into L2 the planes of the CTA pf launches later (0: none).
  * psfd_autotune times the candidate shapes on the context's own grid, illuminations and
  * buffers (CUDA events around 3 applications each, one tunable at a time, each from the best
  * shape so far) in the precision of the context's Krylov loop (FP32 for PSFD_FP32_REFINED,

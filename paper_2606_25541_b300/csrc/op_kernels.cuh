@@ -351,11 +351,7 @@ __device__ __forceinline__ void half_prefetch(const OpCall<C>& a, const C* uin) 
     if (a.dot_mask & DOT_R0_OUT) l2_prefetch(a.r0 + plane, bytes);
   } else {
     l2_prefetch(a.V + ((size_t)a.rhsp[g].clip * a.nslab + p) * (NX * NY), bytes);
-    if constexpr (IN != IN_SUPDATE) l2_prefetch(a.u + plane, bytes);
-    if constexpr (IN != IN_PLAIN) {
-      l2_prefetch(a.r + plane, bytes);
-      l2_prefetch(a.v + plane, bytes);
-    }
+    l2_prefetch(a.u + plane, bytes);
   }
 }
 
@@ -368,7 +364,10 @@ __global__ void __launch_bounds__(NT, 2) k_half_fwd(OpCall<C> a) {
   C* twy = twx + NX;  // exp(-2 pi i r / NY), r < H
   C* twh = twy + H;   // exp(-2 pi i t / H), t < H
   const int p = blockIdx.x >> 1, h = blockIdx.x & 1, c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
-  if (a.pf && threadIdx.x == 0) half_prefetch<C, NX, NY, IN, false>(a, nullptr);
+  // the update stages (p, s) read three vectors and V per plane: prefetching all of them ahead
+  // measured slower inside the solve, so only the plain input stage prefetches
+  if constexpr (IN == IN_PLAIN)
+    if (a.pf && threadIdx.x == 0) half_prefetch<C, NX, NY, IN, false>(a, nullptr);
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
   for (int i = threadIdx.x; i < NX; i += NT) twx[i] = from_c64<C>(a.twx[i]);
