@@ -92,6 +92,7 @@ struct psfd_ctx {
 
   // device state
   double2 *V64 = nullptr, *eps_stage = nullptr, *twx = nullptr, *twy = nullptr, *twz = nullptr;
+  float2 *twx32 = nullptr, *twy32 = nullptr, *twz32 = nullptr;  // the twiddle tables rounded to FP32
   float2* V32 = nullptr;
   psfd::RhsParam* rhsp = nullptr;
   double* slot_par = nullptr;  // [rhs][4]: q_inc x, q_inc y, cos phi, sin phi

@@ -84,8 +84,10 @@ struct OpCall {
   int nx, ny, nslab, nf;
   int rhs0, nrhs;
   double dx, dy, dz, kb;
+  float dz32, kb32;                             // dz and kb rounded to FP32 (FP32 kernels)
   const C* V;                                   // [nslab][ny][nx]
   const double2 *twx, *twy, *twz;               // exp(-2 pi i t / n) tables (FP64)
+  const float2 *twx32, *twy32, *twz32;          // the same tables rounded to FP32 (FP32 kernels)
   const RhsParam* rhsp;
   const ModeEntry* modes;
   const ModeF32* modes32;  // FP32 column constants (used by the FP32 z-column kernel)

@@ -46,6 +46,15 @@ __device__ __forceinline__ void split_hi_lo_r(double v, double& hi, double& lo) 
   lo = 0.0;
 }
 
+// Twiddle entry in the working precision. The FP32 kernels read the tables rounded to FP32
+// once per context (the values a conversion of the FP64 entry gives), so no FP64 conversion
+// runs per CTA: the FP64 pipe of this GPU issues them far slower than the FP32 pipes.
+template <typename C>
+__device__ __forceinline__ C twid(const double2* t64, const float2* t32, int i) {
+  if constexpr (sizeof(C) == sizeof(float2)) return t32[i];
+  else return t64[i];
+}
+
 // a / b through one reciprocal of |b|^2; here |b| stays far from under- and overflow
 // (|kappa + beta| >= |beta| and |delta| >= 1/(2L) on this branch).
 __device__ __forceinline__ float2 cdiv_fast(float2 a, float2 b) {
@@ -66,7 +75,22 @@ __device__ __forceinline__ InScal<C> load_in_scalars(const OpCall<C>& a, int g) 
   InScal<C> s;
   s.a = mk((typename RealOf<C>::T)0, (typename RealOf<C>::T)0);
   s.b = s.a;
-  if constexpr (IN == IN_PUPDATE) {
+  if constexpr (sizeof(C) == sizeof(float2) && IN != IN_PLAIN) {
+    // one lane per warp converts the FP64 scalars and the warp shares them: the FP64 pipe of
+    // this GPU issues conversions far slower than the FP32 pipes (the whole CTA calls this)
+    if ((threadIdx.x & 31) == 0) {
+      if constexpr (IN == IN_PUPDATE) {
+        s.a = from_c64<C>(a.sc[g].beta);
+        s.b = from_c64<C>(a.sc[g].omega);
+      } else {
+        s.a = from_c64<C>(a.sc[g].alpha);
+      }
+    }
+    s.a.x = __shfl_sync(0xffffffffu, s.a.x, 0);
+    s.a.y = __shfl_sync(0xffffffffu, s.a.y, 0);
+    s.b.x = __shfl_sync(0xffffffffu, s.b.x, 0);
+    s.b.y = __shfl_sync(0xffffffffu, s.b.y, 0);
+  } else if constexpr (IN == IN_PUPDATE) {
     s.a = from_c64<C>(a.sc[g].beta);
     s.b = from_c64<C>(a.sc[g].omega);
   } else if constexpr (IN == IN_SUPDATE) {
@@ -191,6 +215,26 @@ __device__ __forceinline__ double2 shfl_down_d2(double2 v, int o) {
   return make_double2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
 }
 
+// Sum of v over the warp as an unevaluated pair hi + lo of FP32 numbers (lane 0 holds it):
+// Knuth's TwoSum of the high parts at each level of the tree, the low parts and the rounding
+// error added, then Dekker's FastTwoSum renormalises. About 48 bits: the block's FP64
+// reduction receives the warp's sum without FP64 arithmetic in every warp.
+__device__ __forceinline__ float2 warp_sum_pair(float v) {
+  float hi = v, lo = 0.0f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+    const float s = __fadd_rn(hi, h2);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(h2, bp));
+    const float t = __fadd_rn(__fadd_rn(lo, l2), e);
+    hi = __fadd_rn(s, t);
+    lo = __fsub_rn(t, __fsub_rn(hi, s));
+  }
+  return make_float2(hi, lo);
+}
+
 // Deterministic block reduction of the (up to three) dot products; thread 0 writes
 // dst[k * stride] for every requested k. Needs 3 * 32 double2 of shared scratch.
 template <typename C>
@@ -200,10 +244,18 @@ __device__ __forceinline__ void block_write_dots(const Dots<C>& dt, int mask, do
 #pragma unroll
   for (int k = 0; k < NDOT; ++k) {
     if (!(mask & (1 << k))) continue;
-    double2 v = as_c64(dt.d[k]);
+    if constexpr (sizeof(C) == sizeof(float2)) {
+      // FP32 partial sums: the warp adds them as FP32 pairs (about 48 bits) and one lane
+      // converts the pair, so that no warp runs an FP64 reduction tree on the slow FP64 pipe
+      const float2 re = warp_sum_pair(dt.d[k].x), im = warp_sum_pair(dt.d[k].y);
+      if (lane == 0)
+        scratch[k * 32 + warp] = make_double2((double)re.x + (double)re.y, (double)im.x + (double)im.y);
+    } else {
+      double2 v = as_c64(dt.d[k]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = cadd(v, shfl_down_d2(v, o));
-    if (lane == 0) scratch[k * 32 + warp] = v;
+      for (int o = 16; o > 0; o >>= 1) v = cadd(v, shfl_down_d2(v, o));
+      if (lane == 0) scratch[k * 32 + warp] = v;
+    }
   }
   __syncthreads();
   if (warp == 0) {
@@ -248,8 +300,8 @@ __global__ void __launch_bounds__(NT) k_plane_fwd(OpCall<C> a) {
   const int p = blockIdx.x, c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
-  for (int i = threadIdx.x; i < NX; i += NT) twx[i] = from_c64<C>(a.twx[i]);
-  for (int i = threadIdx.x; i < NY; i += NT) twy[i] = from_c64<C>(a.twy[i]);
+  for (int i = threadIdx.x; i < NX; i += NT) twx[i] = twid<C>(a.twx, a.twx32, i);
+  for (int i = threadIdx.x; i < NY; i += NT) twy[i] = twid<C>(a.twy, a.twy32, i);
   const InScal<C> s = load_in_scalars<C, IN>(a, g);
   const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
   const C* Vp = a.V + ((size_t)a.rhsp[g].clip * a.nslab + p) * (NX * NY);
@@ -273,8 +325,8 @@ __global__ void __launch_bounds__(NT) k_plane_inv(OpCall<C> a, const C* uin) {
   const int p = blockIdx.x, c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
-  for (int i = threadIdx.x; i < NX; i += NT) twx[i] = from_c64<C>(a.twx[i]);
-  for (int i = threadIdx.x; i < NY; i += NT) twy[i] = from_c64<C>(a.twy[i]);
+  for (int i = threadIdx.x; i < NX; i += NT) twx[i] = twid<C>(a.twx, a.twx32, i);
+  for (int i = threadIdx.x; i < NY; i += NT) twy[i] = twid<C>(a.twy, a.twy32, i);
   const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
   for (int i = threadIdx.x; i < NX * NY; i += NT) tile[plane_slot<NX>(i)] = a.work[plane + i];
   __syncthreads();
@@ -370,10 +422,10 @@ __global__ void __launch_bounds__(NT, 2) k_half_fwd(OpCall<C> a) {
     if (a.pf && threadIdx.x == 0) half_prefetch<C, NX, NY, IN, false>(a, nullptr);
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
-  for (int i = threadIdx.x; i < NX; i += NT) twx[i] = from_c64<C>(a.twx[i]);
+  for (int i = threadIdx.x; i < NX; i += NT) twx[i] = twid<C>(a.twx, a.twx32, i);
   for (int i = threadIdx.x; i < H; i += NT) {
-    twy[i] = from_c64<C>(a.twy[i]);
-    twh[i] = from_c64<C>(a.twy[2 * i]);
+    twy[i] = twid<C>(a.twy, a.twy32, i);
+    twh[i] = twid<C>(a.twy, a.twy32, 2 * i);
   }
   __syncthreads();
   const InScal<C> s = load_in_scalars<C, IN>(a, g);
@@ -426,10 +478,10 @@ __global__ void __launch_bounds__(NT, 2) k_half_inv(OpCall<C> a, const C* uin) {
   if (a.pf && threadIdx.x == 0) half_prefetch<C, NX, NY, IN_PLAIN, true>(a, uin);
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
-  for (int i = threadIdx.x; i < NX; i += NT) twx[i] = from_c64<C>(a.twx[i]);
+  for (int i = threadIdx.x; i < NX; i += NT) twx[i] = twid<C>(a.twx, a.twx32, i);
   for (int i = threadIdx.x; i < H; i += NT) {
-    twy[i] = from_c64<C>(a.twy[i]);
-    twh[i] = from_c64<C>(a.twy[2 * i]);
+    twy[i] = twid<C>(a.twy, a.twy32, i);
+    twh[i] = twid<C>(a.twy, a.twy32, 2 * i);
   }
   __syncthreads();
   const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
@@ -505,7 +557,7 @@ __global__ void __launch_bounds__(NT, split_min_blocks<C, NX>()) k_rows_fwd(OpCa
   const int c = blockIdx.x % 3, lr = blockIdx.x / 3, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
-  for (int i = threadIdx.x; i < NX; i += NT) tw[i] = from_c64<C>(a.twx[i]);
+  for (int i = threadIdx.x; i < NX; i += NT) tw[i] = twid<C>(a.twx, a.twx32, i);
   const InScal<C> s = load_in_scalars<C, IN>(a, g);
   const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
   const C* Vp = a.V + (((size_t)a.rhsp[g].clip * a.nslab + p) * a.ny + y0) * NX;
@@ -528,7 +580,7 @@ __global__ void __launch_bounds__(NT, split_min_blocks<C, NX>()) k_rows_inv(OpCa
   const int c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
-  for (int i = threadIdx.x; i < NX; i += NT) tw[i] = from_c64<C>(a.twx[i]);
+  for (int i = threadIdx.x; i < NX; i += NT) tw[i] = twid<C>(a.twx, a.twx32, i);
   const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
   for (int i = threadIdx.x; i < rb * NX; i += NT) tile[(i / NX) * RP + fpad(i % NX)] = a.work[base + i];
   __syncthreads();
@@ -556,7 +608,7 @@ __global__ void __launch_bounds__(NT, split_min_blocks<C, NY>()) k_cols(OpCall<C
   const int c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
-  for (int i = threadIdx.x; i < NY; i += NT) tw[i] = from_c64<C>(a.twy[i]);
+  for (int i = threadIdx.x; i < NY; i += NT) tw[i] = twid<C>(a.twy, a.twy32, i);
   const size_t base = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)NY * a.nx + x0;
   const int t0 = threadIdx.x % tx, y0 = threadIdx.x / tx, ystep = NT / tx;
   for (int y = y0; y < NY; y += ystep) tile[t0 * PITCH + fpad(y)] = a.work[base + (size_t)y * a.nx + t0];
@@ -580,29 +632,39 @@ __global__ void __launch_bounds__(NT, split_min_blocks<C, NY>()) k_cols(OpCall<C
 // stays accurate in FP32 when beta ~ kappa. S and E depend on l only through kappa and
 // the parity of l, so one evaluation serves l and nf - l.
 template <typename C>
-__device__ __forceinline__ void green_scalars(typename RealOf<C>::T kh, typename RealOf<C>::T kl, C bh, C bl, C E,
-                                              typename RealOf<C>::T L, typename RealOf<C>::T cinv,
-                                              typename RealOf<C>::T scale, C& S, C& Es) {
+__device__ __forceinline__ bool green_scalars_far(typename RealOf<C>::T kh, typename RealOf<C>::T kl, C bh, C bl,
+                                                  C E, typename RealOf<C>::T L, typename RealOf<C>::T cinv,
+                                                  typename RealOf<C>::T scale, C& S, C& Es) {
   using R = typename RealOf<C>::T;
   const C d = mk((bh.x - kh) + (bl.x - kl), bh.y + bl.y);
   const C kpb = mk((kh + bh.x) + (kl + bl.x), bh.y + bl.y);
   const C w = mk(-d.y * L, d.x * L);
-  if (w.x * w.x + w.y * w.y < (R)0.25) {
-    // phi1(w) = 1 + w/2 (1 + w/3 (1 + ...)), Horner from the innermost term
-    C phi = mk((R)1, (R)0);
+  if (w.x * w.x + w.y * w.y < (R)0.25) return false;  // near: green_scalars_near
+  S = cscale(cdiv_fast(mk(E.x - (R)1, E.y), cmul(d, kpb)), scale);
+  Es = cscale(E, cinv * scale);
+  return true;
+}
+// The same scalars for |delta L| < 1/2, through phi1's Taylor series.
+template <typename C>
+__device__ __forceinline__ void green_scalars_near(typename RealOf<C>::T kh, typename RealOf<C>::T kl, C bh, C bl,
+                                                   C E, typename RealOf<C>::T L, typename RealOf<C>::T cinv,
+                                                   typename RealOf<C>::T scale, C& S, C& Es) {
+  using R = typename RealOf<C>::T;
+  const C d = mk((bh.x - kh) + (bl.x - kl), bh.y + bl.y);
+  const C kpb = mk((kh + bh.x) + (kl + bl.x), bh.y + bl.y);
+  const C w = mk(-d.y * L, d.x * L);
+  // phi1(w) = 1 + w/2 (1 + w/3 (1 + ...)), Horner from the innermost term
+  C phi = mk((R)1, (R)0);
 #pragma unroll
-    for (int k = Prec<C>::PHI_TERMS; k >= 2; --k) {
-      const R ik = (R)1 / (R)k;
-      const C t = cmul(w, phi);
-      phi = mk((R)1 + t.x * ik, t.y * ik);
-    }
-    S = cdiv_fast(mk(-phi.y * L, phi.x * L), kpb);  // i L phi1 / (kappa + beta)
-  } else {
-    S = cdiv_fast(mk(E.x - (R)1, E.y), cmul(d, kpb));
+  for (int k = Prec<C>::PHI_TERMS; k >= 2; --k) {
+    const R ik = (R)1 / (R)k;
+    const C t = cmul(w, phi);
+    phi = mk((R)1 + t.x * ik, t.y * ik);
   }
-  S = cscale(S, scale);
+  S = cscale(cdiv_fast(mk(-phi.y * L, phi.x * L), kpb), scale);  // i L phi1 / (kappa + beta)
   Es = cscale(E, cinv * scale);
 }
+
 
 // W = S (J - k (k.J) / kb^2) - (E / kb^2) z (z.J) for k = (qx, qy, kz), in place.
 template <typename C>
@@ -678,7 +740,12 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
   constexpr bool F32 = sizeof(C) == sizeof(float2);
   constexpr bool REG = zcol_reg<C, NF>();
   constexpr bool R10 = zcol_r10<C, NF>();
-  constexpr int P = zcol_pitch(NF, F32 && REG);  // column pitch; element z of a column at fpad(z)
+  constexpr int P = zcol_pitch(NF, F32 && REG);  // column pitch; spectral element z at spos(z)
+  // The FP32 register transform keeps the spectrum unpadded: every access to it is a run of
+  // consecutive elements (16 of them, 128 bytes, cover the 32 banks once at any alignment),
+  // while padded runs straddle pad slots and conflict. The other paths keep fpad's layout.
+  constexpr bool SPAD = !(REG && F32);
+  auto spos = [](int z) { return SPAD ? fpad(z) : z; };
   C* col = reinterpret_cast<C*>(smem);
   C* tw = col + 3 * tx * P;
   R* kh = reinterpret_cast<R*>(tw + NF);
@@ -691,18 +758,47 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
   C* ce8 = ce1 + tx;                          // exp(i beta 8 dz)
   C* R0 = ce8 + tx;                           // 3 tx: T_R E(plane 0)
   C* ptab = R0 + 3 * tx;                      // tx phase_entries<NF>(): exp(i beta dz j)
-  R* cqx = reinterpret_cast<R*>(ptab + tx * phase_pitch<NF>());
+  C* crs = ptab + tx * phase_pitch<NF>();     // FP32: r_s, r_p and beta / kb per column
+  C* crp = crs + tx;
+  C* cbq = crp + tx;
+  R* cqx = reinterpret_cast<R*>(cbq + tx);
   R* cqy = cqx + tx;
+  R* chx = cqy + tx;                           // FP32: unit transverse direction and |q| / kb
+  R* chy = chx + tx;
+  R* cqn = chy + tx;
+  int* near = reinterpret_cast<int*>(cqn + tx);  // per column: the l of phi1's series, or -1
 
   const int x0 = blockIdx.x * tx, y = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
+  const int slot = a.rhsp[g].slot;  // loaded together with the activity flag
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
   const int nx = a.nx, ny = a.ny, ns = a.nslab;
-  const int slot = a.rhsp[g].slot;
   const size_t mbase = ((size_t)slot * ny + y) * nx + x0;
+  const size_t pstride = (size_t)ny * nx;
+  constexpr int N2 = NF / 16, R1 = N2 > 0 ? 16 / N2 : 1;
+  const int rf = threadIdx.x / (N2 > 0 ? N2 : 1), rj = threadIdx.x % (N2 > 0 ? N2 : 1);
+  const bool rvalid = REG && rf < 3 * tx;
+  // Register transform: lane rj of the group of column rf holds planes rj + N2 k (k < 8, the
+  // nonzero half: ns + 1 <= NF/2), read straight from HBM. In FP32 the loads are issued
+  // before the tables below are set up, so that their latency overlaps that work.
+  C v[16];
+  auto load_column = [&]() {
+    if (rvalid) {
+      const int cc = rf / tx, t = rf % tx;
+      const C* src = a.work + ((size_t)lr * 3 + cc) * ns * pstride + (size_t)y * nx + x0 + t;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int n = rj + N2 * k;
+        v[k] = (n >= 1 && n <= ns) ? src[(size_t)(n - 1) * pstride] : mk((R)0, (R)0);
+      }
+#pragma unroll
+      for (int k = 8; k < 16; ++k) v[k] = mk((R)0, (R)0);
+    }
+  };
+  if constexpr (REG && F32) load_column();
 
   for (int i = threadIdx.x; i < NF; i += NT) {
-    tw[i] = from_c64<C>(a.twz[i]);
+    tw[i] = twid<C>(a.twz, a.twz32, i);
     if constexpr (F32) {
       kh[i] = a.ktab32[i];
       kl[i] = a.ktab32[NF + i];
@@ -725,6 +821,12 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
       ce8[t] = m.e8;
       cqx[t] = m.qx;
       cqy[t] = m.qy;
+      crs[t] = m.rs;
+      crp[t] = m.rp;
+      cbq[t] = m.bq;
+      chx[t] = m.hx;
+      chy[t] = m.hy;
+      cqn[t] = m.qnk;
     } else {
       const RhsParam& rp = a.rhsp[g];
       const double qx64 = rp.qix + two_pi * (double)fft_freq(x0 + t, nx) / ((double)nx * a.dx);
@@ -737,31 +839,18 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
       cqx[t] = (R)qx64;
       cqy[t] = (R)qy64;
     }
+    near[t] = -1;
   }
   constexpr int HF = NF / 2;
   // thread -> (column t0, planes p0, p0 + pstep, ...): no divisions inside the copy loops
   const int t0 = threadIdx.x % tx, p0 = threadIdx.x / tx, pstep = NT / tx;
-  const size_t pstride = (size_t)ny * nx;
   C* gcol = a.work + (size_t)lr * 3 * ns * pstride + (size_t)y * nx + x0 + t0;
-  constexpr int N2 = NF / 16, R1 = N2 > 0 ? 16 / N2 : 1;
   constexpr int EP = 16 * (N2 + 1) <= P ? N2 + 1 : N2;  // exchange row pitch
-  const int rf = threadIdx.x / (N2 > 0 ? N2 : 1), rj = threadIdx.x % (N2 > 0 ? N2 : 1);
-  const bool rvalid = REG && rf < 3 * tx;
   C* rex = col + (rvalid ? rf : 0) * P;  // the group's column: exchange scratch, then spectrum
   if constexpr (REG) {
-    // planes j + N2 k (k < 8, the nonzero half: ns + 1 <= NF/2) straight from HBM
+    if constexpr (!F32) load_column();
     __syncthreads();  // twiddles
-    C v[16];
     if (rvalid) {
-      const int cc = rf / tx, t = rf % tx;
-      const C* src = a.work + (size_t)lr * 3 * ns * pstride + (size_t)cc * ns * pstride + (size_t)y * nx + x0 + t;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int n = rj + N2 * k;
-        v[k] = (n >= 1 && n <= ns) ? src[(size_t)(n - 1) * pstride] : mk((R)0, (R)0);
-      }
-#pragma unroll
-      for (int k = 8; k < 16; ++k) v[k] = mk((R)0, (R)0);
       reg_fft_step1<C, NF, false, true>(v, rj, tw);
 #pragma unroll
       for (int k1 = 0; k1 < 16; ++k1) rex[k1 * EP + rj] = v[k1];
@@ -774,7 +863,7 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
 #pragma unroll
       for (int r = 0; r < R1; ++r)
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) rex[fpad(rj + N2 * r + 16 * k2)] = o[r * N2 + k2];
+        for (int k2 = 0; k2 < N2; ++k2) rex[spos(rj + N2 * r + 16 * k2)] = o[r * N2 + k2];
     }
   } else if constexpr (R10) {
     __syncthreads();  // twiddles
@@ -829,8 +918,15 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
   __syncthreads();
 
   // constants in the working precision (no FP64 arithmetic in the FP32 kernel)
-  const R L = (R)0.5 * (R)NF * (R)a.dz;
-  const R kbr = (R)a.kb;
+  R dzr, kbr;  // FP32: rounded on the host (no FP64 conversion in every thread)
+  if constexpr (F32) {
+    dzr = a.dz32;
+    kbr = a.kb32;
+  } else {
+    dzr = a.dz;
+    kbr = a.kb;
+  }
+  const R L = (R)0.5 * (R)NF * dzr;
   const R cinv = (R)1 / (kbr * kbr);
   const R scale = (R)1 / ((R)NF * (R)nx * (R)ny);
   const bool sph = F32 ? a.sph32 != nullptr : a.sph64 != nullptr;
@@ -851,32 +947,47 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
       C* c0 = col + (0 * tx + t) * P;
       C* c1 = col + (1 * tx + t) * P;
       C* c2 = col + (2 * tx + t) * P;
-      dyadic_sph(c0 + fpad(l), c1 + fpad(l), c2 + fpad(l), cqx[t], cqy[t], kzs[l], A, Bt);
+      dyadic_sph(c0 + spos(l), c1 + spos(l), c2 + spos(l), cqx[t], cqy[t], kzs[l], A, Bt);
       if (l > 0 && l < HF)
-        dyadic_sph(c0 + fpad(NF - l), c1 + fpad(NF - l), c2 + fpad(NF - l), cqx[t], cqy[t], kzs[NF - l], A, Bt);
+        dyadic_sph(c0 + spos(NF - l), c1 + spos(NF - l), c2 + spos(NF - l), cqx[t], cqy[t], kzs[NF - l], A, Bt);
     }
   }
-  // pairs (l, nf - l) share S and E; l = 0 stands alone, l = nf/2 follows below
-  for (int i = threadIdx.x; i < (sph ? 0 : tx * HF); i += NT) {
-    const int t = i / HF, l = i % HF;
-    C E = cebl[t];
-    if (l & 1) E = cneg(E);
-    C S, Es;
-    green_scalars(kh[l], kl[l], cb_h[t], cb_l[t], E, L, cinv, scale, S, Es);
+  // Pairs (l, nf - l) share S and E; l = 0 and l = nf/2 stand alone. Of each column's
+  // l = 0 .. nf/2 at most one lies near the removable singularity (|delta L| < 1/2 needs
+  // |Re(beta) L - pi l| < 1/2, and consecutive l are pi apart): the loop leaves it to the
+  // pass after it, so that its warps do not diverge on phi1's series.
+  constexpr int HL = HF + 1;
+  auto apply_l = [&](int t, int l, C S, C Es) {
     const R qx = cqx[t], qy = cqy[t];
     C* c0 = col + (0 * tx + t) * P;
     C* c1 = col + (1 * tx + t) * P;
     C* c2 = col + (2 * tx + t) * P;
-    dyadic_apply(c0 + fpad(l), c1 + fpad(l), c2 + fpad(l), qx, qy, kzs[l], S, Es, cinv);
-    if (l) dyadic_apply(c0 + fpad(NF - l), c1 + fpad(NF - l), c2 + fpad(NF - l), qx, qy, kzs[NF - l], S, Es, cinv);
-  }
-  for (int t = threadIdx.x; t < (sph ? 0 : tx); t += NT) {
+    dyadic_apply(c0 + spos(l), c1 + spos(l), c2 + spos(l), qx, qy, kzs[l], S, Es, cinv);
+    if (l > 0 && l < HF)
+      dyadic_apply(c0 + spos(NF - l), c1 + spos(NF - l), c2 + spos(NF - l), qx, qy, kzs[NF - l], S, Es, cinv);
+  };
+  for (int i = threadIdx.x; i < (sph ? 0 : tx * HL); i += NT) {
+    // items (t, l < nf/2) in order, then (t, nf/2): a half-warp's l stay in one column
+    const bool tail = i >= tx * HF;
+    const int t = tail ? i - tx * HF : i / HF, l = tail ? HF : i % HF;
     C E = cebl[t];
-    if (HF & 1) E = cneg(E);
+    if (l & 1) E = cneg(E);
     C S, Es;
-    green_scalars(kh[HF], kl[HF], cb_h[t], cb_l[t], E, L, cinv, scale, S, Es);
-    dyadic_apply(col + (0 * tx + t) * P + fpad(HF), col + (1 * tx + t) * P + fpad(HF),
-                 col + (2 * tx + t) * P + fpad(HF), cqx[t], cqy[t], kzs[HF], S, Es, cinv);
+    if (!green_scalars_far(kh[l], kl[l], cb_h[t], cb_l[t], E, L, cinv, scale, S, Es)) {
+      near[t] = l;
+      continue;
+    }
+    apply_l(t, l, S, Es);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < (sph ? 0 : tx); t += NT) {
+    const int l = near[t];
+    if (l < 0) continue;
+    C E = cebl[t];
+    if (l & 1) E = cneg(E);
+    C S, Es;
+    green_scalars_near(kh[l], kl[l], cb_h[t], cb_l[t], E, L, cinv, scale, S, Es);
+    apply_l(t, l, S, Es);
   }
   __syncthreads();
   // FP32 register transform: the output leaves from the registers (below); in FP64 the
@@ -887,7 +998,7 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
     C v[16];
     if (rvalid) {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = rex[fpad(rj + N2 * k)];
+      for (int k = 0; k < 16; ++k) v[k] = rex[spos(rj + N2 * k)];
     }
     __syncwarp();
     if (rvalid) {
@@ -904,7 +1015,7 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
           const int n = rj + N2 * r + 16 * k2;
-          if (REG_OUT ? (n == 0 || n == ns + 1) : n <= HF) rex[fpad(n)] = o[r * N2 + k2];
+          if (REG_OUT ? (n == 0 || n == ns + 1) : n <= HF) rex[spos(n)] = o[r * N2 + k2];
         }
     }
   } else if constexpr (R10) {
@@ -948,23 +1059,24 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
       const int cc = i / tx, t = i % tx;
       const size_t o = (((size_t)g * 2) * 3 + cc) * ny * nx + (size_t)y * nx + x0 + t;
       a.side[o] = col[(cc * tx + t) * P];
-      a.side[o + (size_t)3 * ny * nx] = col[(cc * tx + t) * P + fpad(ns + 1)];
+      a.side[o + (size_t)3 * ny * nx] = col[(cc * tx + t) * P + spos(ns + 1)];
     }
   }
   // stack reflection of the downgoing field on plane 0: R0 = T_R E0 (Eq. (9)),
   // T_R = r_s s s^T + r_p p+ p-^T with s = z x q/|q|, p+- = (-+beta qhat, |q|)/kb.
   for (int t = threadIdx.x; t < tx; t += NT) {
-    if constexpr (F32) {
-      const ModeF32 m = a.modes32[mbase + t];
+    if constexpr (F32) {  // the column's mode constants were staged in shared memory
+      const float hx = chx[t], hy = chy[t], qnk = cqn[t];
+      const float2 bq = cbq[t];
       const float2 e0 = col[(0 * tx + t) * P], e1 = col[(1 * tx + t) * P], e2 = col[(2 * tx + t) * P];
-      const float2 sE = mk(-m.hy * e0.x + m.hx * e1.x, -m.hy * e0.y + m.hx * e1.y);
-      const float2 tq = cadd(cscale(e0, m.hx), cscale(e1, m.hy));
-      const float2 pmE = cadd(cmul(m.bq, tq), cscale(e2, m.qnk));
-      const float2 as = cmul(m.rs, sE), ap = cmul(m.rp, pmE);
-      const float2 apb = cmul(ap, m.bq);
-      R0[0 * tx + t] = csub(cscale(as, -m.hy), cscale(apb, m.hx));
-      R0[1 * tx + t] = csub(cscale(as, m.hx), cscale(apb, m.hy));
-      R0[2 * tx + t] = cscale(ap, m.qnk);
+      const float2 sE = mk(-hy * e0.x + hx * e1.x, -hy * e0.y + hx * e1.y);
+      const float2 tq = cadd(cscale(e0, hx), cscale(e1, hy));
+      const float2 pmE = cadd(cmul(bq, tq), cscale(e2, qnk));
+      const float2 as = cmul(crs[t], sE), ap = cmul(crp[t], pmE);
+      const float2 apb = cmul(ap, bq);
+      R0[0 * tx + t] = csub(cscale(as, -hy), cscale(apb, hx));
+      R0[1 * tx + t] = csub(cscale(as, hx), cscale(apb, hy));
+      R0[2 * tx + t] = cscale(ap, qnk);
       continue;
     }
     const int x = x0 + t;
@@ -1014,23 +1126,28 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
   const bool reflect = !a.no_reflect;  // the free-space operator adds no reflection
   if constexpr (REG_OUT) {
     // straight from the registers: plane pl = n - 1 gets R0 exp(i beta pl dz); a warp's four
-    // columns are consecutive x-modes, so each plane is written as one 32- (64-) byte run
+    // columns are consecutive x-modes, so each plane is written as one 32- (64-) byte run.
+    // The planes of one r share pl mod 16 = jm, so R0 exp(i beta jm dz) is formed once and
+    // each plane multiplies it by exp(i beta 16 dz (pl >> 4)) (coarse entry 2 (pl >> 4)).
     if (rvalid) {
       const int cc = rf / tx, t = rf % tx;
-      const C r0 = R0[cc * tx + t];
+      const C* pt = ptab + t * PP;
       C* dst = a.work + ((size_t)lr * 3 + cc) * ns * pstride + (size_t)y * nx + x0 + t;
 #pragma unroll
-      for (int r = 0; r < R1; ++r)
+      for (int r = 0; r < R1; ++r) {
+        const int jm = (rj + N2 * r + 15) & 15;
+        const C rb = reflect ? cmul(R0[cc * tx + t], cmul(pt[jm & 7], pt[8 + (jm >> 3)])) : mk((R)0, (R)0);
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
           const int n = rj + N2 * r + 16 * k2;
           if (n >= 1 && n <= ns) {
             const int pl = n - 1;
             C val = o[r * N2 + k2];
-            if (reflect) val = cadd(val, cmul(r0, cmul(ptab[t * PP + (pl & 7)], ptab[t * PP + 8 + (pl >> 3)])));
+            if (reflect) val = cadd(val, cmul(rb, pt[8 + 2 * (pl >> 4)]));
             dst[(size_t)pl * pstride] = val;
           }
         }
+      }
     }
   } else {
     const int pl_end = reflect ? ns : 0;

@@ -177,7 +177,7 @@ inline size_t zcol_smem_bytes(int nf, int tx) {
   const int pe = (8 + (nf + 15) / 16) | 1;  // phase_pitch
   const bool f32reg = sizeof(C) == sizeof(float2) && (nf == 64 || nf == 128 || nf == 256);  // zcol_reg
   return (size_t)(3 * tx * zcol_pitch(nf, f32reg) + nf) * sizeof(C) + 3 * (size_t)nf * sizeof(R) +
-         (size_t)(8 + pe) * tx * sizeof(C) + 2 * (size_t)tx * sizeof(R) + 16;
+         (size_t)(11 + pe) * tx * sizeof(C) + 5 * (size_t)tx * sizeof(R) + (size_t)tx * sizeof(int) + 16;
 }
 template <typename C>
 inline int zcol_tile(int nx, int nf) {

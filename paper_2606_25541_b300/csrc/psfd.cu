@@ -164,6 +164,9 @@ int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs
   A(&ctx->twx, grid->nx);
   A(&ctx->twy, grid->ny);
   A(&ctx->twz, grid->nf);
+  A(&ctx->twx32, grid->nx);
+  A(&ctx->twy32, grid->ny);
+  A(&ctx->twz32, grid->nf);
   A(&ctx->rhsp, R);
   A(&ctx->slot_par, 4 * R);
   A(&ctx->modes, R * P.plane);
@@ -233,6 +236,19 @@ int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs
   cudaError_t e = cudaMemcpy(ctx->twx, tx.data(), tx.size() * 16, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ctx->twy, ty.data(), ty.size() * 16, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ctx->twz, tz.data(), tz.size() * 16, cudaMemcpyHostToDevice);
+  {
+    // FP32 copies for the FP32 kernels: each entry rounded to nearest, the value those kernels
+    // would get by converting the FP64 entry themselves
+    auto f32 = [](const std::vector<double2>& t) {
+      std::vector<float2> r(t.size());
+      for (size_t i = 0; i < t.size(); ++i) r[i] = make_float2((float)t[i].x, (float)t[i].y);
+      return r;
+    };
+    const auto fx = f32(tx), fy = f32(ty), fz = f32(tz);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->twx32, fx.data(), fx.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->twy32, fy.data(), fy.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->twz32, fz.data(), fz.size() * 8, cudaMemcpyHostToDevice);
+  }
   {
     // signed z wavenumbers kz_l = 2 pi l / (nf dz), and |kz_l| split into FP32 hi + lo
     std::vector<float> k32(3 * (size_t)grid->nf);
@@ -418,10 +434,15 @@ static OpCall<C> base_call(psfd_ctx* ctx, int rhs0, int nrhs, const C* V) {
   a.dy = ctx->g.dy;
   a.dz = ctx->g.dz;
   a.kb = ctx->kb;
+  a.dz32 = (float)ctx->g.dz;
+  a.kb32 = (float)ctx->kb;
   a.V = V;
   a.twx = ctx->twx;
   a.twy = ctx->twy;
   a.twz = ctx->twz;
+  a.twx32 = ctx->twx32;
+  a.twy32 = ctx->twy32;
+  a.twz32 = ctx->twz32;
   a.rhsp = ctx->rhsp;
   a.modes = ctx->modes;
   a.modes32 = ctx->modes32;

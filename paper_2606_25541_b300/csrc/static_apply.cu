@@ -50,11 +50,12 @@ int scratch_base(void** out) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-__global__ void k_static_twiddles(double2* tw, int n) {
+__global__ void k_static_twiddles(double2* tw, float2* tw32, int n) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     double s, c;
     sincospi(-2.0 * (double)t / (double)n, &s, &c);
     tw[t] = make_double2(c, s);
+    tw32[t] = make_float2((float)c, (float)s);
   }
 }
 
@@ -115,6 +116,9 @@ extern "C" int psfd_apply_fp32_static(const psfd_grid* g, int n_layers, const do
   const size_t o_twx = off; off = align256(off + g->nx * sizeof(double2));
   const size_t o_twy = off; off = align256(off + g->ny * sizeof(double2));
   const size_t o_twz = off; off = align256(off + g->nf * sizeof(double2));
+  const size_t o_twx32 = off; off = align256(off + g->nx * sizeof(float2));
+  const size_t o_twy32 = off; off = align256(off + g->ny * sizeof(float2));
+  const size_t o_twz32 = off; off = align256(off + g->nf * sizeof(float2));
   const size_t o_rhs = off; off = align256(off + sizeof(RhsParam));
   const size_t o_sq = off; off = align256(off + 4 * sizeof(double));
   const size_t o_k32 = off; off = align256(off + 3 * (size_t)g->nf * sizeof(float));
@@ -179,9 +183,12 @@ extern "C" int psfd_apply_fp32_static(const psfd_grid* g, int n_layers, const do
   double2* twx = reinterpret_cast<double2*>(base + o_twx);
   double2* twy = reinterpret_cast<double2*>(base + o_twy);
   double2* twz = reinterpret_cast<double2*>(base + o_twz);
-  k_static_twiddles<<<4, 256, 0, st>>>(twx, g->nx);
-  k_static_twiddles<<<4, 256, 0, st>>>(twy, g->ny);
-  k_static_twiddles<<<4, 256, 0, st>>>(twz, g->nf);
+  float2* twx32 = reinterpret_cast<float2*>(base + o_twx32);
+  float2* twy32 = reinterpret_cast<float2*>(base + o_twy32);
+  float2* twz32 = reinterpret_cast<float2*>(base + o_twz32);
+  k_static_twiddles<<<4, 256, 0, st>>>(twx, twx32, g->nx);
+  k_static_twiddles<<<4, 256, 0, st>>>(twy, twy32, g->ny);
+  k_static_twiddles<<<4, 256, 0, st>>>(twz, twz32, g->nf);
   RhsParam* rhsp = reinterpret_cast<RhsParam*>(base + o_rhs);
   double* sq = reinterpret_cast<double*>(base + o_sq);
   k_static_params<<<1, 1, 0, st>>>(rhsp, sq, qix, qiy, std::cos(ph), std::sin(ph));
@@ -224,10 +231,15 @@ extern "C" int psfd_apply_fp32_static(const psfd_grid* g, int n_layers, const do
   a.dy = g->dy;
   a.dz = g->dz;
   a.kb = kb;
+  a.dz32 = (float)g->dz;
+  a.kb32 = (float)kb;
   a.V = V32;
   a.twx = twx;
   a.twy = twy;
   a.twz = twz;
+  a.twx32 = twx32;
+  a.twy32 = twy32;
+  a.twz32 = twz32;
   a.rhsp = rhsp;
   a.modes = modes;
   a.modes32 = m.modes32;

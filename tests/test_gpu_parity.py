@@ -408,13 +408,18 @@ def test_fixed_point_converges_to_the_folded_solution(psfd, precision):
 
 def test_sweeps_are_solved_only_as_far_as_the_target_needs(psfd, contact_hole_reference):
     """psfd_solve_opts.inner_tol: a sweep starting from FP64 residual rho is solved to
-    max(inner_tol, tol / (4 rho)). At the metric's 1e-6 order error one FP32 sweep to 2e-7
-    meets tol = 3e-7; a second sweep, when needed, asks only for what is left (its Krylov
-    estimates stop near tol / 4, not at inner_tol times its starting residual)."""
+    max(inner_tol, tol / (4 rho)). One FP32 sweep to 2e-7 leaves an FP64 residual of about
+    inner_tol plus the FP32 operator's rounding (2.2e-7 of G*(V u) on this clip), so at
+    tol = 3e-7 it lands within 2 inner_tol and a second sweep at most finishes the job; that
+    sweep asks only for what is left (its Krylov estimates stop near tol / 4, not at
+    inner_tol times its starting residual)."""
     prob, ref, _ = contact_hole_reference
     s = _solver(psfd, prob, psfd.FP32_REFINED)
     rep = s.solve(tol=3e-7, inner_tol=2e-7, max_iter=300, max_outer=10)
-    assert rep["outer"] == 1 and rep["relres"] <= 3e-7
+    assert rep["outer"] <= 2 and rep["relres"] <= 3e-7
+    h = s.residual_history(0)
+    first = h["relres"][h["kind"] == 1][1]  # FP64 residual after the first sweep
+    assert first <= 2 * 2e-7, first
     assert _orders_err(s.diffraction_orders(0), ref) < 1e-6
     rep = s.solve(tol=1e-9, inner_tol=1e-6, max_iter=300, max_outer=10)
     assert rep["relres"] <= 1e-9
