@@ -98,6 +98,9 @@ struct psfd_ctx {
   double* slot_par = nullptr;  // [rhs][4]: q_inc x, q_inc y, cos phi, sin phi
   psfd::ModeEntry* modes = nullptr;
   psfd::ModeF32* modes32 = nullptr;
+  psfd::ModeDF* modesdf = nullptr;  // double-float column constants of the residual's z pass
+  float4* twzdf = nullptr;          // z twiddles and kz_l as double-float pairs
+  float2* kzdf = nullptr;
   float* ktab32 = nullptr;
   double* ktab64 = nullptr;
   double2* d_eps_l = nullptr;
@@ -122,6 +125,7 @@ struct psfd_ctx {
   std::vector<double> h_tol;
   int* d_mask[4] = {nullptr, nullptr, nullptr, nullptr};  // per-phase selections
   int *d_nord = nullptr, *d_mn = nullptr;
+  int* d_slots = nullptr;  // the distinct table rows of an illumination set-up
   double* d_ordout = nullptr;
   double2* fp_b0 = nullptr;  // [max_rhs][U]: b = E_inc + R[E_inc] during a fixed-point solve (lazy)
   // isolated clip (psfd_set_green): spherically windowed kernel of radius green_R, tabulated

@@ -41,6 +41,20 @@ struct ModeF32 {
   float2 bq;        // beta / kb
 };
 
+// Double-float copy (unevaluated pairs hi + lo of FP32 numbers) of what the FP64 residual's
+// double-float z pass needs per mode, prepared by the FP64 stack kernel once per illumination
+// set-up, so that the pass itself runs no FP64 arithmetic. Complex values are float4
+// (re.hi, re.lo, im.hi, im.lo), reals float2 (hi, lo).
+struct ModeDF {
+  float4 beta, ebL;  // beta, exp(i beta L)
+  float4 e1, e8;     // exp(i beta dz), exp(i beta 8 dz)
+  float4 rs, rp;     // stack reflection coefficients
+  float4 bq;         // beta / kb
+  float2 qx, qy;     // transverse wavevector
+  float2 hx, hy;     // unit transverse direction (azimuth of the illumination at q = 0)
+  float2 qnk, pad;   // |q| / kb
+};
+
 // Krylov scalars per right-hand side (BiCGStab), all FP64.
 struct KScal {
   double2 rho, alpha, omega, beta;
@@ -91,6 +105,10 @@ struct OpCall {
   const RhsParam* rhsp;
   const ModeEntry* modes;
   const ModeF32* modes32;  // FP32 column constants (used by the FP32 z-column kernel)
+  const ModeDF* modesdf;   // double-float column constants (the residual's double-float z pass)
+  const float4* twzdf;     // [nf]: the z twiddles as double-float pairs
+  const float2* kzdf;      // [nf]: signed kz_l as double-float pairs
+  float2 dfL, dfcinv, dfscale;  // pairs of L = nf dz / 2, 1 / kb^2, 1 / (nf nx ny)
   const float* ktab32;     // [3][nf]: |kz_l| hi, |kz_l| lo, signed kz_l (FP32)
   const double* ktab64;    // [nf]: signed kz_l (FP64)
   const int* active;  // per global rhs, or null = all active

@@ -7,9 +7,11 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "ctx.h"
+#include "dfloat.cuh"
 #include "dfloat_ops.h"
 
 using namespace psfd;
@@ -93,8 +95,8 @@ Plan make_plan(const psfd_grid& g, int precision, int max_rhs, int max_clips) {
   b += p.plane * g.nslab * (Cl * (16 + 8) + 16);             // V64, V32 per clip, eps staging
   b += (size_t)(g.nx + g.ny + g.nf) * 16;                    // twiddles
   b += R * (sizeof(RhsParam) + 4 * sizeof(double));          // illumination parameters
-  b += R * p.plane * (sizeof(ModeEntry) + sizeof(ModeF32));  // mode tables (FP64 and FP32)
-  b += (size_t)g.nf * (3 * sizeof(float) + sizeof(double));  // kz tables
+  b += R * p.plane * (sizeof(ModeEntry) + sizeof(ModeF32) + sizeof(ModeDF));  // mode tables (FP64, FP32, pairs)
+  b += (size_t)g.nf * (3 * sizeof(float) + sizeof(double) + 16 + 8);  // kz tables, pair-format twiddles and kz
   b += R * p.U * 16 * 4;                                     // b64, x64, r64, work64
   b += R * 6 * p.plane * 16;                                 // side spectra
   const size_t kvec = precision == PSFD_FP64 ? 16 : 8;       // Krylov working precision
@@ -171,6 +173,9 @@ int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs
   A(&ctx->slot_par, 4 * R);
   A(&ctx->modes, R * P.plane);
   A(&ctx->modes32, R * P.plane);
+  A(&ctx->modesdf, R * P.plane);
+  A(&ctx->twzdf, grid->nf);
+  A(&ctx->kzdf, grid->nf);
   A(&ctx->ktab32, 3 * (size_t)grid->nf);
   A(&ctx->ktab64, grid->nf);
   A(&ctx->d_eps_l, kStackMaxLayers);
@@ -203,6 +208,7 @@ int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs
   A(&ctx->d_tol, R);
   for (int i = 0; i < 4; ++i) A(&ctx->d_mask[i], R);
   A(&ctx->d_nord, R);
+  A(&ctx->d_slots, R);
   A(&ctx->d_mn, R * (size_t)P.max_orders * 2);
   A(&ctx->d_ordout, R * (size_t)P.max_orders * 12);
   if (rc != PSFD_OK) {
@@ -264,6 +270,18 @@ int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs
     }
     if (e == cudaSuccess) e = cudaMemcpy(ctx->ktab32, k32.data(), sizeof(float) * k32.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(ctx->ktab64, k64.data(), sizeof(double) * k64.size(), cudaMemcpyHostToDevice);
+    // pair-format copies for the double-float z pass (the host conversion gives the same
+    // pairs as the device's integer-path conversion)
+    std::vector<float4> tdf(grid->nf);
+    std::vector<float2> kdf(grid->nf);
+    for (int l = 0; l < grid->nf; ++l) {
+      const dfc t = to_dfc(tz[l]);
+      tdf[l] = make_float4(t.x.hi, t.x.lo, t.y.hi, t.y.lo);
+      const dfr k = to_dfr(k64[l]);
+      kdf[l] = make_float2(k.hi, k.lo);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->twzdf, tdf.data(), sizeof(float4) * tdf.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->kzdf, kdf.data(), sizeof(float2) * kdf.size(), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = cudaMemset(ctx->sc, 0, sizeof(KScal) * R);
   if (e == cudaSuccess) e = cudaMemset(ctx->sc64, 0, sizeof(KScal) * R);
@@ -300,6 +318,8 @@ int ctx_set_rhs(psfd_ctx* ctx, int g0, int n, const double* theta_deg, const dou
     return ctx->fail(PSFD_E_ARG, "invalid illumination slots");
   const int M = ctx->plan.max_orders;
   std::vector<double> spar(4 * (size_t)n);
+  std::vector<int> slots;                  // the table rows this call computes
+  std::vector<std::pair<int, int>> dups;   // (row, row it is copied from)
   for (int i = 0; i < n; ++i) {
     if (!std::isfinite(theta_deg[i]) || !std::isfinite(phi_deg[i]) || (pol[i] != 0 && pol[i] != 1))
       return ctx->fail(PSFD_E_ARG, "invalid angle or polarisation");
@@ -313,6 +333,18 @@ int ctx_set_rhs(psfd_ctx* ctx, int g0, int n, const double* theta_deg, const dou
     p.pol = pol[i];
     p.slot = gi;
     p.clip = clip;
+    // The mode tables depend on the angles (and on the stack, common to the call), not on the
+    // polarisation: a row whose angles an earlier illumination of this call has is copied
+    // from that one's row instead of being computed again (the s and p illuminations of an
+    // angle run the FP64 stack recursion once).
+    int src = gi;
+    for (int j = 0; j < i; ++j)
+      if (theta_deg[j] == theta_deg[i] && phi_deg[j] == phi_deg[i]) {
+        src = g0 + j;
+        break;
+      }
+    if (src == gi) slots.push_back(gi);
+    else dups.push_back({gi, src});
     // propagating orders (|q| < k_bg) and the anomaly check, in FFT order (y outer, x inner)
     int cnt = 0;
     for (int y = 0; y < g.ny; ++y) {
@@ -378,8 +410,20 @@ int ctx_set_rhs(psfd_ctx* ctx, int g0, int n, const double* theta_deg, const dou
   }
   m.modes = ctx->modes;
   m.modes32 = ctx->modes32;
+  m.modesdf = ctx->modesdf;
   m.anomaly = ctx->anomaly;
-  RC(launch_modes(m, n, st));
+  m.slots = ctx->d_slots;
+  CK(cudaMemcpyAsync(ctx->d_slots, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice, st));
+  RC(launch_modes(m, (int)slots.size(), st));
+  const size_t pl = ctx->plan.plane;
+  for (const auto& d : dups) {
+    CK(cudaMemcpyAsync(ctx->modes + d.first * pl, ctx->modes + d.second * pl, sizeof(ModeEntry) * pl,
+                       cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->modes32 + d.first * pl, ctx->modes32 + d.second * pl, sizeof(ModeF32) * pl,
+                       cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->modesdf + d.first * pl, ctx->modesdf + d.second * pl, sizeof(ModeDF) * pl,
+                       cudaMemcpyDeviceToDevice, st));
+  }
   if (ctx->green == PSFD_GREEN_SPHERICAL) {
     SphArgs sa;
     sa.slot0 = g0;
@@ -446,6 +490,20 @@ static OpCall<C> base_call(psfd_ctx* ctx, int rhs0, int nrhs, const C* V) {
   a.rhsp = ctx->rhsp;
   a.modes = ctx->modes;
   a.modes32 = ctx->modes32;
+  a.modesdf = ctx->modesdf;
+  a.twzdf = ctx->twzdf;
+  a.kzdf = ctx->kzdf;
+  {
+    // the double-float z pass's constants, formed in FP64 and split once here
+    auto r2 = [](double v) {
+      const dfr d = to_dfr(v);
+      return make_float2(d.hi, d.lo);
+    };
+    const psfd_grid& g = ctx->g;
+    a.dfL = r2(0.5 * (double)g.nf * g.dz);
+    a.dfcinv = r2(1.0 / (ctx->kb * ctx->kb));
+    a.dfscale = r2(1.0 / ((double)g.nf * (double)g.nx * (double)g.ny));
+  }
   a.ktab32 = ctx->ktab32;
   a.ktab64 = ctx->ktab64;
   a.partials = ctx->partials;

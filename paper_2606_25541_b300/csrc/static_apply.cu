@@ -204,6 +204,7 @@ extern "C" int psfd_apply_fp32_static(const psfd_grid* g, int n_layers, const do
   ModeEntry* modes = reinterpret_cast<ModeEntry*>(base + o_modes);
   ModesArgs m;
   m.slot0 = 0;
+  m.slots = nullptr;
   m.nx = g->nx;
   m.ny = g->ny;
   m.dx = g->dx;
@@ -217,6 +218,7 @@ extern "C" int psfd_apply_fp32_static(const psfd_grid* g, int n_layers, const do
   m.stack = stack;
   m.modes = modes;
   m.modes32 = reinterpret_cast<ModeF32*>(base + o_m32);
+  m.modesdf = nullptr;
   m.anomaly = reinterpret_cast<int*>(base + o_anom);
   if ((rc = launch_modes(m, 1, st))) return rc;
 

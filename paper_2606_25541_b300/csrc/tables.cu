@@ -6,6 +6,7 @@
 #include "fft.cuh"
 #include "krylov.cuh"
 #include "tables.h"
+#include "dfloat.cuh"
 
 namespace psfd {
 
@@ -206,7 +207,8 @@ void stack_dedup(StackDev& st, const double2* eps_layers, const double* d_layers
 
 // grid (ceil(nx / 128), ny, n_slots)
 __global__ void k_modes(ModesArgs a) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, slot = a.slot0 + blockIdx.z;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  const int slot = a.slots ? a.slots[blockIdx.z] : a.slot0 + blockIdx.z;
   if (x >= a.nx) return;
   const double two_pi = 6.283185307179586476925286766559;
   const double* sp = a.slot_par + 4 * slot;
@@ -249,6 +251,33 @@ __global__ void k_modes(ModesArgs a) {
     f.pad = 0.f;
     f.bq = to_c32(cscale(beta, 1.0 / a.kb));
     a.modes32[idx] = f;
+  }
+  if (a.modesdf) {
+    // the same quantities as pairs, each converted once from its FP64 value
+    auto c4 = [](double2 v) {
+      const dfc d = to_dfc(v);
+      return make_float4(d.x.hi, d.x.lo, d.y.hi, d.y.lo);
+    };
+    auto r2 = [](double v) {
+      const dfr d = to_dfr(v);
+      return make_float2(d.hi, d.lo);
+    };
+    ModeDF f;
+    f.beta = c4(beta);
+    f.ebL = c4(m.ebL);
+    f.e1 = c4(cexp_d(make_double2(-beta.y * a.dz, beta.x * a.dz)));
+    f.e8 = c4(cexp_d(make_double2(-8.0 * beta.y * a.dz, 8.0 * beta.x * a.dz)));
+    f.rs = c4(m.rs);
+    f.rp = c4(m.rp);
+    f.bq = c4(cscale(beta, 1.0 / a.kb));
+    f.qx = r2(qx);
+    f.qy = r2(qy);
+    const double qn = sqrt(q2);
+    f.hx = r2(qn > 0.0 ? qx / qn : sp[2]);
+    f.hy = r2(qn > 0.0 ? qy / qn : sp[3]);
+    f.qnk = r2(qn / a.kb);
+    f.pad = make_float2(0.f, 0.f);
+    a.modesdf[idx] = f;
   }
 }
 
@@ -495,26 +524,66 @@ int launch_norm(int n, int nblk, int rhs0, int nrhs, const int* mask, const doub
   return launched();
 }
 
-// rs = r64 / ||r64|| in the Krylov precision (right-hand sides selected by act)
+// FP32 <-> FP64 of one value by integer operations (df_f32_rn / df_f64_of), falling back to
+// the conversion instruction outside their range: this GPU's FP64 pipe, which runs those
+// instructions, is far slower than its integer and FP32 pipes.
+__device__ __forceinline__ float f32_of(double d) {
+  float f;
+  return df_f32_rn(d, f) ? f : (float)d;
+}
+__device__ __forceinline__ double f64_of(float f) {
+  double d;
+  return df_f64_of(f, d) ? d : (double)f;
+}
+
+// rs = r64 / ||r64|| in the Krylov precision (right-hand sides selected by act). 1/||r64|| is
+// formed once per CTA. In FP32 each element is rounded to FP32 and scaled there (when the scale
+// is moderate, so that no element that matters leaves the FP32 range): no FP64 arithmetic per
+// element, against one FP64 scaling before the rounding otherwise.
 template <typename C>
 __global__ void k_ref_scale(int n, int rhs0, const int* act, const KScal* sc, const double2* r64, C* rs) {
   const int lr = blockIdx.y, g = rhs0 + lr;
   if (!act[g]) return;
-  const double inv = 1.0 / sqrt(sc[g].rnorm2);
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) s_inv = 1.0 / sqrt(sc[g].rnorm2);
+  __syncthreads();
+  const double inv = s_inv;
   const size_t off = (size_t)lr * n;
+  if constexpr (sizeof(C) == sizeof(float2)) {
+    if (inv > 0x1p-60 && inv < 0x1p60) {
+      const float fi = f32_of(inv);
+      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double2 r = r64[off + i];
+        rs[off + i] = make_float2(f32_of(r.x) * fi, f32_of(r.y) * fi);
+      }
+      return;
+    }
+  }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     rs[off + i] = from_c64<C>(cscale(r64[off + i], inv));
 }
 
-// x64 += ||r64|| xc
+// x64 += ||r64|| xc (the FP32 correction widened exactly by integer operations; ||r64|| once
+// per CTA)
 template <typename C>
 __global__ void k_ref_update(int n, int rhs0, const int* act, const KScal* sc, double2* x64, const C* xc) {
   const int lr = blockIdx.y, g = rhs0 + lr;
   if (!act[g]) return;
-  const double s = sqrt(sc[g].rnorm2);
+  __shared__ double s_s;
+  if (threadIdx.x == 0) s_s = sqrt(sc[g].rnorm2);
+  __syncthreads();
+  const double s = s_s;
   const size_t off = (size_t)lr * n;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    x64[off + i] = cadd(x64[off + i], cscale(as_c64(xc[off + i]), s));
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double2 d;
+    if constexpr (sizeof(C) == sizeof(float2)) {
+      const C v = xc[off + i];
+      d = make_double2(f64_of(v.x), f64_of(v.y));
+    } else {
+      d = xc[off + i];
+    }
+    x64[off + i] = cadd(x64[off + i], cscale(d, s));
+  }
 }
 
 __global__ void k_vec_add(int n, int rhs0, const int* mask, double2* a, const double2* b) {

@@ -36,12 +36,14 @@ void stack_dedup(StackDev& st, const double2* eps_layers, const double* d_layers
 
 struct ModesArgs {
   int slot0;  // first table row written (one launch covers rows slot0 .. slot0 + n_slots - 1)
+  const int* slots;  // or, when not null, the rows slots[0 .. n_slots - 1] (device)
   int nx, ny;
   double dx, dy, dz, k0, kb, eps_bg, L;
   const double* slot_par;  // [slot][4]: q_inc x, q_inc y, cos phi, sin phi
   StackDev stack;
   ModeEntry* modes;   // [slot][ny][nx]
   ModeF32* modes32;   // [slot][ny][nx] or null
+  ModeDF* modesdf;    // [slot][ny][nx] or null
   int* anomaly;
 };
 

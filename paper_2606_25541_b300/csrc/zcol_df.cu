@@ -12,8 +12,11 @@
 //     and the dyadic products in double-float (dfloat.cuh: ~48 significant bits);
 //   - the Green's scalars S_l, E_l in double-float too (the FP32 reciprocal refined by a
 //     Newton step; the same closed forms and series as the FP64 kernel);
-//   - the reflection T_R E(plane 0) and the per-column exponentials in FP64 (a few dozen
-//     FP64 operations per column, not per element);
+//   - the reflection T_R E(plane 0) in double-float, from per-mode pairs (beta, exp(i beta L),
+//     exp(i beta dz), exp(i beta 8 dz), r_s, r_p, q and its direction) that the FP64 stack
+//     kernel prepares once per illumination set-up: the pass itself runs no FP64 operation
+//     (this GPU's FP64 pipe is slow, and the per-column FP64 work ran in a few threads while
+//     the rest of the CTA waited at a barrier);
 //   - the reflection phase table by binary powering in double-float.
 // Columns of length 64 and 128 on the periodic (z-windowed) kernel; other lengths and the
 // isolated clip's spherical kernel stay on the FP64 k_zcol.
@@ -34,10 +37,10 @@ __host__ __device__ constexpr int df_pitch() { return fft_phys(NF) | 1; }
 template <int NF>
 size_t df_smem_bytes(int tx) {
   const size_t c16 = (size_t)3 * tx * df_pitch<NF>() + NF + 3 * tx + (size_t)tx * phase_pitch<NF>();
-  // beta, exp(i beta L) (FP64), exp(i beta dz), exp(i beta 8 dz), beta, exp(i beta L) (double-float), (qx, qy)
+  // per column: beta, exp(i beta L), exp(i beta dz), exp(i beta 8 dz), r_s, r_p, beta / kb
   const size_t c16col = 7 * (size_t)tx;
-  const size_t c8 = 2 * (size_t)NF;               // kz (dfr) and kz (FP64)
-  return (c16 + c16col) * 16 + c8 * 8 + 16;
+  const size_t c8 = (size_t)NF + 5 * (size_t)tx;  // kz_l; qx, qy, hx, hy, |q| / kb per column
+  return (c16 + c16col) * 16 + c8 * 8 + (size_t)tx * sizeof(int) + 16;
 }
 
 // 1 / x in double-float: the FP32 reciprocal refined by one Newton step, r (1 + (1 - x r)),
@@ -71,22 +74,35 @@ __device__ __forceinline__ void df_phi1_horner(dfc w, dfc& phi) {
 // (-1)^l exp(i beta L), S = (E - 1) / (delta (kap + beta)), or i L phi1(i delta L) / (kap + beta)
 // by its Taylor series where |delta L| < 1/2 (15 terms: below 1e-15 there); both scaled by the
 // inverse-transform normalisation, Es = E / kb^2 likewise.
-__device__ __forceinline__ void green_scalars_df(dfr kap, dfc beta, dfc E, dfr L, dfr cinv, dfr scale, dfc& S,
-                                                 dfc& Es) {
+// false (and nothing written) near the removable singularity, |delta L| < 1/2: that case is
+// green_scalars_df_near's
+__device__ __forceinline__ bool green_scalars_df_far(dfr kap, dfc beta, dfc E, dfr L, dfr cinv, dfr scale, dfc& S,
+                                                     dfc& Es) {
   const dfc d = mk(beta.x - kap, beta.y);
   const dfc kpb = mk(kap + beta.x, beta.y);
   const dfc w = mk(-(d.y * L), d.x * L);
-  if (w.x.hi * w.x.hi + w.y.hi * w.y.hi < 0.25f) {
-    dfc phi = mk(dfr(1.0f, 0.0f), dfr(0.0f, 0.0f));
-    df_phi1_horner<15>(w, phi);
-    S = df_cdiv(mk(-(phi.y * L), phi.x * L), kpb);
-  } else {
-    S = df_cdiv(mk(E.x - dfr(1.0f, 0.0f), E.y), cmul(d, kpb));
-  }
+  if (w.x.hi * w.x.hi + w.y.hi * w.y.hi < 0.25f) return false;
+  S = df_cdiv(mk(E.x - dfr(1.0f, 0.0f), E.y), cmul(d, kpb));
+  S = mk(S.x * scale, S.y * scale);
+  const dfr es = cinv * scale;
+  Es = mk(E.x * es, E.y * es);
+  return true;
+}
+__device__ __forceinline__ void green_scalars_df_near(dfr kap, dfc beta, dfc E, dfr L, dfr cinv, dfr scale, dfc& S,
+                                                      dfc& Es) {
+  const dfc d = mk(beta.x - kap, beta.y);
+  const dfc kpb = mk(kap + beta.x, beta.y);
+  const dfc w = mk(-(d.y * L), d.x * L);
+  dfc phi = mk(dfr(1.0f, 0.0f), dfr(0.0f, 0.0f));
+  df_phi1_horner<15>(w, phi);
+  S = df_cdiv(mk(-(phi.y * L), phi.x * L), kpb);
   S = mk(S.x * scale, S.y * scale);
   const dfr es = cinv * scale;
   Es = mk(E.x * es, E.y * es);
 }
+
+__device__ __forceinline__ dfc dfc_of(float4 v) { return mk(dfr(v.x, v.y), dfr(v.z, v.w)); }
+__device__ __forceinline__ dfr dfr_of(float2 v) { return dfr(v.x, v.y); }
 
 // CTAs per SM the kernel is compiled for: at nf = 128 three (96 registers, a few bytes of
 // spill) measured faster than two at 168 registers (the pass is issue- and latency-bound,
@@ -103,64 +119,74 @@ __global__ void __launch_bounds__(NT, df_min_blocks<NF>()) k_zcol_df(OpCall<doub
   constexpr int EP = 16 * (N2 + 1) <= P ? N2 + 1 : N2;  // exchange row pitch
   dfc* col = reinterpret_cast<dfc*>(smem);
   dfc* tw = col + 3 * tx * P;
-  dfc* R0 = tw + NF;            // 3 tx: T_R E(plane 0)
-  dfc* ptab = R0 + 3 * tx;      // tx PP: exp(i beta dz j), j < 8, and exp(i beta 8 dz j')
-  double2* cbeta = reinterpret_cast<double2*>(ptab + tx * PP);
-  double2* cebl = cbeta + tx;   // exp(i beta L)
-  dfc* ce1 = reinterpret_cast<dfc*>(cebl + tx);  // exp(i beta dz)
-  dfc* ce8 = ce1 + tx;                            // exp(i beta 8 dz)
-  dfc* cbeta_d = ce8 + tx;                        // beta
-  dfc* cebl_d = cbeta_d + tx;                      // exp(i beta L)
-  dfr* cq = reinterpret_cast<dfr*>(cebl_d + tx);  // 2 tx: qx, qy
-  dfr* kzd = cq + 2 * tx;       // signed kz_l
-  double* kz64 = reinterpret_cast<double*>(kzd + NF);
+  dfc* R0 = tw + NF;             // 3 tx: T_R E(plane 0)
+  dfc* ptab = R0 + 3 * tx;       // tx PP: exp(i beta dz j), j < 8, and exp(i beta 8 dz j')
+  dfc* cbeta_d = ptab + tx * PP;  // per column (from the mode table's pairs): beta
+  dfc* cebl_d = cbeta_d + tx;     // exp(i beta L)
+  dfc* ce1 = cebl_d + tx;         // exp(i beta dz)
+  dfc* ce8 = ce1 + tx;            // exp(i beta 8 dz)
+  dfc* crs = ce8 + tx;            // r_s, r_p, beta / kb
+  dfc* crp = crs + tx;
+  dfc* cbq = crp + tx;
+  dfr* cq = reinterpret_cast<dfr*>(cbq + tx);  // 2 tx: qx, qy
+  dfr* chx = cq + 2 * tx;         // unit transverse direction, |q| / kb
+  dfr* chy = chx + tx;
+  dfr* cqn = chy + tx;
+  dfr* kzd = cqn + tx;            // signed kz_l
+  int* near = reinterpret_cast<int*>(kzd + NF);  // per column: the l of phi1's series, or -1
 
   const int x0 = blockIdx.x * tx, y = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
+  const int slot = a.rhsp[g].slot;  // loaded together with the activity flag
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
   const int nx = a.nx, ny = a.ny, ns = a.nslab;
-  const RhsParam& rp = a.rhsp[g];
-  const size_t mbase = ((size_t)rp.slot * ny + y) * nx + x0;
-  const double two_pi = 6.283185307179586476925286766559;
-
-  for (int i = threadIdx.x; i < NF; i += NT) {
-    tw[i] = to_dfc(a.twz[i]);
-    kz64[i] = a.ktab64[i];
-    kzd[i] = to_dfr(a.ktab64[i]);
-  }
-  for (int t = threadIdx.x; t < tx; t += NT) {
-    const ModeEntry me = a.modes[mbase + t];
-    cbeta[t] = me.beta;
-    cebl[t] = me.ebL;
-    cbeta_d[t] = to_dfc(me.beta);
-    cebl_d[t] = to_dfc(me.ebL);
-    ce1[t] = to_dfc(cexp_d(make_double2(-me.beta.y * a.dz, me.beta.x * a.dz)));
-    ce8[t] = to_dfc(cexp_d(make_double2(-8.0 * me.beta.y * a.dz, 8.0 * me.beta.x * a.dz)));
-    cq[2 * t] = to_dfr(rp.qix + two_pi * (double)fft_freq(x0 + t, nx) / ((double)nx * a.dx));
-    cq[2 * t + 1] = to_dfr(rp.qiy + two_pi * (double)fft_freq(y, ny) / ((double)ny * a.dy));
-  }
+  const size_t mbase = ((size_t)slot * ny + y) * nx + x0;
   const size_t pstride = (size_t)ny * nx;
   const int rf = threadIdx.x / N2, rj = threadIdx.x % N2;
   const bool rvalid = rf < 3 * tx;
   dfc* rex = col + (rvalid ? rf : 0) * P;  // the group's column: exchange scratch, then spectrum
   const dfc zero = mk(dfr(0.0), dfr(0.0));
+  for (int i = threadIdx.x; i < NF; i += NT) {
+    tw[i] = dfc_of(a.twzdf[i]);
+    kzd[i] = dfr_of(a.kzdf[i]);
+  }
+  for (int t = threadIdx.x; t < tx; t += NT) {
+    const ModeDF& m = a.modesdf[mbase + t];
+    cbeta_d[t] = dfc_of(m.beta);
+    cebl_d[t] = dfc_of(m.ebL);
+    ce1[t] = dfc_of(m.e1);
+    ce8[t] = dfc_of(m.e8);
+    crs[t] = dfc_of(m.rs);
+    crp[t] = dfc_of(m.rp);
+    cbq[t] = dfc_of(m.bq);
+    cq[2 * t] = dfr_of(m.qx);
+    cq[2 * t + 1] = dfr_of(m.qy);
+    chx[t] = dfr_of(m.hx);
+    chy[t] = dfr_of(m.hy);
+    cqn[t] = dfr_of(m.qnk);
+    near[t] = -1;
+  }
+  // forward: planes j + N2 k (k < 8, the nonzero half: ns + 1 <= NF/2) straight from HBM,
+  // issued before the barrier (earlier, their registers would spill under the cap)
+  dfc v[16];
+  if (rvalid) {
+    const int cc = rf / tx, t = rf % tx;
+    const size_t so = ((size_t)lr * 3 + cc) * ns * pstride + (size_t)y * nx + x0 + t;
+    const double2* src = a.work + so;
+    const dfc* srcd = reinterpret_cast<const dfc*>(a.work) + so;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int n = rj + N2 * k;
+      if (n >= 1 && n <= ns) v[k] = WDF ? srcd[(size_t)(n - 1) * pstride] : to_dfc(src[(size_t)(n - 1) * pstride]);
+      else v[k] = zero;
+    }
+#pragma unroll
+    for (int k = 8; k < 16; ++k) v[k] = zero;
+  }
+
   __syncthreads();  // twiddles
   {
-    // forward: planes j + N2 k (k < 8, the nonzero half: ns + 1 <= NF/2) straight from HBM
-    dfc v[16];
     if (rvalid) {
-      const int cc = rf / tx, t = rf % tx;
-      const size_t so = ((size_t)lr * 3 + cc) * ns * pstride + (size_t)y * nx + x0 + t;
-      const double2* src = a.work + so;
-      const dfc* srcd = reinterpret_cast<const dfc*>(a.work) + so;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int n = rj + N2 * k;
-        if (n >= 1 && n <= ns) v[k] = WDF ? srcd[(size_t)(n - 1) * pstride] : to_dfc(src[(size_t)(n - 1) * pstride]);
-        else v[k] = zero;
-      }
-#pragma unroll
-      for (int k = 8; k < 16; ++k) v[k] = zero;
       reg_fft_step1<dfc, NF, false, true>(v, rj, tw);
 #pragma unroll
       for (int k1 = 0; k1 < 16; ++k1) rex[k1 * EP + rj] = v[k1];
@@ -170,34 +196,53 @@ __global__ void __launch_bounds__(NT, df_min_blocks<NF>()) k_zcol_df(OpCall<doub
     if (rvalid) reg_fft_step2<dfc, NF, false, EP>(rex, rj, o);
     __syncwarp();
     if (rvalid) {
+      // the spectrum stays unpadded: every access to it is a run of consecutive elements
 #pragma unroll
       for (int r = 0; r < R1; ++r)
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) rex[fpad(rj + N2 * r + 16 * k2)] = o[r * N2 + k2];
+        for (int k2 = 0; k2 < N2; ++k2) rex[rj + N2 * r + 16 * k2] = o[r * N2 + k2];
     }
   }
   __syncthreads();
 
-  // Green's scalars (one evaluation serves l and nf - l) and products in double-float
-  const dfr L_d = to_dfr(0.5 * (double)NF * a.dz);
-  const dfr cinv_d = to_dfr(1.0 / (a.kb * a.kb));
-  const dfr scale_d = to_dfr(1.0 / ((double)NF * (double)nx * (double)ny));
-  for (int i = threadIdx.x; i < tx * (HF + 1); i += NT) {
-    const int t = i / (HF + 1), l = i % (HF + 1);
-    dfc E = cebl_d[t];
-    if (l & 1) E = cneg(E);
-    const dfr kz = kzd[l];
-    const dfr kap = kz.hi < 0.0f ? -kz : kz;
-    dfc Sd, Ed;
-    green_scalars_df(kap, cbeta_d[t], E, L_d, cinv_d, scale_d, Sd, Ed);
+  // Green's scalars (one evaluation serves l and nf - l) and products in double-float. Items
+  // run column by column (l < nf/2, then l = nf/2), so a quarter-warp's l stay in one column;
+  // each column's one l near the removable singularity (|delta L| < 1/2) is left to the pass
+  // after the loop, so that no warp diverges on phi1's series.
+  const dfr L_d = dfr_of(a.dfL), cinv_d = dfr_of(a.dfcinv), scale_d = dfr_of(a.dfscale);
+  auto apply_l = [&](int t, int l, dfc Sd, dfc Ed) {
     const dfr qx = cq[2 * t], qy = cq[2 * t + 1];
     dfc* c0 = col + (0 * tx + t) * P;
     dfc* c1 = col + (1 * tx + t) * P;
     dfc* c2 = col + (2 * tx + t) * P;
-    dyadic_apply<dfc>(c0 + fpad(l), c1 + fpad(l), c2 + fpad(l), qx, qy, kzd[l], Sd, Ed, cinv_d);
-    if (l > 0 && l < HF)
-      dyadic_apply<dfc>(c0 + fpad(NF - l), c1 + fpad(NF - l), c2 + fpad(NF - l), qx, qy, kzd[NF - l], Sd, Ed,
-                        cinv_d);
+    dyadic_apply<dfc>(c0 + l, c1 + l, c2 + l, qx, qy, kzd[l], Sd, Ed, cinv_d);
+    if (l > 0 && l < HF) dyadic_apply<dfc>(c0 + (NF - l), c1 + (NF - l), c2 + (NF - l), qx, qy, kzd[NF - l], Sd, Ed, cinv_d);
+  };
+  auto kappa = [&](int l) {
+    const dfr kz = kzd[l];
+    return kz.hi < 0.0f ? -kz : kz;
+  };
+  for (int i = threadIdx.x; i < tx * (HF + 1); i += NT) {
+    const bool tail = i >= tx * HF;
+    const int t = tail ? i - tx * HF : i / HF, l = tail ? HF : i % HF;
+    dfc E = cebl_d[t];
+    if (l & 1) E = cneg(E);
+    dfc Sd, Ed;
+    if (!green_scalars_df_far(kappa(l), cbeta_d[t], E, L_d, cinv_d, scale_d, Sd, Ed)) {
+      near[t] = l;
+      continue;
+    }
+    apply_l(t, l, Sd, Ed);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < tx; t += NT) {
+    const int l = near[t];
+    if (l < 0) continue;
+    dfc E = cebl_d[t];
+    if (l & 1) E = cneg(E);
+    dfc Sd, Ed;
+    green_scalars_df_near(kappa(l), cbeta_d[t], E, L_d, cinv_d, scale_d, Sd, Ed);
+    apply_l(t, l, Sd, Ed);
   }
   __syncthreads();
   {
@@ -205,7 +250,7 @@ __global__ void __launch_bounds__(NT, df_min_blocks<NF>()) k_zcol_df(OpCall<doub
     dfc v[16];
     if (rvalid) {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = rex[fpad(rj + N2 * k)];
+      for (int k = 0; k < 16; ++k) v[k] = rex[rj + N2 * k];
     }
     __syncwarp();
     if (rvalid) {
@@ -223,7 +268,7 @@ __global__ void __launch_bounds__(NT, df_min_blocks<NF>()) k_zcol_df(OpCall<doub
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
           const int n = rj + N2 * r + 16 * k2;
-          if (n <= HF) rex[fpad(n)] = o[r * N2 + k2];
+          if (n <= HF) rex[n] = o[r * N2 + k2];
         }
     }
   }
@@ -235,32 +280,23 @@ __global__ void __launch_bounds__(NT, df_min_blocks<NF>()) k_zcol_df(OpCall<doub
       const int cc = i / tx, t = i % tx;
       const size_t o = (((size_t)g * 2) * 3 + cc) * ny * nx + (size_t)y * nx + x0 + t;
       a.side[o] = to_d2(col[(cc * tx + t) * P]);
-      a.side[o + (size_t)3 * ny * nx] = to_d2(col[(cc * tx + t) * P + fpad(ns + 1)]);
+      a.side[o + (size_t)3 * ny * nx] = to_d2(col[(cc * tx + t) * P + ns + 1]);
     }
   }
-  // stack reflection of the downgoing field on plane 0 (Eq. (9)) in FP64, once per column:
-  // R0 = T_R E0, T_R = r_s s s^T + r_p p+ p-^T, s = z x q/|q|, p+- = (-+beta qhat, |q|)/kb
+  // stack reflection of the downgoing field on plane 0 (Eq. (9)) in double-float, once per
+  // column: R0 = T_R E0, T_R = r_s s s^T + r_p p+ p-^T, s = z x q/|q|, p+- = (-+beta qhat, |q|)/kb
   for (int t = threadIdx.x; t < tx; t += NT) {
-    const ModeEntry me = a.modes[mbase + t];
-    const double qx64 = rp.qix + two_pi * (double)fft_freq(x0 + t, nx) / ((double)nx * a.dx);
-    const double qy64 = rp.qiy + two_pi * (double)fft_freq(y, ny) / ((double)ny * a.dy);
-    const double qn = sqrt(qx64 * qx64 + qy64 * qy64);
-    const double hx = qn > 0.0 ? qx64 / qn : rp.cphi;
-    const double hy = qn > 0.0 ? qy64 / qn : rp.sphi;
-    const double2 e0 = to_d2(col[(0 * tx + t) * P]);
-    const double2 e1 = to_d2(col[(1 * tx + t) * P]);
-    const double2 e2 = to_d2(col[(2 * tx + t) * P]);
-    const double ikb = 1.0 / a.kb;
-    const double2 sE = make_double2(-hy * e0.x + hx * e1.x, -hy * e0.y + hx * e1.y);
-    const double2 bq = cscale(me.beta, ikb);
-    const double2 tq = cadd(cscale(e0, hx), cscale(e1, hy));
-    const double2 pmE = cadd(cmul(bq, tq), cscale(e2, qn * ikb));
-    const double2 as = cmul(me.rs, sE);
-    const double2 ap = cmul(me.rp, pmE);
-    const double2 mbq = cneg(bq);
-    R0[0 * tx + t] = to_dfc(cadd(cscale(as, -hy), cmul(ap, cscale(mbq, hx))));
-    R0[1 * tx + t] = to_dfc(cadd(cscale(as, hx), cmul(ap, cscale(mbq, hy))));
-    R0[2 * tx + t] = to_dfc(cscale(ap, qn * ikb));
+    const dfr hx = chx[t], hy = chy[t], qnk = cqn[t];
+    const dfc bq = cbq[t];
+    const dfc e0 = col[(0 * tx + t) * P], e1 = col[(1 * tx + t) * P], e2 = col[(2 * tx + t) * P];
+    const dfc sE = mk(e1.x * hx - e0.x * hy, e1.y * hx - e0.y * hy);  // s . E0
+    const dfc tq = mk(e0.x * hx + e1.x * hy, e0.y * hx + e1.y * hy);  // qhat . E0
+    const dfc pmE = cadd(cmul(bq, tq), mk(e2.x * qnk, e2.y * qnk));   // p- . E0
+    const dfc as = cmul(crs[t], sE), ap = cmul(crp[t], pmE);
+    const dfc apb = cmul(ap, bq);
+    R0[0 * tx + t] = mk(-(as.x * hy) - apb.x * hx, -(as.y * hy) - apb.y * hx);
+    R0[1 * tx + t] = mk(as.x * hx - apb.x * hy, as.y * hx - apb.y * hy);
+    R0[2 * tx + t] = mk(ap.x * qnk, ap.y * qnk);
   }
   // phase table: powers of exp(i beta dz) (j < 8) and of exp(i beta 8 dz) (steps from FP64)
   // by binary powering in double-float
@@ -284,7 +320,7 @@ __global__ void __launch_bounds__(NT, df_min_blocks<NF>()) k_zcol_df(OpCall<doub
       const dfc ph = cmul(ptab[t0 * PP + (pl & 7)], ptab[t0 * PP + 8 + (pl >> 3)]);
 #pragma unroll
       for (int cc = 0; cc < 3; ++cc) {
-        dfc* e = col + (cc * tx + t0) * P + fpad(pl + 1);
+        dfc* e = col + (cc * tx + t0) * P + pl + 1;
         *e = cadd(*e, cmul(R0[cc * tx + t0], ph));
       }
     }
@@ -297,7 +333,7 @@ __global__ void __launch_bounds__(NT, df_min_blocks<NF>()) k_zcol_df(OpCall<doub
   for (int cc = 0; cc < 3; ++cc) {
 #pragma unroll 4
     for (int pl = p0; pl < ns; pl += pstep) {
-      const dfc v = col[(cc * tx + t0) * P + fpad(pl + 1)];
+      const dfc v = col[(cc * tx + t0) * P + pl + 1];
       if constexpr (WDF) gcold[((size_t)cc * ns + pl) * pstride] = v;
       else gcol[((size_t)cc * ns + pl) * pstride] = to_d2(v);
     }
@@ -323,7 +359,8 @@ int launch(const OpCall<double2>& a, bool wdf) {
 // (the plane loop of the write-back needs the tile to divide the CTA).
 bool zcol_df_supported(const OpCall<double2>& a) {
   const int tx = a.nx < kDfTile ? a.nx : kDfTile;
-  return (a.nf == 64 || a.nf == 128) && a.sph64 == nullptr && tx >= 1 && (tx & (tx - 1)) == 0 && a.nx % tx == 0;
+  return (a.nf == 64 || a.nf == 128) && a.sph64 == nullptr && a.modesdf && a.twzdf && a.kzdf && tx >= 1 &&
+         (tx & (tx - 1)) == 0 && a.nx % tx == 0;
 }
 
 int launch_zcol_df(const OpCall<double2>& a, bool wdf) {
