@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kColNT, 2) k_cols_df(OpCall<double2> a, int tx
   const int c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
-  for (int i = threadIdx.x; i < NY; i += kColNT) tw[i] = to_dfc(a.twy[i]);
+  for (int i = threadIdx.x; i < NY; i += kColNT) tw[i] = a.twydf ? dfc_of(a.twydf[i]) : to_dfc(a.twy[i]);
   const size_t base = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)NY * a.nx + x0;
   const int t0 = threadIdx.x % tx, y0 = threadIdx.x / tx, ystep = kColNT / tx;
   dfc* wd = reinterpret_cast<dfc*>(a.work);

@@ -100,6 +100,8 @@ struct psfd_ctx {
   psfd::ModeF32* modes32 = nullptr;
   psfd::ModeDF* modesdf = nullptr;  // double-float column constants of the residual's z pass
   float4* twzdf = nullptr;          // z twiddles and kz_l as double-float pairs
+  float4 *twxdf = nullptr, *twydf = nullptr;  // x and y twiddles as pairs
+  float4* Vdf = nullptr;            // V64 as pairs (the residual's double-float row pass)
   float2* kzdf = nullptr;
   float* ktab32 = nullptr;
   double* ktab64 = nullptr;

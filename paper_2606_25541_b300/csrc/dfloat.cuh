@@ -212,4 +212,8 @@ __host__ __device__ __forceinline__ double to_d(dfr a) {
 }
 __host__ __device__ __forceinline__ double2 to_d2(dfc a) { return make_double2(to_d(a.x), to_d(a.y)); }
 
+// Pairs stored as float4 (re.hi, re.lo, im.hi, im.lo) / float2 (hi, lo) in device tables.
+__host__ __device__ __forceinline__ dfc dfc_of(float4 v) { return mk(dfr(v.x, v.y), dfr(v.z, v.w)); }
+__host__ __device__ __forceinline__ dfr dfr_of(float2 v) { return dfr(v.x, v.y); }
+
 }  // namespace psfd

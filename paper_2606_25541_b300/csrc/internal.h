@@ -107,6 +107,8 @@ struct OpCall {
   const ModeF32* modes32;  // FP32 column constants (used by the FP32 z-column kernel)
   const ModeDF* modesdf;   // double-float column constants (the residual's double-float z pass)
   const float4* twzdf;     // [nf]: the z twiddles as double-float pairs
+  const float4 *twxdf, *twydf;  // [nx], [ny]: the x and y twiddles as pairs
+  const float4* Vdf;       // V as pairs (same layout as V), or null
   const float2* kzdf;      // [nf]: signed kz_l as double-float pairs
   float2 dfL, dfcinv, dfscale;  // pairs of L = nf dz / 2, 1 / kb^2, 1 / (nf nx ny)
   const float* ktab32;     // [3][nf]: |kz_l| hi, |kz_l| lo, signed kz_l (FP32)

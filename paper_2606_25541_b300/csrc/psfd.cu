@@ -92,8 +92,8 @@ Plan make_plan(const psfd_grid& g, int precision, int max_rhs, int max_clips) {
   p.max_orders = (int)std::min<double>((double)p.plane, bound);
   const size_t R = (size_t)max_rhs, Cl = (size_t)max_clips;
   size_t b = 0;
-  b += p.plane * g.nslab * (Cl * (16 + 8) + 16);             // V64, V32 per clip, eps staging
-  b += (size_t)(g.nx + g.ny + g.nf) * 16;                    // twiddles
+  b += p.plane * g.nslab * (Cl * (16 + 8 + 16) + 16);        // V64, V32, V as pairs per clip, eps staging
+  b += (size_t)(g.nx + g.ny + g.nf) * (16 + 8) + (size_t)(g.nx + g.ny) * 16;  // twiddles: FP64, FP32, x/y pairs
   b += R * (sizeof(RhsParam) + 4 * sizeof(double));          // illumination parameters
   b += R * p.plane * (sizeof(ModeEntry) + sizeof(ModeF32) + sizeof(ModeDF));  // mode tables (FP64, FP32, pairs)
   b += (size_t)g.nf * (3 * sizeof(float) + sizeof(double) + 16 + 8);  // kz tables, pair-format twiddles and kz
@@ -162,6 +162,7 @@ int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs
   };
   A(&ctx->V64, P.plane * grid->nslab * max_clips);
   A(&ctx->V32, P.plane * grid->nslab * max_clips);
+  A(&ctx->Vdf, P.plane * grid->nslab * max_clips);
   A(&ctx->eps_stage, P.plane * grid->nslab);
   A(&ctx->twx, grid->nx);
   A(&ctx->twy, grid->ny);
@@ -169,6 +170,8 @@ int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs
   A(&ctx->twx32, grid->nx);
   A(&ctx->twy32, grid->ny);
   A(&ctx->twz32, grid->nf);
+  A(&ctx->twxdf, grid->nx);
+  A(&ctx->twydf, grid->ny);
   A(&ctx->rhsp, R);
   A(&ctx->slot_par, 4 * R);
   A(&ctx->modes, R * P.plane);
@@ -254,6 +257,18 @@ int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs
     if (e == cudaSuccess) e = cudaMemcpy(ctx->twx32, fx.data(), fx.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(ctx->twy32, fy.data(), fy.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(ctx->twz32, fz.data(), fz.size() * 8, cudaMemcpyHostToDevice);
+    // pair copies of the x and y tables for the residual's double-float row and column passes
+    auto df4 = [](const std::vector<double2>& t) {
+      std::vector<float4> r(t.size());
+      for (size_t i = 0; i < t.size(); ++i) {
+        const dfc d = to_dfc(t[i]);
+        r[i] = make_float4(d.x.hi, d.x.lo, d.y.hi, d.y.lo);
+      }
+      return r;
+    };
+    const auto dx4 = df4(tx), dy4 = df4(ty);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->twxdf, dx4.data(), dx4.size() * 16, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->twydf, dy4.data(), dy4.size() * 16, cudaMemcpyHostToDevice);
   }
   {
     // signed z wavenumbers kz_l = 2 pi l / (nf dz), and |kz_l| split into FP32 hi + lo
@@ -306,7 +321,7 @@ int ctx_set_potential(psfd_ctx* ctx, int clip, const double* eps_complex, int wh
     src = ctx->eps_stage;
   }
   RC(launch_potential(n, src, ctx->k0 * ctx->k0, ctx->g.eps_bg, ctx->V64 + (size_t)clip * n,
-                      ctx->V32 + (size_t)clip * n, ctx->stream));
+                      ctx->V32 + (size_t)clip * n, ctx->Vdf + (size_t)clip * n, ctx->stream));
   return PSFD_OK;
 }
 
@@ -493,6 +508,9 @@ static OpCall<C> base_call(psfd_ctx* ctx, int rhs0, int nrhs, const C* V) {
   a.modesdf = ctx->modesdf;
   a.twzdf = ctx->twzdf;
   a.kzdf = ctx->kzdf;
+  a.twxdf = ctx->twxdf;
+  a.twydf = ctx->twydf;
+  a.Vdf = (const void*)V == (const void*)ctx->V64 ? ctx->Vdf : nullptr;
   {
     // the double-float z pass's constants, formed in FP64 and split once here
     auto r2 = [](double v) {

@@ -45,24 +45,27 @@ __global__ void __launch_bounds__(kRowNT, 2) k_rows_fwd_df(OpCall<double2> a, in
   const int c = blockIdx.x % 3, lr = blockIdx.x / 3, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
-  for (int i = threadIdx.x; i < NX; i += kRowNT) tw[i] = to_dfc(a.twx[i]);
+  for (int i = threadIdx.x; i < NX; i += kRowNT) tw[i] = a.twxdf ? dfc_of(a.twxdf[i]) : to_dfc(a.twx[i]);
   const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
-  const double2* Vp = a.V + (((size_t)a.rhsp[g].clip * a.nslab + p) * a.ny + y0) * NX;
+  const size_t voff = (((size_t)a.rhsp[g].clip * a.nslab + p) * a.ny + y0) * NX;
+  const double2* Vp = a.V + voff;
+  const float4* Vq = a.Vdf ? a.Vdf + voff : nullptr;  // V as pairs: no conversion of V here
   const int n = rb * NX;
   for (int i0 = threadIdx.x; i0 < n; i0 += 2 * kRowNT) {
-    double2 uu[2], vv[2];
+    double2 uu[2];
+    dfc vv[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int i = i0 + j * kRowNT;
       if (i < n) {
         uu[j] = a.u[base + i];
-        vv[j] = Vp[i];
+        vv[j] = Vq ? dfc_of(Vq[i]) : to_dfc(Vp[i]);
       }
     }
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int i = i0 + j * kRowNT;
-      if (i < n) tile[(i / NX) * RP + fpad(i % NX)] = cmul(to_dfc(vv[j]), to_dfc(uu[j]));
+      if (i < n) tile[(i / NX) * RP + fpad(i % NX)] = cmul(vv[j], to_dfc(uu[j]));
     }
   }
   __syncthreads();
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(kRowNT, 2) k_rows_inv_df(OpCall<double2> a, co
   const int c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
-  for (int i = threadIdx.x; i < NX; i += kRowNT) tw[i] = to_dfc(a.twx[i]);
+  for (int i = threadIdx.x; i < NX; i += kRowNT) tw[i] = a.twxdf ? dfc_of(a.twxdf[i]) : to_dfc(a.twx[i]);
   const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
   const int n = rb * NX;
   for (int i = threadIdx.x; i < n; i += kRowNT) {

@@ -19,18 +19,23 @@ static int launched() {
 // ---------------------------------------------------------------------------
 // V = k0^2 (eps - eps_bg) in FP64 and FP32 (Sec. 2, Eq. (1); Sec. 3, Eq. (10))
 // ---------------------------------------------------------------------------
-__global__ void k_potential(size_t n, const double2* eps, double k02, double eps_bg, double2* V64, float2* V32) {
+__global__ void k_potential(size_t n, const double2* eps, double k02, double eps_bg, double2* V64, float2* V32,
+                            float4* Vdf) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double2 e = eps[i];
     const double2 v = make_double2(k02 * (e.x - eps_bg), k02 * e.y);
     V64[i] = v;
     V32[i] = to_c32(v);
+    if (Vdf) {  // the pairs the residual's double-float row pass multiplies by (once per potential)
+      const dfc d = to_dfc(v);
+      Vdf[i] = make_float4(d.x.hi, d.x.lo, d.y.hi, d.y.lo);
+    }
   }
 }
 
-int launch_potential(size_t n, const double2* eps, double k02, double eps_bg, double2* V64, float2* V32,
+int launch_potential(size_t n, const double2* eps, double k02, double eps_bg, double2* V64, float2* V32, float4* Vdf,
                      cudaStream_t st) {
-  k_potential<<<592, 256, 0, st>>>(n, eps, k02, eps_bg, V64, V32);
+  k_potential<<<592, 256, 0, st>>>(n, eps, k02, eps_bg, V64, V32, Vdf);
   return launched();
 }
 
@@ -234,22 +239,30 @@ __global__ void k_modes(ModesArgs a) {
   }
   const size_t idx = ((size_t)slot * a.ny + y) * a.nx + x;
   a.modes[idx] = m;
+  if (!a.modes32 && !a.modesdf) return;
+  // per-column constants of the z pass, evaluated once in FP64 for both copies
+  const double2 e1 = cexp_d(make_double2(-beta.y * a.dz, beta.x * a.dz));
+  const double2 e8 = cexp_d(make_double2(-8.0 * beta.y * a.dz, 8.0 * beta.x * a.dz));
+  const double qn = sqrt(q2);
+  const double hx = qn > 0.0 ? qx / qn : sp[2];
+  const double hy = qn > 0.0 ? qy / qn : sp[3];
+  const double qnk = qn / a.kb;
+  const double2 bq = cscale(beta, 1.0 / a.kb);
   if (a.modes32) {
     ModeF32 f;
     f.qx = (float)qx;
     f.qy = (float)qy;
     split_hi_lo(beta, f.bh, f.bl);
     f.ebL = to_c32(m.ebL);
-    f.e1 = to_c32(cexp_d(make_double2(-beta.y * a.dz, beta.x * a.dz)));
-    f.e8 = to_c32(cexp_d(make_double2(-8.0 * beta.y * a.dz, 8.0 * beta.x * a.dz)));
+    f.e1 = to_c32(e1);
+    f.e8 = to_c32(e8);
     f.rs = to_c32(m.rs);
     f.rp = to_c32(m.rp);
-    const double qn = sqrt(q2);
-    f.hx = (float)(qn > 0.0 ? qx / qn : sp[2]);
-    f.hy = (float)(qn > 0.0 ? qy / qn : sp[3]);
-    f.qnk = (float)(qn / a.kb);
+    f.hx = (float)hx;
+    f.hy = (float)hy;
+    f.qnk = (float)qnk;
     f.pad = 0.f;
-    f.bq = to_c32(cscale(beta, 1.0 / a.kb));
+    f.bq = to_c32(bq);
     a.modes32[idx] = f;
   }
   if (a.modesdf) {
@@ -265,17 +278,16 @@ __global__ void k_modes(ModesArgs a) {
     ModeDF f;
     f.beta = c4(beta);
     f.ebL = c4(m.ebL);
-    f.e1 = c4(cexp_d(make_double2(-beta.y * a.dz, beta.x * a.dz)));
-    f.e8 = c4(cexp_d(make_double2(-8.0 * beta.y * a.dz, 8.0 * beta.x * a.dz)));
+    f.e1 = c4(e1);
+    f.e8 = c4(e8);
     f.rs = c4(m.rs);
     f.rp = c4(m.rp);
-    f.bq = c4(cscale(beta, 1.0 / a.kb));
+    f.bq = c4(bq);
     f.qx = r2(qx);
     f.qy = r2(qy);
-    const double qn = sqrt(q2);
-    f.hx = r2(qn > 0.0 ? qx / qn : sp[2]);
-    f.hy = r2(qn > 0.0 ? qy / qn : sp[3]);
-    f.qnk = r2(qn / a.kb);
+    f.hx = r2(hx);
+    f.hy = r2(hy);
+    f.qnk = r2(qnk);
     f.pad = make_float2(0.f, 0.f);
     a.modesdf[idx] = f;
   }

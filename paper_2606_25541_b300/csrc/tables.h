@@ -71,7 +71,7 @@ struct OrdersArgs {
   const int* mask;      // right-hand sides to evaluate (null = all)
 };
 
-int launch_potential(size_t n, const double2* eps, double k02, double eps_bg, double2* V64, float2* V32,
+int launch_potential(size_t n, const double2* eps, double k02, double eps_bg, double2* V64, float2* V32, float4* Vdf,
                      cudaStream_t st);
 int launch_modes(const ModesArgs& a, int n_slots, cudaStream_t st);
 int launch_rhs(int rhs0, int nrhs, RhsParam* rp, const ModeEntry* modes, int nx, int ny, int nslab, double dz,

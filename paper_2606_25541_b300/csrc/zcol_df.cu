@@ -101,8 +101,6 @@ __device__ __forceinline__ void green_scalars_df_near(dfr kap, dfc beta, dfc E, 
   Es = mk(E.x * es, E.y * es);
 }
 
-__device__ __forceinline__ dfc dfc_of(float4 v) { return mk(dfr(v.x, v.y), dfr(v.z, v.w)); }
-__device__ __forceinline__ dfr dfr_of(float2 v) { return dfr(v.x, v.y); }
 
 // CTAs per SM the kernel is compiled for: at nf = 128 three (96 registers, a few bytes of
 // spill) measured faster than two at 168 registers (the pass is issue- and latency-bound,
