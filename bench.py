@@ -61,6 +61,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in tile shapes")
+    ap.add_argument("--groups", type=int, default=1,
+                    help="headline: contexts the 18 illuminations are split over, solved side by side "
+                         "(psfd_solve_group); 1 = one context")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the sampled precision sweep and large clip in the default run")
     ap.add_argument("--profile-only", action="store_true", help="one profiled step, for ncu launch lists")
@@ -1000,6 +1003,47 @@ def orders_all(solver, n_rhs):
     return [solver.diffraction_orders(i) for i in range(n_rhs)]
 
 
+class SolverGroup:
+    """A batch of illuminations split over k contexts, each on its own stream, solved together
+    through psfd_solve_group (k = 1: one context and psfd_solve). Each context's inputs are set on
+    its own stream after the main stream's work; the main stream waits for every context's
+    stream after a solve, so events on it bracket the whole batch."""
+
+    def __init__(self, psfd, prob, precision, k, main_stream, dev):
+        import torch
+        self.psfd = psfd
+        k = max(1, min(int(k), prob.n_rhs))
+        cut = np.linspace(0, prob.n_rhs, k + 1).round().astype(int)
+        self.parts = [prob.with_illumination(prob.theta_deg[a:b], prob.phi_deg[a:b], prob.pol[a:b])
+                      for a, b in zip(cut[:-1], cut[1:])]
+        self.main = main_stream
+        self.streams = [main_stream] + [torch.cuda.Stream(dev) for _ in range(k - 1)]
+        self.solvers = [psfd.Solver.from_problem(p, precision, stream=st) for p, st in zip(self.parts, self.streams)]
+
+    def set_inputs(self, eps):
+        for s, p, st in zip(self.solvers, self.parts, self.streams):
+            st.wait_stream(self.main)
+            s.set_potential(eps)
+            s.set_illumination(p.theta_deg, p.phi_deg, p.pol)
+
+    def solve(self, **kw):
+        if len(self.solvers) == 1:
+            reps = [self.solvers[0].solve(**kw)]
+        else:
+            reps = self.psfd.solve_group(self.solvers, **kw)
+        for st in self.streams[1:]:
+            self.main.wait_stream(st)
+        return {"iterations": max(r["iterations"] for r in reps), "outer": max(r["outer"] for r in reps),
+                "relres": max(r["relres"] for r in reps)}
+
+    def orders(self):
+        return [s.diffraction_orders(i) for s, p in zip(self.solvers, self.parts) for i in range(p.n_rhs)]
+
+    def close(self):
+        for s in self.solvers:
+            s.close()
+
+
 def orders_rel_err(a, b):
     num = sum(float(np.sum(np.abs(x["amp"] - y["amp"]) ** 2)) for x, y in zip(a, b))
     den = sum(float(np.sum(np.abs(y["amp"]) ** 2)) for y in b)
@@ -1025,28 +1069,35 @@ def run_ours(args):
     solve_kw = dict(tol=args.tol, inner_tol=args.inner_tol, max_iter=400, max_outer=12, check_every=4,
                     krylov=psfd.GMRES if args.krylov == "gmres" else psfd.BICGSTAB, restart=args.restart)
 
-    solver = psfd.Solver.from_problem(prob, psfd.FP32_REFINED, stream=stream)
     eps_dev = torch.from_numpy(prob.eps).to(dev)
     th, ph, po = prob.theta_deg, prob.phi_deg, prob.pol
 
-    def step(s):
+    def step_single(s, kw=solve_kw):
         s.set_potential(eps_dev)
         s.set_illumination(th, ph, po)
-        return s.solve(**solve_kw)
+        return s.solve(**kw)
 
     if args.profile_only:
+        solver = psfd.Solver.from_problem(prob, psfd.FP32_REFINED, stream=stream)
         if args.plain_launches:  # every kernel its own launch (ncu lists no kernels inside a graph's loop)
             solver.set_graphs(False)
-        step(solver)
+        step_single(solver)
         torch.cuda.synchronize()
         return 0
 
+    # the batch as args.groups contexts solved side by side, each on its own stream
+    group = SolverGroup(psfd, prob, psfd.FP32_REFINED, args.groups, stream, dev)
+
+    def step(g, kw=solve_kw, eps=None):
+        g.set_inputs(eps_dev if eps is None else eps)
+        return g.solve(**kw)
+
     for _ in range(args.warmup):
-        rep = step(solver)
+        rep = step(group)
     torch.cuda.synchronize()
     # first use of this grid: time the tile shapes once (bitwise the same results), untimed
-    tuned = None if args.no_autotune else solver.autotune()
-    step(solver)
+    tuned = None if args.no_autotune else group.solvers[0].autotune()
+    step(group)
     torch.cuda.synchronize()
 
     # reference orders for the order error the metric is quoted at: FP64 solve to 1e-11 (untimed)
@@ -1070,7 +1121,7 @@ def run_ours(args):
     ev[0].record(stream)
     reps = []
     for k in range(args.steps):
-        reps.append(step(solver))
+        reps.append(step(group))
         ev[k + 1].record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -1080,26 +1131,30 @@ def run_ours(args):
     t_ms = reduce_max(ev[0].elapsed_time(ev[-1]), world, dev)
     value = n_rhs * args.steps * world / (t_ms * 1e-3)
 
-    # ---- per-kernel timing of the same steps (CUDA events on the solver's stream) ----
+    # ---- per-kernel timing of the same workload: one context of the whole batch, launches one
+    #      after another (CUDA events on its stream; per-pass records need sequential launches) ----
+    psolver = psfd.Solver.from_problem(prob, psfd.FP32_REFINED, stream=stream)
+    step_single(psolver)
+    torch.cuda.synchronize()
     psfd.profile_enable(True)
     for _ in range(args.steps):
-        step(solver)
+        step_single(psolver)
     torch.cuda.synchronize()
     psfd.profile_enable(False)
     prof = psfd.profile_read()
     total_prof_ms = sum(v["ms"] for v in prof.values())
+    psolver.close()
 
-    # ---- end to end through the C ABI with host buffers ----
+    # ---- end to end through the C ABI with host buffers: eps copied once per step from pinned
+    #      host memory (every context reads the device copy), the orders read back ----
     eps_host = torch.from_numpy(prob.eps).pin_memory()
-    e2e_solver = solver
     d2h = 0
 
     def e2e_step():
         nonlocal d2h
-        e2e_solver.set_potential(eps_host)
-        e2e_solver.set_illumination(th, ph, po)
-        e2e_solver.solve(**solve_kw)
-        out = orders_all(e2e_solver, n_rhs)
+        eps_in = eps_host.to(dev, non_blocking=True)
+        step(group, eps=eps_in)
+        out = group.orders()
         d2h = sum(o["m"].nbytes + o["n"].nbytes + o["amp"].nbytes + o["a_s"].nbytes + o["a_p"].nbytes
                   + o["eff"].nbytes for o in out)
         return out
@@ -1115,10 +1170,10 @@ def run_ours(args):
     t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
     h2d = prob.eps.nbytes + th.nbytes + ph.nbytes + po.nbytes
 
-    # ---- plain FP64 path on the same batch, and the order difference ----
+    # ---- plain FP64 path on the same batch (grouped the same way), and the order difference ----
     fp64 = None
     if not args.no_fp64:
-        s64 = psfd.Solver.from_problem(prob, psfd.FP64, stream=stream)
+        s64 = SolverGroup(psfd, prob, psfd.FP64, args.groups, stream, dev)
         step(s64)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1127,7 +1182,7 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         t64 = reduce_max(e0.elapsed_time(e1), world, dev)
-        orders64 = orders_all(s64, n_rhs)
+        orders64 = s64.orders()
         fp64 = {"value": n_rhs * world / (t64 * 1e-3), "unit": UNIT, "ms_per_step": t64, "tol": args.tol,
                 "iterations": rep64["iterations"], "relres": rep64["relres"],
                 "order_error_vs_fp64_1e-11": order_error(orders64),
@@ -1137,35 +1192,30 @@ def run_ours(args):
     # ---- the same FP32 + refinement step solved 30x tighter (FP64 residual 1e-8) ----
     tight_kw = dict(solve_kw, tol=DEFAULT_TOL, inner_tol=DEFAULT_INNER_TOL)
 
-    def step_tight(s):
-        s.set_potential(eps_dev)
-        s.set_illumination(th, ph, po)
-        return s.solve(**tight_kw)
-
-    step_tight(solver)
+    step(group, tight_kw)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        rep_t = step_tight(solver)
+        rep_t = step(group, tight_kw)
     e1.record(stream)
     torch.cuda.synchronize()
     t_tight = reduce_max(e0.elapsed_time(e1), world, dev)
     tight = {"value": n_rhs * args.steps * world / (t_tight * 1e-3), "unit": UNIT, "tol": DEFAULT_TOL,
              "inner_tol": DEFAULT_INNER_TOL, "iterations": rep_t["iterations"], "outer": rep_t["outer"],
-             "relres": rep_t["relres"], "order_error_vs_fp64_1e-11": order_error(orders_all(solver, n_rhs))}
+             "relres": rep_t["relres"], "order_error_vs_fp64_1e-11": order_error(group.orders())}
 
     # the other workloads, sampled: cfg 3's precision sweep (256^2 Manhattan, both paths and the
     # tensor-core stage) and cfg 5's large clip (1024^2, 2 of its 8 illuminations), at 1e-8
     extra = {}
     if world == 1 and not args.no_extra:
-        solver.close()
+        group.close()
         torch.cuda.empty_cache()
         extra["precision_sweep_manhattan_256"] = precision_sweep(DEFAULT_TOL, DEFAULT_INNER_TOL, 1, 1)
         torch.cuda.empty_cache()
         extra["large_clip_curvilinear_1024_2rhs"] = large_clip(DEFAULT_TOL, DEFAULT_INNER_TOL, 1, n_rhs=2)
         torch.cuda.empty_cache()
-        solver = None
+        group = None
 
     serving = None
     if args.serve > 0 and world == 1:
@@ -1209,6 +1259,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "grid": [prob.nx, prob.ny, prob.nslab, prob.nf], "dx_nm": prob.dx,
                    "n_rhs": n_rhs, "precision": f"FP32 {'GMRES' if args.krylov == 'gmres' else 'BiCGStab'} inside FP64 defect correction",
                    "tol": args.tol, "inner_tol": args.inner_tol, "parallelism": f"replicas x{world}",
+                   "contexts": f"{len(group.solvers) if group else args.groups} contexts of the batch solved side by side on their own streams (psfd_solve_group)",
                    "l2": f"inputs larger than L2: {solver_bytes(prob) / 1e9:.1f} GB working set per step"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "what": "per-step (18-illumination batch) device time"},
@@ -1227,8 +1278,8 @@ def run_ours(args):
         **extra,
     }
     print(json.dumps(line), flush=True)
-    if solver is not None:
-        solver.close()
+    if group is not None:
+        group.close()
     return 0
 
 

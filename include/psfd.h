@@ -246,6 +246,21 @@ int psfd_set_illumination(psfd_ctx* ctx, int n_rhs, const double* theta_deg,
  * right-hand side missed the tolerance (the solution is still stored). */
 int psfd_solve(psfd_ctx* ctx, const psfd_solve_opts* opts, psfd_report* report);
 
+/* psfd_solve on n distinct contexts at once (no counterpart in the paper: a way to run a
+ * batch of illuminations split over several contexts, e.g. the two halves of a set of
+ * angles). Each context is solved by its own host thread on its own stream, so the
+ * contexts' kernels run side by side: the z pass, bound by instruction issue, overlaps the
+ * latency-bound plane passes of the other context. Each context's results are bitwise those
+ * of psfd_solve on it alone (the arithmetic of a context does not depend on the others).
+ *   ctxs     host array of n context pointers, all distinct and non-null; contexts sharing
+ *            one stream are correct but run one after the other
+ *   opts     as for psfd_solve, applied to every context (may be NULL)
+ *   reports  host array of n reports, or NULL
+ * Returns PSFD_OK, PSFD_E_ARG (null, n < 1 or a repeated context), or the first non-OK status
+ * of the contexts in order (every context is solved either way). Per-pass profiling
+ * (psfd_profile_enable) records launches of one context at a time: leave it off here. */
+int psfd_solve_group(psfd_ctx* const* ctxs, int n, const psfd_solve_opts* opts, psfd_report* reports);
+
 /* The paper's outer fixed-point iteration (Sec. 3, Eqs. (8)-(9)) in place of the folded
  * operator: outer step k solves the free-space problem u_k - G*(V u_k) = b_k with
  * b_k = E_inc + R[E_inc + E_mask^(k-1)], E_mask^(0) = 0, so R is rebuilt from the mask

@@ -53,6 +53,7 @@ struct psfd_ctx {
   int max_rhs = 0, max_clips = 1;
   size_t budget = 0, allocated = 0;
   cudaStream_t stream = nullptr;
+  int device = 0;  // the CUDA device current when the context was created
   psfd::Plan plan;
   double k0 = 0, kb = 0, L = 0;
   std::string err;

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -140,6 +141,7 @@ int ctx_create(psfd_ctx** out, const psfd_grid* grid, int precision, int max_rhs
       (precision != PSFD_FP64 && precision != PSFD_FP32_REFINED))
     return PSFD_E_ARG;
   psfd_ctx* ctx = new psfd_ctx();
+  cudaGetDevice(&ctx->device);
   ctx->g = *grid;
   ctx->precision = precision;
   ctx->max_rhs = max_rhs;
@@ -360,16 +362,21 @@ int ctx_set_rhs(psfd_ctx* ctx, int g0, int n, const double* theta_deg, const dou
       }
     if (src == gi) slots.push_back(gi);
     else dups.push_back({gi, src});
-    // propagating orders (|q| < k_bg) and the anomaly check, in FFT order (y outer, x inner)
+    // propagating orders (|q| < k_bg) and the anomaly check, in FFT order (y outer, x inner).
+    // |beta| < 1e-9 k0 is tested as |d| < (1e-9 k0)^2; a row with qy^2 > k_bg^2 + (1e-9 k0)^2
+    // holds only evanescent orders far from the anomaly and is skipped (host time here is GPU
+    // idle time between solves)
     int cnt = 0;
+    const double kb2 = ctx->kb * ctx->kb, an2 = (1e-9 * ctx->k0) * (1e-9 * ctx->k0);
     for (int y = 0; y < g.ny; ++y) {
       const int ni = y < (g.ny + 1) / 2 ? y : y - g.ny;
       const double qy = p.qiy + 2.0 * kPi * ni / (g.ny * g.dy);
+      if (qy * qy > kb2 + an2) continue;
       for (int x = 0; x < g.nx; ++x) {
         const int mi = x < (g.nx + 1) / 2 ? x : x - g.nx;
         const double qx = p.qix + 2.0 * kPi * mi / (g.nx * g.dx);
-        const double d = ctx->kb * ctx->kb - (qx * qx + qy * qy);
-        if (std::sqrt(std::fabs(d)) < 1e-9 * ctx->k0)
+        const double d = kb2 - (qx * qx + qy * qy);
+        if (std::fabs(d) < an2)
           return ctx->fail(PSFD_E_ANOMALY, "order (" + std::to_string(mi) + ", " + std::to_string(ni) +
                                                ") of illumination " + std::to_string(gi) + " has beta = 0");
         if (d > 0) {
@@ -776,6 +783,33 @@ int psfd_solve(psfd_ctx* ctx, const psfd_solve_opts* opts, psfd_report* report) 
     if (!active) break;
   }
   return report_slots(ctx, t0, report);
+}
+
+int psfd_solve_group(psfd_ctx* const* ctxs, int n, const psfd_solve_opts* opts, psfd_report* reports) {
+  if (!ctxs || n < 1) return PSFD_E_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return PSFD_E_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return PSFD_E_ARG;
+  }
+  // one host thread per context beyond the first: each drives its own context's engine on its
+  // own stream, so the contexts' kernels run side by side on the device
+  std::vector<int> st(n, PSFD_OK);
+  std::vector<std::thread> th;
+  th.reserve(n - 1);
+  for (int i = 1; i < n; ++i)
+    th.emplace_back([&, i] {
+      if (cudaSetDevice(ctxs[i]->device) != cudaSuccess) {
+        st[i] = PSFD_E_CUDA;
+        return;
+      }
+      st[i] = psfd_solve(ctxs[i], opts, reports ? reports + i : nullptr);
+    });
+  st[0] = psfd_solve(ctxs[0], opts, reports);
+  for (auto& t : th) t.join();
+  for (int s : st)
+    if (s != PSFD_OK) return s;
+  return PSFD_OK;
 }
 
 int psfd_solve_fixed_point(psfd_ctx* ctx, const psfd_solve_opts* opts, int max_steps, double step_tol,

@@ -88,6 +88,7 @@ _SIGS = {
     "psfd_tune_reset": (_I, []),
     "psfd_set_green": (_I, [_P, _I, ctypes.c_double]),
     "psfd_solve": (_I, [_P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Report)]),
+    "psfd_solve_group": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(SolveOpts), ctypes.POINTER(Report)]),
     "psfd_solve_fixed_point": (_I, [_P, ctypes.POINTER(SolveOpts), _I, ctypes.c_double, ctypes.POINTER(Report)]),
     "psfd_num_orders": (_I, [_P, _I, _IP]),
     "psfd_diffraction_orders": (_I, [_P, _I, _I, _IP, _IP, _D, _D, _D]),
@@ -281,6 +282,24 @@ def workspace_bytes(grid: Grid, precision: int, max_rhs: int) -> int:
     if st != OK:
         raise PsfdError(st, strerror(st))
     return int(out.value)
+
+
+def solve_group(solvers, tol=1e-10, max_iter=500, max_outer=12, inner_tol=1e-4, check_every=4,
+                raise_on_error=True, krylov=BICGSTAB, restart=0):
+    """psfd_solve_group: solve several distinct Solvers at once, each on its own stream (its
+    results are bitwise those of its own solve). Returns one report per solver."""
+    n = len(solvers)
+    lib = load()
+    o = SolveOpts(float(tol), int(max_iter), int(max_outer), float(inner_tol), int(check_every), int(krylov),
+                  int(restart))
+    ctxs = (_P * n)(*[s.ctx for s in solvers])
+    reps = (Report * n)()
+    st = lib.psfd_solve_group(ctxs, n, ctypes.byref(o), reps)
+    out = [{"iterations": r.iterations, "outer": r.outer, "relres": r.relres, "seconds": r.seconds, "status": st}
+           for r in reps]
+    if raise_on_error and st != OK:
+        raise PsfdError(st, strerror(st))
+    return out
 
 
 class Solver:
