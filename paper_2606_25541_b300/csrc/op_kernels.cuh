@@ -432,7 +432,9 @@ __global__ void __launch_bounds__(NT, 2) k_half_fwd(OpCall<C> a) {
   const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
   const C* Vp = a.V + ((size_t)a.rhsp[g].clip * a.nslab + p) * (NX * NY);
   constexpr int TOT = H * NX;
-  constexpr int BT = TOT % (2 * NT) == 0 ? 2 : 1;  // elements per thread whose loads overlap
+  // elements per thread whose loads overlap: four for the plain and s-update stages (two and
+  // three operands per element), two for the p update, whose four operands would spill
+  constexpr int BT = (IN != IN_PUPDATE && TOT % (4 * NT) == 0) ? 4 : (TOT % (2 * NT) == 0 ? 2 : 1);
   static_assert(TOT % NT == 0, "half plane must be a multiple of the CTA size");
   for (int i0 = threadIdx.x; i0 < TOT; i0 += BT * NT) {
     InVals<C, IN> in0[BT], in1[BT];
