@@ -387,6 +387,14 @@ int psfd_server_progress(psfd_server* s, int* n_pending);
  * buckets on priority streams. Call between progress() calls with no round in flight
  * (PSFD_E_STATE otherwise). */
 int psfd_server_set_rounds(psfd_server* s, int ticks_per_round);
+/* Requests in flight at once over all buckets (no counterpart in the paper). n > 0: a
+ * queued request is admitted only while fewer than n requests are running, still in arrival
+ * order; the running ones share the device (the oldest on the highest stream priority).
+ * Sharing shortens the waits of short requests but stretches the long ones that set the
+ * tail latency; a small n keeps most of the overlap and the tail close to one request at a
+ * time. 0 (default): every request that fits is admitted. Takes effect at the next
+ * admission. Errors: PSFD_E_ARG (null server or n < 0). */
+int psfd_server_set_max_running(psfd_server* s, int n);
 /* *state: 0 queued, 1 running, 2 done; *status: PSFD_OK or the request's failure. */
 int psfd_server_status(psfd_server* s, long long ticket, int* state, int* status);
 /* Orders of illumination rhs of a finished request (layout as psfd_diffraction_orders). */

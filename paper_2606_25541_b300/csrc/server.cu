@@ -91,6 +91,7 @@ struct psfd_server {
   // fused rounds (psfd_server_set_rounds): every bucket runs on round_stream, and the Krylov
   // ticks of all buckets inside a sweep run as one graph launch per round
   int round_ticks = 0;  // 0: buckets advance independently on their own streams
+  int max_running = 0;  // requests in flight at once over all buckets (0: as many as fit)
   cudaStream_t round_stream = nullptr;
   cudaEvent_t round_done = nullptr;
   bool round_in_flight = false;
@@ -196,6 +197,11 @@ bool find_slots(Bucket* b, int n, int* clip, int* g0) {
 
 int admit(psfd_server* s, Request* r, bool* admitted) {
   *admitted = false;
+  if (s->max_running > 0) {  // the request waits, in arrival order, for a running one to retire
+    int running = 0;
+    for (auto& bp : s->buckets) running += bp->running;
+    if (running >= s->max_running) return PSFD_OK;
+  }
   Bucket* b = nullptr;
   int clip = -1, g0 = -1;
   for (auto& bp : s->buckets)
@@ -479,6 +485,12 @@ int progress_round(psfd_server* s, bool* moved) {
 }  // namespace
 
 extern "C" {
+
+int psfd_server_set_max_running(psfd_server* s, int n) {
+  if (!s || n < 0) return PSFD_E_ARG;
+  s->max_running = n;
+  return PSFD_OK;
+}
 
 int psfd_server_set_rounds(psfd_server* s, int ticks_per_round) {
   if (!s || ticks_per_round < 0) return PSFD_E_ARG;

@@ -114,6 +114,7 @@ _SIGS = {
     "psfd_server_submit": (_I, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)]),
     "psfd_server_progress": (_I, [_P, _IP]),
     "psfd_server_set_rounds": (_I, [_P, _I]),
+    "psfd_server_set_max_running": (_I, [_P, _I]),
     "psfd_server_status": (_I, [_P, ctypes.c_longlong, _IP, _IP]),
     "psfd_server_orders": (_I, [_P, ctypes.c_longlong, _I, _I, _IP, _IP, _D, _D, _D]),
     "psfd_server_release": (_I, [_P, ctypes.c_longlong]),
@@ -557,6 +558,10 @@ class Server:
         """Fused rounds: one graph launch per round advances every bucket inside a Krylov sweep
         by up to ticks_per_round ticks (0: buckets advance independently)."""
         self._check(self.lib.psfd_server_set_rounds(self.h, int(ticks_per_round)))
+
+    def set_max_running(self, n: int):
+        """Requests in flight at once (0: as many as fit)."""
+        self._check(self.lib.psfd_server_set_max_running(self.h, int(n)))
 
     def submit(self, prob, theta=None, phi=None, pol=None) -> int:
         """Queue one clip (a layouts.Problem); illuminations default to the problem's."""

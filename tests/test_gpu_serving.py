@@ -146,3 +146,33 @@ def test_request_over_the_budget_is_rejected_and_queued_one_cancelled(psfd):
     ref = _solve_alone(psfd, clips[2], psfd.FP32_REFINED)
     np.testing.assert_array_equal(srv.orders(tc, 0)["amp"], ref[0]["amp"])
     srv.close()
+
+
+@pytest.mark.parametrize("cap", [1, 2])
+def test_requests_in_flight_are_capped_and_results_unchanged(psfd, cap):
+    """psfd_server_set_max_running: never more than cap requests running after a progress()
+    call, admission still in arrival order, and every request's orders bitwise those of its
+    solve alone."""
+    clips = _clips()
+    alone = [_solve_alone(psfd, p, 1) for p in clips]
+    srv = psfd.Server(1, slots_per_context=6, tol=1e-9)
+    srv.set_max_running(cap)
+    tickets = [srv.submit(p) for p in clips]
+    first_running = []
+    for _ in range(100000):
+        srv.progress()
+        states = [srv.status(t)[0] for t in tickets]
+        assert sum(s == 1 for s in states) <= cap
+        for i, s in enumerate(states):
+            if s >= 1 and i not in first_running:
+                first_running.append(i)
+        if all(s == 2 for s in states):
+            break
+    assert all(srv.status(t)[0] == 2 for t in tickets)
+    assert first_running == sorted(first_running)  # admitted in arrival order
+    for t, p, ref in zip(tickets, clips, alone):
+        assert srv.status(t)[1] == psfd.OK
+        for i in range(p.n_rhs):
+            got = srv.orders(t, i)
+            assert np.array_equal(got["amp"], ref[i]["amp"])
+    srv.close()
