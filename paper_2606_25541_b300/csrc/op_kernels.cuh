@@ -668,28 +668,52 @@ __device__ __forceinline__ void green_scalars_near(typename RealOf<C>::T kh, typ
 }
 
 
-// W = S (J - k (k.J) / kb^2) - (E / kb^2) z (z.J) for k = (qx, qy, kz), in place.
+// W = S (J - k (k.J) / kb^2) - (E / kb^2) z (z.J) for k = (qx, qy, kz), in place (registers).
+template <typename C>
+__device__ __forceinline__ void dyadic_reg(C& J0, C& J1, C& J2, typename RealOf<C>::T qx, typename RealOf<C>::T qy,
+                                           typename RealOf<C>::T kz, C S, C Es, typename RealOf<C>::T cinv) {
+  const C kJ = cadd(cadd(cscale(J0, qx), cscale(J1, qy)), cscale(J2, kz));
+  const C ckJ = cscale(kJ, cinv);
+  const C w0 = cmul(S, csub(J0, cscale(ckJ, qx)));
+  const C w1 = cmul(S, csub(J1, cscale(ckJ, qy)));
+  const C w2 = csub(cmul(S, csub(J2, cscale(ckJ, kz))), cmul(Es, J2));
+  J0 = w0;
+  J1 = w1;
+  J2 = w2;
+}
+// The same product on three shared-memory elements.
 template <typename C>
 __device__ __forceinline__ void dyadic_apply(C* c0, C* c1, C* c2, typename RealOf<C>::T qx, typename RealOf<C>::T qy,
                                              typename RealOf<C>::T kz, C S, C Es, typename RealOf<C>::T cinv) {
-  const C J0 = *c0, J1 = *c1, J2 = *c2;
-  const C kJ = cadd(cadd(cscale(J0, qx), cscale(J1, qy)), cscale(J2, kz));
-  const C ckJ = cscale(kJ, cinv);
-  *c0 = cmul(S, csub(J0, cscale(ckJ, qx)));
-  *c1 = cmul(S, csub(J1, cscale(ckJ, qy)));
-  *c2 = csub(cmul(S, csub(J2, cscale(ckJ, kz))), cmul(Es, J2));
+  C J0 = *c0, J1 = *c1, J2 = *c2;
+  dyadic_reg(J0, J1, J2, qx, qy, kz, S, Es, cinv);
+  *c0 = J0;
+  *c1 = J1;
+  *c2 = J2;
 }
 
 // W = A J + (B/|k|^2) k (k.J) for k = (qx, qy, kz): the spherically windowed kernel of an
-// isolated clip (Eqs. (15)-(17)), in place.
+// isolated clip (Eqs. (15)-(17)), in place (registers).
+template <typename C>
+__device__ __forceinline__ void dyadic_sph_reg(C& J0, C& J1, C& J2, typename RealOf<C>::T qx,
+                                               typename RealOf<C>::T qy, typename RealOf<C>::T kz, C A, C Bt) {
+  const C t = cmul(Bt, cadd(cadd(cscale(J0, qx), cscale(J1, qy)), cscale(J2, kz)));
+  const C w0 = cadd(cmul(A, J0), cscale(t, qx));
+  const C w1 = cadd(cmul(A, J1), cscale(t, qy));
+  const C w2 = cadd(cmul(A, J2), cscale(t, kz));
+  J0 = w0;
+  J1 = w1;
+  J2 = w2;
+}
+// The same product on three shared-memory elements.
 template <typename C>
 __device__ __forceinline__ void dyadic_sph(C* c0, C* c1, C* c2, typename RealOf<C>::T qx, typename RealOf<C>::T qy,
                                            typename RealOf<C>::T kz, C A, C Bt) {
-  const C J0 = *c0, J1 = *c1, J2 = *c2;
-  const C t = cmul(Bt, cadd(cadd(cscale(J0, qx), cscale(J1, qy)), cscale(J2, kz)));
-  *c0 = cadd(cmul(A, J0), cscale(t, qx));
-  *c1 = cadd(cmul(A, J1), cscale(t, qy));
-  *c2 = cadd(cmul(A, J2), cscale(t, kz));
+  C J0 = *c0, J1 = *c1, J2 = *c2;
+  dyadic_sph_reg(J0, J1, J2, qx, qy, kz, A, Bt);
+  *c0 = J0;
+  *c1 = J1;
+  *c2 = J2;
 }
 
 // Entries of the per-column reflection phase table exp(i beta dz j): j < 8 (fine
