@@ -53,7 +53,7 @@ template <int RUN> __host__ __device__ __forceinline__ int fpadr(int i) { return
 // holds at most 16 complex values per stage; such groups synchronise with a named barrier.
 template <typename C>
 __host__ __device__ constexpr int fft_group_lanes(int n) {
-  const int cap = n <= 512 ? 32 : (sizeof(C) == 16 ? 128 : 64);
+  const int cap = sizeof(C) == 16 ? (n <= 512 ? 32 : 128) : (n <= 256 ? 32 : 128);
   int g = 1;
   while (g * 2 <= n / 8 && g * 2 <= cap) g *= 2;
   return g;
