@@ -540,6 +540,12 @@ __global__ void __launch_bounds__(NT, 2) k_half_inv(OpCall<C> a, const C* uin) {
 // up to 256 points a cap of 128 registers keeps two CTAs per SM without spills (an explicit
 // minimum of one let the compiler take 130-136 registers, one CTA per SM and a 30 % slower
 // FP64 residual); longer FP64 transforms would spill under that cap and keep one CTA.
+// Padding run of the split passes' tiles: one spare slot after every 16 FP32 elements (a
+// half-warp's run of 16 consecutive elements -- the loads and the later stores of a Stockham
+// stage whose group spans whole warps -- stays inside one run), every 8 FP64 elements (eight
+// 16-byte elements fill the banks).
+template <typename C> __host__ __device__ constexpr int split_run() { return sizeof(C) == 8 ? 16 : 8; }
+
 template <typename C, int N> __host__ __device__ constexpr int split_min_blocks() {
   return sizeof(C) == 8 ? 3 : (N <= 256 ? 2 : 1);
 }
@@ -549,7 +555,8 @@ template <typename C, int N> __host__ __device__ constexpr int split_min_blocks(
 template <typename C, int NX, int IN, int NT>
 __global__ void __launch_bounds__(NT, split_min_blocks<C, NX>()) k_rows_fwd(OpCall<C> a, int rb) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int RP = fft_phys(NX);  // row pitch of the tile
+  constexpr int RUN = split_run<C>();
+  constexpr int RP = fft_physr<RUN>(NX);  // row pitch of the tile
   C* tile = reinterpret_cast<C*>(smem);
   C* tw = tile + rb * RP;
   // blockIdx.x = rhs * 3 + component, blockIdx.y = row block, blockIdx.z = plane: the CTAs
@@ -563,17 +570,18 @@ __global__ void __launch_bounds__(NT, split_min_blocks<C, NX>()) k_rows_fwd(OpCa
   const InScal<C> s = load_in_scalars<C, IN>(a, g);
   const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
   const C* Vp = a.V + (((size_t)a.rhsp[g].clip * a.nslab + p) * a.ny + y0) * NX;
-  stage_in<C, IN, NT>(a, s, base, Vp, rb * NX, tile, [](int i) { return (i / NX) * RP + fpad(i % NX); });
+  stage_in<C, IN, NT>(a, s, base, Vp, rb * NX, tile, [](int i) { return (i / NX) * RP + fpadr<RUN>(i % NX); });
   __syncthreads();
-  cta_fft<C, NX, false>(tile, rb, RP, tw);
+  cta_fft<C, NX, false, false, 1, false, RUN>(tile, rb, RP, tw);
   __syncthreads();
-  for (int i = threadIdx.x; i < rb * NX; i += NT) a.work[base + i] = tile[(i / NX) * RP + fpad(i % NX)];
+  for (int i = threadIdx.x; i < rb * NX; i += NT) a.work[base + i] = tile[(i / NX) * RP + fpadr<RUN>(i % NX)];
 }
 
 template <typename C, int NX, int EPI, int NT>
 __global__ void __launch_bounds__(NT, split_min_blocks<C, NX>()) k_rows_inv(OpCall<C> a, const C* uin, int rb) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int RP = fft_phys(NX);
+  constexpr int RUN = split_run<C>();
+  constexpr int RP = fft_physr<RUN>(NX);
   C* tile = reinterpret_cast<C*>(smem);
   C* tw = tile + rb * RP;
   double2* scratch = align16<double2>(tw + NX);
@@ -584,13 +592,24 @@ __global__ void __launch_bounds__(NT, split_min_blocks<C, NX>()) k_rows_inv(OpCa
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
   for (int i = threadIdx.x; i < NX; i += NT) tw[i] = twid<C>(a.twx, a.twx32, i);
   const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
-  for (int i = threadIdx.x; i < rb * NX; i += NT) tile[(i / NX) * RP + fpad(i % NX)] = a.work[base + i];
+  constexpr int LB = 4;  // elements per thread whose loads are in flight together
+  for (int i0 = threadIdx.x; i0 < rb * NX; i0 += LB * NT) {
+    C vv[LB];
+#pragma unroll
+    for (int j = 0; j < LB; ++j)
+      if (i0 + j * NT < rb * NX) vv[j] = a.work[base + i0 + j * NT];
+#pragma unroll
+    for (int j = 0; j < LB; ++j) {
+      const int i = i0 + j * NT;
+      if (i < rb * NX) tile[(i / NX) * RP + fpadr<RUN>(i % NX)] = vv[j];
+    }
+  }
   __syncthreads();
-  cta_fft<C, NX, true>(tile, rb, RP, tw);
+  cta_fft<C, NX, true, false, 1, false, RUN>(tile, rb, RP, tw);
   __syncthreads();
   Dots<C> dt;
   zero_dots(dt);
-  stage_out<C, EPI, NT>(a, uin, base, rb * NX, tile, [](int i) { return (i / NX) * RP + fpad(i % NX); }, dt);
+  stage_out<C, EPI, NT>(a, uin, base, rb * NX, tile, [](int i) { return (i / NX) * RP + fpadr<RUN>(i % NX); }, dt);
   if (a.dot_mask) {
     const int blk = (c * a.nslab + p) * nrb + (y0 / rb);
     block_write_dots(dt, a.dot_mask, a.partials + ((size_t)g * NDOT) * a.maxblk + blk, a.maxblk, scratch);
@@ -602,7 +621,8 @@ __global__ void __launch_bounds__(NT, split_min_blocks<C, NX>()) k_rows_inv(OpCa
 template <typename C, int NY, bool INV, int NT>
 __global__ void __launch_bounds__(NT, split_min_blocks<C, NY>()) k_cols(OpCall<C> a, int tx) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int PITCH = fft_phys(NY) | 1;  // odd column pitch: the transposing copies spread over the banks
+  constexpr int RUN = split_run<C>();
+  constexpr int PITCH = fft_physr<RUN>(NY) | 1;  // odd column pitch: the transposing copies spread over the banks
   C* tile = reinterpret_cast<C*>(smem);
   C* tw = tile + tx * PITCH;
   const int ncb = a.nx / tx;
@@ -624,13 +644,13 @@ __global__ void __launch_bounds__(NT, split_min_blocks<C, NY>()) k_cols(OpCall<C
 #pragma unroll
     for (int j = 0; j < CB; ++j) {
       const int yy = y + j * ystep;
-      if (yy < NY) tile[t0 * PITCH + fpad(yy)] = vv[j];
+      if (yy < NY) tile[t0 * PITCH + fpadr<RUN>(yy)] = vv[j];
     }
   }
   __syncthreads();
-  cta_fft<C, NY, INV>(tile, tx, PITCH, tw);
+  cta_fft<C, NY, INV, false, 1, false, RUN>(tile, tx, PITCH, tw);
   __syncthreads();
-  for (int y = y0; y < NY; y += ystep) a.work[base + (size_t)y * a.nx + t0] = tile[t0 * PITCH + fpad(y)];
+  for (int y = y0; y < NY; y += ystep) a.work[base + (size_t)y * a.nx + t0] = tile[t0 * PITCH + fpadr<RUN>(y)];
 }
 
 // ---------------------------------------------------------------------------
