@@ -800,10 +800,10 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
   constexpr bool REG = zcol_reg<C, NF>();
   constexpr bool R10 = zcol_r10<C, NF>();
   constexpr int P = zcol_pitch(NF, F32 && REG);  // column pitch; spectral element z at spos(z)
-  // The FP32 register transform keeps the spectrum unpadded: every access to it is a run of
+  // The FP32 register transforms keep the spectrum unpadded: every access to it is a run of
   // consecutive elements (16 of them, 128 bytes, cover the 32 banks once at any alignment),
   // while padded runs straddle pad slots and conflict. The other paths keep fpad's layout.
-  constexpr bool SPAD = !(REG && F32);
+  constexpr bool SPAD = !((REG || R10) && F32);
   auto spos = [](int z) { return SPAD ? fpad(z) : z; };
   C* col = reinterpret_cast<C*>(smem);
   C* tw = col + 3 * tx * P;
@@ -955,7 +955,7 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
     __syncwarp();
     if (gok) {
 #pragma unroll
-      for (int k2 = 0; k2 < 10; ++k2) gx[fpad(gj + 16 * k2)] = w10[k2];
+      for (int k2 = 0; k2 < 10; ++k2) gx[spos(gj + 16 * k2)] = w10[k2];
     }
   } else {
     // The forward transform reads only planes 0 .. NF/2-1 (its input vanishes above, as
@@ -1084,7 +1084,7 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
     C v[16];
     if (gok && gj < 10) {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = gx[fpad(gj + 10 * k)];
+      for (int k = 0; k < 16; ++k) v[k] = gx[spos(gj + 10 * k)];
       Dft<C, 16, true>::run(v);
     }
     __syncwarp();
@@ -1104,7 +1104,7 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
 #pragma unroll
       for (int k2 = 0; k2 < 10; ++k2) {
         const int n = gj + 16 * k2;
-        if (n <= HF) gx[fpad(n)] = w10[k2];
+        if (n <= HF) gx[spos(n)] = w10[k2];
       }
     }
   } else {
@@ -1214,7 +1214,7 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
       const C ph = cmul(ptab[t0 * PP + (pl & 7)], ptab[t0 * PP + 8 + (pl >> 3)]);  // exp(i beta pl dz)
 #pragma unroll
       for (int cc = 0; cc < 3; ++cc) {
-        C* e = col + (cc * tx + t0) * P + fpad(pl + 1);
+        C* e = col + (cc * tx + t0) * P + spos(pl + 1);
         *e = cadd(*e, cmul(R0[cc * tx + t0], ph));
       }
     }
@@ -1223,7 +1223,7 @@ __global__ void __launch_bounds__(NT, zcol_min_blocks<C, NF, NT>()) k_zcol(OpCal
     for (int cc = 0; cc < 3; ++cc) {
 #pragma unroll 4
       for (int pl = p0; pl < ns; pl += pstep)
-        gcol[((size_t)cc * ns + pl) * pstride] = col[(cc * tx + t0) * P + fpad(pl + 1)];
+        gcol[((size_t)cc * ns + pl) * pstride] = col[(cc * tx + t0) * P + spos(pl + 1)];
     }
   }
 }
