@@ -72,6 +72,9 @@ def parse_args(argv=None):
     ap.add_argument("--apply", action="store_true",
                     help="operator applications/s only (psfd_apply), for kernel captures")
     ap.add_argument("--rhs", type=int, default=18, help="illuminations used by --apply and --profile-only")
+    ap.add_argument("--apply-clip", choices=["line_space", "split1024"], default="line_space",
+                    help="--apply: the 128^2 line/space clip, or a 1024^2 x 8-plane clip whose planes take "
+                         "the split row and column passes")
     ap.add_argument("--pf", type=str, default=None,
                     help="--apply: comma-separated L2 prefetch distances of the half-plane kernels to time")
     ap.add_argument("--precision", choices=["fp32", "fp64", "fp64df", "both", "all"], default="both",
@@ -233,11 +236,17 @@ def run_apply(args):
     K3 over every illumination of the batch), with CUDA events on the current stream."""
     import torch
     from paper_2606_25541_b300 import psfd
-    prob = layouts.line_space_clip(seed=2)
+    if args.apply_clip == "split1024":  # 1024^2 planes (split row and column passes), 8 planes
+        prob = layouts.small_clip(nx=1024, ny=1024, nslab=8, dx=1.0, dz=1.0, seed=2, stack=layouts.ru_mosi_stack(40),
+                                  theta=(6.0,), phi=(0.0,), pol=(0,))
+        workload = f"small_clip_1024x1024x8_nf{prob.nf}_{args.rhs}rhs"
+    else:
+        prob = layouts.line_space_clip(seed=2)
+        workload = WORKLOAD.replace("18rhs", f"{args.rhs}rhs")
     sel = np.arange(args.rhs) % prob.n_rhs
     prob = prob.with_illumination(prob.theta_deg[sel], prob.phi_deg[sel], prob.pol[sel])
     stream = torch.cuda.current_stream()
-    out = {"mode": "apply", "workload": WORKLOAD.replace("18rhs", f"{args.rhs}rhs")}
+    out = {"mode": "apply", "workload": workload}
     precs = {"both": ["fp32", "fp64"], "all": ["fp32", "fp64", "fp64df"]}.get(args.precision, [args.precision])
     for name in precs:
         prec = psfd.FP64 if name == "fp64" else psfd.FP32_REFINED
