@@ -546,6 +546,19 @@ __global__ void __launch_bounds__(NT, 2) k_half_inv(OpCall<C> a, const C* uin) {
 // 16-byte elements fill the banks).
 template <typename C> __host__ __device__ constexpr int split_run() { return sizeof(C) == 8 ? 16 : 8; }
 
+// Column pitch of the column pass's tile: a memory phase of its transposing copies holds tx
+// columns x (16 / tx) rows (FP32: 16 lanes of 8 bytes) or tx x (8 / tx) (FP64: 8 lanes of 16
+// bytes); a pitch of 16 / tx (8 / tx) modulo 16 (8) elements puts them on distinct banks (an
+// odd pitch once tx fills the phase). The transforms run along one column per group of lanes,
+// where the pitch plays no part.
+template <typename C>
+__host__ __device__ inline int cols_pitch(int ny, int tx) {
+  constexpr int PH = sizeof(C) == 8 ? 16 : 8;
+  const int base = fft_physr<split_run<C>()>(ny);
+  const int pmod = tx >= PH ? 1 : PH / tx;
+  return base + ((pmod - base % PH) % PH + PH) % PH;
+}
+
 template <typename C, int N> __host__ __device__ constexpr int split_min_blocks() {
   return sizeof(C) == 8 ? 3 : (N <= 256 ? 2 : 1);
 }
@@ -622,7 +635,7 @@ template <typename C, int NY, bool INV, int NT>
 __global__ void __launch_bounds__(NT, split_min_blocks<C, NY>()) k_cols(OpCall<C> a, int tx) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int RUN = split_run<C>();
-  constexpr int PITCH = fft_physr<RUN>(NY) | 1;  // odd column pitch: the transposing copies spread over the banks
+  const int PITCH = cols_pitch<C>(NY, tx);
   C* tile = reinterpret_cast<C*>(smem);
   C* tw = tile + tx * PITCH;
   const int ncb = a.nx / tx;

@@ -161,7 +161,7 @@ int launch_rows_inv(const OpCall<C>& a, const C* uin) {
 // Columns per CTA of the column pass: COL_TILE, halved while the tile exceeds COLS_SMEM.
 template <typename C>
 inline size_t cols_smem_bytes(int ny, int tx) {
-  return (size_t)(tx * (fft_phys(ny) | 1) + ny) * sizeof(C);
+  return (size_t)(tx * cols_pitch<C>(ny, tx) + ny) * sizeof(C);
 }
 template <typename C>
 inline int cols_tile(int nx, int ny) {
