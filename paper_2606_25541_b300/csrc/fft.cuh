@@ -35,6 +35,30 @@ __host__ __device__ constexpr int fft_plan_stages(int n) {
   return s;
 }
 
+// Per-stage twiddle table of the plan of length n. A Stockham stage of radix R after stages
+// whose radices multiply to NS > 1 multiplies input r of butterfly b by w_n^{r j TWS},
+// j = b mod NS, TWS = n / (NS R). In the plain table those reads are strided by r j TWS, and
+// the lanes of a stage meet bank conflicts; here row j of the stage holds its R - 1 twiddles
+// contiguously, rows of odd length (R - 1) | 1, so that lanes reading consecutive rows hit
+// distinct banks. Same values as the plain table; every offset is a compile-time constant
+// (offsets computed in the stage loop at run time cost more than the conflicts they remove).
+__host__ __device__ constexpr int stw_stride(int n, int stage) {
+  int ns = 1;
+  for (int s = 0; s < stage; ++s) ns *= fft_plan_radix(n, s);
+  return ns;
+}
+__host__ __device__ constexpr int stw_count(int n, int stage) {
+  return stw_stride(n, stage) > 1 ? stw_stride(n, stage) * ((fft_plan_radix(n, stage) - 1) | 1) : 0;
+}
+__host__ __device__ constexpr int stw_offset(int n, int stage) {
+  int o = 0;
+  for (int s = 0; s < stage; ++s) o += stw_count(n, s);
+  return o;
+}
+__host__ __device__ constexpr int stw_size(int n) { return stw_offset(n, fft_plan_stages(n)); }
+// Whether the staged table fits where the plain one (n entries) sits: every power-of-two plan.
+__host__ __device__ constexpr bool stw_fits(int n) { return stw_size(n) <= n; }
+
 // Shared-memory layout of a transform: element i sits at fpad(i) = i + i/8 (times the
 // element stride), one spare slot after every eight elements. Without it the first
 // radix-8 stage stores with a stride of eight elements and eight lanes of a half-warp
@@ -345,7 +369,29 @@ __device__ __forceinline__ void reg_fft_step2(const C* ex, int j, C (&out)[16]) 
 // compile-time constants, so only the first address of a butterfly is computed.
 // HALF_IN: the input is zero on [N/2, N) and only its lower half is read.
 // ---------------------------------------------------------------------------
-template <typename C, int N, int G, bool INV, int S, int NS, int ES, bool HALF_IN, int RUN = 8>
+// Fills the staged table of length N from the plain table (FP64 and FP32 copies; entry mul * k
+// is w_N^k), one stage after another with compile-time offsets and divisors; the calling
+// threads share the entries and the caller synchronises.
+template <typename C, int N, int S = 0>
+__device__ __forceinline__ void build_stw(C* ts, const double2* src64, const float2* src32, int mul, int tid,
+                                          int nthreads) {
+  if constexpr (S < fft_plan_stages(N)) {
+    constexpr int CNT = stw_count(N, S);
+    if constexpr (CNT > 0) {
+      constexpr int OFF = stw_offset(N, S), R = fft_plan_radix(N, S), RS = (R - 1) | 1;
+      constexpr int TWS = N / (stw_stride(N, S) * R);
+      for (int i = tid; i < CNT; i += nthreads) {
+        const int j = i / RS, r = i - j * RS + 1;
+        const int k = r < R ? r * j * TWS : 0;
+        if constexpr (sizeof(C) == sizeof(float2)) ts[OFF + i] = src32[mul * k];
+        else ts[OFF + i] = src64[mul * k];
+      }
+    }
+    build_stw<C, N, S + 1>(ts, src64, src32, mul, tid, nthreads);
+  }
+}
+
+template <typename C, int N, int G, bool INV, int S, int NS, int ES, bool HALF_IN, int RUN = 8, bool STW = false>
 __device__ __forceinline__ void fft_stages(C* a, int g, const C* tw, bool valid, int bar) {
   if constexpr (S < fft_plan_stages(N)) {
     constexpr int R = fft_plan_radix(N, S);
@@ -368,12 +414,23 @@ __device__ __forceinline__ void fft_stages(C* a, int g, const C* tw, bool valid,
           for (int r = 0; r < RL; ++r) v[k][r] = a[fpadr<RUN>(b + r * NB) * ES];
         }
         if constexpr (NS > 1) {
-          const int jt = (b % NS) * TWS;
+          if constexpr (STW) {
+            constexpr int OFF = stw_offset(N, S), RS = (R - 1) | 1;
+            const C* tr = tw + (OFF - 1) + (b % NS) * RS;
 #pragma unroll
-          for (int r = 1; r < R; ++r) {
-            C w = tw[r * jt];
-            if (INV) w = cconj(w);
-            v[k][r] = cmul(v[k][r], w);
+            for (int r = 1; r < R; ++r) {
+              C w = tr[r];
+              if (INV) w = cconj(w);
+              v[k][r] = cmul(v[k][r], w);
+            }
+          } else {
+            const int jt = (b % NS) * TWS;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+              C w = tw[r * jt];
+              if (INV) w = cconj(w);
+              v[k][r] = cmul(v[k][r], w);
+            }
           }
         }
         if constexpr (HIN) {
@@ -405,16 +462,16 @@ __device__ __forceinline__ void fft_stages(C* a, int g, const C* tw, bool valid,
       }
     }
     group_sync<G>(bar);
-    fft_stages<C, N, G, INV, S + 1, NS * R, ES, HALF_IN, RUN>(a, g, tw, valid, bar);
+    fft_stages<C, N, G, INV, S + 1, NS * R, ES, HALF_IN, RUN, STW>(a, g, tw, valid, bar);
   }
 }
 
 // One length-N transform per group of G lanes. Every lane of the warp must call this
 // (lanes of groups without work pass valid = false) because stages end in __syncwarp.
-template <typename C, int N, bool INV, int ES = 1, bool HALF_IN = false, int RUN = 8>
+template <typename C, int N, bool INV, int ES = 1, bool HALF_IN = false, int RUN = 8, bool STW = false>
 __device__ __forceinline__ void group_fft(C* a, int g, const C* tw, bool valid, int bar = 0) {
   constexpr int G = fft_group_lanes<C>(N);
-  fft_stages<C, N, G, INV, 0, 1, ES, HALF_IN, RUN>(a, g, tw, valid, bar);
+  fft_stages<C, N, G, INV, 0, 1, ES, HALF_IN, RUN, STW>(a, g, tw, valid, bar);
 }
 
 // Batched transforms by a whole CTA: `count` transforms, transform f starting at
@@ -422,8 +479,9 @@ __device__ __forceinline__ void group_fft(C* a, int g, const C* tw, bool valid, 
 // 2-D tile) else f, element i at fpadr<RUN>(i) * ES. Groups of G <= 32 lanes share a warp
 // (32/G transforms per warp at a time); larger groups are G consecutive threads with
 // named barrier 1 + (thread / G), so the CTA size must be a multiple of G and below 16 G.
+// STW: tw is the staged table of build_stw (stw_fits(N)), else the plain table.
 template <typename C, int N, bool INV, bool PADF = false, int ES = 1, bool HALF_IN = false, int RUN = 8,
-          int FRUN = 8>
+          int FRUN = 8, bool STW = false>
 __device__ __forceinline__ void cta_fft(C* a, int count, int fs, const C* tw) {
   constexpr int G = fft_group_lanes<C>(N);
   int gid, ngroups, bar = 0;
@@ -441,7 +499,7 @@ __device__ __forceinline__ void cta_fft(C* a, int count, int fs, const C* tw) {
     const int f = gid + it * ngroups;
     const bool valid = f < count;
     const int fo = valid ? (PADF ? fpadr<FRUN>(f) : f) : 0;
-    group_fft<C, N, INV, ES, HALF_IN, RUN>(a + fo * fs, g, tw, valid, bar);
+    group_fft<C, N, INV, ES, HALF_IN, RUN, STW>(a + fo * fs, g, tw, valid, bar);
   }
 }
 

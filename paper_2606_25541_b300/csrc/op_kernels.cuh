@@ -55,6 +55,20 @@ __device__ __forceinline__ C twid(const double2* t64, const float2* t32, int i) 
   else return t64[i];
 }
 
+// FP32 transforms of the plane passes read their twiddles from the per-stage table.
+template <typename C, int N> __host__ __device__ constexpr bool plane_stw() {
+  return sizeof(C) == sizeof(float2) && stw_fits(N);
+}
+
+// Copies the twiddles of a length-N transform into shared memory: entry mul * i of the
+// global table is w_N^i. Plain table, or the per-stage table when plane_stw<C, N>().
+template <typename C, int N, int NT>
+__device__ __forceinline__ void stage_twiddles(C* dst, const double2* t64, const float2* t32, int mul) {
+  if constexpr (plane_stw<C, N>()) build_stw<C, N>(dst, t64, t32, mul, threadIdx.x, NT);
+  else
+    for (int i = threadIdx.x; i < N; i += NT) dst[i] = twid<C>(t64, t32, mul * i);
+}
+
 // a / b through one reciprocal of |b|^2; here |b| stays far from under- and overflow
 // (|kappa + beta| >= |beta| and |delta| >= 1/(2L) on this branch).
 __device__ __forceinline__ float2 cdiv_fast(float2 a, float2 b) {
@@ -422,11 +436,9 @@ __global__ void __launch_bounds__(NT, 2) k_half_fwd(OpCall<C> a) {
     if (a.pf && threadIdx.x == 0) half_prefetch<C, NX, NY, IN, false>(a, nullptr);
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
-  for (int i = threadIdx.x; i < NX; i += NT) twx[i] = twid<C>(a.twx, a.twx32, i);
-  for (int i = threadIdx.x; i < H; i += NT) {
-    twy[i] = twid<C>(a.twy, a.twy32, i);
-    twh[i] = twid<C>(a.twy, a.twy32, 2 * i);
-  }
+  stage_twiddles<C, NX, NT>(twx, a.twx, a.twx32, 1);
+  stage_twiddles<C, H, NT>(twh, a.twy, a.twy32, 2);
+  for (int i = threadIdx.x; i < H; i += NT) twy[i] = twid<C>(a.twy, a.twy32, i);
   __syncthreads();
   const InScal<C> s = load_in_scalars<C, IN>(a, g);
   const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
@@ -457,9 +469,9 @@ __global__ void __launch_bounds__(NT, 2) k_half_fwd(OpCall<C> a) {
     }
   }
   __syncthreads();
-  cta_fft<C, NX, false, true, 1, false, kHalfXRun, 8>(tile, H, PITCH, twx);
+  cta_fft<C, NX, false, true, 1, false, kHalfXRun, 8, plane_stw<C, NX>()>(tile, H, PITCH, twx);
   __syncthreads();
-  cta_fft<C, H, false, true, PITCH, false, 8, kHalfXRun>(tile, NX, 1, twh);
+  cta_fft<C, H, false, true, PITCH, false, 8, kHalfXRun, plane_stw<C, H>()>(tile, NX, 1, twh);
   __syncthreads();
   for (int i = threadIdx.x; i < H * NX; i += NT) {
     const int m = i / NX, x = i % NX;
@@ -480,11 +492,9 @@ __global__ void __launch_bounds__(NT, 2) k_half_inv(OpCall<C> a, const C* uin) {
   if (a.pf && threadIdx.x == 0) half_prefetch<C, NX, NY, IN_PLAIN, true>(a, uin);
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
-  for (int i = threadIdx.x; i < NX; i += NT) twx[i] = twid<C>(a.twx, a.twx32, i);
-  for (int i = threadIdx.x; i < H; i += NT) {
-    twy[i] = twid<C>(a.twy, a.twy32, i);
-    twh[i] = twid<C>(a.twy, a.twy32, 2 * i);
-  }
+  stage_twiddles<C, NX, NT>(twx, a.twx, a.twx32, 1);
+  stage_twiddles<C, H, NT>(twh, a.twy, a.twy32, 2);
+  for (int i = threadIdx.x; i < H; i += NT) twy[i] = twid<C>(a.twy, a.twy32, i);
   __syncthreads();
   const size_t plane = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)(NX * NY);
   constexpr int BL = (H * NX) % (4 * NT) == 0 ? 4 : 1;  // elements per thread whose loads overlap
@@ -502,9 +512,9 @@ __global__ void __launch_bounds__(NT, 2) k_half_inv(OpCall<C> a, const C* uin) {
     }
   }
   __syncthreads();
-  cta_fft<C, H, true, true, PITCH, false, 8, kHalfXRun>(tile, NX, 1, twh);
+  cta_fft<C, H, true, true, PITCH, false, 8, kHalfXRun, plane_stw<C, H>()>(tile, NX, 1, twh);
   __syncthreads();
-  cta_fft<C, NX, true, true, 1, false, kHalfXRun, 8>(tile, H, PITCH, twx);
+  cta_fft<C, NX, true, true, 1, false, kHalfXRun, 8, plane_stw<C, NX>()>(tile, H, PITCH, twx);
   __syncthreads();
   Dots<C> dt;
   zero_dots(dt);
@@ -579,13 +589,13 @@ __global__ void __launch_bounds__(NT, split_min_blocks<C, NX>()) k_rows_fwd(OpCa
   const int c = blockIdx.x % 3, lr = blockIdx.x / 3, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
-  for (int i = threadIdx.x; i < NX; i += NT) tw[i] = twid<C>(a.twx, a.twx32, i);
+  stage_twiddles<C, NX, NT>(tw, a.twx, a.twx32, 1);
   const InScal<C> s = load_in_scalars<C, IN>(a, g);
   const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
   const C* Vp = a.V + (((size_t)a.rhsp[g].clip * a.nslab + p) * a.ny + y0) * NX;
   stage_in<C, IN, NT>(a, s, base, Vp, rb * NX, tile, [](int i) { return (i / NX) * RP + fpadr<RUN>(i % NX); });
   __syncthreads();
-  cta_fft<C, NX, false, false, 1, false, RUN>(tile, rb, RP, tw);
+  cta_fft<C, NX, false, false, 1, false, RUN, 8, plane_stw<C, NX>()>(tile, rb, RP, tw);
   __syncthreads();
   for (int i = threadIdx.x; i < rb * NX; i += NT) a.work[base + i] = tile[(i / NX) * RP + fpadr<RUN>(i % NX)];
 }
@@ -603,7 +613,7 @@ __global__ void __launch_bounds__(NT, split_min_blocks<C, NX>()) k_rows_inv(OpCa
   const int c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
-  for (int i = threadIdx.x; i < NX; i += NT) tw[i] = twid<C>(a.twx, a.twx32, i);
+  stage_twiddles<C, NX, NT>(tw, a.twx, a.twx32, 1);
   const size_t base = ((((size_t)lr * 3 + c) * a.nslab + p) * a.ny + y0) * (size_t)NX;
   constexpr int LB = 4;  // elements per thread whose loads are in flight together
   for (int i0 = threadIdx.x; i0 < rb * NX; i0 += LB * NT) {
@@ -618,7 +628,7 @@ __global__ void __launch_bounds__(NT, split_min_blocks<C, NX>()) k_rows_inv(OpCa
     }
   }
   __syncthreads();
-  cta_fft<C, NX, true, false, 1, false, RUN>(tile, rb, RP, tw);
+  cta_fft<C, NX, true, false, 1, false, RUN, 8, plane_stw<C, NX>()>(tile, rb, RP, tw);
   __syncthreads();
   Dots<C> dt;
   zero_dots(dt);
@@ -643,7 +653,7 @@ __global__ void __launch_bounds__(NT, split_min_blocks<C, NY>()) k_cols(OpCall<C
   const int c = blockIdx.y, lr = blockIdx.z, g = a.rhs0 + lr;
   if (a.active && !a.active[g]) return;
   if (a.ctac && threadIdx.x == 0) atomicAdd(a.ctac, 1u);  // profiling: CTAs that did work
-  for (int i = threadIdx.x; i < NY; i += NT) tw[i] = twid<C>(a.twy, a.twy32, i);
+  stage_twiddles<C, NY, NT>(tw, a.twy, a.twy32, 1);
   const size_t base = (((size_t)lr * 3 + c) * a.nslab + p) * (size_t)NY * a.nx + x0;
   const int t0 = threadIdx.x % tx, y0 = threadIdx.x / tx, ystep = NT / tx;
   constexpr int CB = 8;  // column elements per thread whose loads are in flight together
@@ -661,7 +671,7 @@ __global__ void __launch_bounds__(NT, split_min_blocks<C, NY>()) k_cols(OpCall<C
     }
   }
   __syncthreads();
-  cta_fft<C, NY, INV, false, 1, false, RUN>(tile, tx, PITCH, tw);
+  cta_fft<C, NY, INV, false, 1, false, RUN, 8, plane_stw<C, NY>()>(tile, tx, PITCH, tw);
   __syncthreads();
   for (int y = y0; y < NY; y += ystep) a.work[base + (size_t)y * a.nx + t0] = tile[t0 * PITCH + fpadr<RUN>(y)];
 }
