@@ -2,10 +2,11 @@
 // fft.cuh: fft_stages, the stages of cta_fft) for every supported length, compiled by
 // tests/test_stockham_host.py. One lane does every butterfly of a stage (group size 1), so each
 // stage loads all its inputs into registers before it stores any output, which is the order the
-// group barrier enforces on the device. Each length runs with the plain twiddle table and, where
-// it fits, with the per-stage table of build_stw, in FP32 (element padding every 16, as the FP32
-// plane passes) and in FP64 (padding every 8). Reference: the DFT of the same (rounded) input
-// summed in long double. Prints "name value" lines.
+// group barrier enforces on the device. Each length runs in FP32 (element padding every 16, as
+// the FP32 plane passes) and in FP64 with the plain twiddle table and, where it fits, with the
+// per-stage table of build_stw; and in double-float pairs (padding every 8, as the FP64
+// residual's row and column passes) with the plain table. Reference: the DFT of the same
+// (rounded) input summed in long double. Prints "name value" lines.
 #define _GNU_SOURCE 1
 #include <cmath>
 #include <math.h>
@@ -20,6 +21,7 @@ struct HostDim {
 static HostDim threadIdx{0, 0, 0}, blockDim{1, 1, 1};
 #define __syncwarp(...) ((void)0)
 #include "fft.cuh"
+#include "dfloat.cuh"
 
 #include <complex>
 #include <cstdio>
@@ -34,9 +36,11 @@ static const Q kPi = 3.14159265358979323846264338327950288L;
 
 static CQ toq(double2 a) { return CQ(a.x, a.y); }
 static CQ toq(float2 a) { return CQ(a.x, a.y); }
+static CQ toq(dfc a) { return CQ((Q)a.x.hi + (Q)a.x.lo, (Q)a.y.hi + (Q)a.y.lo); }
 template <typename C> C fromd(double re, double im);
 template <> double2 fromd<double2>(double re, double im) { return make_double2(re, im); }
 template <> float2 fromd<float2>(double re, double im) { return make_float2((float)re, (float)im); }
+template <> dfc fromd<dfc>(double re, double im) { return to_dfc(make_double2(re, im)); }
 
 struct Outcome {
   double err;     // normwise relative error against the long-double DFT
@@ -49,11 +53,15 @@ static Outcome run(const std::vector<std::complex<double>>& x, const std::vector
                    const std::vector<float2>& t32) {
   std::vector<C> a(fft_physr<RUN>(N)), tw(N);
   for (int n = 0; n < N; ++n) a[fpadr<RUN>(n)] = fromd<C>(x[n].real(), x[n].imag());
+  // the plain table's entry k in the run's format: FP32 and FP64 copies, or FP64 rounded to pairs
+  auto get = [&](int k) -> C {
+    if constexpr (sizeof(C) == sizeof(float2)) return t32[k];
+    else return fromd<C>(t64[k].x, t64[k].y);
+  };
   if constexpr (STW) {
     build_stw<C, N>(tw.data(), t64.data(), t32.data(), 1, 0, 1);
   } else {
-    for (int k = 0; k < N; ++k)
-      tw[k] = sizeof(C) == sizeof(float2) ? fromd<C>(t32[k].x, t32[k].y) : fromd<C>(t64[k].x, t64[k].y);
+    for (int k = 0; k < N; ++k) tw[k] = get(k);
   }
   fft_stages<C, N, 1, INV, 0, 1, 1, false, RUN, STW>(a.data(), 0, tw.data(), true, 0);
   Outcome o;
@@ -75,7 +83,7 @@ static Outcome run(const std::vector<std::complex<double>>& x, const std::vector
 }
 
 struct Tally {
-  double worst32 = 0, worst64 = 0;
+  double worst32 = 0, worst64 = 0, worstdf = 0;
   long stw_mismatch = 0, stw_checked = 0, lengths = 0, pow2_not_fitting = 0;
 };
 
@@ -101,6 +109,9 @@ static void check_length(Tally& t, std::mt19937_64& rng) {
     const Outcome i64 = run<double2, N, true, 8, false>(x, t64, t32);
     t.worst32 = std::fmax(t.worst32, std::fmax(f32.err, i32.err));
     t.worst64 = std::fmax(t.worst64, std::fmax(f64.err, i64.err));
+    const Outcome fdf = run<dfc, N, false, 8, false>(x, t64, t32);
+    const Outcome idf = run<dfc, N, true, 8, false>(x, t64, t32);
+    t.worstdf = std::fmax(t.worstdf, std::fmax(fdf.err, idf.err));
     if constexpr (stw_fits(N)) {
       const Outcome s[4] = {run<float2, N, false, 16, true>(x, t64, t32), run<float2, N, true, 16, true>(x, t64, t32),
                             run<double2, N, false, 8, true>(x, t64, t32), run<double2, N, true, 8, true>(x, t64, t32)};
@@ -132,8 +143,8 @@ int main() {
   check_length<640>(t, rng);
   check_length<768>(t, rng);
   check_length<1024>(t, rng);
-  std::printf("lengths %ld\nstockham_fp32 %.6e\nstockham_fp64 %.6e\nstw_checked %ld\nstw_mismatch %ld\n"
-              "pow2_not_fitting %ld\n",
-              t.lengths, t.worst32, t.worst64, t.stw_checked, t.stw_mismatch, t.pow2_not_fitting);
+  std::printf("lengths %ld\nstockham_fp32 %.6e\nstockham_fp64 %.6e\nstockham_dfloat %.6e\nstw_checked %ld\n"
+              "stw_mismatch %ld\npow2_not_fitting %ld\n",
+              t.lengths, t.worst32, t.worst64, t.worstdf, t.stw_checked, t.stw_mismatch, t.pow2_not_fitting);
   return 0;
 }
